@@ -1,0 +1,114 @@
+"""Polarized subsurface BRDF from the per-order solutions (Sec. 2.D, Eqs. 1, 12, 39).
+
+For incident basis Stokes vectors e_s (s = I, Q, U, V) the Mueller BRDF is the
+matrix whose column s is the exiting radiance divided by the incident
+irradiance (Eq. 39 with the four unit vectors, so the matrix inverse is the
+identity). The exiting radiance is the Fourier sum of Eq. 12,
+
+    I(0, mu, phi) = 1/2 sum_m Phi_{k(s)}^m(phi - phi_p) I^m(0, mu),
+
+k(s) = 1 for s in {I, Q} and 2 for s in {U, V} (the D_k of Eq. 14 selects it),
+phi_p the azimuth of the beam's propagation direction.
+
+Table conventions: F[i_in, i_out, j, r, s] with mu_in the cosine of the direction
+towards the source, mu_out the cosine towards the viewer, dphi_j = phi_out - phi_in
+(both directions pointing away from the surface, as for the paper's (mu0, phi0) in
+Eq. 4). The beam propagates at azimuth phi_in + pi, so the Fourier argument is
+dphi - pi. Incident Stokes vectors are given on the meridian frame of the beam's
+propagation direction, exiting ones on the meridian frame of the viewing direction.
+F = I_out / (mu_in I0) in 1/sr (the irradiance on the horizontal surface is
+mu_in I0; the paper's Eq. 1 names it without fixing the cosine).
+
+With a dielectric top (n > 1) the external cosines are refracted (Snell), the
+beam is transmitted with M_in, internal radiance leaves with M_out; the external
+specular reflection is not part of the subsurface BRDF.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .dom import solve_order
+from .fresnel import fresnel_beam_in, fresnel_exit, fresnel_internal_reflection, snell_mu
+from .phase import phase_matrix_direct
+from .quadrature import gauss_legendre_01
+
+
+def synthesis_weights(m: int, dphi):
+    """w[j, r, s] = (Phi_{k(s)}^m(dphi_j - pi))_rr of Eq. 7."""
+    dphi = np.atleast_1d(np.asarray(dphi, dtype=float))
+    f = 1.0 if m == 0 else 2.0
+    arg = m * (dphi - np.pi)
+    c = f * np.cos(arg)
+    s = f * np.sin(arg)
+    w = np.zeros((dphi.size, 4, 4))
+    for r in range(4):
+        for col in range(4):
+            iq_row = r < 2
+            iq_col = col < 2
+            if iq_col:     # Phi_1: (cos, cos, sin, sin)
+                w[:, r, col] = c if iq_row else s
+            else:          # Phi_2: (-sin, -sin, cos, cos)
+                w[:, r, col] = -s if iq_row else c
+    return w
+
+
+def brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out):
+    """Per-order internal exiting radiance I^m [M, n_in, n_out, 4, 4] plus interface data."""
+    coef = np.asarray(coef, dtype=float)
+    mu_in = np.atleast_1d(np.asarray(mu_in, dtype=float))
+    mu_out = np.atleast_1d(np.asarray(mu_out, dtype=float))
+    nodes = gauss_legendre_01(N)
+    mu0_int = snell_mu(mu_in, n_interface)
+    mu_out_int = snell_mu(mu_out, n_interface)
+    beam = fresnel_beam_in(mu_in, n_interface)
+    R_top = fresnel_internal_reflection(nodes[0], n_interface) if n_interface > 1.0 else None
+    L = coef.shape[0]
+    Im = np.zeros((M, mu_in.size, mu_out.size, 4, 4))
+    for m in range(min(M, L)):
+        sol = solve_order(m, coef, omega, tau0, N, mu0_int, beam, R_top, nodes)
+        Im[m] = sol.reconstruct_top(mu_out_int)
+    return Im
+
+
+def synthesize(Im, mu_in, mu_out, dphi, n_interface):
+    """F[i_in, i_out, j, r, s] from per-order radiances (Eq. 12) and the interface exit."""
+    M = Im.shape[0]
+    mu_in = np.atleast_1d(np.asarray(mu_in, dtype=float))
+    dphi = np.atleast_1d(np.asarray(dphi, dtype=float))
+    F = np.zeros((Im.shape[1], Im.shape[2], dphi.size, 4, 4))
+    for m in range(M):
+        w = synthesis_weights(m, dphi)
+        F += 0.5 * Im[m][:, :, None, :, :] * w[None, None, :, :, :]
+    Mout = fresnel_exit(mu_out, n_interface)
+    F = np.einsum("oab,iojbc->iojac", Mout, F)
+    return F / mu_in[:, None, None, None, None]
+
+
+def brdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi):
+    """Mueller BRDF table F[n_in, n_out, n_phi, 4, 4] of one layer (FP64)."""
+    Im = brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out)
+    return synthesize(Im, mu_in, mu_out, dphi, n_interface)
+
+
+def single_scatter_brdf(coef, omega, tau0, n_interface, mu_in, mu_out, dphi):
+    """Exact once-scattered BRDF, computed from the directly rotated phase matrix.
+
+    I_ss(0, mu) = (omega / 4 pi) Z(mu, phi; -mu0, phi_in + pi) I0' mu0 (1 - exp(-tau0 (1/mu + 1/mu0))) / (mu + mu0)
+    (Eq. 4 integrated along the exit path), then the interface and the 1/mu_in of
+    the BRDF normalisation. Independent of the Fourier machinery.
+    """
+    mu_in = np.atleast_1d(np.asarray(mu_in, dtype=float))
+    mu_out = np.atleast_1d(np.asarray(mu_out, dtype=float))
+    dphi = np.atleast_1d(np.asarray(dphi, dtype=float))
+    mi = snell_mu(mu_in, n_interface)
+    mo = snell_mu(mu_out, n_interface)
+    Min = fresnel_beam_in(mu_in, n_interface)
+    Mout = fresnel_exit(mu_out, n_interface)
+    F = np.zeros((mu_in.size, mu_out.size, dphi.size, 4, 4))
+    for i in range(mu_in.size):
+        for o in range(mu_out.size):
+            depth = mi[i] * -np.expm1(-tau0 * (1.0 / mo[o] + 1.0 / mi[i])) / (mo[o] + mi[i])
+            for j, dp in enumerate(dphi):
+                Z = phase_matrix_direct(coef, mo[o], dp, -mi[i], np.pi)
+                F[i, o, j] = Mout[o] @ (omega / (4 * np.pi) * depth * Z @ Min[i]) / mu_in[i]
+    return F
