@@ -61,9 +61,13 @@ def wigner_d_family(lmax: int, m: int, n: int, x) -> np.ndarray:
     xi = 1.0 if n >= m else (-1.0) ** (m - n)
     logc = -l0 * math.log(2.0) + 0.5 * (math.lgamma(2 * l0 + 1) - math.lgamma(abs(m - n) + 1)
                                         - math.lgamma(abs(m + n) + 1))
+    # (1 - x)^0 = 1 at x = 1: add a logarithm only where its exponent is positive
+    log_seed = np.full(x.shape, logc)
     with np.errstate(divide="ignore"):
-        log_seed = (logc + 0.5 * abs(m - n) * np.log(np.clip(1.0 - x, 0.0, None))
-                    + 0.5 * abs(m + n) * np.log(np.clip(1.0 + x, 0.0, None)))
+        if m != n:
+            log_seed = log_seed + 0.5 * abs(m - n) * np.log(np.clip(1.0 - x, 0.0, None))
+        if m != -n:
+            log_seed = log_seed + 0.5 * abs(m + n) * np.log(np.clip(1.0 + x, 0.0, None))
     out[l0] = xi * np.exp(log_seed)
     for l in range(l0, lmax):
         denom = l * math.sqrt((l + 1) ** 2 - m * m) * math.sqrt((l + 1) ** 2 - n * n)

@@ -175,3 +175,18 @@ def test_A_matrix_symmetries():
         Apm = O.A_matrix(m, coef, mu, -mup)
         assert np.allclose(Amm, D @ A @ D, atol=1e-13)
         assert np.allclose(Amp, D @ Apm @ D, atol=1e-13)
+
+
+def test_tables_at_the_poles():
+    """x = +-1 (normal incidence/exit): d^l_{mn}(0) = delta_mn, d^l_{mn}(pi) = (-1)^(l+m) delta_{m,-n}."""
+    for m in range(0, 5):
+        for n in (0, 2, -2):
+            fam = wigner_d_family(12, m, n, np.array([1.0, -1.0]))
+            assert np.all(np.isfinite(fam))
+            for l in range(max(abs(m), abs(n)), 13):
+                assert abs(fam[l, 0] - (1.0 if m == n else 0.0)) < 1e-14
+                assert abs(fam[l, 1] - ((-1.0) ** (l + m) if m == -n else 0.0)) < 1e-14
+    c = monodisperse_coefficients(1.5 + 0.01j, 2.0, 12)
+    A1 = O.A_matrix(0, c, [1.0], [0.4])
+    A2 = O.A_matrix(0, c, [1.0 - 1e-12], [0.4])
+    assert np.all(np.isfinite(A1)) and np.abs(A1 - A2).max() < 1e-9

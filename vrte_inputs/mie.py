@@ -134,9 +134,12 @@ def _wigner_d_family(lmax: int, m: int, n: int, x):
     xi = 1.0 if n >= m else (-1.0) ** (m - n)
     logc = (-l0 * math.log(2.0) + 0.5 * (math.lgamma(2 * l0 + 1) - math.lgamma(abs(m - n) + 1)
                                           - math.lgamma(abs(m + n) + 1)))
+    lg = np.full(x.shape, logc)
     with np.errstate(divide="ignore"):
-        lg = (logc + 0.5 * abs(m - n) * np.log(np.maximum(1.0 - x, 0.0))
-              + 0.5 * abs(m + n) * np.log(np.maximum(1.0 + x, 0.0)))
+        if m != n:
+            lg = lg + 0.5 * abs(m - n) * np.log(np.maximum(1.0 - x, 0.0))
+        if m != -n:
+            lg = lg + 0.5 * abs(m + n) * np.log(np.maximum(1.0 + x, 0.0))
     out[l0] = xi * np.exp(lg)
     for l in range(l0, lmax):
         c_prev = (l + 1) * math.sqrt(l * l - m * m) * math.sqrt(l * l - n * n) if l > l0 else 0.0
