@@ -1,0 +1,178 @@
+/*
+ * vrte.h -- C ABI of the GB300 DOM solver for the vector radiative transfer
+ * equation (VRTE) of a flat particulate layer and its polarized subsurface BRDF.
+ *
+ * Method: Collin & Pattanaik, "GPU accelerated computation of Polarized
+ * Subsurface BRDF for Flat Particulate Layers" (arXiv 1707.05882).
+ *   - Sec. 2.B, Eqs. 6-15: azimuthal Fourier decomposition; every order m is an
+ *     independent discrete-ordinate problem built from the phase-matrix
+ *     expansion coefficients at N double-Gauss nodes per hemisphere.
+ *   - Sec. 3.A, Eqs. 40-45: homogeneous solution through the 4N x 4N product FE.
+ *   - Sec. 3.B, Eqs. 46-48: particular solution for a collimated beam.
+ *   - Sec. 3.C, Eqs. 49-56: boundary-condition system, one per order, with every
+ *     incident direction and Stokes basis vector as a right-hand side.
+ *   - Sec. 2.C, Eqs. 36-38 and Sec. 3.D: source-function reconstruction at
+ *     arbitrary outgoing angles.
+ *   - Sec. 2.D, Eqs. 1, 12, 39: Fourier synthesis into the 4x4 Mueller BRDF.
+ *
+ * Conventions (the paper leaves them open; the library fixes them):
+ *   - optical depth grows downward, mu > 0 is an upward propagation direction;
+ *   - Stokes vectors on the meridian frame (e_theta, e_phi) of the propagation
+ *     direction, V = -2 Im(E_theta E_phi*);
+ *   - F[r][s] = exiting radiance component r for a unit incident Stokes basis
+ *     vector s, divided by the irradiance mu_in * I0 on the horizontal surface
+ *     (units 1/sr); mu_in is the cosine towards the source, mu_out towards the
+ *     viewer, dphi = phi_out - phi_in, both directions pointing away from the
+ *     surface;
+ *   - optional smooth dielectric top of relative index n > 1 (Fresnel
+ *     transmission in and out, internal specular reflection as the top boundary
+ *     condition); n <= 1 means a bare top. Black lower boundary.
+ *
+ * Threading and ownership: a plan is used by one host thread at a time. All
+ * d_* pointers are device memory owned by the caller; the plan owns its
+ * workspace (allocated by vrte_plan_create / vrte_set_layer, freed by
+ * vrte_destroy). Every call is asynchronous on the caller's stream except where
+ * stated; errors found on the device are recorded in a device status word and
+ * reported by vrte_plan_status (which synchronizes) and by the next call.
+ */
+#ifndef VRTE_H
+#define VRTE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  VRTE_OK = 0,
+  VRTE_ERR_INVALID_ARG = 1,   /* rejected before any launch */
+  VRTE_ERR_STATE = 2,         /* call order violated (e.g. solve before set_layer) */
+  VRTE_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  VRTE_ERR_OOM = 4,           /* workspace allocation failed */
+  VRTE_ERR_NO_CONVERGENCE = 5,/* eigen iteration hit its sweep limit */
+  VRTE_ERR_SINGULAR = 6,      /* a pivot below tolerance in an LU / inverse */
+  VRTE_ERR_NONFINITE = 7,     /* a NaN or Inf reached the output */
+  VRTE_ERR_UNSUPPORTED = 8    /* valid request the library does not implement */
+} vrte_status;
+
+typedef enum {
+  VRTE_FP64 = 0,   /* every stage in FP64 on CUDA cores */
+  VRTE_MIXED = 1   /* dense contractions on tcgen05 tensor cores, FP64 where it matters */
+} vrte_precision;
+
+typedef enum {
+  VRTE_OUT_F32 = 0,
+  VRTE_OUT_F64 = 1
+} vrte_dtype;
+
+/* Plan descriptor. Grids are host arrays copied at plan creation. */
+typedef struct {
+  int n_nodes_max;     /* N: Gauss nodes per hemisphere, 1 <= N <= 96 */
+  int n_orders_max;    /* M: Fourier orders m = 0..M-1, 1 <= M <= 1024 */
+  int n_coef_max;      /* L: expansion coefficients l = 0..L-1, 1 <= L <= 1024 */
+  int n_layers_max;    /* independent layers solved in one call */
+  int n_mu_in;         /* incident cosines (towards the source), 1..16384 */
+  int n_mu_out;        /* outgoing cosines (towards the viewer), 1..16384 */
+  int n_phi;           /* azimuth differences */
+  const double* mu_in; /* host [n_mu_in],  each in (0, 1] */
+  const double* mu_out;/* host [n_mu_out], each in (0, 1] */
+  const double* phi;   /* host [n_phi], radians, dphi = phi_out - phi_in */
+  int precision;       /* vrte_precision */
+  unsigned flags;      /* VRTE_FLAG_* bits; unknown bits are rejected */
+} vrte_plan_desc;
+
+/* Records CUDA events around every pipeline stage on the solve stream, read back
+ * with vrte_profile_stages. Adds two event records per stage and order batch. */
+#define VRTE_FLAG_PROFILE 1u
+
+/* Per-stage statistics accumulated since the last vrte_profile_reset. */
+typedef struct {
+  char name[24];        /* stage name, e.g. "eigen", "recon_gemm", "synthesis" */
+  long long launches;   /* kernels launched by the stage (counted with or without the flag) */
+  double ms;            /* summed event time (0 without VRTE_FLAG_PROFILE) */
+  double flops;         /* algorithmic floating-point operations of the stage */
+  double bytes;         /* algorithmic HBM bytes of the stage (compulsory traffic) */
+} vrte_stage_stat;
+
+/* Per-layer parameters (host). */
+typedef struct {
+  double tau;          /* optical thickness tau0 > 0 */
+  double omega;        /* single-scattering albedo, 0 <= omega < 1 */
+  double n_interface;  /* relative index of a smooth top; <= 1 means none; at most 3 */
+  int n_nodes;         /* N of this layer, 1..n_nodes_max */
+  int n_orders;        /* M of this layer, 1..n_orders_max; orders >= n_coef contribute 0 */
+  int n_coef;          /* L of this layer, 1..n_coef_max */
+} vrte_layer;
+
+typedef struct vrte_plan vrte_plan;
+
+/* Creates a plan: validates the descriptor, copies the grids to the device and
+ * allocates per-plan tables. Returns VRTE_ERR_INVALID_ARG for out-of-range
+ * sizes or cosines, VRTE_ERR_OOM / VRTE_ERR_CUDA on device failures. */
+vrte_status vrte_plan_create(const vrte_plan_desc* desc, vrte_plan** out);
+
+/* Sets the layers to solve. host_params: [n_layers] parameters (copied).
+ * d_coeffs: device FP64 [n_layers][n_coef_max][6] expansion coefficients
+ * (alpha1, alpha2, alpha3, alpha4, beta1, beta2) per l, zero-padded beyond each
+ * layer's n_coef; the pointer is kept and read by each solve (the caller keeps
+ * it alive). Allocates the solve workspace for these layers. */
+vrte_status vrte_set_layer(vrte_plan* plan, int n_layers, const vrte_layer* host_params,
+                           const double* d_coeffs);
+
+/* Solves every layer and writes the BRDF table
+ *   d_brdf[n_layers][n_mu_in][n_mu_out][n_phi][4][4]   (row r = exiting Stokes
+ *   component, column s = incident Stokes basis vector),
+ * FP32 or FP64 per out_dtype, on `stream` (a cudaStream_t; NULL = legacy default
+ * stream). Asynchronous: no host synchronization and no allocation inside. */
+vrte_status vrte_solve_brdf(vrte_plan* plan, void* d_brdf, int out_dtype, void* stream);
+
+/* Same solve with host buffers: copies h_coeffs (host FP64, layout as d_coeffs
+ * of vrte_set_layer) to the plan's staging buffer, solves, copies the table to
+ * h_brdf (host, layout as d_brdf) and synchronizes `stream` before returning.
+ * Pinned host memory gives full copy bandwidth. */
+vrte_status vrte_solve_brdf_host(vrte_plan* plan, const double* h_coeffs, void* h_brdf,
+                                 int out_dtype, void* stream);
+
+/* Gradient of a scalar loss through the BRDF table (not implemented in this
+ * version: returns VRTE_ERR_UNSUPPORTED). */
+vrte_status vrte_brdf_backward(vrte_plan* plan, const void* d_grad_brdf, int grad_dtype,
+                               double* d_grad_params, void* stream);
+
+/* Synchronizes the plan's last stream and returns the device status word as a
+ * vrte_status (VRTE_OK if no device-side error was recorded), then clears it. */
+vrte_status vrte_plan_status(vrte_plan* plan);
+
+/* Copies up to max_stages stage statistics into out (host) and returns the number of
+ * stages (or -1 for a NULL plan). Synchronizes the plan's last stream. */
+int vrte_profile_stages(vrte_plan* plan, vrte_stage_stat* out, int max_stages);
+
+/* Clears the stage statistics and the recorded events. */
+void vrte_profile_reset(vrte_plan* plan);
+
+/* Diagnostic read of one internal buffer of the most recent order batch, for
+ * stage-level checks: copies min(bytes, buffer size) bytes into host_dst and returns
+ * the buffer's full size in *size_out (may be NULL). Synchronizes. Names: "pts",
+ * "nodes", "weights", "E", "F", "FE", "schur", "X", "Y", "lam_re", "lam_im", "K",
+ * "Kinv", "Xinv", "beam_p", "beam_r", "SD", "RHS", "C", "Upm", "Hhat", "T1", "Isyn",
+ * "mode_res" (per-order mode residual of the reduced eigen-decomposition),
+ * and "status" (the raw device status bits as one double, not cleared).
+ * Unknown names return VRTE_ERR_INVALID_ARG; calling before a solve returns
+ * VRTE_ERR_STATE. */
+vrte_status vrte_debug_copy(vrte_plan* plan, const char* name, void* host_dst, size_t bytes,
+                            size_t* size_out);
+
+/* Bytes of device workspace the plan currently holds. */
+size_t vrte_workspace_bytes(const vrte_plan* plan);
+
+/* Frees the plan and its workspace. Accepts NULL. */
+void vrte_destroy(vrte_plan* plan);
+
+/* Static string for a status code. */
+const char* vrte_status_string(vrte_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VRTE_H */

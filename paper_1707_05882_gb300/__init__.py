@@ -1,0 +1,248 @@
+"""GB300 DOM solver for the polarized subsurface BRDF of flat particulate layers.
+
+Thin Python binding over the C ABI in include/vrte.h (libvrte.so, built in-tree by
+paper_1707_05882_gb300.build). Argument marshalling only: every step of the solve
+runs in the library's CUDA kernels. PyTorch supplies device memory and streams.
+There is no CPU fallback: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+VRTE_FP64, VRTE_MIXED = 0, 1
+VRTE_OUT_F32, VRTE_OUT_F64 = 0, 1
+
+STATUS_NAMES = {
+    0: "VRTE_OK", 1: "VRTE_ERR_INVALID_ARG", 2: "VRTE_ERR_STATE", 3: "VRTE_ERR_CUDA",
+    4: "VRTE_ERR_OOM", 5: "VRTE_ERR_NO_CONVERGENCE", 6: "VRTE_ERR_SINGULAR",
+    7: "VRTE_ERR_NONFINITE", 8: "VRTE_ERR_UNSUPPORTED",
+}
+
+EXPORTED = ["vrte_plan_create", "vrte_set_layer", "vrte_solve_brdf", "vrte_solve_brdf_host",
+            "vrte_brdf_backward", "vrte_plan_status", "vrte_profile_stages", "vrte_profile_reset",
+            "vrte_debug_copy",
+            "vrte_workspace_bytes", "vrte_destroy", "vrte_status_string"]
+
+
+class VrteError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {STATUS_NAMES.get(code, code)}")
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("n_nodes_max", ctypes.c_int), ("n_orders_max", ctypes.c_int),
+                ("n_coef_max", ctypes.c_int), ("n_layers_max", ctypes.c_int),
+                ("n_mu_in", ctypes.c_int), ("n_mu_out", ctypes.c_int), ("n_phi", ctypes.c_int),
+                ("mu_in", ctypes.POINTER(ctypes.c_double)),
+                ("mu_out", ctypes.POINTER(ctypes.c_double)),
+                ("phi", ctypes.POINTER(ctypes.c_double)),
+                ("precision", ctypes.c_int), ("flags", ctypes.c_uint)]
+
+
+VRTE_FLAG_PROFILE = 1
+
+
+class StageStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong),
+                ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class Layer(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("omega", ctypes.c_double),
+                ("n_interface", ctypes.c_double), ("n_nodes", ctypes.c_int),
+                ("n_orders", ctypes.c_int), ("n_coef", ctypes.c_int)]
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libvrte.so (building it first if asked); raises if it cannot be loaded."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.LIB
+    if build_if_missing and (not os.path.exists(path) or _build._stale()):
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libvrte.so not found at {path}; run paper_1707_05882_gb300.build")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.vrte_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(P)]
+    lib.vrte_set_layer.argtypes = [P, ctypes.c_int, ctypes.POINTER(Layer), P]
+    lib.vrte_solve_brdf.argtypes = [P, P, ctypes.c_int, P]
+    lib.vrte_solve_brdf_host.argtypes = [P, P, P, ctypes.c_int, P]
+    lib.vrte_brdf_backward.argtypes = [P, P, ctypes.c_int, P, P]
+    lib.vrte_plan_status.argtypes = [P]
+    lib.vrte_profile_stages.argtypes = [P, ctypes.POINTER(StageStat), ctypes.c_int]
+    lib.vrte_profile_stages.restype = ctypes.c_int
+    lib.vrte_profile_reset.argtypes = [P]
+    lib.vrte_profile_reset.restype = None
+    lib.vrte_debug_copy.argtypes = [P, ctypes.c_char_p, P, ctypes.c_size_t,
+                                    ctypes.POINTER(ctypes.c_size_t)]
+    lib.vrte_debug_copy.restype = ctypes.c_int
+    lib.vrte_workspace_bytes.argtypes = [P]
+    lib.vrte_workspace_bytes.restype = ctypes.c_size_t
+    lib.vrte_destroy.argtypes = [P]
+    lib.vrte_destroy.restype = None
+    lib.vrte_status_string.argtypes = [ctypes.c_int]
+    lib.vrte_status_string.restype = ctypes.c_char_p
+    for name in ["vrte_plan_create", "vrte_set_layer", "vrte_solve_brdf", "vrte_solve_brdf_host",
+                 "vrte_brdf_backward", "vrte_plan_status"]:
+        getattr(lib, name).restype = ctypes.c_int
+    _LIB = lib
+    return lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise VrteError(code, where)
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+class Plan:
+    """A solver plan (vrte_plan_create / vrte_set_layer / vrte_solve_brdf / vrte_destroy)."""
+
+    def __init__(self, mu_in, mu_out, dphi, n_nodes_max, n_orders_max, n_coef_max,
+                 n_layers_max=1, precision=VRTE_FP64, profile=False):
+        self.lib = load_library()
+        self._mu_in = np.ascontiguousarray(mu_in, dtype=np.float64)
+        self._mu_out = np.ascontiguousarray(mu_out, dtype=np.float64)
+        self._phi = np.ascontiguousarray(dphi, dtype=np.float64)
+        d = PlanDesc(int(n_nodes_max), int(n_orders_max), int(n_coef_max), int(n_layers_max),
+                     self._mu_in.size, self._mu_out.size, self._phi.size, _dptr(self._mu_in),
+                     _dptr(self._mu_out), _dptr(self._phi), int(precision),
+                     VRTE_FLAG_PROFILE if profile else 0)
+        h = ctypes.c_void_p()
+        _check(self.lib.vrte_plan_create(ctypes.byref(d), ctypes.byref(h)), "vrte_plan_create")
+        self.handle = h
+        self.n_coef_max = int(n_coef_max)
+        self.n_layers = 0
+        self._coeffs = None
+
+    @property
+    def table_shape(self):
+        return (self.n_layers, self._mu_in.size, self._mu_out.size, self._phi.size, 4, 4)
+
+    def set_layers(self, layers, d_coeffs):
+        """layers: list of dict(tau, omega, n_interface, n_nodes, n_orders, n_coef);
+        d_coeffs: CUDA float64 tensor [n_layers, n_coef_max, 6] (kept alive by the plan)."""
+        arr = (Layer * len(layers))()
+        for i, l in enumerate(layers):
+            arr[i] = Layer(float(l["tau"]), float(l["omega"]), float(l.get("n_interface", 1.0)),
+                           int(l["n_nodes"]), int(l["n_orders"]), int(l["n_coef"]))
+        self._coeffs = d_coeffs
+        _check(self.lib.vrte_set_layer(self.handle, len(layers), arr,
+                                       ctypes.c_void_p(d_coeffs.data_ptr())), "vrte_set_layer")
+        self.n_layers = len(layers)
+
+    def solve(self, out, stream=None):
+        """Writes the table into the CUDA tensor `out` (float32 or float64) on `stream`."""
+        import torch
+        dt = VRTE_OUT_F64 if out.dtype == torch.float64 else VRTE_OUT_F32
+        _check(self.lib.vrte_solve_brdf(self.handle, ctypes.c_void_p(out.data_ptr()), dt,
+                                        _stream_handle(stream)), "vrte_solve_brdf")
+        return out
+
+    def solve_host(self, h_coeffs, h_out, stream=None):
+        """Host-buffer solve (copies in, solves, copies out, synchronizes)."""
+        import torch
+        dt = VRTE_OUT_F64 if h_out.dtype == torch.float64 else VRTE_OUT_F32
+        _check(self.lib.vrte_solve_brdf_host(self.handle, ctypes.c_void_p(h_coeffs.data_ptr()),
+                                             ctypes.c_void_p(h_out.data_ptr()), dt,
+                                             _stream_handle(stream)), "vrte_solve_brdf_host")
+        return h_out
+
+    def status(self):
+        return self.lib.vrte_plan_status(self.handle)
+
+    def stages(self):
+        """Per-stage statistics since the last reset: list of dicts (synchronizes)."""
+        arr = (StageStat * 32)()
+        n = self.lib.vrte_profile_stages(self.handle, arr, 32)
+        return [dict(name=arr[i].name.decode(), launches=int(arr[i].launches), ms=arr[i].ms,
+                     flops=arr[i].flops, bytes=arr[i].bytes) for i in range(max(n, 0))]
+
+    def debug_buffer(self, name):
+        """float64 copy of an internal buffer of the most recent order batch."""
+        size = ctypes.c_size_t()
+        _check(self.lib.vrte_debug_copy(self.handle, name.encode(), None, 0, ctypes.byref(size)),
+               "vrte_debug_copy")
+        out = np.empty(size.value // 8, dtype=np.float64)
+        _check(self.lib.vrte_debug_copy(self.handle, name.encode(),
+                                        out.ctypes.data_as(ctypes.c_void_p), size.value, None),
+               "vrte_debug_copy")
+        return out
+
+    def reset_stages(self):
+        self.lib.vrte_profile_reset(self.handle)
+
+    def workspace_bytes(self):
+        return int(self.lib.vrte_workspace_bytes(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.vrte_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_coefficients(layers, n_coef_max=None):
+    """[n_layers, n_coef_max, 6] float64 array from each layer's 'coef' [L, 6] (zero padded)."""
+    if n_coef_max is None:
+        n_coef_max = max(np.asarray(l["coef"]).shape[0] for l in layers)
+    out = np.zeros((len(layers), n_coef_max, 6))
+    for i, l in enumerate(layers):
+        c = np.asarray(l["coef"], dtype=np.float64)
+        out[i, :c.shape[0]] = c
+    return out
+
+
+def brdf(layers, mu_in, mu_out, dphi, precision=VRTE_FP64, out_dtype=None, stream=None):
+    """Solve the BRDF tables of `layers` on the current CUDA device.
+
+    layers: list of dict(tau, omega, n_interface, n_nodes, n_orders, coef[L, 6]).
+    Returns a CUDA tensor [n_layers, n_in, n_out, n_phi, 4, 4].
+    """
+    import torch
+    if out_dtype is None:
+        out_dtype = torch.float64
+    coef = pack_coefficients(layers)
+    d_coef = torch.from_numpy(coef).cuda()
+    lay = [dict(l, n_coef=np.asarray(l["coef"]).shape[0]) for l in layers]
+    plan = Plan(mu_in, mu_out, dphi, max(l["n_nodes"] for l in lay),
+                max(l["n_orders"] for l in lay), coef.shape[1], len(lay), precision)
+    try:
+        plan.set_layers(lay, d_coef)
+        out = torch.empty(plan.table_shape, dtype=out_dtype, device="cuda")
+        plan.solve(out, stream)
+        code = plan.status()
+        _check(code, "solve status")
+        return out
+    finally:
+        plan.close()

@@ -1,0 +1,229 @@
+// Step a1: assembly of the order-m operators from the expansion coefficients.
+//
+// Every operator the path needs is built from the parity-split sums
+//   S+-(x, y) = sum_{l=m}^{L-1} P_l^m(x) B_l (I +- (-1)^(l-m) D) P_l^m(y)
+// (Sec. 3.A, Eq. 41; P_l^m and B_l as in Eqs. 9-10), where
+// (I + (-1)^(l-m) D) is 2 diag(1,1,0,0) for even l-m and 2 diag(0,0,1,1) for odd
+// l-m. With p, r, t the entries of P_l^m (p on I and V, r/t on the Q-U block) the
+// product P(x) B_l diag(1,1,0,0) P(y) has nine non-zero entries and
+// P(x) B_l diag(0,0,1,1) P(y) nine more, so each l costs 18 multiply-adds per
+// point pair instead of a dense 4x4x4x4 product.
+#include "vrte_internal.cuh"
+
+namespace vrte {
+
+struct SPair {
+  double sp[4][4];
+  double sm[4][4];
+};
+
+// Accumulate S+ and S- for table points kx, ky of order unit u.
+__device__ inline void accumulate_S(int m, int L, int P, const double* __restrict__ coef,
+                                    const double* __restrict__ pt, const double* __restrict__ rt,
+                                    const double* __restrict__ tt, size_t ubase, int kx, int ky,
+                                    SPair& S) {
+  // buckets: e1/o1 = T1 part for even/odd l-m, e2/o2 = T2 part
+  double e1[9] = {0}, o1[9] = {0}, e2[9] = {0}, o2[9] = {0};
+  for (int l = m; l < L; ++l) {
+    size_t row = ubase + (size_t)l * P;
+    double p = pt[row + kx], r = rt[row + kx], t = tt[row + kx];
+    double pp = pt[row + ky], rp = rt[row + ky], tp = tt[row + ky];
+    const double* c = coef + 6 * l;
+    double a1 = c[0], a2 = c[1], a3 = c[2], a4 = c[3], b1 = c[4], b2 = c[5];
+    double v1[9], v2[9];
+    // T1 = P(x) B diag(1,1,0,0) P(y): rows 0..2, columns 0..2
+    v1[0] = p * a1 * pp;  v1[1] = p * b1 * rp;  v1[2] = -p * b1 * tp;
+    v1[3] = r * b1 * pp;  v1[4] = r * a2 * rp;  v1[5] = -r * a2 * tp;
+    v1[6] = -t * b1 * pp; v1[7] = -t * a2 * rp; v1[8] = t * a2 * tp;
+    // T2 = P(x) B diag(0,0,1,1) P(y): rows 1..3, columns 1..3
+    v2[0] = t * a3 * tp;  v2[1] = -t * a3 * rp; v2[2] = -t * b2 * pp;
+    v2[3] = -r * a3 * tp; v2[4] = r * a3 * rp;  v2[5] = r * b2 * pp;
+    v2[6] = p * b2 * tp;  v2[7] = -p * b2 * rp; v2[8] = p * a4 * pp;
+    if (((l - m) & 1) == 0) {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) { e1[q] += v1[q]; e2[q] += v2[q]; }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 9; ++q) { o1[q] += v1[q]; o2[q] += v2[q]; }
+    }
+  }
+  // S+ = 2 (e1 + o2), S- = 2 (o1 + e2), with T1 at (0..2, 0..2) and T2 at (1..3, 1..3)
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) { S.sp[a][b] = 0.0; S.sm[a][b] = 0.0; }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      S.sp[a][b] += 2.0 * e1[3 * a + b];
+      S.sm[a][b] += 2.0 * o1[3 * a + b];
+      S.sp[a + 1][b + 1] += 2.0 * o2[3 * a + b];
+      S.sm[a + 1][b + 1] += 2.0 * e2[3 * a + b];
+    }
+}
+
+// Block matrix [[a, b, 0, 0], [b, a, 0, 0], [0, 0, c, d], [0, 0, -d, c]] entry (i, j).
+__device__ inline double blk(const double* q, int i, int j) {
+  if (i < 2 && j < 2) return i == j ? q[0] : q[1];
+  if (i >= 2 && j >= 2) return i == j ? q[2] : (i == 2 ? q[3] : -q[3]);
+  return 0.0;
+}
+
+// E'[4i+a][4j+b] = (delta - (omega/2) alpha_j S+_ab(i, j)) / mu_i, F' with S-  (Eq. 41,
+// in the row-scaled form E' = M^-1 (...) whose product F'E' is similar to the paper's FE).
+__global__ void k_assemble_EF(OrderBatch b, const double* pt, const double* rt, const double* tt,
+                              const double* mu_nodes, const double* w_nodes, double* E, double* F) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y;
+  int u = blockIdx.z;
+  if (j >= b.N) return;
+  int m = b.m0 + u;
+  SPair S;
+  accumulate_S(m, b.L, b.P, b.coef, pt, rt, tt, (size_t)u * b.L * b.P, i, j, S);
+  double inv_mu = 1.0 / mu_nodes[i];
+  double f = 0.5 * b.omega * w_nodes[j];
+  size_t base = (size_t)u * b.n * b.n;
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 4; ++c) {
+      double delta = (i == j && a == c) ? 1.0 : 0.0;
+      size_t idx = base + (size_t)(4 * i + a) * b.n + 4 * j + c;
+      E[idx] = (delta - f * S.sp[a][c]) * inv_mu;
+      F[idx] = (delta - f * S.sm[a][c]) * inv_mu;
+    }
+}
+
+void launch_assemble_EF(const OrderBatch& b, const double* p, const double* r, const double* t,
+                        const double* mu_nodes, const double* w_nodes, double* E, double* F,
+                        cudaStream_t s) {
+  dim3 grid((b.N + 63) / 64, b.N, b.n_units);
+  k_assemble_EF<<<grid, 64, 0, s>>>(b, p, r, t, mu_nodes, w_nodes, E, F);
+}
+
+// Beam vectors of the reduced particular problem (Sec. 3.B, Eq. 47), for the
+// collimated source q(+-mu_i) = (omega/2pi) A^m(+-mu_i, -mu0) b_k (Eq. 14):
+//   p = M^-1 (q+ + D q-) = (omega/2pi) / mu_i  S+(mu_i, mu0) D b_k
+//   r = M^-1 (q+ - D q-) = -(omega/2pi) / mu_i S-(mu_i, mu0) D b_k
+// b_k = beam block of incident k (columns = incident Stokes basis vectors).
+// Layout Pm[u][4i+a][4k+s].
+__global__ void k_assemble_beam(OrderBatch b, const double* pt, const double* rt, const double* tt,
+                                const double* mu_nodes, const double* min4, double* Pm,
+                                double* Rm) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y;
+  int u = blockIdx.z;
+  if (k >= b.n_in) return;
+  int m = b.m0 + u;
+  SPair S;
+  accumulate_S(m, b.L, b.P, b.coef, pt, rt, tt, (size_t)u * b.L * b.P, i, b.N + k, S);
+  double cq = b.omega / (2.0 * kPi) / mu_nodes[i];
+  const double* q = min4 + 4 * k;
+  int R = 4 * b.n_in;
+  size_t base = (size_t)u * b.n * R;
+  for (int a = 0; a < 4; ++a)
+    for (int s = 0; s < 4; ++s) {
+      double vp = 0.0, vm = 0.0;
+      for (int c = 0; c < 4; ++c) {
+        double db = (c < 2 ? 1.0 : -1.0) * blk(q, c, s);
+        vp += S.sp[a][c] * db;
+        vm += S.sm[a][c] * db;
+      }
+      size_t idx = base + (size_t)(4 * i + a) * R + 4 * k + s;
+      Pm[idx] = cq * vp;
+      Rm[idx] = -cq * vm;
+    }
+}
+
+void launch_assemble_beam(const OrderBatch& b, const double* p, const double* r, const double* t,
+                          const double* mu_nodes, const double* min4, double* Pm, double* Rm,
+                          cudaStream_t s) {
+  dim3 grid((b.n_in + 63) / 64, b.N, b.n_units);
+  k_assemble_beam<<<grid, 64, 0, s>>>(b, p, r, t, mu_nodes, min4, Pm, Rm);
+}
+
+// Reconstruction operators (Sec. 2.C, Eq. 38 and Sec. 3.D): the scattering part of the
+// source at outgoing mu_o acting on a nodal field, split by the same parity sums:
+//   U+-[4o+a][4j+c] = (omega/4) alpha_j (M_out[o] S+-(mu_o, mu_j))_ac.
+// Stored as Upm[u][4o+a][0..2n) = [U+ | U-].
+__global__ void k_assemble_U(OrderBatch b, const double* pt, const double* rt, const double* tt,
+                             const double* w_nodes, const double* mout4, double* U) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int o = blockIdx.y;
+  int u = blockIdx.z;
+  if (j >= b.N) return;
+  int m = b.m0 + u;
+  SPair S;
+  accumulate_S(m, b.L, b.P, b.coef, pt, rt, tt, (size_t)u * b.L * b.P, b.N + b.n_in + o, j, S);
+  double f = 0.25 * b.omega * w_nodes[j];
+  const double* q = mout4 + 4 * o;
+  int n2 = 2 * b.n;
+  size_t base = (size_t)u * (4 * b.n_out) * n2;
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 4; ++c) {
+      double vp = 0.0, vm = 0.0;
+      for (int e = 0; e < 4; ++e) {
+        double mo = blk(q, a, e);
+        vp += mo * S.sp[e][c];
+        vm += mo * S.sm[e][c];
+      }
+      size_t row = base + (size_t)(4 * o + a) * n2;
+      U[row + 4 * j + c] = f * vp;
+      U[row + b.n + 4 * j + c] = f * vm;
+    }
+}
+
+void launch_assemble_U(const OrderBatch& b, const double* p, const double* r, const double* t,
+                       const double* w_nodes, const double* mout4, double* U, cudaStream_t s) {
+  dim3 grid((b.N + 63) / 64, b.n_out, b.n_units);
+  k_assemble_U<<<grid, 64, 0, s>>>(b, p, r, t, w_nodes, mout4, U);
+}
+
+// Direct (once-scattered) source term of the reconstruction (Eq. 38, Q term), already
+// multiplied by the depth integral g0 of exp(-t/mu0) along the exit path:
+//   T1[u][4o+a][4k+s] = g0(o, k) (omega/2pi) (M_out[o] A^m(mu_o, -mu0_k) b_k)_as,
+//   A^m(x, -y) = (S+(x, y) - S-(x, y)) D / 2,
+//   g0 = (1 - exp(-tau0 (1/mu_o + 1/mu0))) / (mu_o (1/mu_o + 1/mu0)).
+__global__ void k_assemble_direct(OrderBatch b, const double* pt, const double* rt,
+                                  const double* tt, const double* pts, const double* min4,
+                                  const double* mout4, double* T1) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int o = blockIdx.y;
+  int u = blockIdx.z;
+  if (k >= b.n_in) return;
+  int m = b.m0 + u;
+  SPair S;
+  accumulate_S(m, b.L, b.P, b.coef, pt, rt, tt, (size_t)u * b.L * b.P, b.N + b.n_in + o, b.N + k,
+               S);
+  double mu_o = pts[b.N + b.n_in + o], mu0 = pts[b.N + k];
+  double xs = 1.0 / mu_o + 1.0 / mu0;
+  double g0 = -expm1(-b.tau * xs) / (mu_o * xs);
+  double f = g0 * b.omega / (2.0 * kPi) * 0.5;
+  const double* qi = min4 + 4 * k;
+  const double* qo = mout4 + 4 * o;
+  int R = 4 * b.n_in;
+  size_t base = (size_t)u * (4 * b.n_out) * R;
+  double A[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 4; ++c) A[a][c] = (S.sp[a][c] - S.sm[a][c]) * (c < 2 ? 1.0 : -1.0);
+  for (int a = 0; a < 4; ++a)
+    for (int s = 0; s < 4; ++s) {
+      double v = 0.0;
+      for (int e = 0; e < 4; ++e) {
+        double mo = blk(qo, a, e);
+        if (mo == 0.0) continue;
+        double w = 0.0;
+        for (int c = 0; c < 4; ++c) w += A[e][c] * blk(qi, c, s);
+        v += mo * w;
+      }
+      T1[base + (size_t)(4 * o + a) * R + 4 * k + s] = f * v;
+    }
+}
+
+void launch_assemble_direct(const OrderBatch& b, const double* p, const double* r,
+                            const double* t, const double* pts, const double* min4,
+                            const double* mout4, double* T1, cudaStream_t s) {
+  dim3 grid((b.n_in + 63) / 64, b.n_out, b.n_units);
+  k_assemble_direct<<<grid, 64, 0, s>>>(b, p, r, t, pts, min4, mout4, T1);
+}
+
+}  // namespace vrte

@@ -1,0 +1,241 @@
+// Dense FP64 linear algebra on CUDA cores: batched GEMM (with an epilogue hook for the
+// reconstruction) and batched in-place Gauss-Jordan inversion with partial pivoting.
+// FP64 stays on the CUDA cores: sm_103a has no FP64 tensor-core path worth using.
+#include "vrte_internal.cuh"
+
+namespace vrte {
+
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+
+struct EpiStore {
+  double alpha, beta;
+  double* C;
+  int ldc;
+  long long sC;
+  __device__ void operator()(int u, int i, int j, double acc) const {
+    double* c = C + (size_t)u * sC + (size_t)i * ldc + j;
+    *c = beta == 0.0 ? alpha * acc : alpha * acc + beta * *c;
+  }
+};
+
+// Reconstruction epilogue: row i = 4o + a (outgoing o, exiting component a),
+// column j = 4k + s (incident k, incident basis s). Writes the order-m radiance
+// Isyn[m][k][o][a][s] = T1[i][j] + g0(o, k) * acc.
+struct EpiPart {
+  const double* T1;
+  double* Isyn;
+  const double* pts;
+  int N, n_in, n_out, m0;
+  double tau;
+  __device__ void operator()(int u, int i, int j, double acc) const {
+    int R = 4 * n_in;
+    int o = i >> 2, a = i & 3, k = j >> 2, s = j & 3;
+    double mu_o = pts[N + n_in + o], mu0 = pts[N + k];
+    double xs = 1.0 / mu_o + 1.0 / mu0;
+    double g0 = -expm1(-tau * xs) / (mu_o * xs);
+    double v = T1[(size_t)u * (4 * n_out) * R + (size_t)i * R + j] + g0 * acc;
+    size_t dst = (((size_t)(m0 + u) * n_in + k) * n_out + o) * 16 + 4 * a + s;
+    Isyn[dst] = v;
+  }
+};
+
+// Tiled FP64 GEMM: 64x64 output tile, 256 threads, 4x4 outputs per thread (strided by 16
+// so shared-memory reads are conflict free), K staged 16 at a time. Row-major operands;
+// tA / tB select op(A) = A^T (A stored K x M) and op(B) = B^T (B stored N x K).
+template <class Epi>
+__global__ void __launch_bounds__(256) k_dgemm(int M, int N, int K, const double* __restrict__ A,
+                                               int lda, long long sA, bool tA,
+                                               const double* __restrict__ B, int ldb,
+                                               long long sB, bool tB, Epi epi, const int* mask) {
+  __shared__ double As[GB_K][GB_M + 1];
+  __shared__ double Bs[GB_K][GB_N + 1];
+  int u = blockIdx.z;
+  if (mask && !mask[u]) return;
+  int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+  int tid = threadIdx.x;
+  int tx = tid & 15, ty = tid >> 4;
+  const double* Ab = A + (size_t)u * sA;
+  const double* Bb = B + (size_t)u * sB;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k0 = 0; k0 < K; k0 += GB_K) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int row, kk;
+      if (!tA) { kk = tid & 15; row = (tid >> 4) + 16 * q; }
+      else { row = tid & 63; kk = (tid >> 6) + 4 * q; }
+      int gi = m0 + row, gk = k0 + kk;
+      double v = 0.0;
+      if (gi < M && gk < K) v = tA ? Ab[(size_t)gk * lda + gi] : Ab[(size_t)gi * lda + gk];
+      As[kk][row] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int col, kk;
+      if (!tB) { col = tid & 63; kk = (tid >> 6) + 4 * q; }
+      else { kk = tid & 15; col = (tid >> 4) + 16 * q; }
+      int gj = n0 + col, gk = k0 + kk;
+      double v = 0.0;
+      if (gj < N && gk < K) v = tB ? Bb[(size_t)gj * ldb + gk] : Bb[(size_t)gk * ldb + gj];
+      Bs[kk][col] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GB_K; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int gi = m0 + ty + 16 * i, gj = n0 + tx + 16 * j;
+      if (gi < M && gj < N) epi(u, gi, gj, acc[i][j]);
+    }
+}
+
+template <class Epi>
+static void run_dgemm(int M, int N, int K, const double* A, int lda, long long sA, bool tA,
+                      const double* B, int ldb, long long sB, bool tB, Epi epi, int batch,
+                      cudaStream_t s, const int* mask = nullptr) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  dim3 grid((N + GB_N - 1) / GB_N, (M + GB_M - 1) / GB_M, batch);
+  k_dgemm<Epi><<<grid, 256, 0, s>>>(M, N, K, A, lda, sA, tA, B, ldb, sB, tB, epi, mask);
+}
+
+void dgemm_batched_mask(bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
+                        int lda, long long sA, const double* B, int ldb, long long sB, double beta,
+                        double* C, int ldc, long long sC, int batch, const int* mask,
+                        cudaStream_t s) {
+  EpiStore e{alpha, beta, C, ldc, sC};
+  run_dgemm(M, N, K, A, lda, sA, tA, B, ldb, sB, tB, e, batch, s, mask);
+}
+
+void dgemm_batched_t(bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
+                     int lda, long long sA, const double* B, int ldb, long long sB, double beta,
+                     double* C, int ldc, long long sC, int batch, cudaStream_t s) {
+  EpiStore e{alpha, beta, C, ldc, sC};
+  run_dgemm(M, N, K, A, lda, sA, tA, B, ldb, sB, tB, e, batch, s);
+}
+
+void dgemm_batched(int M, int N, int K, double alpha, const double* A, int lda, long long sA,
+                   const double* B, int ldb, long long sB, double beta, double* C, int ldc,
+                   long long sC, int batch, cudaStream_t s) {
+  dgemm_batched_t(false, false, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, batch, s);
+}
+
+void dgemm_part_epilogue(const OrderBatch& b, const double* A, const double* B, const double* T1,
+                         const double* pts, double* Isyn, cudaStream_t s) {
+  int Ro = 4 * b.n_out, R = 4 * b.n_in, n2 = 2 * b.n;
+  EpiPart e{T1, Isyn, pts, b.N, b.n_in, b.n_out, b.m0, b.tau};
+  run_dgemm(Ro, R, n2, A, n2, (long long)Ro * n2, false, B, R, (long long)n2 * R, false, e,
+            b.n_units, s);
+}
+
+// In-place Gauss-Jordan inversion with partial (row) pivoting, one CTA per matrix.
+// Step k: pick the largest |W[i][k]|, i >= k; swap rows; scale the pivot row; subtract
+// multiples of it from every other row (the pivot column takes the inverse's column).
+// Row swaps are undone at the end by swapping columns in reverse order.
+// A zero or non-finite pivot sets ST_SINGULAR (the matrix is still processed).
+__global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict__ A,
+                                                 double* __restrict__ Ainv, unsigned* status) {
+  extern __shared__ double sh[];
+  double* colk = sh;            // [n]
+  double* rowk = sh + n;        // [n]
+  int* perm = (int*)(sh + 2 * n);
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  int u = blockIdx.x;
+  const double* Ab = A + (size_t)u * n * n;
+  double* W = Ainv + (size_t)u * n * n;
+  int tid = threadIdx.x, nt = blockDim.x;
+  for (size_t e = tid; e < (size_t)n * n; e += nt) W[e] = Ab[e];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    // pivot search
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + tid; i < n; i += nt) {
+      double v = fabs(W[(size_t)i * n + k]);
+      if (v > best) { best = v; bi = i; }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      double ov = __shfl_down_sync(0xffffffffu, best, off);
+      int oi = __shfl_down_sync(0xffffffffu, bi, off);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+    __syncthreads();
+    if (tid < 32) {
+      int nw = (nt + 31) >> 5;
+      best = tid < nw ? red_v[tid] : -1.0;
+      bi = tid < nw ? red_i[tid] : k;
+      for (int off = 16; off > 0; off >>= 1) {
+        double ov = __shfl_down_sync(0xffffffffu, best, off);
+        int oi = __shfl_down_sync(0xffffffffu, bi, off);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+      }
+      if (tid == 0) { red_i[0] = bi; perm[k] = bi; }
+    }
+    __syncthreads();
+    int p = red_i[0];
+    if (p != k) {
+      for (int j = tid; j < n; j += nt) {
+        double t = W[(size_t)k * n + j];
+        W[(size_t)k * n + j] = W[(size_t)p * n + j];
+        W[(size_t)p * n + j] = t;
+      }
+    }
+    __syncthreads();
+    double piv = W[(size_t)k * n + k];
+    if (tid == 0 && (piv == 0.0 || !isfinite(piv))) atomicOr(status, ST_SINGULAR);
+    double pinv = 1.0 / piv;
+    for (int i = tid; i < n; i += nt) colk[i] = W[(size_t)i * n + k];
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) {
+      double v = (j == k) ? pinv : W[(size_t)k * n + j] * pinv;
+      rowk[j] = v;
+      W[(size_t)k * n + j] = v;
+    }
+    __syncthreads();
+    for (size_t e = tid; e < (size_t)n * n; e += nt) {
+      int i = (int)(e / n), j = (int)(e - (size_t)i * n);
+      if (i == k) continue;
+      double w = (j == k) ? 0.0 : W[e];
+      W[e] = w - colk[i] * rowk[j];
+    }
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    int p = perm[k];
+    if (p != k) {
+      for (int i = tid; i < n; i += nt) {
+        double t = W[(size_t)i * n + k];
+        W[(size_t)i * n + k] = W[(size_t)i * n + p];
+        W[(size_t)i * n + p] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void batched_inverse(int n, double* A, double* Ainv, int batch, unsigned* status, cudaStream_t s) {
+  size_t smem = 2 * n * sizeof(double) + n * sizeof(int);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_inverse<<<batch, 512, smem, s>>>(n, A, Ainv, status);
+}
+
+}  // namespace vrte

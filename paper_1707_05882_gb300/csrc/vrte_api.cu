@@ -1,0 +1,555 @@
+// C ABI of the VRTE BRDF solver: plan lifetime, workspace, and the per-order pipeline.
+//
+// Pipeline for each layer and each batch of Fourier orders (all on one stream):
+//   a0 tables      Gauss nodes, Fresnel data, generalized spherical functions
+//   a1 assembly    E', F' (Eq. 41), beam vectors p, r (Eq. 47), reconstruction operators
+//   a2 homogeneous F'E' -> eigenpairs (Eqs. 43-45), Y = E'X / kappa
+//   a3 boundary    K (Eqs. 49-56) and its inverse
+//   a4/a5 particular  (F'E' - 1/mu0^2) s = F'p - r/mu0 solved in the eigenbasis (Eq. 47),
+//                  d = mu0 (p - E's) (Eq. 48)
+//   a6 boundary solve  C = K^-1 [-(Z-(0) - R_F Z+(0)); -Z+(tau0) e^{-tau0/mu0}]
+//   a7 reconstruction  I^m(0, mu_out) = [Hhat | U+-] [C ; s ; d] with depth integrals (Eqs. 36, 38)
+//   a8 synthesis   sum over orders with the Fourier factors (Eqs. 7, 12)
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "vrte_internal.cuh"
+
+using namespace vrte;
+
+namespace {
+enum Stage {
+  ST_TABLES, ST_ASSEMBLE, ST_EIGEN, ST_MODES, ST_PARTICULAR, ST_BC_SOLVE, ST_RECON_OPS,
+  ST_RECON_GEMM, ST_SYNTHESIS, kStages
+};
+const char* kStageNames[kStages] = {"tables", "assemble", "eigen", "modes_bc_inverse",
+                                    "particular", "bc_solve", "recon_ops", "recon_gemm",
+                                    "synthesis"};
+}  // namespace
+
+struct vrte_plan {
+  vrte_plan_desc desc{};
+  int n_in = 0, n_out = 0, n_phi = 0;
+  double *d_mu_in = nullptr, *d_mu_out = nullptr, *d_phi = nullptr;
+  double *d_wc = nullptr, *d_ws = nullptr;  // [M_max][n_phi]
+  unsigned* d_status = nullptr;
+  cudaStream_t last_stream = nullptr;
+  // layers
+  std::vector<vrte_layer> layers;
+  const double* d_coeffs = nullptr;
+  int n_layers = 0;
+  // per-layer tables (sized for N_max)
+  double *d_mu_nodes = nullptr, *d_w_nodes = nullptr, *d_pts = nullptr, *d_min4 = nullptr,
+         *d_mout4 = nullptr, *d_rtop4 = nullptr;
+  // order-batch workspace (sized for the largest layer)
+  int chunk = 0;
+  double *gp = nullptr, *gr = nullptr, *gt = nullptr;
+  double *E = nullptr, *F = nullptr, *FE = nullptr, *X = nullptr, *EX = nullptr, *Y = nullptr,
+         *Xinv = nullptr, *Hs = nullptr, *Zs = nullptr, *Vs = nullptr;
+  double *lam_re = nullptr, *lam_im = nullptr, *bal = nullptr;
+  double *K = nullptr, *Kinv = nullptr;
+  double *Pb = nullptr, *Rb = nullptr, *Wv = nullptr, *Yv = nullptr, *Es = nullptr;
+  double *SD = nullptr, *RHS = nullptr, *C = nullptr;
+  double *Upm = nullptr, *P1 = nullptr, *P2 = nullptr, *Hhat = nullptr, *T1 = nullptr;
+  // block-form eigen fallback (2n x 2n per order)
+  double *FY = nullptr, *mode_res = nullptr, *Bm = nullptr, *Hb = nullptr, *Zb = nullptr,
+         *Vb = nullptr, *Xb = nullptr, *kb_re = nullptr, *kb_im = nullptr, *balb = nullptr;
+  int* mode_flag = nullptr;
+  double* Isyn = nullptr;  // [M_max][n_in][n_out][16]
+  // host-API staging
+  double* d_coef_stage = nullptr;
+  size_t coef_stage_bytes = 0;
+  void* d_out_stage = nullptr;
+  size_t out_stage_bytes = 0;
+  std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;
+  // stage statistics: launches always, event pairs when VRTE_FLAG_PROFILE is set
+  vrte_stage_stat stats[kStages];
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
+  bool profile = false;
+  // geometry of the most recent order batch (for vrte_debug_copy)
+  int last_n = 0, last_U = 0, last_P = 0, last_Meff = 0;
+};
+
+namespace {
+
+vrte_status alloc(vrte_plan* p, void** ptr, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return VRTE_ERR_OOM;
+  }
+  p->allocs.push_back(*ptr);
+  p->alloc_bytes.push_back(bytes);
+  return VRTE_OK;
+}
+
+template <typename T>
+vrte_status allocd(vrte_plan* p, T** ptr, size_t count) {
+  return alloc(p, (void**)ptr, count * sizeof(T));
+}
+
+void free_workspace(vrte_plan* p, size_t keep) {
+  // frees allocations made after index `keep`
+  while (p->allocs.size() > keep) {
+    cudaFree(p->allocs.back());
+    p->allocs.pop_back();
+    p->alloc_bytes.pop_back();
+  }
+}
+
+// Stage bracket: counts launches, adds algorithmic work, records events if profiling.
+struct StageScope {
+  vrte_plan* p;
+  int st;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  StageScope(vrte_plan* p_, int st_, cudaStream_t s_, int launches, double flops, double bytes)
+      : p(p_), st(st_), s(s_) {
+    p->stats[st].launches += launches;
+    p->stats[st].flops += flops;
+    p->stats[st].bytes += bytes;
+    if (p->profile && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, s);
+  }
+  ~StageScope() {
+    if (!e0) return;
+    cudaEvent_t e1;
+    if (cudaEventCreate(&e1) == cudaSuccess) {
+      cudaEventRecord(e1, s);
+      p->events.push_back({st, {e0, e1}});
+    } else {
+      cudaEventDestroy(e0);
+    }
+  }
+};
+
+void reset_stats(vrte_plan* p) {
+  for (auto& e : p->events) {
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  p->events.clear();
+  for (int i = 0; i < kStages; ++i) {
+    memset(&p->stats[i], 0, sizeof(vrte_stage_stat));
+    strncpy(p->stats[i].name, kStageNames[i], sizeof(p->stats[i].name) - 1);
+  }
+}
+
+// buffers allocated by vrte_plan_create (kept by vrte_set_layer)
+constexpr size_t kPlanAllocs = 6;
+
+}  // namespace
+
+extern "C" {
+
+const char* vrte_status_string(vrte_status st) {
+  switch (st) {
+    case VRTE_OK: return "ok";
+    case VRTE_ERR_INVALID_ARG: return "invalid argument";
+    case VRTE_ERR_STATE: return "call order violated";
+    case VRTE_ERR_CUDA: return "CUDA runtime error";
+    case VRTE_ERR_OOM: return "device allocation failed";
+    case VRTE_ERR_NO_CONVERGENCE: return "eigen iteration did not converge";
+    case VRTE_ERR_SINGULAR: return "singular pivot";
+    case VRTE_ERR_NONFINITE: return "non-finite value";
+    case VRTE_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+vrte_status vrte_plan_create(const vrte_plan_desc* d, vrte_plan** out) {
+  if (!d || !out) return VRTE_ERR_INVALID_ARG;
+  *out = nullptr;
+  // size limits keep every launch inside the grid and shared-memory limits
+  if (d->n_nodes_max < 1 || d->n_nodes_max > 96 || d->n_orders_max < 1 ||
+      d->n_orders_max > 1024 || d->n_coef_max < 1 || d->n_coef_max > 1024 ||
+      d->n_layers_max < 1 || d->n_mu_in < 1 || d->n_mu_in > 16384 || d->n_mu_out < 1 ||
+      d->n_mu_out > 16384 || d->n_phi < 1 || !d->mu_in || !d->mu_out || !d->phi ||
+      (d->flags & ~VRTE_FLAG_PROFILE) != 0)
+    return VRTE_ERR_INVALID_ARG;
+  if (d->precision != VRTE_FP64 && d->precision != VRTE_MIXED) return VRTE_ERR_INVALID_ARG;
+  for (int i = 0; i < d->n_mu_in; ++i)
+    if (!(d->mu_in[i] > 0.0 && d->mu_in[i] <= 1.0)) return VRTE_ERR_INVALID_ARG;
+  for (int i = 0; i < d->n_mu_out; ++i)
+    if (!(d->mu_out[i] > 0.0 && d->mu_out[i] <= 1.0)) return VRTE_ERR_INVALID_ARG;
+  for (int i = 0; i < d->n_phi; ++i)
+    if (!(d->phi[i] == d->phi[i])) return VRTE_ERR_INVALID_ARG;
+  vrte_plan* p = new vrte_plan();
+  p->desc = *d;
+  p->desc.mu_in = p->desc.mu_out = p->desc.phi = nullptr;
+  p->n_in = d->n_mu_in;
+  p->n_out = d->n_mu_out;
+  p->n_phi = d->n_phi;
+  p->profile = (d->flags & VRTE_FLAG_PROFILE) != 0;
+  reset_stats(p);
+  vrte_status st = VRTE_OK;
+  int Mx = d->n_orders_max;
+  if ((st = allocd(p, &p->d_mu_in, p->n_in)) || (st = allocd(p, &p->d_mu_out, p->n_out)) ||
+      (st = allocd(p, &p->d_phi, p->n_phi)) || (st = allocd(p, &p->d_wc, (size_t)Mx * p->n_phi)) ||
+      (st = allocd(p, &p->d_ws, (size_t)Mx * p->n_phi)) || (st = allocd(p, &p->d_status, 1))) {
+    vrte_destroy(p);
+    return st;
+  }
+  if (cudaMemcpy(p->d_mu_in, d->mu_in, p->n_in * sizeof(double), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(p->d_mu_out, d->mu_out, p->n_out * sizeof(double), cudaMemcpyHostToDevice) ||
+      cudaMemcpy(p->d_phi, d->phi, p->n_phi * sizeof(double), cudaMemcpyHostToDevice) ||
+      cudaMemset(p->d_status, 0, sizeof(unsigned))) {
+    vrte_destroy(p);
+    return VRTE_ERR_CUDA;
+  }
+  launch_trig_table(Mx, p->n_phi, p->d_phi, p->d_wc, p->d_ws, 0);
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    vrte_destroy(p);
+    return VRTE_ERR_CUDA;
+  }
+  *out = p;
+  return VRTE_OK;
+}
+
+vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, const double* d_coeffs) {
+  if (!p || !hp || !d_coeffs || n_layers < 1 || n_layers > p->desc.n_layers_max)
+    return VRTE_ERR_INVALID_ARG;
+  for (int b = 0; b < n_layers; ++b) {
+    const vrte_layer& l = hp[b];
+    if (!(l.tau > 0.0) || !(l.omega >= 0.0 && l.omega < 1.0) || !(l.n_interface <= 3.0) ||
+        l.n_nodes < 1 || l.n_nodes > p->desc.n_nodes_max || l.n_orders < 1 ||
+        l.n_orders > p->desc.n_orders_max || l.n_coef < 1 || l.n_coef > p->desc.n_coef_max)
+      return VRTE_ERR_INVALID_ARG;
+  }
+  cudaDeviceSynchronize();
+  free_workspace(p, kPlanAllocs);
+  p->Isyn = nullptr;
+  p->layers.assign(hp, hp + n_layers);
+  p->n_layers = n_layers;
+  p->d_coeffs = d_coeffs;
+  int Nx = 0, Lx = 0, Mx = 0;
+  for (auto& l : p->layers) {
+    Nx = std::max(Nx, l.n_nodes);
+    Lx = std::max(Lx, l.n_coef);
+    Mx = std::max(Mx, std::min(l.n_orders, l.n_coef));
+  }
+  size_t n = 4 * (size_t)Nx, R = 4 * (size_t)p->n_in, Ro = 4 * (size_t)p->n_out;
+  size_t P = Nx + p->n_in + p->n_out;
+  size_t per_unit = 3 * (size_t)Lx * P + 10 * n * n + 3 * n + 8 * n * n + 5 * n * R + 6 * n * R +
+                    6 * Ro * n + Ro * R + n * n + 1 + 5 * 4 * n * n + 3 * 2 * n + 1;
+  size_t isyn = (size_t)Mx * p->n_in * p->n_out * 16;
+  size_t free_b = 0, total_b = 0;
+  cudaMemGetInfo(&free_b, &total_b);
+  // the order radiances must fit; the per-order workspace takes at most 35% of what is
+  // left (capped at 48 GiB) so that the caller's output table still fits beside it
+  size_t need_fixed = isyn * sizeof(double) + ((size_t)64 << 20);
+  if (need_fixed >= free_b) return VRTE_ERR_OOM;
+  size_t budget = std::min((size_t)(0.35 * (double)(free_b - need_fixed)), (size_t)48 << 30);
+  size_t units = budget / (per_unit * sizeof(double));
+  units = std::max<size_t>(1, std::min<size_t>(units, (size_t)Mx));
+  p->chunk = (int)units;
+  size_t U = units;
+  vrte_status st = VRTE_OK;
+#define VRTE_ALLOC(ptr, cnt)                        \
+  if ((st = allocd(p, &p->ptr, (cnt))) != VRTE_OK) { \
+    free_workspace(p, kPlanAllocs);                  \
+    p->Isyn = nullptr;                               \
+    return st;                                       \
+  }
+  VRTE_ALLOC(d_mu_nodes, Nx) VRTE_ALLOC(d_w_nodes, Nx) VRTE_ALLOC(d_pts, P) VRTE_ALLOC(d_min4, 4 * (size_t)p->n_in)
+  VRTE_ALLOC(d_mout4, 4 * (size_t)p->n_out) VRTE_ALLOC(d_rtop4, 4 * (size_t)Nx)
+  VRTE_ALLOC(gp, U * Lx * P) VRTE_ALLOC(gr, U * Lx * P) VRTE_ALLOC(gt, U * Lx * P)
+  VRTE_ALLOC(E, U * n * n) VRTE_ALLOC(F, U * n * n) VRTE_ALLOC(FE, U * n * n) VRTE_ALLOC(X, U * n * n) VRTE_ALLOC(EX, U * n * n)
+  VRTE_ALLOC(Y, U * n * n) VRTE_ALLOC(Xinv, U * n * n) VRTE_ALLOC(Hs, U * n * n) VRTE_ALLOC(Zs, U * n * n) VRTE_ALLOC(Vs, U * n * n)
+  VRTE_ALLOC(lam_re, U * n) VRTE_ALLOC(lam_im, U * n) VRTE_ALLOC(bal, U * n)
+  VRTE_ALLOC(K, U * 4 * n * n) VRTE_ALLOC(Kinv, U * 4 * n * n)
+  VRTE_ALLOC(Pb, U * n * R) VRTE_ALLOC(Rb, U * n * R) VRTE_ALLOC(Wv, U * n * R) VRTE_ALLOC(Yv, U * n * R) VRTE_ALLOC(Es, U * n * R)
+  VRTE_ALLOC(SD, U * 2 * n * R) VRTE_ALLOC(RHS, U * 2 * n * R) VRTE_ALLOC(C, U * 2 * n * R)
+  VRTE_ALLOC(Upm, U * Ro * 2 * n) VRTE_ALLOC(P1, U * Ro * n) VRTE_ALLOC(P2, U * Ro * n) VRTE_ALLOC(Hhat, U * Ro * 2 * n)
+  VRTE_ALLOC(T1, U * Ro * R)
+  VRTE_ALLOC(FY, U * n * n) VRTE_ALLOC(mode_res, U) VRTE_ALLOC(mode_flag, U)
+  VRTE_ALLOC(Bm, U * 4 * n * n) VRTE_ALLOC(Hb, U * 4 * n * n) VRTE_ALLOC(Zb, U * 4 * n * n)
+  VRTE_ALLOC(Vb, U * 4 * n * n) VRTE_ALLOC(Xb, U * 4 * n * n)
+  VRTE_ALLOC(kb_re, U * 2 * n) VRTE_ALLOC(kb_im, U * 2 * n) VRTE_ALLOC(balb, U * 2 * n)
+  VRTE_ALLOC(Isyn, isyn)
+#undef VRTE_ALLOC
+  return VRTE_OK;
+}
+
+static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, int out_dtype,
+                             cudaStream_t s) {
+  const size_t table = (size_t)p->n_in * p->n_out * p->n_phi * 16;
+  const size_t esz = out_dtype == VRTE_OUT_F64 ? sizeof(double) : sizeof(float);
+  const int R = 4 * p->n_in, Ro = 4 * p->n_out;
+  for (int lb = 0; lb < p->n_layers; ++lb) {
+    const vrte_layer& ly = p->layers[lb];
+    const int N = ly.n_nodes, n = 4 * N, L = ly.n_coef;
+    const int Meff = std::min(ly.n_orders, ly.n_coef);
+    const int P = N + p->n_in + p->n_out;
+    const double* coef = coeffs + (size_t)lb * p->desc.n_coef_max * 6;
+    {
+      StageScope sc(p, ST_TABLES, s, 2, 0.0, 0.0);
+      launch_gauss_nodes(N, p->d_mu_nodes, p->d_w_nodes, p->d_status, s);
+      launch_interface(N, p->n_in, p->n_out, ly.n_interface, p->d_mu_nodes, p->d_mu_in,
+                       p->d_mu_out, p->d_pts, p->d_min4, p->d_mout4, p->d_rtop4, s);
+    }
+    for (int m0 = 0; m0 < Meff; m0 += p->chunk) {
+      const int U = std::min(p->chunk, Meff - m0);
+      OrderBatch ob{N, n, L, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef, p->d_status};
+      p->last_n = n;
+      p->last_U = U;
+      p->last_P = P;
+      p->last_Meff = Meff;
+      const long long nn = (long long)n * n, nR = (long long)n * R, Ron = (long long)Ro * n;
+      const double dn = n, dR = R, dRo = Ro, dU = U;
+      double lsum = 0.0;  // sum over the batch of (L - m)
+      for (int u = 0; u < U; ++u) lsum += L - (m0 + u);
+      {
+        StageScope sc(p, ST_TABLES, s, 1, 30.0 * P * lsum, 24.0 * P * lsum);
+        launch_gsf_tables(ob, p->d_pts, p->gp, p->gr, p->gt, s);
+      }
+      {
+        StageScope sc(p, ST_ASSEMBLE, s, 2, 72.0 * N * N * lsum + 2.0 * dn * dn * dn * dU,
+                      8.0 * 3 * dn * dn * dU);
+        launch_assemble_EF(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_w_nodes, p->E, p->F, s);
+        dgemm_batched(n, n, n, 1.0, p->F, n, nn, p->E, n, nn, 0.0, p->FE, n, nn, U, s);
+      }
+      {
+        // nominal cost of a real Schur decomposition with eigenvectors: 25 n^3, plus
+        // E'X, Y = E'X / kappa and the mode residual F'Y - X kappa
+        StageScope sc(p, ST_EIGEN, s, 10, (25.0 + 4.0) * dn * dn * dn * dU,
+                      8.0 * 6 * dn * dn * dU);
+        batched_eigen(n, p->FE, p->Hs, p->Zs, p->Vs, p->X, p->lam_re, p->lam_im, p->bal, U,
+                      p->d_status, s);
+        dgemm_batched(n, n, n, 1.0, p->E, n, nn, p->X, n, nn, 0.0, p->EX, n, nn, U, s);
+        launch_pack_Y(ob, p->EX, p->lam_re, p->lam_im, p->Y, s);
+        dgemm_batched(n, n, n, 1.0, p->F, n, nn, p->Y, n, nn, 0.0, p->FY, n, nn, U, s);
+        // the FP64 form re-solves order 0 (diffusion mode) and any order with a poor mode
+        // residual in the 2n block form; the mixed form only catastrophic ones
+        const bool fp64 = p->desc.precision == VRTE_FP64;
+        eigen_block_fallback(n, m0, p->E, p->F, p->FY, p->X, p->Y, p->lam_re, p->lam_im,
+                             fp64 ? 1e-4 : 1e-1, fp64 ? 1 : 0, p->mode_res, p->mode_flag, p->Bm,
+                             p->Hb, p->Zb, p->Vb, p->Xb, p->kb_re, p->kb_im, p->balb, U,
+                             p->d_status, s);
+      }
+      {
+        StageScope sc(p, ST_MODES, s, 3, 16.0 * dn * dn * dn * dU, 8.0 * 12 * dn * dn * dU);
+        launch_build_K(ob, p->X, p->Y, p->lam_re, p->lam_im, p->d_rtop4, p->K, s);
+        batched_inverse(2 * n, p->K, p->Kinv, U, p->d_status, s);
+        batched_inverse(n, p->X, p->Xinv, U, p->d_status, s);
+      }
+      {
+        StageScope sc(p, ST_PARTICULAR, s, 9,
+                      72.0 * N * p->n_in * lsum + 8.0 * dn * dn * dR * dU,
+                      8.0 * 10 * dn * dR * dU);
+        launch_assemble_beam(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_min4, p->Pb, p->Rb, s);
+        dgemm_batched(n, R, n, 1.0, p->F, n, nn, p->Pb, R, nR, 0.0, p->Wv, R, nR, U, s);
+        launch_particular_rhs(ob, p->Wv, p->Rb, p->d_pts, p->Wv, s);
+        dgemm_batched(n, R, n, 1.0, p->Xinv, n, nn, p->Wv, R, nR, 0.0, p->Yv, R, nR, U, s);
+        launch_eigen_scale(ob, p->lam_re, p->lam_im, p->d_pts, p->Yv, s);
+        dgemm_batched(n, R, n, 1.0, p->X, n, nn, p->Yv, R, nR, 0.0, p->SD, R, 2 * nR, U, s);
+        dgemm_batched(n, R, n, 1.0, p->E, n, nn, p->SD, R, 2 * nR, 0.0, p->Es, R, nR, U, s);
+        launch_particular_sd(ob, p->Pb, p->Es, p->d_pts, p->SD, s);
+        launch_bc_rhs(ob, p->SD, nullptr, p->d_rtop4, p->d_pts, p->RHS, s);
+      }
+      {
+        StageScope sc(p, ST_BC_SOLVE, s, 1, 2.0 * 4 * dn * dn * dR * dU,
+                      8.0 * (4 * dn * dn + 4 * dn * dR) * dU);
+        dgemm_batched(2 * n, R, 2 * n, 1.0, p->Kinv, 2 * n, 4 * nn, p->RHS, R, 2 * nR, 0.0, p->C,
+                      R, 2 * nR, U, s);
+      }
+      {
+        StageScope sc(p, ST_RECON_OPS, s, 5,
+                      72.0 * N * p->n_out * lsum + 4.0 * dRo * dn * dn * dU +
+                          72.0 * p->n_in * p->n_out * lsum,
+                      8.0 * (6 * dRo * dn + dRo * dR) * dU);
+        launch_assemble_U(ob, p->gp, p->gr, p->gt, p->d_w_nodes, p->d_mout4, p->Upm, s);
+        dgemm_batched(Ro, n, n, 1.0, p->Upm, 2 * n, 2 * Ron, p->X, n, nn, 0.0, p->P1, n, Ron, U, s);
+        dgemm_batched(Ro, n, n, 1.0, p->Upm + n, 2 * n, 2 * Ron, p->Y, n, nn, 0.0, p->P2, n, Ron,
+                      U, s);
+        launch_build_Hhat(ob, p->P1, p->P2, p->lam_re, p->lam_im, p->d_pts, p->Hhat, s);
+        launch_assemble_direct(ob, p->gp, p->gr, p->gt, p->d_pts, p->d_min4, p->d_mout4, p->T1,
+                               s);
+      }
+      {
+        // two contractions [4 n_out x 2n] x [2n x 4 n_in] per order
+        StageScope sc(p, ST_RECON_GEMM, s, 2, 2.0 * 2 * dRo * dR * 2 * dn * dU,
+                      8.0 * (2 * dRo * 2 * dn + 2 * 2 * dn * dR + 3 * dRo * dR) * dU);
+        dgemm_batched(Ro, R, 2 * n, 1.0, p->Hhat, 2 * n, 2 * Ron, p->C, R, 2 * nR, 1.0, p->T1, R,
+                      (long long)Ro * R, U, s);
+        dgemm_part_epilogue(ob, p->Upm, p->SD, p->T1, p->d_pts, p->Isyn, s);
+      }
+    }
+    char* outb = (char*)d_brdf + (size_t)lb * table * esz;
+    {
+      StageScope sc(p, ST_SYNTHESIS, s, 1, 2.0 * table * Meff,
+                    (double)table * esz + (double)Meff * p->n_in * p->n_out * 16 * 8);
+      launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, p->Isyn, p->d_wc, p->d_ws, outb,
+                            out_dtype, p->d_status, s);
+    }
+  }
+  if (cudaGetLastError() != cudaSuccess) return VRTE_ERR_CUDA;
+  return VRTE_OK;
+}
+
+vrte_status vrte_solve_brdf(vrte_plan* p, void* d_brdf, int out_dtype, void* stream) {
+  if (!p || !d_brdf) return VRTE_ERR_INVALID_ARG;
+  if (out_dtype != VRTE_OUT_F32 && out_dtype != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
+  if (p->n_layers < 1 || !p->d_coeffs || !p->Isyn) return VRTE_ERR_STATE;
+  if (p->desc.precision == VRTE_MIXED) return VRTE_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  p->last_stream = s;
+  return run_solve(p, p->d_coeffs, d_brdf, out_dtype, s);
+}
+
+vrte_status vrte_solve_brdf_host(vrte_plan* p, const double* h_coeffs, void* h_brdf,
+                                 int out_dtype, void* stream) {
+  if (!p || !h_coeffs || !h_brdf) return VRTE_ERR_INVALID_ARG;
+  if (out_dtype != VRTE_OUT_F32 && out_dtype != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
+  if (p->n_layers < 1 || !p->Isyn) return VRTE_ERR_STATE;
+  if (p->desc.precision == VRTE_MIXED) return VRTE_ERR_UNSUPPORTED;
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t cbytes = (size_t)p->n_layers * p->desc.n_coef_max * 6 * sizeof(double);
+  size_t obytes = (size_t)p->n_layers * p->n_in * p->n_out * p->n_phi * 16 *
+                  (out_dtype == VRTE_OUT_F64 ? sizeof(double) : sizeof(float));
+  // staging buffers persist across calls; the first call (or a larger request) allocates
+  if (cbytes > p->coef_stage_bytes) {
+    if (p->d_coef_stage) cudaFree(p->d_coef_stage);
+    p->d_coef_stage = nullptr;
+    if (cudaMalloc(&p->d_coef_stage, cbytes) != cudaSuccess) { cudaGetLastError(); return VRTE_ERR_OOM; }
+    p->coef_stage_bytes = cbytes;
+  }
+  if (obytes > p->out_stage_bytes) {
+    if (p->d_out_stage) cudaFree(p->d_out_stage);
+    p->d_out_stage = nullptr;
+    if (cudaMalloc(&p->d_out_stage, obytes) != cudaSuccess) { cudaGetLastError(); return VRTE_ERR_OOM; }
+    p->out_stage_bytes = obytes;
+  }
+  if (cudaMemcpyAsync(p->d_coef_stage, h_coeffs, cbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return VRTE_ERR_CUDA;
+  p->last_stream = s;
+  vrte_status st = run_solve(p, p->d_coef_stage, p->d_out_stage, out_dtype, s);
+  if (st != VRTE_OK) return st;
+  if (cudaMemcpyAsync(h_brdf, p->d_out_stage, obytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return VRTE_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return VRTE_ERR_CUDA;
+  return VRTE_OK;
+}
+
+vrte_status vrte_brdf_backward(vrte_plan* p, const void* g, int gd, double* d_grad, void* stream) {
+  (void)g; (void)gd; (void)d_grad; (void)stream;
+  if (!p) return VRTE_ERR_INVALID_ARG;
+  return VRTE_ERR_UNSUPPORTED;
+}
+
+vrte_status vrte_plan_status(vrte_plan* p) {
+  if (!p) return VRTE_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return VRTE_ERR_CUDA;
+  unsigned h = 0;
+  if (cudaMemcpy(&h, p->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VRTE_ERR_CUDA;
+  cudaMemset(p->d_status, 0, sizeof(unsigned));
+  if (h & ST_NONFINITE) return VRTE_ERR_NONFINITE;
+  if (h & ST_NO_CONVERGENCE) return VRTE_ERR_NO_CONVERGENCE;
+  if (h & ST_SINGULAR) return VRTE_ERR_SINGULAR;
+  if (h) return VRTE_ERR_CUDA;
+  return VRTE_OK;
+}
+
+vrte_status vrte_debug_copy(vrte_plan* p, const char* name, void* dst, size_t bytes,
+                            size_t* size_out) {
+  if (!p || !name) return VRTE_ERR_INVALID_ARG;
+  if (strcmp(name, "status") == 0) {  // raw device status bits, as one double
+    unsigned h = 0;
+    if (cudaStreamSynchronize(p->last_stream) != cudaSuccess ||
+        cudaMemcpy(&h, p->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return VRTE_ERR_CUDA;
+    double v = (double)h;
+    if (size_out) *size_out = sizeof(double);
+    if (dst && bytes >= sizeof(double)) memcpy(dst, &v, sizeof(double));
+    return VRTE_OK;
+  }
+  if (p->last_U == 0) return VRTE_ERR_STATE;
+  size_t n = p->last_n, U = p->last_U, R = 4 * (size_t)p->n_in, Ro = 4 * (size_t)p->n_out;
+  const void* src = nullptr;
+  size_t cnt = 0;
+  struct Entry { const char* nm; const double* ptr; size_t count; };
+  const Entry tab[] = {
+      {"pts", p->d_pts, (size_t)p->last_P},
+      {"nodes", p->d_mu_nodes, n / 4},
+      {"weights", p->d_w_nodes, n / 4},
+      {"E", p->E, U * n * n},
+      {"F", p->F, U * n * n},
+      {"FE", p->FE, U * n * n},
+      {"schur", p->Hs, U * n * n},
+      {"X", p->X, U * n * n},
+      {"Y", p->Y, U * n * n},
+      {"lam_re", p->lam_re, U * n},
+      {"lam_im", p->lam_im, U * n},
+      {"K", p->K, U * 4 * n * n},
+      {"Kinv", p->Kinv, U * 4 * n * n},
+      {"Xinv", p->Xinv, U * n * n},
+      {"beam_p", p->Pb, U * n * R},
+      {"beam_r", p->Rb, U * n * R},
+      {"SD", p->SD, U * 2 * n * R},
+      {"RHS", p->RHS, U * 2 * n * R},
+      {"C", p->C, U * 2 * n * R},
+      {"Upm", p->Upm, U * Ro * 2 * n},
+      {"Hhat", p->Hhat, U * Ro * 2 * n},
+      {"T1", p->T1, U * Ro * R},
+      {"Isyn", p->Isyn, (size_t)p->last_Meff * p->n_in * p->n_out * 16},
+      {"mode_res", p->mode_res, U},
+  };
+  for (const Entry& e : tab)
+    if (strcmp(e.nm, name) == 0) { src = e.ptr; cnt = e.count; }
+  if (!src) return VRTE_ERR_INVALID_ARG;
+  size_t full = cnt * sizeof(double);
+  if (size_out) *size_out = full;
+  if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return VRTE_ERR_CUDA;
+  if (dst && bytes)
+    if (cudaMemcpy(dst, src, std::min(bytes, full), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return VRTE_ERR_CUDA;
+  return VRTE_OK;
+}
+
+int vrte_profile_stages(vrte_plan* p, vrte_stage_stat* out, int max_stages) {
+  if (!p) return -1;
+  cudaStreamSynchronize(p->last_stream);
+  for (auto& e : p->events) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e.second.first, e.second.second) == cudaSuccess)
+      p->stats[e.first].ms += ms;
+    cudaEventDestroy(e.second.first);
+    cudaEventDestroy(e.second.second);
+  }
+  p->events.clear();
+  cudaGetLastError();
+  int n = std::min(max_stages, (int)kStages);
+  for (int i = 0; out && i < n; ++i) out[i] = p->stats[i];
+  return kStages;
+}
+
+void vrte_profile_reset(vrte_plan* p) {
+  if (!p) return;
+  cudaStreamSynchronize(p->last_stream);
+  reset_stats(p);
+}
+
+size_t vrte_workspace_bytes(const vrte_plan* p) {
+  if (!p) return 0;
+  size_t t = p->coef_stage_bytes + p->out_stage_bytes;
+  for (size_t b : p->alloc_bytes) t += b;
+  return t;
+}
+
+void vrte_destroy(vrte_plan* p) {
+  if (!p) return;
+  cudaDeviceSynchronize();
+  reset_stats(p);
+  free_workspace(p, 0);
+  if (p->d_coef_stage) cudaFree(p->d_coef_stage);
+  if (p->d_out_stage) cudaFree(p->d_out_stage);
+  delete p;
+}
+
+}  // extern "C"

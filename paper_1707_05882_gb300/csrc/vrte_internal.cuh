@@ -1,0 +1,101 @@
+// Internal declarations shared by the CUDA translation units of the VRTE library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vrte.h"
+
+namespace vrte {
+
+// Device status word bits (set with atomicOr by kernels, read by vrte_plan_status).
+enum : unsigned {
+  ST_NO_CONVERGENCE = 1u << 0,
+  ST_SINGULAR = 1u << 1,
+  ST_NONFINITE = 1u << 2,
+  ST_BAD_INDEX = 1u << 3,
+};
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Per-layer geometry of one batch of Fourier orders m0 .. m0 + n_units - 1.
+struct OrderBatch {
+  int N;        // nodes per hemisphere
+  int n;        // 4N
+  int L;        // expansion coefficients
+  int m0;       // first order of the batch
+  int n_units;  // orders in the batch
+  int n_in, n_out;
+  int P;        // table points: N nodes, then n_in incident, then n_out outgoing
+  double tau, omega;
+  const double* coef;  // [L][6]
+  unsigned* status;
+};
+
+// ---------------------------------------------------------------- tables (k_tables.cu)
+void launch_gauss_nodes(int N, double* mu, double* w, unsigned* status, cudaStream_t s);
+void launch_interface(int N, int n_in, int n_out, double nif, const double* mu_nodes,
+                      const double* mu_in, const double* mu_out, double* pts, double* min4,
+                      double* mout4, double* rtop4, cudaStream_t s);
+void launch_gsf_tables(const OrderBatch& b, const double* pts, double* p, double* r, double* t,
+                       cudaStream_t s);
+void launch_trig_table(int M, int n_phi, const double* phi, double* wc, double* ws, cudaStream_t s);
+
+// ---------------------------------------------------------------- assembly (k_assemble.cu)
+// Parity-split sums S+-(x, y) = sum_l P_l^m(x) B_l (I +- (-1)^(l-m) D) P_l^m(y) at
+// table points, written into the operator each stage needs.
+void launch_assemble_EF(const OrderBatch& b, const double* p, const double* r, const double* t,
+                        const double* mu_nodes, const double* w_nodes, double* E, double* F,
+                        cudaStream_t s);
+void launch_assemble_beam(const OrderBatch& b, const double* p, const double* r, const double* t,
+                          const double* mu_nodes, const double* min4, double* Pm, double* Rm,
+                          cudaStream_t s);
+void launch_assemble_U(const OrderBatch& b, const double* p, const double* r, const double* t,
+                       const double* w_nodes, const double* mout4, double* U, cudaStream_t s);
+void launch_assemble_direct(const OrderBatch& b, const double* p, const double* r,
+                            const double* t, const double* pts, const double* min4,
+                            const double* mout4, double* T1, cudaStream_t s);
+
+// ---------------------------------------------------------------- dense FP64 (k_linalg.cu)
+// C[u] = alpha * A[u] (M x K, row-major, lda) * B[u] (K x N, ldb) + beta * C[u]
+void dgemm_batched(int M, int N, int K, double alpha, const double* A, int lda, long long sA,
+                   const double* B, int ldb, long long sB, double beta, double* C, int ldc,
+                   long long sC, int batch, cudaStream_t s);
+// Reconstruction epilogue: Isyn[m][k][o][a][s] = T1[ro][rc] + g0(o, k) * (A @ B)[ro][rc]
+void dgemm_part_epilogue(const OrderBatch& b, const double* A, const double* B, const double* T1,
+                         const double* pts, double* Isyn, cudaStream_t s);
+void batched_inverse(int n, double* A, double* Ainv, int batch, unsigned* status, cudaStream_t s);
+void batched_eigen(int n, const double* A, double* H, double* Z, double* V, double* X,
+                   double* lam_re, double* lam_im, double* scale, int batch, unsigned* status,
+                   cudaStream_t s, const int* mask = nullptr);
+// Re-solves orders whose reduced eigenvectors are not accurate enough with the 2n x 2n
+// block form (see k_eigen.cu); overwrites X, Y and lambda of the flagged orders.
+void eigen_block_fallback(int n, int m0, const double* E, const double* F, const double* FY,
+                          double* X, double* Y, double* lam_re, double* lam_im, double tol,
+                          int force0, double* res, int* flag, double* B, double* Hb, double* Zb,
+                          double* Vb, double* Xb, double* kb_re, double* kb_im, double* balb,
+                          int batch, unsigned* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- mode algebra (k_modes.cu)
+void launch_pack_Y(const OrderBatch& b, const double* EX, const double* lam_re,
+                   const double* lam_im, double* Y, cudaStream_t s);
+void launch_build_K(const OrderBatch& b, const double* X, const double* Y, const double* lam_re,
+                    const double* lam_im, const double* rtop4, double* K, cudaStream_t s);
+void launch_particular_rhs(const OrderBatch& b, const double* w_in, const double* r,
+                           const double* pts, double* w_out, cudaStream_t s);
+void launch_eigen_scale(const OrderBatch& b, const double* lam_re, const double* lam_im,
+                        const double* pts, double* y, cudaStream_t s);
+void launch_particular_sd(const OrderBatch& b, const double* pbeam, const double* Es,
+                          const double* pts, double* d, cudaStream_t s);
+void launch_bc_rhs(const OrderBatch& b, const double* sv, const double* d, const double* rtop4,
+                   const double* pts, double* rhs, cudaStream_t s);
+void launch_build_Hhat(const OrderBatch& b, const double* P1, const double* P2,
+                       const double* lam_re, const double* lam_im, const double* pts,
+                       double* Hhat, cudaStream_t s);
+
+// ---------------------------------------------------------------- synthesis (k_synth.cu)
+void launch_synthesis_fp64(int M, int n_in, int n_out, int n_phi, const double* Isyn,
+                           const double* wc, const double* ws, void* out, int out_dtype,
+                           unsigned* status, cudaStream_t s);
+
+}  // namespace vrte
