@@ -25,7 +25,7 @@ STATUS_NAMES = {
 
 EXPORTED = ["vrte_plan_create", "vrte_set_layer", "vrte_solve_brdf", "vrte_solve_brdf_host",
             "vrte_brdf_backward", "vrte_plan_status", "vrte_profile_stages", "vrte_profile_reset",
-            "vrte_debug_copy",
+            "vrte_debug_copy", "vrte_eigen_noalloc",
             "vrte_workspace_bytes", "vrte_destroy", "vrte_status_string"]
 
 
@@ -91,6 +91,8 @@ def load_library(build_if_missing: bool = True):
     lib.vrte_debug_copy.argtypes = [P, ctypes.c_char_p, P, ctypes.c_size_t,
                                     ctypes.POINTER(ctypes.c_size_t)]
     lib.vrte_debug_copy.restype = ctypes.c_int
+    lib.vrte_eigen_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
+    lib.vrte_eigen_noalloc.restype = ctypes.c_int
     lib.vrte_workspace_bytes.argtypes = [P]
     lib.vrte_workspace_bytes.restype = ctypes.c_size_t
     lib.vrte_destroy.argtypes = [P]
