@@ -156,7 +156,9 @@ void vrte_profile_reset(vrte_plan* plan);
  * "nodes", "weights", "E", "F", "FE", "schur", "X", "Y", "lam_re", "lam_im", "K",
  * "Kinv", "Xinv", "beam_p", "beam_r", "SD", "RHS", "C", "Upm", "Hhat", "T1", "Isyn",
  * "mode_res" (per-order mode residual of the reduced eigen-decomposition),
- * and "status" (the raw device status bits as one double, not cleared).
+ * "status" (the raw device status bits as one double, not cleared) and "refined"
+ * (mixed form: number of (order, incident) column blocks of the last solve whose
+ * reconstruction was recomputed in FP64, as one double).
  * Unknown names return VRTE_ERR_INVALID_ARG; calling before a solve returns
  * VRTE_ERR_STATE. */
 vrte_status vrte_debug_copy(vrte_plan* plan, const char* name, void* host_dst, size_t bytes,
@@ -185,6 +187,24 @@ vrte_status vrte_debug_copy(vrte_plan* plan, const char* name, void* host_dst, s
  * Asynchronous on `stream`. */
 vrte_status vrte_eigen_noalloc(const double* d_A, int n, int batch, double* d_lam_re,
                                double* d_lam_im, double* d_X, unsigned* d_status, void* stream);
+
+/* Batched C = A B in FP64 on the tcgen05 tensor cores by exact fixed-point slicing:
+ * every row of A and column of B is scaled by a power of two and cut into `slices`
+ * signed 7-bit integer slices (each times a power of two) held in BF16; each slice
+ * product is exact, products of equal scale are accumulated exactly in FP32 for K <= 1024,
+ * so the error is the slices dropped (relative to max|A_i| max|B_j| per term: 1 -> 8e-3,
+ * 4 -> 4e-9, 6 -> 3e-13, 7 -> 2e-15, 8 -> 1e-15).
+ * A [batch][M][K] (row stride lda, unit stride stride_a), B [batch][K][N] (ldb,
+ * stride_b), C [batch][M][N] (ldc, stride_c): device FP64, row-major, caller-owned.
+ * d_workspace: device buffer of vrte_gemm_sliced_workspace() bytes. d_status: device word
+ * (caller zeroes it) receiving device error bits (16 = a bounded wait timed out).
+ * Limits: 1 <= slices <= 8, 1 <= K <= 1024, else VRTE_ERR_INVALID_ARG. Asynchronous on
+ * `stream`; not thread-safe against other calls sharing the workspace. */
+size_t vrte_gemm_sliced_workspace(int M, int N, int K, int batch, int slices);
+vrte_status vrte_gemm_sliced(int M, int N, int K, const double* d_A, int lda, long long stride_a,
+                             const double* d_B, int ldb, long long stride_b, double* d_C, int ldc,
+                             long long stride_c, int batch, int slices, void* d_workspace,
+                             size_t workspace_bytes, unsigned* d_status, void* stream);
 
 /* Bytes of device workspace the plan currently holds. */
 size_t vrte_workspace_bytes(const vrte_plan* plan);

@@ -25,7 +25,7 @@ STATUS_NAMES = {
 
 EXPORTED = ["vrte_plan_create", "vrte_set_layer", "vrte_solve_brdf", "vrte_solve_brdf_host",
             "vrte_brdf_backward", "vrte_plan_status", "vrte_profile_stages", "vrte_profile_reset",
-            "vrte_debug_copy", "vrte_eigen_noalloc",
+            "vrte_debug_copy", "vrte_eigen_noalloc", "vrte_gemm_sliced", "vrte_gemm_sliced_workspace",
             "vrte_workspace_bytes", "vrte_destroy", "vrte_status_string"]
 
 
@@ -93,6 +93,12 @@ def load_library(build_if_missing: bool = True):
     lib.vrte_debug_copy.restype = ctypes.c_int
     lib.vrte_eigen_noalloc.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P, P, P]
     lib.vrte_eigen_noalloc.restype = ctypes.c_int
+    lib.vrte_gemm_sliced_workspace.argtypes = [ctypes.c_int] * 5
+    lib.vrte_gemm_sliced_workspace.restype = ctypes.c_size_t
+    I, LL = ctypes.c_int, ctypes.c_longlong
+    lib.vrte_gemm_sliced.argtypes = [I, I, I, P, I, LL, P, I, LL, P, I, LL, I, I, P,
+                                     ctypes.c_size_t, P, P]
+    lib.vrte_gemm_sliced.restype = ctypes.c_int
     lib.vrte_workspace_bytes.argtypes = [P]
     lib.vrte_workspace_bytes.restype = ctypes.c_size_t
     lib.vrte_destroy.argtypes = [P]
@@ -223,6 +229,30 @@ def pack_coefficients(layers, n_coef_max=None):
         c = np.asarray(l["coef"], dtype=np.float64)
         out[i, :c.shape[0]] = c
     return out
+
+
+def gemm_sliced(A, B, slices=4, stream=None):
+    """C = A @ B (CUDA float64 tensors [batch, M, K] x [batch, K, N]) on the tensor cores
+    through vrte_gemm_sliced (exact 7-bit slicing, relative accuracy ~2^(-7 slices))."""
+    import torch
+    lib = load_library()
+    b, M, K = A.shape
+    N = B.shape[2]
+    A = A.contiguous()
+    B = B.contiguous()
+    C = torch.empty((b, M, N), dtype=torch.float64, device=A.device)
+    nbytes = lib.vrte_gemm_sliced_workspace(M, N, K, b, slices)
+    if nbytes == 0:
+        raise VrteError(1, "vrte_gemm_sliced_workspace")
+    work = torch.empty(nbytes, dtype=torch.uint8, device=A.device)
+    status = torch.zeros(1, dtype=torch.int32, device=A.device)
+    _check(lib.vrte_gemm_sliced(M, N, K, ctypes.c_void_p(A.data_ptr()), K, M * K,
+                                ctypes.c_void_p(B.data_ptr()), N, K * N,
+                                ctypes.c_void_p(C.data_ptr()), N, M * N, b, slices,
+                                ctypes.c_void_p(work.data_ptr()), nbytes,
+                                ctypes.c_void_p(status.data_ptr()), _stream_handle(stream)),
+           "vrte_gemm_sliced")
+    return C, status
 
 
 def brdf(layers, mu_in, mu_out, dphi, precision=VRTE_FP64, out_dtype=None, stream=None):

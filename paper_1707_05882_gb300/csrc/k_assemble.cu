@@ -144,7 +144,7 @@ void launch_assemble_beam(const OrderBatch& b, const double* p, const double* r,
 // Reconstruction operators (Sec. 2.C, Eq. 38 and Sec. 3.D): the scattering part of the
 // source at outgoing mu_o acting on a nodal field, split by the same parity sums:
 //   U+-[4o+a][4j+c] = (omega/4) alpha_j (M_out[o] S+-(mu_o, mu_j))_ac.
-// Stored as Upm[u][4o+a][0..2n) = [U+ | U-].
+// Stored as Upm[u][4o+a][0..2n) = [U+ | U-] (row stride b.ldU).
 __global__ void k_assemble_U(OrderBatch b, const double* pt, const double* rt, const double* tt,
                              const double* w_nodes, const double* mout4, double* U) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -156,8 +156,7 @@ __global__ void k_assemble_U(OrderBatch b, const double* pt, const double* rt, c
   accumulate_S(m, b.L, b.P, b.coef, pt, rt, tt, (size_t)u * b.L * b.P, b.N + b.n_in + o, j, S);
   double f = 0.25 * b.omega * w_nodes[j];
   const double* q = mout4 + 4 * o;
-  int n2 = 2 * b.n;
-  size_t base = (size_t)u * (4 * b.n_out) * n2;
+  size_t base = (size_t)u * (4 * b.n_out) * b.ldU;
   for (int a = 0; a < 4; ++a)
     for (int c = 0; c < 4; ++c) {
       double vp = 0.0, vm = 0.0;
@@ -166,7 +165,7 @@ __global__ void k_assemble_U(OrderBatch b, const double* pt, const double* rt, c
         vp += mo * S.sp[e][c];
         vm += mo * S.sm[e][c];
       }
-      size_t row = base + (size_t)(4 * o + a) * n2;
+      size_t row = base + (size_t)(4 * o + a) * b.ldU;
       U[row + 4 * j + c] = f * vp;
       U[row + b.n + 4 * j + c] = f * vm;
     }
@@ -224,6 +223,83 @@ void launch_assemble_direct(const OrderBatch& b, const double* p, const double* 
                             const double* mout4, double* T1, cudaStream_t s) {
   dim3 grid((b.n_in + 63) / 64, b.n_out, b.n_units);
   k_assemble_direct<<<grid, 64, 0, s>>>(b, p, r, t, pts, min4, mout4, T1);
+}
+
+// Direct-term operators for the mixed form (Eq. 38, Q term, as a contraction over the
+// pairs (l, component c) so that the tensor cores can fold it into the particular
+// contraction): with P = P_l^m and B = B_l,
+//   Adir[(o, a), (l, c)] = (M_out[o] P(mu_o) B)_ac,
+//   Bdir[(l, c), (k, s)] = (omega/2pi) (-1)^(l-m) (D P(mu0_k) D b_k)_cs,
+// so that sum_{l,c} Adir Bdir = (omega/2pi) M_out A^m(mu_o, -mu0) b_k; zero for l < m.
+__global__ void k_direct_A(OrderBatch b, const double* pt, const double* rt, const double* tt,
+                           const double* mout4, double* Uext) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  int o = blockIdx.y, u = blockIdx.z;
+  if (l >= b.L) return;
+  int m = b.m0 + u;
+  double* row0 = Uext + (size_t)u * (4 * b.n_out) * b.ldU + (size_t)(4 * o) * b.ldU + 2 * b.n + 4 * l;
+  double PB[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 4; ++c) PB[a][c] = 0.0;
+  if (l >= m) {
+    size_t idx = (size_t)u * b.L * b.P + (size_t)l * b.P + b.N + b.n_in + o;
+    double p = pt[idx], r = rt[idx], t = tt[idx];
+    const double* cf = b.coef + 6 * l;
+    double Bm[4][4] = {{cf[0], cf[4], 0.0, 0.0}, {cf[4], cf[1], 0.0, 0.0},
+                       {0.0, 0.0, cf[2], cf[5]}, {0.0, 0.0, -cf[5], cf[3]}};
+    double P[4][4] = {{p, 0, 0, 0}, {0, r, -t, 0}, {0, -t, r, 0}, {0, 0, 0, p}};
+    const double* q = mout4 + 4 * o;
+    for (int a = 0; a < 4; ++a)
+      for (int c = 0; c < 4; ++c) {
+        double v = 0.0;
+        for (int e = 0; e < 4; ++e) {
+          double mp = 0.0;
+          for (int f = 0; f < 4; ++f) mp += blk(q, a, f) * P[f][e];
+          v += mp * Bm[e][c];
+        }
+        PB[a][c] = v;
+      }
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 4; ++c) row0[(size_t)a * b.ldU + c] = PB[a][c];
+}
+
+__global__ void k_direct_B(OrderBatch b, const double* pt, const double* rt, const double* tt,
+                           const double* min4, double* SDext) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int l = blockIdx.y, u = blockIdx.z;
+  if (k >= b.n_in) return;
+  int m = b.m0 + u;
+  int R = 4 * b.n_in;
+  double* col0 = SDext + (size_t)u * b.sSD + (size_t)(2 * b.n + 4 * l) * R + 4 * k;
+  double V[4][4];
+  for (int c = 0; c < 4; ++c)
+    for (int s = 0; s < 4; ++s) V[c][s] = 0.0;
+  if (l >= m) {
+    size_t idx = (size_t)u * b.L * b.P + (size_t)l * b.P + b.N + k;
+    double p = pt[idx], r = rt[idx], t = tt[idx];
+    // D P D flips the sign of the t entries
+    double P[4][4] = {{p, 0, 0, 0}, {0, r, t, 0}, {0, t, r, 0}, {0, 0, 0, p}};
+    double f = b.omega / (2.0 * kPi) * (((l - m) & 1) ? -1.0 : 1.0);
+    const double* q = min4 + 4 * k;
+    for (int c = 0; c < 4; ++c)
+      for (int s = 0; s < 4; ++s) {
+        double v = 0.0;
+        for (int e = 0; e < 4; ++e) v += P[c][e] * blk(q, e, s);
+        V[c][s] = f * v;
+      }
+  }
+  for (int c = 0; c < 4; ++c)
+    for (int s = 0; s < 4; ++s) col0[(size_t)c * R + s] = V[c][s];
+}
+
+void launch_direct_operators(const OrderBatch& b, const double* p, const double* r,
+                             const double* t, const double* min4, const double* mout4,
+                             double* Uext, double* SDext, cudaStream_t s) {
+  dim3 ga((b.L + 63) / 64, b.n_out, b.n_units);
+  k_direct_A<<<ga, 64, 0, s>>>(b, p, r, t, mout4, Uext);
+  dim3 gb((b.n_in + 63) / 64, b.L, b.n_units);
+  k_direct_B<<<gb, 64, 0, s>>>(b, p, r, t, min4, SDext);
 }
 
 }  // namespace vrte

@@ -18,27 +18,6 @@ struct EpiStore {
   }
 };
 
-// Reconstruction epilogue: row i = 4o + a (outgoing o, exiting component a),
-// column j = 4k + s (incident k, incident basis s). Writes the order-m radiance
-// Isyn[m][k][o][a][s] = T1[i][j] + g0(o, k) * acc.
-struct EpiPart {
-  const double* T1;
-  double* Isyn;
-  const double* pts;
-  int N, n_in, n_out, m0;
-  double tau;
-  __device__ void operator()(int u, int i, int j, double acc) const {
-    int R = 4 * n_in;
-    int o = i >> 2, a = i & 3, k = j >> 2, s = j & 3;
-    double mu_o = pts[N + n_in + o], mu0 = pts[N + k];
-    double xs = 1.0 / mu_o + 1.0 / mu0;
-    double g0 = -expm1(-tau * xs) / (mu_o * xs);
-    double v = T1[(size_t)u * (4 * n_out) * R + (size_t)i * R + j] + g0 * acc;
-    size_t dst = (((size_t)(m0 + u) * n_in + k) * n_out + o) * 16 + 4 * a + s;
-    Isyn[dst] = v;
-  }
-};
-
 // Tiled FP64 GEMM: 64x64 output tile, 256 threads, 4x4 outputs per thread (strided by 16
 // so shared-memory reads are conflict free), K staged 16 at a time. Row-major operands;
 // tA / tB select op(A) = A^T (A stored K x M) and op(B) = B^T (B stored N x K).
@@ -140,7 +119,7 @@ void dgemm_part_epilogue(const OrderBatch& b, const double* A, const double* B, 
                          const double* pts, double* Isyn, cudaStream_t s) {
   int Ro = 4 * b.n_out, R = 4 * b.n_in, n2 = 2 * b.n;
   EpiPart e{T1, Isyn, pts, b.N, b.n_in, b.n_out, b.m0, b.tau};
-  run_dgemm(Ro, R, n2, A, n2, (long long)Ro * n2, false, B, R, (long long)n2 * R, false, e,
+  run_dgemm(Ro, R, n2, A, b.ldU, (long long)Ro * b.ldU, false, B, R, b.sSD, false, e,
             b.n_units, s);
 }
 

@@ -204,32 +204,32 @@ void launch_eigen_scale(const OrderBatch& b, const double* lam_re, const double*
 }
 
 // d = mu0 (p - E's), written into the second half of SD = [s; d].
-__global__ void k_particular_sd(int n, int R, int N, const double* pbeam, const double* Es,
-                                const double* pts, double* SD) {
+__global__ void k_particular_sd(int n, int R, int N, long long sSD, const double* pbeam,
+                                const double* Es, const double* pts, double* SD) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y, u = blockIdx.z;
   if (c >= R) return;
   size_t idx = (size_t)u * n * R + (size_t)i * R + c;
   double mu0 = pts[N + (c >> 2)];
-  SD[(size_t)u * 2 * n * R + (size_t)(n + i) * R + c] = mu0 * (pbeam[idx] - Es[idx]);
+  SD[(size_t)u * sSD + (size_t)(n + i) * R + c] = mu0 * (pbeam[idx] - Es[idx]);
 }
 
 void launch_particular_sd(const OrderBatch& b, const double* pbeam, const double* Es,
                           const double* pts, double* SD, cudaStream_t s) {
   int R = 4 * b.n_in;
   dim3 grid((R + 127) / 128, b.n, b.n_units);
-  k_particular_sd<<<grid, 128, 0, s>>>(b.n, R, b.N, pbeam, Es, pts, SD);
+  k_particular_sd<<<grid, 128, 0, s>>>(b.n, R, b.N, b.sSD, pbeam, Es, pts, SD);
 }
 
 // Right-hand side of the boundary system (Eq. 54 with the dielectric top):
 //   top:    -(Z-(mu_i) - R_F Z+(mu_i))
 //   bottom: -Z+(mu_i) exp(-tau0 / mu0)
-__global__ void k_bc_rhs(int N, int n, int R, double tau, const double* SD, const double* rtop4,
-                         const double* pts, double* rhs) {
+__global__ void k_bc_rhs(int N, int n, int R, long long sSD, double tau, const double* SD,
+                         const double* rtop4, const double* pts, double* rhs) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y, u = blockIdx.z;
   if (c >= R) return;
-  const double* sv = SD + (size_t)u * 2 * n * R;
+  const double* sv = SD + (size_t)u * sSD;
   const double* dv = sv + (size_t)n * R;
   double zp[4], zm[4];
   for (int a = 0; a < 4; ++a) {
@@ -254,7 +254,7 @@ void launch_bc_rhs(const OrderBatch& b, const double* SD, const double* d, const
   (void)d;
   int R = 4 * b.n_in;
   dim3 grid((R + 127) / 128, b.N, b.n_units);
-  k_bc_rhs<<<grid, 128, 0, s>>>(b.N, b.n, R, b.tau, SD, rtop4, pts, rhs);
+  k_bc_rhs<<<grid, 128, 0, s>>>(b.N, b.n, R, b.sSD, b.tau, SD, rtop4, pts, rhs);
 }
 
 // ------------------------------------------------------------------ reconstruction operator

@@ -1,0 +1,175 @@
+// Mixed form: FP64 recomputation of ill-conditioned reconstruction columns.
+//
+// Near a resonance between an incident cosine and a mode (mu0 kappa_j ~ 1) the
+// eigenbasis particular solution (Sec. 3.B, Eq. 47) grows like 1 / (kappa_j^2 - mu0^-2)
+// and the boundary solve answers with a homogeneous coefficient that cancels it
+// (Eqs. 45-46), so the exiting radiance of that incident column is a small difference
+// of two large contractions (Eq. 38). The sliced tensor-core product is accurate to
+// ~eps K max|row| max|column| per element; this pass estimates that bound for every
+// (order, incident) column block from the row and column maxima of the operands,
+// compares it with the order-0 radiance I_00 of the same pair, and recomputes the flagged column
+// blocks in FP64 from the FP64 operators (boundary coefficients from K^-1 and the
+// right-hand side, then both reconstruction contractions), overwriting I^m.
+#include "vrte_internal.cuh"
+
+namespace vrte {
+
+// out[u][r] = max_c |A[u][r][c]|, c < cols: one warp per row.
+__global__ void k_row_absmax(int rows, int cols, const double* __restrict__ A, int lda,
+                             long long sA, double* __restrict__ out) {
+  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  int u = blockIdx.y;
+  if (warp >= rows) return;
+  const double* a = A + (size_t)u * sA + (size_t)warp * lda;
+  double m = 0.0;
+  for (int c = lane; c < cols; c += 32) m = fmax(m, fabs(a[c]));
+  for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+  if (lane == 0) out[(size_t)u * rows + warp] = m;
+}
+
+// out[u][c] = max_r |B[u][r][c]|, r < rows: one thread per column (coalesced rows).
+__global__ void k_col_absmax(int rows, int cols, const double* __restrict__ B, int ldb,
+                             long long sB, double* __restrict__ out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int u = blockIdx.y;
+  if (c >= cols) return;
+  const double* b = B + (size_t)u * sB + c;
+  double m = 0.0;
+  for (int r = 0; r < rows; ++r) m = fmax(m, fabs(b[(size_t)r * ldb]));
+  out[(size_t)u * cols + c] = m;
+}
+
+// One thread per (incident k, order unit u): flags the column block when, for some
+// outgoing o, the error bound of the sliced contractions exceeds tol |I^0_00(o, k)|
+// (order 0 sets the scale of the synthesized radiance at that pair).
+__global__ void k_flag_columns(OrderBatch b, const double* __restrict__ rmH,
+                               const double* __restrict__ rmU, const double* __restrict__ cmC,
+                               const double* __restrict__ cmSD, const double* __restrict__ pts,
+                               const double* __restrict__ Isyn, double epsK1, double epsK2,
+                               double tol, int* count, int* total, int2* list, int cap) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int u = blockIdx.y;
+  if (k >= b.n_in) return;
+  const int Ro = 4 * b.n_out, R = 4 * b.n_in;
+  double cC = 0.0, cS = 0.0;
+  for (int s = 0; s < 4; ++s) {
+    cC = fmax(cC, cmC[(size_t)u * R + 4 * k + s]);
+    cS = fmax(cS, cmSD[(size_t)u * R + 4 * k + s]);
+  }
+  double mu0 = pts[b.N + k];
+  bool flag = false;
+  for (int o = 0; o < b.n_out && !flag; ++o) {
+    double rH = 0.0, rU = 0.0;
+    for (int a = 0; a < 4; ++a) {
+      rH = fmax(rH, rmH[(size_t)u * Ro + 4 * o + a]);
+      rU = fmax(rU, rmU[(size_t)u * Ro + 4 * o + a]);
+    }
+    double mu_o = pts[b.N + b.n_in + o];
+    double xs = 1.0 / mu_o + 1.0 / mu0;
+    double g0 = -expm1(-b.tau * xs) / (mu_o * xs);
+    double bound = epsK1 * rH * cC + epsK2 * g0 * rU * cS;
+    // the scale of the synthesized radiance is that of order 0 at the same pair
+    double ref = Isyn[((size_t)k * b.n_out + o) * 16];
+    double own = Isyn[(((size_t)(b.m0 + u) * b.n_in + k) * b.n_out + o) * 16];
+    if (!isfinite(own) || !isfinite(ref)) flag = true;
+    else if (bound > tol * fabs(ref)) flag = true;
+  }
+  if (flag) {
+    int slot = atomicAdd(count, 1);
+    atomicAdd(total, 1);
+    if (slot < cap) list[slot] = make_int2(u, k);
+  }
+}
+
+// Persistent grid over the flagged (u, k): FP64 C' = K^-1 RHS[:, 4k..4k+3] in shared
+// memory, then one warp per output row r = 4o + a:
+//   I^m[k][o][a][s] = sum_i Hhat[r][i] C'[i][s] + g0(o, k) sum_i U[r][i] SD[i][4k + s].
+__global__ void __launch_bounds__(256) k_fix_columns(
+    OrderBatch b, const double* __restrict__ Kinv, const double* __restrict__ RHS,
+    const double* __restrict__ Hhat, const double* __restrict__ Uext,
+    const double* __restrict__ SD, const double* __restrict__ pts, int Kpart,
+    const int* __restrict__ count, const int2* __restrict__ list, int cap,
+    double* __restrict__ Isyn) {
+  extern __shared__ double Cs[];  // [2n][4]
+  const int n2 = 2 * b.n, R = 4 * b.n_in, Ro = 4 * b.n_out;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int items = min(*count, cap);
+  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+    int2 e = list[it];
+    int u = e.x, k = e.y;
+    const double* Ki = Kinv + (size_t)u * n2 * n2;
+    const double* rh = RHS + (size_t)u * n2 * R + 4 * k;
+    __syncthreads();  // Cs of the previous item is no longer read
+    for (int i = warp; i < n2; i += nw) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int j = lane; j < n2; j += 32) {
+        double kv = Ki[(size_t)i * n2 + j];
+        const double* r = rh + (size_t)j * R;
+        for (int s = 0; s < 4; ++s) acc[s] = fma(kv, r[s], acc[s]);
+      }
+      for (int s = 0; s < 4; ++s)
+        for (int off = 16; off > 0; off >>= 1) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], off);
+      if (lane == 0)
+        for (int s = 0; s < 4; ++s) Cs[4 * i + s] = acc[s];
+    }
+    __syncthreads();
+    const double* H = Hhat + (size_t)u * Ro * n2;
+    const double* Ub = Uext + (size_t)u * Ro * b.ldU;
+    const double* sd = SD + (size_t)u * b.sSD + 4 * k;
+    double mu0 = pts[b.N + k];
+    for (int r = warp; r < Ro; r += nw) {
+      double h[4] = {0.0, 0.0, 0.0, 0.0}, q[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int i = lane; i < n2; i += 32) {
+        double hv = H[(size_t)r * n2 + i];
+        for (int s = 0; s < 4; ++s) h[s] = fma(hv, Cs[4 * i + s], h[s]);
+      }
+      for (int i = lane; i < Kpart; i += 32) {
+        double uv = Ub[(size_t)r * b.ldU + i];
+        const double* col = sd + (size_t)i * R;
+        for (int s = 0; s < 4; ++s) q[s] = fma(uv, col[s], q[s]);
+      }
+      for (int s = 0; s < 4; ++s)
+        for (int off = 16; off > 0; off >>= 1) {
+          h[s] += __shfl_xor_sync(0xffffffffu, h[s], off);
+          q[s] += __shfl_xor_sync(0xffffffffu, q[s], off);
+        }
+      if (lane == 0) {
+        int o = r >> 2, a = r & 3;
+        double mu_o = pts[b.N + b.n_in + o];
+        double xs = 1.0 / mu_o + 1.0 / mu0;
+        double g0 = -expm1(-b.tau * xs) / (mu_o * xs);
+        double* dst = Isyn + (((size_t)(b.m0 + u) * b.n_in + k) * b.n_out + o) * 16 + 4 * a;
+        for (int s = 0; s < 4; ++s) dst[s] = h[s] + g0 * q[s];
+      }
+    }
+  }
+}
+
+void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
+                    const double* C, const double* Hhat, const double* Uext, const double* SD,
+                    const double* pts, double eps, double tol, double* scratch, int* counters,
+                    int2* list, int cap, double* Isyn, cudaStream_t s) {
+  const int U = b.n_units, n2 = 2 * b.n, R = 4 * b.n_in, Ro = 4 * b.n_out;
+  double* rmH = scratch;
+  double* rmU = rmH + (size_t)U * Ro;
+  double* cmC = rmU + (size_t)U * Ro;
+  double* cmSD = cmC + (size_t)U * R;
+  k_row_absmax<<<dim3((Ro + 7) / 8, U), 256, 0, s>>>(Ro, n2, Hhat, n2, (long long)Ro * n2, rmH);
+  k_row_absmax<<<dim3((Ro + 7) / 8, U), 256, 0, s>>>(Ro, Kpart, Uext, b.ldU,
+                                                      (long long)Ro * b.ldU, rmU);
+  k_col_absmax<<<dim3((R + 127) / 128, U), 128, 0, s>>>(n2, R, C, R, (long long)n2 * R, cmC);
+  k_col_absmax<<<dim3((R + 127) / 128, U), 128, 0, s>>>(Kpart, R, SD, R, b.sSD, cmSD);
+  cudaMemsetAsync(counters, 0, sizeof(int), s);
+  k_flag_columns<<<dim3((b.n_in + 127) / 128, U), 128, 0, s>>>(
+      b, rmH, rmU, cmC, cmSD, pts, Isyn, eps * n2, eps * Kpart, tol, counters, counters + 1,
+      list, cap);
+  size_t smem = (size_t)n2 * 4 * sizeof(double);
+  k_fix_columns<<<2 * 152, 256, smem, s>>>(b, Kinv, RHS, Hhat, Uext, SD, pts, Kpart, counters,
+                                           list, cap, Isyn);
+}
+
+size_t refine_scratch_doubles(int U, int n_in, int n_out) {
+  return (size_t)U * (8 * (size_t)n_out + 8 * (size_t)n_in);
+}
+
+}  // namespace vrte

@@ -1,0 +1,566 @@
+// FP64-accurate batched GEMM on the tcgen05 tensor cores by exact fixed-point slicing.
+//
+// Every row i of A is scaled by 2^-e_i (e_i: the exponent of max_k |A_ik|) and written as
+//   A_ik 2^-e_i = 2^-6 sum_p a_ikp,   a_ikp = 2^(-7p) x integer of magnitude <= 64,
+// likewise every column j of B with 2^-f_j and slices b_kjq. Each slice is a 7-bit integer
+// times a power of two, which BF16 represents exactly, and every product a_ikp b_kjq is an
+// integer of magnitude <= 2^12 times 2^(-7(p+q)). Products on one diagonal d = p + q share
+// a scale, so a FP32 accumulator that collects only diagonal d sums them exactly as long
+// as the integer total stays within 2^24: diagonals 0 .. 3 (at most 4 pairs, K <= 1024)
+// get one TMEM accumulator each. The diagonals 4 .. S-1 share a fifth accumulator whose
+// FP32 rounding sits 2^-28 below the leading term (~1e-15 of it). Pairs with p + q >= S
+// are dropped. The epilogue adds the accumulators in FP64 and scales by
+//   C_ij = 2^(e_i + f_j - 12) (acc_0 + ... + acc_4),
+// so the error is the dropped slices (and the fifth accumulator's rounding): relative to
+// max|A_i| max|B_j| per term ~3e-9 at S = 4, ~3e-13 at S = 6, ~2e-15 at S = 7.
+//
+// Data flow: `k_slice_rows` / `k_slice_cols` write the slices directly as the shared-
+// memory image of 128B-swizzled K-major tiles ([unit][slice][tile][k-block] blocks of
+// 128 x 64 or 64 x 64 BF16), so the GEMM kernel loads each tile with one bulk copy. The
+// GEMM kernel computes a 128 x 64 output tile per CTA with up to five accumulators of 64
+// columns in TMEM, two shared-memory stages while S <= 4 (one above), one thread issuing
+// bulk copies and MMAs, and four warps draining TMEM in the epilogue. Every mbarrier wait
+// is bounded; on timeout the kernel records ST_TIMEOUT, waits (bounded) for its copies,
+// frees TMEM and returns.
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "vrte_internal.cuh"
+
+namespace vrte {
+
+constexpr int TC_M = 128;       // output rows per CTA (MMA M)
+constexpr int TC_N = 64;        // output columns per CTA (MMA N)
+constexpr int TC_KB = 64;       // K per stage (one 128-byte swizzle atom of BF16)
+constexpr int TC_MAXS = 8;      // maximum number of slices
+constexpr int TC_NACC = 5;      // TMEM accumulators: diagonals 0 .. 3 and 4 .. S-1
+constexpr int TC_STAGES = 2;    // shared-memory stages (at most)
+constexpr int TC_SMEM_MAX = 227 * 1024;
+constexpr int A_TILE_BYTES = TC_M * TC_KB * 2;   // 16 KiB
+constexpr int B_TILE_BYTES = TC_N * TC_KB * 2;   // 8 KiB
+constexpr long long WAIT_LIMIT = 1ll << 22;      // polls before a wait is declared stuck
+
+__device__ __host__ inline int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+// two stages of S slices of A and B tiles while they fit in shared memory, else one
+__device__ __host__ inline int tc_stages(int S) {
+  return 2 * S * (A_TILE_BYTES + B_TILE_BYTES) + 1024 <= TC_SMEM_MAX ? 2 : 1;
+}
+__device__ __host__ inline int tc_smem_bytes(int S) {
+  return tc_stages(S) * S * (A_TILE_BYTES + B_TILE_BYTES) + 1024;
+}
+
+// Byte offset of element (row r, k) inside a 128B-swizzled K-major tile of 64 BF16 per row:
+// 8-row groups of 1024 bytes, 128 bytes per row, 16-byte chunk index XOR (row mod 8).
+__device__ inline int swz_offset(int r, int k) {
+  int chunk = k >> 3, within = k & 7;
+  return (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4) + within * 2;
+}
+
+// Slices of a float64 value x in (-1, 1): x = 2^-6 sum_p s_p with s_p = 2^(-7p) q_p and
+// q_p an integer, |q_p| <= 64 (each s_p is exact in BF16).
+__device__ inline void slice_value(double x, int S, float* s) {
+  double r = x * 64.0, f = 1.0;
+  for (int p = 0; p < S; ++p) {
+    double q = rint(r);
+    s[p] = (float)(q * f);
+    r = (r - q) * 128.0;
+    f *= 1.0 / 128.0;
+  }
+}
+
+// A rows: A[u][i][k] (row-major, lda, unit stride sA), M x K. Writes
+//   out[u][p][mt][kb] tiles (128 x 64 BF16 images) and e[u][i] (int exponent).
+// One CTA per (row block of 128, unit); threads cooperate over k.
+__global__ void k_slice_rows(int M, int K, int S, const double* __restrict__ A, int lda,
+                             long long sA, unsigned short* out, int* e_out) {
+  int mt = blockIdx.x, u = blockIdx.y;
+  int Mp = pad_to(M, TC_M), Kp = pad_to(K, TC_KB), KB = Kp / TC_KB, MT = Mp / TC_M;
+  __shared__ int ex[TC_M];
+  const double* Ab = A + (size_t)u * sA;
+  // per-row exponent: warp per row
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = warp; r < TC_M; r += nw) {
+    int i = mt * TC_M + r;
+    double mx = 0.0;
+    if (i < M)
+      for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(Ab[(size_t)i * lda + k]));
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if (lane == 0) {
+      int ee = 0;
+      if (mx > 0.0 && isfinite(mx)) {
+        frexp(mx, &ee);  // mx = f 2^ee with f in [0.5, 1)
+      }
+      ex[r] = ee;
+      if (i < M) e_out[(size_t)u * Mp + i] = ee;
+    }
+  }
+  __syncthreads();
+  size_t tile_elems = (size_t)TC_M * TC_KB;
+  for (int idx = threadIdx.x; idx < TC_M * Kp; idx += blockDim.x) {
+    int r = idx / Kp, k = idx - r * Kp;
+    int i = mt * TC_M + r;
+    double x = 0.0;
+    if (i < M && k < K) x = ldexp(Ab[(size_t)i * lda + k], -ex[r]);
+    if (!isfinite(x)) x = 0.0;
+    float s[TC_MAXS];
+    slice_value(x, S, s);
+    int kb = k / TC_KB, kk = k - kb * TC_KB;
+    int off = swz_offset(r, kk) >> 1;
+    for (int p = 0; p < S; ++p) {
+      size_t base = ((((size_t)u * S + p) * MT + mt) * KB + kb) * tile_elems;
+      // a 7-bit integer times a power of two: the upper half of its FP32 pattern is its
+      // exact BF16
+      out[base + off] = (unsigned short)(__float_as_uint(s[p]) >> 16);
+    }
+  }
+}
+
+// B columns: B[u][k][j] (row-major, ldb, unit stride sB), K x N, sliced per column j
+// into K-major tiles out[u][q][nt][kb] (64 x 64 BF16 images, row = j) and f[u][j].
+__global__ void k_slice_cols(int N, int K, int S, const double* __restrict__ B, int ldb,
+                             long long sB, unsigned short* out, int* f_out) {
+  int nt = blockIdx.x, u = blockIdx.y;
+  int Np = pad_to(N, TC_N), Kp = pad_to(K, TC_KB), KB = Kp / TC_KB, NT = Np / TC_N;
+  __shared__ int ex[TC_N];
+  __shared__ double red[8][TC_N];
+  const double* Bb = B + (size_t)u * sB;
+  // per-column max: threads over columns (coalesced rows), 8 row groups
+  int c = threadIdx.x % TC_N, g = threadIdx.x / TC_N;  // blockDim = 512 -> 8 groups
+  int j = nt * TC_N + c;
+  double mx = 0.0;
+  if (j < N)
+    for (int k = g; k < K; k += 8) mx = fmax(mx, fabs(Bb[(size_t)k * ldb + j]));
+  red[g][c] = mx;
+  __syncthreads();
+  if (g == 0) {
+    double m2 = 0.0;
+    for (int q = 0; q < 8; ++q) m2 = fmax(m2, red[q][c]);
+    int ee = 0;
+    if (m2 > 0.0 && isfinite(m2)) frexp(m2, &ee);
+    ex[c] = ee;
+    if (j < N) f_out[(size_t)u * Np + j] = ee;
+  }
+  __syncthreads();
+  size_t tile_elems = (size_t)TC_N * TC_KB;
+  for (int idx = threadIdx.x; idx < TC_N * Kp; idx += blockDim.x) {
+    int k = idx / TC_N, cc = idx - k * TC_N;  // consecutive threads: consecutive columns
+    int jj = nt * TC_N + cc;
+    double x = 0.0;
+    if (jj < N && k < K) x = ldexp(Bb[(size_t)k * ldb + jj], -ex[cc]);
+    if (!isfinite(x)) x = 0.0;
+    float s[TC_MAXS];
+    slice_value(x, S, s);
+    int kb = k / TC_KB, kk = k - kb * TC_KB;
+    int off = swz_offset(cc, kk) >> 1;
+    for (int q = 0; q < S; ++q) {
+      size_t base = ((((size_t)u * S + q) * NT + nt) * KB + kb) * tile_elems;
+      out[base + off] = (unsigned short)(__float_as_uint(s[q]) >> 16);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ inline uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ inline void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ inline void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ inline bool mbar_try_wait(uint64_t* bar, unsigned phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
+  return ok != 0;
+}
+// bounded wait: returns false if the barrier did not complete within WAIT_LIMIT polls
+__device__ inline bool mbar_wait(uint64_t* bar, unsigned phase) {
+  for (long long it = 0; it < WAIT_LIMIT; ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+__device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ inline uint64_t smem_desc_sw128(const void* p) {
+  uint64_t a = (uint64_t)(smem_u32(p) >> 4) & 0x3FFF;
+  return a | ((uint64_t)1 << 16)          // leading byte offset (unused for swizzled K-major)
+         | ((uint64_t)(1024 >> 4) << 32)  // stride byte offset: 8 rows x 128 bytes
+         | ((uint64_t)1 << 46)            // descriptor version for sm_100-family
+         | ((uint64_t)2 << 61);           // 128-byte swizzle
+}
+__device__ inline void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+__device__ inline void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::
+                   "r"(smem_u32(bar)) : "memory");
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
+                                                 const unsigned short* __restrict__ As,
+                                                 const int* __restrict__ ea,
+                                                 const unsigned short* __restrict__ Bs,
+                                                 const int* __restrict__ fb, Epi epi,
+                                                 unsigned* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  // align the dynamic region to 1024 bytes (128B swizzle atoms)
+  unsigned char* smem =
+      (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int u = blockIdx.z, mt = blockIdx.x, nt = blockIdx.y;
+  const int Mp = pad_to(M, TC_M), Np = pad_to(N, TC_N), Kp = pad_to(K, TC_KB);
+  const int KB = Kp / TC_KB, MT = Mp / TC_M, NT = Np / TC_N;
+  const int stage_bytes = S * (A_TILE_BYTES + B_TILE_BYTES);
+  const int nst = tc_stages(S);
+  const int nacc = S < TC_NACC ? S : TC_NACC;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t ncols = (nacc * TC_N <= 128) ? 128 : (nacc * TC_N <= 256 ? 256 : 512);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&done_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(ncols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_slot;
+
+  // instruction descriptor: D = F32, A = B = BF16, K-major, N = 64, M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                         ((uint32_t)(TC_M >> 4) << 24);
+  const size_t a_unit = (size_t)S * MT * KB * (A_TILE_BYTES / 2);
+  const size_t b_unit = (size_t)S * NT * KB * (B_TILE_BYTES / 2);
+
+  if (threadIdx.x == 0) {
+    bool ok = true;
+    auto issue_copies = [&](int kb, int s) {
+      unsigned char* st = smem + (size_t)s * stage_bytes;
+      mbar_expect_tx(&full_bar[s], (unsigned)stage_bytes);
+      for (int p = 0; p < S; ++p) {
+        const unsigned short* src =
+            As + (size_t)u * a_unit + (((size_t)p * MT + mt) * KB + kb) * (A_TILE_BYTES / 2);
+        bulk_g2s(st + p * A_TILE_BYTES, src, A_TILE_BYTES, &full_bar[s]);
+      }
+      for (int q = 0; q < S; ++q) {
+        const unsigned short* src =
+            Bs + (size_t)u * b_unit + (((size_t)q * NT + nt) * KB + kb) * (B_TILE_BYTES / 2);
+        bulk_g2s(st + S * A_TILE_BYTES + q * B_TILE_BYTES, src, B_TILE_BYTES, &full_bar[s]);
+      }
+    };
+    int issued = 0;
+    bool pending[TC_STAGES] = {false, false};
+    for (; issued < KB && issued < nst; ++issued) {
+      issue_copies(issued, issued);
+      pending[issued] = true;
+    }
+    uint32_t full_phase[TC_STAGES] = {0, 0}, empty_phase[TC_STAGES] = {0, 0};
+    unsigned written = 0;  // accumulators that hold a value (the first MMA overwrites)
+    for (int kb = 0; kb < KB && ok; ++kb) {
+      int s = kb % nst;
+      if (!mbar_wait(&full_bar[s], full_phase[s])) { ok = false; break; }
+      full_phase[s] ^= 1;
+      pending[s] = false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      unsigned char* st = smem + (size_t)s * stage_bytes;
+      for (int p = 0; p < S; ++p)
+        for (int q = 0; p + q < S; ++q) {
+          int a = p + q < TC_NACC ? p + q : TC_NACC - 1;
+          uint32_t dt = tmem + (uint32_t)(a * TC_N);
+          for (int k16 = 0; k16 < TC_KB / 16; ++k16) {
+            uint64_t ad = smem_desc_sw128(st + p * A_TILE_BYTES) + (uint64_t)(k16 * 2);
+            uint64_t bd = smem_desc_sw128(st + S * A_TILE_BYTES + q * B_TILE_BYTES) +
+                          (uint64_t)(k16 * 2);
+            uint32_t acc = (k16 == 0 && !((written >> a) & 1u)) ? 0u : 1u;
+            mma_bf16(dt, ad, bd, idesc, acc);
+          }
+          written |= 1u << a;
+        }
+      mma_commit(&empty_bar[s]);
+      if (issued < KB) {
+        // reuse stage s once the MMAs that read it have completed
+        if (!mbar_wait(&empty_bar[s], empty_phase[s])) { ok = false; break; }
+        empty_phase[s] ^= 1;
+        issue_copies(issued, s);
+        pending[s] = true;
+        ++issued;
+      }
+    }
+    if (ok) {
+      mma_commit(&done_bar);
+      if (!mbar_wait(&done_bar, 0)) ok = false;
+    }
+    if (!ok) {
+      abort_flag = 1;
+      atomicOr(status, ST_TIMEOUT);
+      // let the copies still in flight land before the CTA exits (bounded)
+      for (int s = 0; s < TC_STAGES; ++s)
+        if (pending[s]) mbar_wait(&full_bar[s], full_phase[s]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  if (!abort_flag) {
+    // epilogue: warp w drains TMEM lanes 32w..32w+31 (output rows), 16 columns at a time
+    const int r = warp * 32 + lane;
+    const int i = mt * TC_M + r;
+    const int erow = (i < M) ? ea[(size_t)u * Mp + i] : 0;
+    for (int c0 = 0; c0 < TC_N; c0 += 16) {
+      double v[16];
+#pragma unroll
+      for (int t = 0; t < 16; ++t) v[t] = 0.0;
+      for (int a = nacc - 1; a >= 0; --a) {
+        uint32_t regs[16];
+        uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * TC_N + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15}, [%16];\n"
+            : "=r"(regs[0]), "=r"(regs[1]), "=r"(regs[2]), "=r"(regs[3]), "=r"(regs[4]),
+              "=r"(regs[5]), "=r"(regs[6]), "=r"(regs[7]), "=r"(regs[8]), "=r"(regs[9]),
+              "=r"(regs[10]), "=r"(regs[11]), "=r"(regs[12]), "=r"(regs[13]), "=r"(regs[14]),
+              "=r"(regs[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // smallest accumulator first; acc_0 .. acc_3 add exactly (<= 24 + 21 bits)
+#pragma unroll
+        for (int t = 0; t < 16; ++t) v[t] += (double)__uint_as_float(regs[t]);
+      }
+      if (i < M) {
+        for (int t = 0; t < 16; ++t) {
+          int j = nt * TC_N + c0 + t;
+          if (j < N) epi(u, i, j, ldexp(v[t], erow + fb[(size_t)u * Np + j] - 12));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                 : "memory");
+}
+
+
+struct TcLayout {
+  int Mp, Np, Kp, MT, NT, KB;
+  size_t a_bytes, b_bytes, e_bytes, f_bytes;
+};
+
+static TcLayout tc_layout(int M, int N, int K, int batch, int S) {
+  TcLayout L;
+  L.Mp = pad_to(M, TC_M);
+  L.Np = pad_to(N, TC_N);
+  L.Kp = pad_to(K, TC_KB);
+  L.MT = L.Mp / TC_M;
+  L.NT = L.Np / TC_N;
+  L.KB = L.Kp / TC_KB;
+  auto al = [](size_t b) { return (b + 1023) / 1024 * 1024; };
+  L.a_bytes = al((size_t)batch * S * L.Mp * L.Kp * 2);
+  L.b_bytes = al((size_t)batch * S * L.Np * L.Kp * 2);
+  L.e_bytes = al((size_t)batch * L.Mp * 4);
+  L.f_bytes = al((size_t)batch * L.Np * 4);
+  return L;
+}
+
+size_t tc_workspace_bytes(int M, int N, int K, int batch, int S) {
+  TcLayout L = tc_layout(M, N, K, batch, S);
+  return L.a_bytes + L.b_bytes + L.e_bytes + L.f_bytes;
+}
+
+bool tc_shape_ok(int K, int S) { return S >= 1 && S <= TC_MAXS && K >= 1 && K <= 1024; }
+
+template <class Epi>
+void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const double* B, int ldb,
+             long long sB, Epi epi, int batch, int S, void* work, unsigned* status,
+             cudaStream_t s) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  TcLayout L = tc_layout(M, N, K, batch, S);
+  unsigned char* w = (unsigned char*)work;
+  unsigned short* As = (unsigned short*)w;
+  unsigned short* Bs = (unsigned short*)(w + L.a_bytes);
+  int* ea = (int*)(w + L.a_bytes + L.b_bytes);
+  int* fb = (int*)(w + L.a_bytes + L.b_bytes + L.e_bytes);
+  k_slice_rows<<<dim3(L.MT, batch), 256, 0, s>>>(M, K, S, A, lda, sA, As, ea);
+  k_slice_cols<<<dim3(L.NT, batch), 512, 0, s>>>(N, K, S, B, ldb, sB, Bs, fb);
+  int smem = tc_smem_bytes(S);
+  cudaFuncSetAttribute(k_tc_gemm<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  k_tc_gemm<Epi><<<dim3(L.MT, L.NT, batch), 128, smem, s>>>(M, N, K, S, As, ea, Bs, fb, epi,
+                                                              status);
+}
+
+struct TcEpiStore {
+  double* C;
+  int ldc;
+  long long sC;
+  double beta;
+  __device__ void operator()(int u, int i, int j, double v) const {
+    double* c = C + (size_t)u * sC + (size_t)i * ldc + j;
+    *c = beta == 0.0 ? v : v + beta * *c;
+  }
+};
+
+void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, const double* B,
+                   int ldb, long long sB, double beta, double* C, int ldc, long long sC,
+                   int batch, int S, void* work, unsigned* status, cudaStream_t s) {
+  tc_gemm(M, N, K, A, lda, sA, B, ldb, sB, TcEpiStore{C, ldc, sC, beta}, batch, S, work, status,
+          s);
+}
+
+void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
+                  const double* B, long long sB, const double* T1, const double* pts,
+                  double* Isyn, int S, void* work, cudaStream_t s) {
+  EpiPart e{T1, Isyn, pts, b.N, b.n_in, b.n_out, b.m0, b.tau};
+  tc_gemm(4 * b.n_out, 4 * b.n_in, K, A, lda, sA, B, 4 * b.n_in, sB, e, b.n_units, S, work,
+          b.status, s);
+}
+
+// ------------------------------------------------------------------ synthesis
+// The 16 Mueller elements split into two classes by their Fourier factor (Eq. 7):
+// cos for (IQ, IQ) and (UV, UV), sin for the off-diagonal blocks (+ for UV rows, - for IQ
+// rows). Each class is one GEMM: rows (pair, element) gathered from I^m, K = orders,
+// columns = azimuths of the cos or sin weight table.
+__constant__ int c_synth_elem[2][8] = {{0, 1, 4, 5, 10, 11, 14, 15}, {2, 3, 6, 7, 8, 9, 12, 13}};
+__constant__ double c_synth_sign[2][8] = {{1, 1, 1, 1, 1, 1, 1, 1},
+                                          {-1, -1, -1, -1, 1, 1, 1, 1}};
+
+// rows r = 8 (pair - pair0) + e, A(r, m) = Isyn[m][pair][elem(e)]; one thread per row
+__global__ void k_slice_synth_rows(int n_rows, int pair0, long long pairs_total, int M, int S,
+                                   int cls, const double* __restrict__ Isyn,
+                                   unsigned short* out, int* e_out) {
+  int mt = blockIdx.x;
+  int r = threadIdx.x;
+  int row = mt * TC_M + r;
+  int Mp = pad_to(n_rows, TC_M), Kp = pad_to(M, TC_KB), KB = Kp / TC_KB, MT = Mp / TC_M;
+  bool valid = row < n_rows;
+  size_t base_addr = 0;
+  if (valid) {
+    long long pair = pair0 + row / 8;
+    base_addr = (size_t)pair * 16 + c_synth_elem[cls][row & 7];
+  }
+  double mx = 0.0;
+  if (valid)
+    for (int m = 0; m < M; ++m) mx = fmax(mx, fabs(Isyn[(size_t)m * pairs_total * 16 + base_addr]));
+  int ee = 0;
+  if (mx > 0.0 && isfinite(mx)) frexp(mx, &ee);
+  if (valid) e_out[row] = ee;
+  size_t tile_elems = (size_t)TC_M * TC_KB;
+  for (int k = 0; k < Kp; ++k) {
+    double x = 0.0;
+    if (valid && k < M) x = ldexp(Isyn[(size_t)k * pairs_total * 16 + base_addr], -ee);
+    if (!isfinite(x)) x = 0.0;
+    float sl[TC_MAXS];
+    slice_value(x, S, sl);
+    int kb = k / TC_KB, kk = k - kb * TC_KB;
+    int off = swz_offset(r, kk) >> 1;
+    for (int p = 0; p < S; ++p) {
+      size_t base = ((((size_t)p) * MT + mt) * KB + kb) * tile_elems;
+      out[base + off] = (unsigned short)(__float_as_uint(sl[p]) >> 16);
+    }
+  }
+}
+
+template <typename T>
+struct EpiSynth {
+  T* out;
+  int pair0, n_phi, cls;
+  unsigned* status;
+  __device__ void operator()(int, int i, int j, double v) const {
+    long long pair = pair0 + i / 8;
+    int e = i & 7;
+    double w = c_synth_sign[cls][e] * v;
+    if (!isfinite(w)) atomicOr(status, ST_NONFINITE);
+    out[((size_t)pair * n_phi + j) * 16 + c_synth_elem[cls][e]] = (T)w;
+  }
+};
+
+size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int S, int k_block) {
+  int rows = 8 * std::min(k_block, n_in) * n_out;
+  return tc_workspace_bytes(rows, n_phi, M, 1, S);
+}
+
+void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, const double* wc,
+                  const double* ws, void* out, int out_dtype, int S, int k_block, void* work,
+                  unsigned* status, cudaStream_t s) {
+  long long pairs_total = (long long)n_in * n_out;
+  for (int k0 = 0; k0 < n_in; k0 += k_block) {
+    int kb = std::min(k_block, n_in - k0);
+    int rows = 8 * kb * n_out;
+    int pair0 = k0 * n_out;
+    TcLayout L = tc_layout(rows, n_phi, M, 1, S);
+    unsigned char* w = (unsigned char*)work;
+    unsigned short* As = (unsigned short*)w;
+    unsigned short* Bs = (unsigned short*)(w + L.a_bytes);
+    int* ea = (int*)(w + L.a_bytes + L.b_bytes);
+    int* fb = (int*)(w + L.a_bytes + L.b_bytes + L.e_bytes);
+    int smem = tc_smem_bytes(S);
+    for (int cls = 0; cls < 2; ++cls) {
+      k_slice_synth_rows<<<L.MT, TC_M, 0, s>>>(rows, pair0, pairs_total, M, S, cls, Isyn, As, ea);
+      k_slice_cols<<<dim3(L.NT, 1), 512, 0, s>>>(n_phi, M, S, cls ? ws : wc, n_phi, 0, Bs, fb);
+      if (out_dtype == VRTE_OUT_F64) {
+        EpiSynth<double> e{(double*)out, pair0, n_phi, cls, status};
+        cudaFuncSetAttribute(k_tc_gemm<EpiSynth<double>>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_tc_gemm<EpiSynth<double>><<<dim3(L.MT, L.NT, 1), 128, smem, s>>>(rows, n_phi, M, S, As,
+                                                                         ea, Bs, fb, e, status);
+      } else {
+        EpiSynth<float> e{(float*)out, pair0, n_phi, cls, status};
+        cudaFuncSetAttribute(k_tc_gemm<EpiSynth<float>>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        k_tc_gemm<EpiSynth<float>><<<dim3(L.MT, L.NT, 1), 128, smem, s>>>(rows, n_phi, M, S, As,
+                                                                        ea, Bs, fb, e, status);
+      }
+    }
+  }
+}
+
+}  // namespace vrte
+
+extern "C" size_t vrte_gemm_sliced_workspace(int M, int N, int K, int batch, int slices) {
+  if (M < 1 || N < 1 || batch < 1 || !vrte::tc_shape_ok(K, slices)) return 0;
+  return vrte::tc_workspace_bytes(M, N, K, batch, slices);
+}
+
+extern "C" vrte_status vrte_gemm_sliced(int M, int N, int K, const double* d_A, int lda,
+                                        long long stride_a, const double* d_B, int ldb,
+                                        long long stride_b, double* d_C, int ldc,
+                                        long long stride_c, int batch, int slices,
+                                        void* d_workspace, size_t workspace_bytes,
+                                        unsigned* d_status, void* stream) {
+  if (M < 1 || N < 1 || batch < 1 || !vrte::tc_shape_ok(K, slices) || !d_A || !d_B || !d_C ||
+      !d_workspace || !d_status || lda < K || ldb < N || ldc < N)
+    return VRTE_ERR_INVALID_ARG;
+  if (workspace_bytes < vrte::tc_workspace_bytes(M, N, K, batch, slices))
+    return VRTE_ERR_INVALID_ARG;
+  vrte::tc_gemm_store(M, N, K, d_A, lda, stride_a, d_B, ldb, stride_b, 0.0, d_C, ldc, stride_c,
+                      batch, slices, d_workspace, d_status, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? VRTE_OK : VRTE_ERR_CUDA;
+}

@@ -26,6 +26,17 @@ enum Stage {
   ST_TABLES, ST_ASSEMBLE, ST_EIGEN, ST_MODES, ST_PARTICULAR, ST_BC_SOLVE, ST_RECON_OPS,
   ST_RECON_GEMM, ST_SYNTHESIS, kStages
 };
+// mixed form: BF16 slices per FP64 operand (exact products, ~1e-12 relative per term) and
+// incident cosines per tensor-core synthesis block
+constexpr int kSlices = 7;
+constexpr int kSlicesSynth = 5;
+constexpr int kSynthBlock = 64;
+// per-term error of the 7-slice product relative to max|A_i| max|B_j| (measured ~2e-15),
+// and the bound, relative to the order-0 I_00 of the same (incident, outgoing) pair,
+// above which a column block is recomputed in FP64
+constexpr double kSliceEps = 1e-14;
+constexpr double kRefineTol = 1e-7;
+
 const char* kStageNames[kStages] = {"tables", "assemble", "eigen", "modes_bc_inverse",
                                     "particular", "bc_solve", "recon_ops", "recon_gemm",
                                     "synthesis"};
@@ -59,6 +70,14 @@ struct vrte_plan {
   double *FY = nullptr, *mode_res = nullptr, *Bm = nullptr, *Hb = nullptr, *Zb = nullptr,
          *Vb = nullptr, *Xb = nullptr, *kb_re = nullptr, *kb_im = nullptr, *balb = nullptr;
   int* mode_flag = nullptr;
+  // mixed form: slice workspace of the tensor-core GEMMs (shared with the synthesis)
+  void* tcw = nullptr;
+  size_t tcw_bytes = 0;
+  // mixed form: FP64 refinement of ill-conditioned columns (maxima, counters, work list)
+  double* rscratch = nullptr;
+  int* rcount = nullptr;  // [flagged in this batch, flagged in this solve]
+  int2* rlist = nullptr;
+  int kdir = 0;  // extra K of the direct term in the mixed form (4 L_max)
   double* Isyn = nullptr;  // [M_max][n_in][n_out][16]
   // host-API staging
   double* d_coef_stage = nullptr;
@@ -72,7 +91,7 @@ struct vrte_plan {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
   bool profile = false;
   // geometry of the most recent order batch (for vrte_debug_copy)
-  int last_n = 0, last_U = 0, last_P = 0, last_Meff = 0;
+  int last_n = 0, last_U = 0, last_P = 0, last_Meff = 0, last_ldU = 0;
 };
 
 namespace {
@@ -220,6 +239,10 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
         l.n_nodes < 1 || l.n_nodes > p->desc.n_nodes_max || l.n_orders < 1 ||
         l.n_orders > p->desc.n_orders_max || l.n_coef < 1 || l.n_coef > p->desc.n_coef_max)
       return VRTE_ERR_INVALID_ARG;
+    // the mixed form folds the direct term into the particular contraction: K = 2n + 4L
+    // must stay within the exact-accumulation limit of the sliced tensor-core GEMM
+    if (p->desc.precision == VRTE_MIXED && 8 * l.n_nodes + 4 * l.n_coef > 1024)
+      return VRTE_ERR_UNSUPPORTED;
   }
   cudaDeviceSynchronize();
   free_workspace(p, kPlanAllocs);
@@ -235,8 +258,21 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   }
   size_t n = 4 * (size_t)Nx, R = 4 * (size_t)p->n_in, Ro = 4 * (size_t)p->n_out;
   size_t P = Nx + p->n_in + p->n_out;
-  size_t per_unit = 3 * (size_t)Lx * P + 10 * n * n + 3 * n + 8 * n * n + 5 * n * R + 6 * n * R +
-                    6 * Ro * n + Ro * R + n * n + 1 + 5 * 4 * n * n + 3 * 2 * n + 1;
+  const bool mixed = p->desc.precision == VRTE_MIXED;
+  p->kdir = mixed ? 4 * Lx : 0;
+  size_t kd = p->kdir;
+  const int S = kSlices;
+  size_t tc_unit = 0;
+  if (mixed) {
+    size_t c[3] = {tc_workspace_bytes((int)(2 * n), (int)R, (int)(2 * n), 1, S),
+                   tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n), 1, S),
+                   tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n + kd), 1, S)};
+    for (size_t v : c) tc_unit = std::max(tc_unit, v);
+  }
+  size_t per_unit = 3 * (size_t)Lx * P + 10 * n * n + 3 * n + 8 * n * n + 5 * n * R +
+                    (4 * n + kd) * R + 2 * n * R + 4 * Ro * n + Ro * (2 * n + kd) + Ro * R + n * n +
+                    1 + 5 * 4 * n * n + 3 * 2 * n + 1 + (tc_unit + 7) / 8 +
+                    (mixed ? refine_scratch_doubles(1, p->n_in, p->n_out) + p->n_in : 0);
   size_t isyn = (size_t)Mx * p->n_in * p->n_out * 16;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
@@ -264,13 +300,27 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   VRTE_ALLOC(lam_re, U * n) VRTE_ALLOC(lam_im, U * n) VRTE_ALLOC(bal, U * n)
   VRTE_ALLOC(K, U * 4 * n * n) VRTE_ALLOC(Kinv, U * 4 * n * n)
   VRTE_ALLOC(Pb, U * n * R) VRTE_ALLOC(Rb, U * n * R) VRTE_ALLOC(Wv, U * n * R) VRTE_ALLOC(Yv, U * n * R) VRTE_ALLOC(Es, U * n * R)
-  VRTE_ALLOC(SD, U * 2 * n * R) VRTE_ALLOC(RHS, U * 2 * n * R) VRTE_ALLOC(C, U * 2 * n * R)
-  VRTE_ALLOC(Upm, U * Ro * 2 * n) VRTE_ALLOC(P1, U * Ro * n) VRTE_ALLOC(P2, U * Ro * n) VRTE_ALLOC(Hhat, U * Ro * 2 * n)
+  VRTE_ALLOC(SD, U * (2 * n + kd) * R) VRTE_ALLOC(RHS, U * 2 * n * R) VRTE_ALLOC(C, U * 2 * n * R)
+  VRTE_ALLOC(Upm, U * Ro * (2 * n + kd)) VRTE_ALLOC(P1, U * Ro * n) VRTE_ALLOC(P2, U * Ro * n) VRTE_ALLOC(Hhat, U * Ro * 2 * n)
   VRTE_ALLOC(T1, U * Ro * R)
   VRTE_ALLOC(FY, U * n * n) VRTE_ALLOC(mode_res, U) VRTE_ALLOC(mode_flag, U)
   VRTE_ALLOC(Bm, U * 4 * n * n) VRTE_ALLOC(Hb, U * 4 * n * n) VRTE_ALLOC(Zb, U * 4 * n * n)
   VRTE_ALLOC(Vb, U * 4 * n * n) VRTE_ALLOC(Xb, U * 4 * n * n)
   VRTE_ALLOC(kb_re, U * 2 * n) VRTE_ALLOC(kb_im, U * 2 * n) VRTE_ALLOC(balb, U * 2 * n)
+  if (mixed) {
+    size_t synth = tc_synthesis_workspace(Mx, p->n_in, p->n_out, p->n_phi, kSlicesSynth,
+                                          kSynthBlock);
+    p->tcw_bytes = std::max(tc_unit * U, synth);
+    if ((st = alloc(p, &p->tcw, p->tcw_bytes)) != VRTE_OK ||
+        (st = allocd(p, &p->rscratch, refine_scratch_doubles((int)U, p->n_in, p->n_out))) !=
+            VRTE_OK ||
+        (st = allocd(p, &p->rcount, 2)) != VRTE_OK ||
+        (st = allocd(p, &p->rlist, U * p->n_in)) != VRTE_OK) {
+      free_workspace(p, kPlanAllocs);
+      p->Isyn = nullptr;
+      return st;
+    }
+  }
   VRTE_ALLOC(Isyn, isyn)
 #undef VRTE_ALLOC
   return VRTE_OK;
@@ -281,6 +331,8 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
   const size_t table = (size_t)p->n_in * p->n_out * p->n_phi * 16;
   const size_t esz = out_dtype == VRTE_OUT_F64 ? sizeof(double) : sizeof(float);
   const int R = 4 * p->n_in, Ro = 4 * p->n_out;
+  if (p->desc.precision == VRTE_MIXED && cudaMemsetAsync(p->rcount, 0, 2 * sizeof(int), s))
+    return VRTE_ERR_CUDA;
   for (int lb = 0; lb < p->n_layers; ++lb) {
     const vrte_layer& ly = p->layers[lb];
     const int N = ly.n_nodes, n = 4 * N, L = ly.n_coef;
@@ -295,12 +347,33 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
     }
     for (int m0 = 0; m0 < Meff; m0 += p->chunk) {
       const int U = std::min(p->chunk, Meff - m0);
-      OrderBatch ob{N, n, L, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef, p->d_status};
+      const bool mixed = p->desc.precision == VRTE_MIXED;
+      // operator rows [U+ | U- | direct] and beams [s; d; direct] carry 4 L extra entries
+      // in the mixed form, where the direct term rides on the particular contraction
+      const int kdir = mixed ? 4 * L : 0;
+      const int ldU = 2 * n + (mixed ? p->kdir : 0);
+      OrderBatch ob{N, n, L, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef, p->d_status,
+                    ldU, (long long)ldU * R};
       p->last_n = n;
       p->last_U = U;
+      p->last_ldU = ldU;
       p->last_P = P;
       p->last_Meff = Meff;
       const long long nn = (long long)n * n, nR = (long long)n * R, Ron = (long long)Ro * n;
+      const long long sU_part = (long long)Ro * ldU;
+      const int gl = mixed ? 3 : 1;  // launches per contraction
+      // boundary solve and reconstruction contractions: FP64 on the CUDA cores, or the
+      // sliced BF16 product on the tensor cores in the mixed form
+      auto gemm = [&](int M_, int N_, int K_, const double* A_, int lda_, long long sA_,
+                      const double* B_, int ldb_, long long sB_, double beta_, double* C_,
+                      int ldc_, long long sC_) {
+        if (mixed)
+          tc_gemm_store(M_, N_, K_, A_, lda_, sA_, B_, ldb_, sB_, beta_, C_, ldc_, sC_, U,
+                        kSlices, p->tcw, p->d_status, s);
+        else
+          dgemm_batched(M_, N_, K_, 1.0, A_, lda_, sA_, B_, ldb_, sB_, beta_, C_, ldc_, sC_, U,
+                        s);
+      };
       const double dn = n, dR = R, dRo = Ro, dU = U;
       double lsum = 0.0;  // sum over the batch of (L - m)
       for (int u = 0; u < U; ++u) lsum += L - (m0 + u);
@@ -343,49 +416,70 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
                       72.0 * N * p->n_in * lsum + 8.0 * dn * dn * dR * dU,
                       8.0 * 10 * dn * dR * dU);
         launch_assemble_beam(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_min4, p->Pb, p->Rb, s);
+        // FP64 in both forms: near a resonance mu0 ~ 1/kappa_j the eigenbasis solve
+        // amplifies rounding by 1/(kappa_j^2 - mu0^-2), and the homogeneous part cancels it
         dgemm_batched(n, R, n, 1.0, p->F, n, nn, p->Pb, R, nR, 0.0, p->Wv, R, nR, U, s);
         launch_particular_rhs(ob, p->Wv, p->Rb, p->d_pts, p->Wv, s);
         dgemm_batched(n, R, n, 1.0, p->Xinv, n, nn, p->Wv, R, nR, 0.0, p->Yv, R, nR, U, s);
         launch_eigen_scale(ob, p->lam_re, p->lam_im, p->d_pts, p->Yv, s);
-        dgemm_batched(n, R, n, 1.0, p->X, n, nn, p->Yv, R, nR, 0.0, p->SD, R, 2 * nR, U, s);
-        dgemm_batched(n, R, n, 1.0, p->E, n, nn, p->SD, R, 2 * nR, 0.0, p->Es, R, nR, U, s);
+        dgemm_batched(n, R, n, 1.0, p->X, n, nn, p->Yv, R, nR, 0.0, p->SD, R, ob.sSD, U, s);
+        dgemm_batched(n, R, n, 1.0, p->E, n, nn, p->SD, R, ob.sSD, 0.0, p->Es, R, nR, U, s);
         launch_particular_sd(ob, p->Pb, p->Es, p->d_pts, p->SD, s);
         launch_bc_rhs(ob, p->SD, nullptr, p->d_rtop4, p->d_pts, p->RHS, s);
       }
       {
-        StageScope sc(p, ST_BC_SOLVE, s, 1, 2.0 * 4 * dn * dn * dR * dU,
+        StageScope sc(p, ST_BC_SOLVE, s, gl, 2.0 * 4 * dn * dn * dR * dU,
                       8.0 * (4 * dn * dn + 4 * dn * dR) * dU);
-        dgemm_batched(2 * n, R, 2 * n, 1.0, p->Kinv, 2 * n, 4 * nn, p->RHS, R, 2 * nR, 0.0, p->C,
-                      R, 2 * nR, U, s);
+        gemm(2 * n, R, 2 * n, p->Kinv, 2 * n, 4 * nn, p->RHS, R, 2 * nR, 0.0, p->C, R, 2 * nR);
       }
       {
-        StageScope sc(p, ST_RECON_OPS, s, 5,
+        StageScope sc(p, ST_RECON_OPS, s, 4 + (mixed ? 2 : 1),
                       72.0 * N * p->n_out * lsum + 4.0 * dRo * dn * dn * dU +
                           72.0 * p->n_in * p->n_out * lsum,
                       8.0 * (6 * dRo * dn + dRo * dR) * dU);
         launch_assemble_U(ob, p->gp, p->gr, p->gt, p->d_w_nodes, p->d_mout4, p->Upm, s);
-        dgemm_batched(Ro, n, n, 1.0, p->Upm, 2 * n, 2 * Ron, p->X, n, nn, 0.0, p->P1, n, Ron, U, s);
-        dgemm_batched(Ro, n, n, 1.0, p->Upm + n, 2 * n, 2 * Ron, p->Y, n, nn, 0.0, p->P2, n, Ron,
+        // FP64 in both forms: the refinement of resonant columns reuses Hhat
+        dgemm_batched(Ro, n, n, 1.0, p->Upm, ldU, sU_part, p->X, n, nn, 0.0, p->P1, n, Ron, U, s);
+        dgemm_batched(Ro, n, n, 1.0, p->Upm + n, ldU, sU_part, p->Y, n, nn, 0.0, p->P2, n, Ron,
                       U, s);
         launch_build_Hhat(ob, p->P1, p->P2, p->lam_re, p->lam_im, p->d_pts, p->Hhat, s);
-        launch_assemble_direct(ob, p->gp, p->gr, p->gt, p->d_pts, p->d_min4, p->d_mout4, p->T1,
-                               s);
+        if (mixed)
+          launch_direct_operators(ob, p->gp, p->gr, p->gt, p->d_min4, p->d_mout4, p->Upm, p->SD,
+                                  s);
+        else
+          launch_assemble_direct(ob, p->gp, p->gr, p->gt, p->d_pts, p->d_min4, p->d_mout4, p->T1,
+                                 s);
       }
       {
         // two contractions [4 n_out x 2n] x [2n x 4 n_in] per order
-        StageScope sc(p, ST_RECON_GEMM, s, 2, 2.0 * 2 * dRo * dR * 2 * dn * dU,
+        StageScope sc(p, ST_RECON_GEMM, s, mixed ? 2 * gl + 6 : 2, 2.0 * 2 * dRo * dR * 2 * dn * dU,
                       8.0 * (2 * dRo * 2 * dn + 2 * 2 * dn * dR + 3 * dRo * dR) * dU);
-        dgemm_batched(Ro, R, 2 * n, 1.0, p->Hhat, 2 * n, 2 * Ron, p->C, R, 2 * nR, 1.0, p->T1, R,
-                      (long long)Ro * R, U, s);
-        dgemm_part_epilogue(ob, p->Upm, p->SD, p->T1, p->d_pts, p->Isyn, s);
+        // FP64: T1 holds the direct term and gains the homogeneous part; mixed: T1 is the
+        // homogeneous part and the direct term is the tail of the particular contraction
+        gemm(Ro, R, 2 * n, p->Hhat, 2 * n, 2 * Ron, p->C, R, 2 * nR, mixed ? 0.0 : 1.0, p->T1, R,
+             (long long)Ro * R);
+        if (mixed) {
+          tc_gemm_part(ob, 2 * n + kdir, p->Upm, ldU, sU_part, p->SD, ob.sSD, p->T1, p->d_pts,
+                       p->Isyn, kSlices, p->tcw, s);
+          refine_columns(ob, 2 * n + kdir, p->Kinv, p->RHS, p->C, p->Hhat, p->Upm, p->SD,
+                         p->d_pts, kSliceEps, kRefineTol, p->rscratch, p->rcount, p->rlist,
+                         U * p->n_in, p->Isyn, s);
+        } else
+          dgemm_part_epilogue(ob, p->Upm, p->SD, p->T1, p->d_pts, p->Isyn, s);
       }
     }
     char* outb = (char*)d_brdf + (size_t)lb * table * esz;
     {
-      StageScope sc(p, ST_SYNTHESIS, s, 1, 2.0 * table * Meff,
+      const bool mixed = p->desc.precision == VRTE_MIXED;
+      StageScope sc(p, ST_SYNTHESIS, s,
+                    mixed ? 6 * ((p->n_in + kSynthBlock - 1) / kSynthBlock) : 1, 2.0 * table * Meff,
                     (double)table * esz + (double)Meff * p->n_in * p->n_out * 16 * 8);
-      launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, p->Isyn, p->d_wc, p->d_ws, outb,
-                            out_dtype, p->d_status, s);
+      if (mixed)
+        tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, p->Isyn, p->d_wc, p->d_ws, outb, out_dtype,
+                     kSlicesSynth, kSynthBlock, p->tcw, p->d_status, s);
+      else
+        launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, p->Isyn, p->d_wc, p->d_ws, outb,
+                              out_dtype, p->d_status, s);
     }
   }
   if (cudaGetLastError() != cudaSuccess) return VRTE_ERR_CUDA;
@@ -396,7 +490,6 @@ vrte_status vrte_solve_brdf(vrte_plan* p, void* d_brdf, int out_dtype, void* str
   if (!p || !d_brdf) return VRTE_ERR_INVALID_ARG;
   if (out_dtype != VRTE_OUT_F32 && out_dtype != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
   if (p->n_layers < 1 || !p->d_coeffs || !p->Isyn) return VRTE_ERR_STATE;
-  if (p->desc.precision == VRTE_MIXED) return VRTE_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   p->last_stream = s;
   return run_solve(p, p->d_coeffs, d_brdf, out_dtype, s);
@@ -407,7 +500,6 @@ vrte_status vrte_solve_brdf_host(vrte_plan* p, const double* h_coeffs, void* h_b
   if (!p || !h_coeffs || !h_brdf) return VRTE_ERR_INVALID_ARG;
   if (out_dtype != VRTE_OUT_F32 && out_dtype != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
   if (p->n_layers < 1 || !p->Isyn) return VRTE_ERR_STATE;
-  if (p->desc.precision == VRTE_MIXED) return VRTE_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   size_t cbytes = (size_t)p->n_layers * p->desc.n_coef_max * 6 * sizeof(double);
   size_t obytes = (size_t)p->n_layers * p->n_in * p->n_out * p->n_phi * 16 *
@@ -452,7 +544,7 @@ vrte_status vrte_plan_status(vrte_plan* p) {
   if (h & ST_NONFINITE) return VRTE_ERR_NONFINITE;
   if (h & ST_NO_CONVERGENCE) return VRTE_ERR_NO_CONVERGENCE;
   if (h & ST_SINGULAR) return VRTE_ERR_SINGULAR;
-  if (h) return VRTE_ERR_CUDA;
+  if (h) return VRTE_ERR_CUDA;  // ST_TIMEOUT: a bounded device wait gave up
   return VRTE_OK;
 }
 
@@ -463,6 +555,17 @@ vrte_status vrte_debug_copy(vrte_plan* p, const char* name, void* dst, size_t by
     unsigned h = 0;
     if (cudaStreamSynchronize(p->last_stream) != cudaSuccess ||
         cudaMemcpy(&h, p->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return VRTE_ERR_CUDA;
+    double v = (double)h;
+    if (size_out) *size_out = sizeof(double);
+    if (dst && bytes >= sizeof(double)) memcpy(dst, &v, sizeof(double));
+    return VRTE_OK;
+  }
+  if (strcmp(name, "refined") == 0) {  // mixed form: column blocks recomputed in FP64
+    int h = 0;
+    if (p->rcount && (cudaStreamSynchronize(p->last_stream) != cudaSuccess ||
+                      cudaMemcpy(&h, p->rcount + 1, sizeof(int), cudaMemcpyDeviceToHost) !=
+                          cudaSuccess))
       return VRTE_ERR_CUDA;
     double v = (double)h;
     if (size_out) *size_out = sizeof(double);
@@ -491,10 +594,10 @@ vrte_status vrte_debug_copy(vrte_plan* p, const char* name, void* dst, size_t by
       {"Xinv", p->Xinv, U * n * n},
       {"beam_p", p->Pb, U * n * R},
       {"beam_r", p->Rb, U * n * R},
-      {"SD", p->SD, U * 2 * n * R},
+      {"SD", p->SD, U * (size_t)p->last_ldU * R},
       {"RHS", p->RHS, U * 2 * n * R},
       {"C", p->C, U * 2 * n * R},
-      {"Upm", p->Upm, U * Ro * 2 * n},
+      {"Upm", p->Upm, U * Ro * (size_t)p->last_ldU},
       {"Hhat", p->Hhat, U * Ro * 2 * n},
       {"T1", p->T1, U * Ro * R},
       {"Isyn", p->Isyn, (size_t)p->last_Meff * p->n_in * p->n_out * 16},

@@ -14,6 +14,7 @@ enum : unsigned {
   ST_SINGULAR = 1u << 1,
   ST_NONFINITE = 1u << 2,
   ST_BAD_INDEX = 1u << 3,
+  ST_TIMEOUT = 1u << 4,  // a bounded device wait gave up (kernel returned early)
 };
 
 constexpr double kPi = 3.14159265358979323846;
@@ -30,6 +31,29 @@ struct OrderBatch {
   double tau, omega;
   const double* coef;  // [L][6]
   unsigned* status;
+  int ldU;             // row stride of [U+ | U- | direct operator] (2n, or 2n + 4L when mixed)
+  long long sSD;       // unit stride of [s; d; direct beams] (2n R, or (2n + 4L) R when mixed)
+};
+
+// Reconstruction epilogue (row i = 4o + a: outgoing o, exiting component a; column
+// j = 4k + s: incident k, basis s): Isyn[m][k][o][a][s] = T1[i][j] + g0(o, k) acc with
+// g0 the depth integral of exp(-t/mu0) exp(-t/mu_o) / mu_o over the layer.
+struct EpiPart {
+  const double* T1;
+  double* Isyn;
+  const double* pts;
+  int N, n_in, n_out, m0;
+  double tau;
+  __device__ void operator()(int u, int i, int j, double acc) const {
+    int R = 4 * n_in;
+    int o = i >> 2, a = i & 3, k = j >> 2, s = j & 3;
+    double mu_o = pts[N + n_in + o], mu0 = pts[N + k];
+    double xs = 1.0 / mu_o + 1.0 / mu0;
+    double g0 = -expm1(-tau * xs) / (mu_o * xs);
+    double v = T1[(size_t)u * (4 * n_out) * R + (size_t)i * R + j] + g0 * acc;
+    size_t dst = (((size_t)(m0 + u) * n_in + k) * n_out + o) * 16 + 4 * a + s;
+    Isyn[dst] = v;
+  }
 };
 
 // ---------------------------------------------------------------- tables (k_tables.cu)
@@ -55,6 +79,12 @@ void launch_assemble_U(const OrderBatch& b, const double* p, const double* r, co
 void launch_assemble_direct(const OrderBatch& b, const double* p, const double* r,
                             const double* t, const double* pts, const double* min4,
                             const double* mout4, double* T1, cudaStream_t s);
+// Direct (once-scattered) term as a contraction over (l, component): writes
+// Adir = M_out P_l(mu_o) B_l into columns 2n.. of the [U+ | U- | Adir] rows and
+// Bdir = (omega/2pi) (-1)^(l-m) D P_l(mu0) D b_k into rows 2n.. of [s; d; Bdir].
+void launch_direct_operators(const OrderBatch& b, const double* p, const double* r,
+                             const double* t, const double* min4, const double* mout4,
+                             double* Uext, double* SDext, cudaStream_t s);
 
 // ---------------------------------------------------------------- dense FP64 (k_linalg.cu)
 // C[u] = alpha * A[u] (M x K, row-major, lda) * B[u] (K x N, ldb) + beta * C[u]
@@ -75,6 +105,30 @@ void eigen_block_fallback(int n, int m0, const double* E, const double* F, const
                           int force0, double* res, int* flag, double* B, double* Hb, double* Zb,
                           double* Vb, double* Xb, double* kb_re, double* kb_im, double* balb,
                           int batch, unsigned* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- tensor cores (k_tcgemm.cu)
+// C = A B (+ beta C) with A, B FP64 sliced into S exact 7-bit BF16 slices (relative
+// accuracy ~2^-7S per term); K <= 1024, 1 <= S <= 4. `work` holds tc_workspace_bytes.
+size_t tc_workspace_bytes(int M, int N, int K, int batch, int S);
+bool tc_shape_ok(int K, int S);
+void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, const double* B,
+                   int ldb, long long sB, double beta, double* C, int ldc, long long sC,
+                   int batch, int S, void* work, unsigned* status, cudaStream_t s);
+void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
+                  const double* B, long long sB, const double* T1, const double* pts,
+                  double* Isyn, int S, void* work, cudaStream_t s);
+// Mixed form: flags (order, incident) column blocks whose sliced reconstruction error
+// bound eps K max|row| max|column| exceeds tol |I_00| and recomputes them in FP64.
+void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
+                    const double* C, const double* Hhat, const double* Uext, const double* SD,
+                    const double* pts, double eps, double tol, double* scratch, int* counters,
+                    int2* list, int cap, double* Isyn, cudaStream_t s);
+size_t refine_scratch_doubles(int U, int n_in, int n_out);
+// Synthesis of the order radiances on the tensor cores, in blocks of incident cosines.
+size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int S, int k_block);
+void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, const double* wc,
+                  const double* ws, void* out, int out_dtype, int S, int k_block, void* work,
+                  unsigned* status, cudaStream_t s);
 
 // ---------------------------------------------------------------- mode algebra (k_modes.cu)
 void launch_pack_Y(const OrderBatch& b, const double* EX, const double* lam_re,

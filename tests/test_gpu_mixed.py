@@ -1,0 +1,142 @@
+"""Parity of the mixed-precision form (tensor-core contractions, through the C ABI) with
+the FP64 CPU oracle.
+
+Tolerance of the mixed form: every element of the I row of the 4x4 Mueller matrix
+(I -> I, Q, U, V coupling) agrees within 1e-6 of F_00 at the same (incident, outgoing,
+azimuth) point, and every element of the Q, U, V rows within 1e-5 of F_00.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1707_05882_gb300 as vr
+from vrte_inputs import angle_grids, make_config
+from vrte_inputs.mie import monodisperse_coefficients, polydisperse_coefficients
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_I = 1e-6
+TOL_QUV = 1e-5
+
+
+def row_errors(F, G):
+    """(I-row error, QUV-row error), each max |F - G| / |G_00| over points."""
+    scale = np.maximum(np.abs(G[..., 0, 0]), 1e-300)[..., None]
+    e = np.abs(F - G)
+    return float(np.max(e[..., 0, :] / scale)), float(np.max(e[..., 1:, :] / scale[..., None]))
+
+
+def mixed_brdf(layer, mu_in, mu_out, dphi, out_dtype=None):
+    out = vr.brdf([layer], mu_in, mu_out, dphi, precision=vr.VRTE_MIXED,
+                  out_dtype=out_dtype or torch.float64)
+    torch.cuda.synchronize()
+    return out[0].cpu().numpy()
+
+
+def oracle_brdf(layer, mu_in, mu_out, dphi):
+    return O.brdf(layer["coef"], layer["omega"], layer["tau"], layer.get("n_interface", 1.0),
+                  layer["n_nodes"], layer["n_orders"], mu_in, mu_out, dphi)
+
+
+def check(layer, mu_in, mu_out, dphi):
+    F = mixed_brdf(layer, mu_in, mu_out, dphi)
+    G = oracle_brdf(layer, mu_in, mu_out, dphi)
+    assert F.shape == G.shape
+    assert np.all(np.isfinite(F))
+    ei, eq = row_errors(F, G)
+    assert ei < TOL_I, (ei, eq)
+    assert eq < TOL_QUV, (ei, eq)
+    return ei, eq
+
+
+def test_mixed_config1_rayleigh():
+    cfg = make_config(1)
+    check(cfg["layers"][0], cfg["mu_in"], cfg["mu_out"], cfg["dphi"])
+
+
+@pytest.mark.parametrize("n_if", [1.0, 1.5])
+def test_mixed_ragged_multi_tile_mie(n_if):
+    """4N = 80, 4 n_in = 68, 4 n_out = 76, 4L = 160: ragged tails on every tensor-core tile."""
+    coef = polydisperse_coefficients(1.5 + 0.001j, 6.0, 0.1, 40)
+    ly = dict(tau=3.0, omega=0.97, n_interface=n_if, n_nodes=20, n_orders=40, coef=coef)
+    check(ly, *angle_grids(17, 19, 11))
+
+
+def test_mixed_config2_full():
+    cfg = make_config(2)
+    check(cfg["layers"][0], cfg["mu_in"], cfg["mu_out"], cfg["dphi"])
+
+
+def test_mixed_synthesis_spans_several_incident_blocks():
+    """n_in = 150 > 64 incident cosines per synthesis block: three blocks, the last ragged."""
+    coef = monodisperse_coefficients(1.5 + 0.01j, 2.0, 16)
+    ly = dict(tau=2.0, omega=0.95, n_interface=1.33, n_nodes=8, n_orders=16, coef=coef)
+    check(ly, *angle_grids(150, 5, 9))
+
+
+@pytest.mark.parametrize("case", ["thin", "thick", "N1", "orders_beyond_L", "mu_one",
+                                  "one_direction", "albedo_near_one"])
+def test_mixed_edge_cases(case):
+    coef = monodisperse_coefficients(1.5 + 0.01j, 2.0, 12)
+    ly = dict(tau=1.0, omega=0.9, n_interface=1.33, n_nodes=6, n_orders=12, coef=coef)
+    mu_in, mu_out, dphi = angle_grids(5, 6, 7)
+    if case == "thin":
+        ly["tau"] = 1e-4
+    elif case == "thick":
+        ly["tau"] = 100.0
+    elif case == "N1":
+        ly["n_nodes"] = 1
+        ly["coef"] = coef[:2]
+        ly["n_orders"] = 2
+    elif case == "orders_beyond_L":
+        ly["n_orders"] = 20
+    elif case == "mu_one":
+        mu_in = np.array([1.0, 0.5])
+        mu_out = np.array([1.0, 0.3])
+    elif case == "one_direction":
+        mu_in, mu_out, dphi = np.array([0.7]), np.array([0.4]), np.array([1.0])
+    elif case == "albedo_near_one":
+        ly["omega"] = 0.999
+        ly["tau"] = 10.0
+    check(ly, mu_in, mu_out, dphi)
+
+
+def test_mixed_zero_albedo_is_exactly_zero():
+    coef = monodisperse_coefficients(1.5 + 0.01j, 2.0, 12)
+    ly = dict(tau=1.0, omega=0.0, n_interface=1.33, n_nodes=6, n_orders=12, coef=coef)
+    F = mixed_brdf(ly, *angle_grids(5, 6, 7))
+    assert np.abs(F).max() == 0.0
+
+
+def test_mixed_fp32_output_rounds_the_mixed_result():
+    cfg = make_config(1)
+    ly = cfg["layers"][0]
+    F64 = mixed_brdf(ly, cfg["mu_in"], cfg["mu_out"], cfg["dphi"])
+    F32 = mixed_brdf(ly, cfg["mu_in"], cfg["mu_out"], cfg["dphi"], out_dtype=torch.float32)
+    assert np.array_equal(F32, F64.astype(np.float32))
+
+
+def test_mixed_rejects_contraction_beyond_exact_limit():
+    """2 * 4N + 4L > 1024 leaves the exact-accumulation range of the sliced product."""
+    mu = np.array([0.5])
+    plan = vr.Plan(mu, mu, mu, 96, 200, 200, precision=vr.VRTE_MIXED)
+    coef = torch.zeros((1, 200, 6), dtype=torch.float64, device="cuda")
+    ly = dict(tau=1.0, omega=0.5, n_interface=1.0, n_nodes=96, n_orders=8, n_coef=200)
+    with pytest.raises(vr.VrteError) as e:
+        plan.set_layers([ly], coef)
+    assert e.value.code == 8
+    plan.close()
+
+
+def test_mixed_matches_fp64_form_on_the_same_plan_shape():
+    """The two forms differ only by the sliced-product rounding of the contractions."""
+    coef = polydisperse_coefficients(1.5 + 0.001j, 6.0, 0.1, 40)
+    ly = dict(tau=3.0, omega=0.97, n_interface=1.5, n_nodes=20, n_orders=40, coef=coef)
+    mu_in, mu_out, dphi = angle_grids(17, 19, 11)
+    F = mixed_brdf(ly, mu_in, mu_out, dphi)
+    G = vr.brdf([ly], mu_in, mu_out, dphi, precision=vr.VRTE_FP64,
+                out_dtype=torch.float64)[0].cpu().numpy()
+    ei, eq = row_errors(F, G)
+    assert ei < TOL_I and eq < TOL_QUV
+    assert ei > 0.0  # the mixed form really ran the sliced contractions
