@@ -302,4 +302,17 @@ void launch_direct_operators(const OrderBatch& b, const double* p, const double*
   k_direct_B<<<gb, 64, 0, s>>>(b, p, r, t, min4, SDext);
 }
 
+__global__ void k_depth_table(int N, int n_in, int n_out, double tau, const double* pts,
+                              double* g0tab) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int o = blockIdx.y;
+  if (k >= n_in) return;
+  g0tab[(size_t)o * n_in + k] = depth_factor(tau, pts[N + n_in + o], pts[N + k]);
+}
+
+void launch_depth_table(int N, int n_in, int n_out, double tau, const double* pts, double* g0tab,
+                        cudaStream_t s) {
+  k_depth_table<<<dim3((n_in + 127) / 128, n_out), 128, 0, s>>>(N, n_in, n_out, tau, pts, g0tab);
+}
+
 }  // namespace vrte

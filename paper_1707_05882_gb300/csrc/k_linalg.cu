@@ -116,9 +116,9 @@ void dgemm_batched(int M, int N, int K, double alpha, const double* A, int lda, 
 }
 
 void dgemm_part_epilogue(const OrderBatch& b, const double* A, const double* B, const double* T1,
-                         const double* pts, double* Isyn, cudaStream_t s) {
+                         const double* g0tab, double* Isyn, cudaStream_t s) {
   int Ro = 4 * b.n_out, R = 4 * b.n_in, n2 = 2 * b.n;
-  EpiPart e{T1, Isyn, pts, b.N, b.n_in, b.n_out, b.m0, b.tau};
+  EpiPart e{T1, Isyn, g0tab, b.N, b.n_in, b.n_out, b.m0};
   run_dgemm(Ro, R, n2, A, b.ldU, (long long)Ro * b.ldU, false, B, R, b.sSD, false, e,
             b.n_units, s);
 }

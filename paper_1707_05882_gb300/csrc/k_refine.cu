@@ -44,7 +44,7 @@ __global__ void k_col_absmax(int rows, int cols, const double* __restrict__ B, i
 // (order 0 sets the scale of the synthesized radiance at that pair).
 __global__ void k_flag_columns(OrderBatch b, const double* __restrict__ rmH,
                                const double* __restrict__ rmU, const double* __restrict__ cmC,
-                               const double* __restrict__ cmSD, const double* __restrict__ pts,
+                               const double* __restrict__ cmSD, const double* __restrict__ g0tab,
                                const double* __restrict__ Isyn, double epsK1, double epsK2,
                                double tol, int* count, int* total, int2* list, int cap) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -56,7 +56,6 @@ __global__ void k_flag_columns(OrderBatch b, const double* __restrict__ rmH,
     cC = fmax(cC, cmC[(size_t)u * R + 4 * k + s]);
     cS = fmax(cS, cmSD[(size_t)u * R + 4 * k + s]);
   }
-  double mu0 = pts[b.N + k];
   bool flag = false;
   for (int o = 0; o < b.n_out && !flag; ++o) {
     double rH = 0.0, rU = 0.0;
@@ -64,9 +63,7 @@ __global__ void k_flag_columns(OrderBatch b, const double* __restrict__ rmH,
       rH = fmax(rH, rmH[(size_t)u * Ro + 4 * o + a]);
       rU = fmax(rU, rmU[(size_t)u * Ro + 4 * o + a]);
     }
-    double mu_o = pts[b.N + b.n_in + o];
-    double xs = 1.0 / mu_o + 1.0 / mu0;
-    double g0 = -expm1(-b.tau * xs) / (mu_o * xs);
+    double g0 = g0tab[(size_t)o * b.n_in + k];
     double bound = epsK1 * rH * cC + epsK2 * g0 * rU * cS;
     // the scale of the synthesized radiance is that of order 0 at the same pair
     double ref = Isyn[((size_t)k * b.n_out + o) * 16];
@@ -87,7 +84,7 @@ __global__ void k_flag_columns(OrderBatch b, const double* __restrict__ rmH,
 __global__ void __launch_bounds__(256) k_fix_columns(
     OrderBatch b, const double* __restrict__ Kinv, const double* __restrict__ RHS,
     const double* __restrict__ Hhat, const double* __restrict__ Uext,
-    const double* __restrict__ SD, const double* __restrict__ pts, int Kpart,
+    const double* __restrict__ SD, const double* __restrict__ g0tab, int Kpart,
     const int* __restrict__ count, const int2* __restrict__ list, int cap,
     double* __restrict__ Isyn) {
   extern __shared__ double Cs[];  // [2n][4]
@@ -116,7 +113,6 @@ __global__ void __launch_bounds__(256) k_fix_columns(
     const double* H = Hhat + (size_t)u * Ro * n2;
     const double* Ub = Uext + (size_t)u * Ro * b.ldU;
     const double* sd = SD + (size_t)u * b.sSD + 4 * k;
-    double mu0 = pts[b.N + k];
     for (int r = warp; r < Ro; r += nw) {
       double h[4] = {0.0, 0.0, 0.0, 0.0}, q[4] = {0.0, 0.0, 0.0, 0.0};
       for (int i = lane; i < n2; i += 32) {
@@ -135,11 +131,9 @@ __global__ void __launch_bounds__(256) k_fix_columns(
         }
       if (lane == 0) {
         int o = r >> 2, a = r & 3;
-        double mu_o = pts[b.N + b.n_in + o];
-        double xs = 1.0 / mu_o + 1.0 / mu0;
-        double g0 = -expm1(-b.tau * xs) / (mu_o * xs);
+        double g0 = g0tab[(size_t)o * b.n_in + k];
         double* dst = Isyn + (((size_t)(b.m0 + u) * b.n_in + k) * b.n_out + o) * 16 + 4 * a;
-        for (int s = 0; s < 4; ++s) dst[s] = h[s] + g0 * q[s];
+        for (int s = 0; s < 4; ++s) dst[s] = fma(g0, q[s], h[s]);
       }
     }
   }
@@ -147,7 +141,7 @@ __global__ void __launch_bounds__(256) k_fix_columns(
 
 void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
                     const double* C, const double* Hhat, const double* Uext, const double* SD,
-                    const double* pts, double eps, double tol, double* scratch, int* counters,
+                    const double* g0tab, double eps, double tol, double* scratch, int* counters,
                     int2* list, int cap, double* Isyn, cudaStream_t s) {
   const int U = b.n_units, n2 = 2 * b.n, R = 4 * b.n_in, Ro = 4 * b.n_out;
   double* rmH = scratch;
@@ -161,10 +155,10 @@ void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const do
   k_col_absmax<<<dim3((R + 127) / 128, U), 128, 0, s>>>(Kpart, R, SD, R, b.sSD, cmSD);
   cudaMemsetAsync(counters, 0, sizeof(int), s);
   k_flag_columns<<<dim3((b.n_in + 127) / 128, U), 128, 0, s>>>(
-      b, rmH, rmU, cmC, cmSD, pts, Isyn, eps * n2, eps * Kpart, tol, counters, counters + 1,
+      b, rmH, rmU, cmC, cmSD, g0tab, Isyn, eps * n2, eps * Kpart, tol, counters, counters + 1,
       list, cap);
   size_t smem = (size_t)n2 * 4 * sizeof(double);
-  k_fix_columns<<<2 * 152, 256, smem, s>>>(b, Kinv, RHS, Hhat, Uext, SD, pts, Kpart, counters,
+  k_fix_columns<<<2 * 152, 256, smem, s>>>(b, Kinv, RHS, Hhat, Uext, SD, g0tab, Kpart, counters,
                                            list, cap, Isyn);
 }
 

@@ -57,108 +57,163 @@ __device__ inline int swz_offset(int r, int k) {
   return (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4) + within * 2;
 }
 
-// Slices of a float64 value x in (-1, 1): x = 2^-6 sum_p s_p with s_p = 2^(-7p) q_p and
-// q_p an integer, |q_p| <= 64 (each s_p is exact in BF16).
-__device__ inline void slice_value(double x, int S, float* s) {
-  double r = x * 64.0, f = 1.0;
-  for (int p = 0; p < S; ++p) {
-    double q = rint(r);
-    s[p] = (float)(q * f);
-    r = (r - q) * 128.0;
-    f *= 1.0 / 128.0;
+// Exponent field of a float64 for the scale search: 0 for zero and subnormals; a
+// non-finite value counts as zero and sets *bad.
+__device__ inline int exp_field(double x, bool* bad) {
+  int E = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+  if (E == 0x7FF) {
+    *bad = true;
+    return 0;
   }
+  return E;
+}
+// Scale exponent from the largest exponent field of a row or column: max |x| < 2^e.
+__device__ inline int scale_exp(int Emax) { return Emax ? Emax - 1022 : 0; }
+
+// Slices of v 2^-e in (-1, 1) in integer arithmetic: X = round(v 2^(6 + 7(S-1) - e)) is
+// cut into signed base-128 digits q_p in [-64, 64] (most significant first), and slice p
+// is q_p 2^-7p, written as its (exact) BF16 bit pattern. Subnormals and non-finite
+// values give zero slices.
+template <int S>
+__device__ inline void slice_bits(double v, int e, unsigned short* bf) {
+  long long b = __double_as_longlong(v);
+  int E = (int)((b >> 52) & 0x7FF);
+  long long X = 0;
+  if (E != 0 && E != 0x7FF) {
+    long long mant = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
+    int sh = E - 1075 + 6 + 7 * (S - 1) - e;  // |v| < 2^e keeps X below 2^(6 + 7(S-1))
+    if (sh >= 0) X = mant << sh;
+    else if (sh > -63) X = (mant + (1ll << (-sh - 1))) >> (-sh);
+    if (b < 0) X = -X;
+  }
+  float scale = 1.0f;
+#pragma unroll
+  for (int p = 1; p < S; ++p) scale *= 1.0f / 128.0f;
+#pragma unroll
+  for (int p = S - 1; p >= 1; --p) {
+    int d = (int)(((X + 64) & 127) - 64);
+    X = (X - d) >> 7;  // exact: X - d is a multiple of 128
+    bf[p] = (unsigned short)(__float_as_uint((float)d * scale) >> 16);
+    scale *= 128.0f;
+  }
+  bf[0] = (unsigned short)(__float_as_uint((float)X) >> 16);
+}
+
+// Writes the S slices of 8 consecutive K entries (one 16-byte chunk per slice).
+template <int S>
+__device__ inline void put_chunk(const double* v, int e, unsigned short* dst0,
+                                 size_t slice_stride) {
+  uint32_t w[S][4];
+#pragma unroll
+  for (int t = 0; t < 8; t += 2) {
+    unsigned short lo[S], hi[S];
+    slice_bits<S>(v[t], e, lo);
+    slice_bits<S>(v[t + 1], e, hi);
+#pragma unroll
+    for (int p = 0; p < S; ++p) w[p][t >> 1] = (uint32_t)lo[p] | ((uint32_t)hi[p] << 16);
+  }
+#pragma unroll
+  for (int p = 0; p < S; ++p)
+    *(uint4*)(dst0 + p * slice_stride) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
 // A rows: A[u][i][k] (row-major, lda, unit stride sA), M x K. Writes
 //   out[u][p][mt][kb] tiles (128 x 64 BF16 images) and e[u][i] (int exponent).
-// One CTA per (row block of 128, unit); threads cooperate over k.
-__global__ void k_slice_rows(int M, int K, int S, const double* __restrict__ A, int lda,
-                             long long sA, unsigned short* out, int* e_out) {
+// One CTA per (row block of 128, unit); each thread slices 8 consecutive k of one row.
+template <int S>
+__global__ void k_slice_rows(int M, int K, const double* __restrict__ A, int lda,
+                             long long sA, unsigned short* out, int* e_out, unsigned* status) {
   int mt = blockIdx.x, u = blockIdx.y;
   int Mp = pad_to(M, TC_M), Kp = pad_to(K, TC_KB), KB = Kp / TC_KB, MT = Mp / TC_M;
   __shared__ int ex[TC_M];
   const double* Ab = A + (size_t)u * sA;
-  // per-row exponent: warp per row
+  bool bad = false;
+  // per-row exponent: warp per row, integer max of the exponent fields
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int r = warp; r < TC_M; r += nw) {
     int i = mt * TC_M + r;
-    double mx = 0.0;
+    int Em = 0;
     if (i < M)
-      for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(Ab[(size_t)i * lda + k]));
-    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      for (int k = lane; k < K; k += 32) Em = max(Em, exp_field(Ab[(size_t)i * lda + k], &bad));
+    Em = __reduce_max_sync(0xffffffffu, Em);
     if (lane == 0) {
-      int ee = 0;
-      if (mx > 0.0 && isfinite(mx)) {
-        frexp(mx, &ee);  // mx = f 2^ee with f in [0.5, 1)
-      }
-      ex[r] = ee;
-      if (i < M) e_out[(size_t)u * Mp + i] = ee;
+      ex[r] = scale_exp(Em);
+      if (i < M) e_out[(size_t)u * Mp + i] = ex[r];
     }
   }
   __syncthreads();
-  size_t tile_elems = (size_t)TC_M * TC_KB;
-  for (int idx = threadIdx.x; idx < TC_M * Kp; idx += blockDim.x) {
-    int r = idx / Kp, k = idx - r * Kp;
+  const size_t tile_elems = (size_t)TC_M * TC_KB;
+  const size_t slice_stride = (size_t)MT * KB * tile_elems;
+  const int chunks = Kp / 8;
+  for (int idx = threadIdx.x; idx < TC_M * chunks; idx += blockDim.x) {
+    int r = idx / chunks, k0 = 8 * (idx - r * chunks);
     int i = mt * TC_M + r;
-    double x = 0.0;
-    if (i < M && k < K) x = ldexp(Ab[(size_t)i * lda + k], -ex[r]);
-    if (!isfinite(x)) x = 0.0;
-    float s[TC_MAXS];
-    slice_value(x, S, s);
-    int kb = k / TC_KB, kk = k - kb * TC_KB;
-    int off = swz_offset(r, kk) >> 1;
-    for (int p = 0; p < S; ++p) {
-      size_t base = ((((size_t)u * S + p) * MT + mt) * KB + kb) * tile_elems;
-      // a 7-bit integer times a power of two: the upper half of its FP32 pattern is its
-      // exact BF16
-      out[base + off] = (unsigned short)(__float_as_uint(s[p]) >> 16);
-    }
+    double v[8];
+    for (int t = 0; t < 8; ++t)
+      v[t] = (i < M && k0 + t < K) ? Ab[(size_t)i * lda + k0 + t] : 0.0;
+    int kb = k0 / TC_KB;
+    size_t base = ((((size_t)u * S) * MT + mt) * KB + kb) * tile_elems;
+    put_chunk<S>(v, ex[r], out + base + (swz_offset(r, k0 - kb * TC_KB) >> 1), slice_stride);
   }
+  if (bad) atomicOr(status, ST_NONFINITE);
 }
 
 // B columns: B[u][k][j] (row-major, ldb, unit stride sB), K x N, sliced per column j
 // into K-major tiles out[u][q][nt][kb] (64 x 64 BF16 images, row = j) and f[u][j].
-__global__ void k_slice_cols(int N, int K, int S, const double* __restrict__ B, int ldb,
-                             long long sB, unsigned short* out, int* f_out) {
+// Each thread slices 8 consecutive k of one column (consecutive threads: consecutive
+// columns, so every global load is coalesced).
+template <int S>
+__global__ void k_slice_cols(int N, int K, const double* __restrict__ B, int ldb,
+                             long long sB, unsigned short* out, int* f_out, unsigned* status) {
   int nt = blockIdx.x, u = blockIdx.y;
   int Np = pad_to(N, TC_N), Kp = pad_to(K, TC_KB), KB = Kp / TC_KB, NT = Np / TC_N;
   __shared__ int ex[TC_N];
-  __shared__ double red[8][TC_N];
+  __shared__ int red[8][TC_N];
   const double* Bb = B + (size_t)u * sB;
-  // per-column max: threads over columns (coalesced rows), 8 row groups
+  bool bad = false;
+  // per-column max exponent: threads over columns (coalesced rows), 8 row groups
   int c = threadIdx.x % TC_N, g = threadIdx.x / TC_N;  // blockDim = 512 -> 8 groups
   int j = nt * TC_N + c;
-  double mx = 0.0;
+  int Em = 0;
   if (j < N)
-    for (int k = g; k < K; k += 8) mx = fmax(mx, fabs(Bb[(size_t)k * ldb + j]));
-  red[g][c] = mx;
+    for (int k = g; k < K; k += 8) Em = max(Em, exp_field(Bb[(size_t)k * ldb + j], &bad));
+  red[g][c] = Em;
   __syncthreads();
   if (g == 0) {
-    double m2 = 0.0;
-    for (int q = 0; q < 8; ++q) m2 = fmax(m2, red[q][c]);
-    int ee = 0;
-    if (m2 > 0.0 && isfinite(m2)) frexp(m2, &ee);
-    ex[c] = ee;
-    if (j < N) f_out[(size_t)u * Np + j] = ee;
+    int m2 = 0;
+    for (int q = 0; q < 8; ++q) m2 = max(m2, red[q][c]);
+    ex[c] = scale_exp(m2);
+    if (j < N) f_out[(size_t)u * Np + j] = ex[c];
   }
   __syncthreads();
-  size_t tile_elems = (size_t)TC_N * TC_KB;
-  for (int idx = threadIdx.x; idx < TC_N * Kp; idx += blockDim.x) {
-    int k = idx / TC_N, cc = idx - k * TC_N;  // consecutive threads: consecutive columns
+  const size_t tile_elems = (size_t)TC_N * TC_KB;
+  const size_t slice_stride = (size_t)NT * KB * tile_elems;
+  const int chunks = Kp / 8;
+  for (int idx = threadIdx.x; idx < TC_N * chunks; idx += blockDim.x) {
+    int k0 = 8 * (idx / TC_N), cc = idx % TC_N;
     int jj = nt * TC_N + cc;
-    double x = 0.0;
-    if (jj < N && k < K) x = ldexp(Bb[(size_t)k * ldb + jj], -ex[cc]);
-    if (!isfinite(x)) x = 0.0;
-    float s[TC_MAXS];
-    slice_value(x, S, s);
-    int kb = k / TC_KB, kk = k - kb * TC_KB;
-    int off = swz_offset(cc, kk) >> 1;
-    for (int q = 0; q < S; ++q) {
-      size_t base = ((((size_t)u * S + q) * NT + nt) * KB + kb) * tile_elems;
-      out[base + off] = (unsigned short)(__float_as_uint(s[q]) >> 16);
-    }
+    double v[8];
+    for (int t = 0; t < 8; ++t)
+      v[t] = (jj < N && k0 + t < K) ? Bb[(size_t)(k0 + t) * ldb + jj] : 0.0;
+    int kb = k0 / TC_KB;
+    size_t base = ((((size_t)u * S) * NT + nt) * KB + kb) * tile_elems;
+    put_chunk<S>(v, ex[cc], out + base + (swz_offset(cc, k0 - kb * TC_KB) >> 1), slice_stride);
   }
+  if (bad) atomicOr(status, ST_NONFINITE);
 }
+
+// slicers are compiled for each slice count; the host picks one at run time
+#define VRTE_SLICE_DISPATCH(S, CALL) \
+  switch (S) {                       \
+    case 1: CALL(1); break;          \
+    case 2: CALL(2); break;          \
+    case 3: CALL(3); break;          \
+    case 4: CALL(4); break;          \
+    case 5: CALL(5); break;          \
+    case 6: CALL(6); break;          \
+    case 7: CALL(7); break;          \
+    default: CALL(8); break;         \
+  }
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ inline uint32_t smem_u32(const void* p) {
@@ -334,10 +389,16 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
     const int i = mt * TC_M + r;
     const int erow = (i < M) ? ea[(size_t)u * Mp + i] : 0;
     for (int c0 = 0; c0 < TC_N; c0 += 16) {
-      double v[16];
+      // acc_0 .. acc_3 hold integers in units of 2^-7a: combine them exactly in an int64
+      // in units of 2^-21, then one FP64 fma adds the (rounded) fifth accumulator
+      long long I[16];
+      float r4[16];
 #pragma unroll
-      for (int t = 0; t < 16; ++t) v[t] = 0.0;
-      for (int a = nacc - 1; a >= 0; --a) {
+      for (int t = 0; t < 16; ++t) {
+        I[t] = 0;
+        r4[t] = 0.0f;
+      }
+      for (int a = 0; a < nacc; ++a) {
         uint32_t regs[16];
         uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * TC_N + c0);
         asm volatile(
@@ -349,14 +410,29 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
               "=r"(regs[15])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        // smallest accumulator first; acc_0 .. acc_3 add exactly (<= 24 + 21 bits)
+        if (a < TC_NACC - 1) {
+          const float up = (float)(1 << (7 * a));
+          const int sh = 7 * (TC_NACC - 2 - a);
 #pragma unroll
-        for (int t = 0; t < 16; ++t) v[t] += (double)__uint_as_float(regs[t]);
+          for (int t = 0; t < 16; ++t)
+            I[t] += (long long)__float2int_rn(__uint_as_float(regs[t]) * up) << sh;
+        } else {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) r4[t] = __uint_as_float(regs[t]);
+        }
       }
       if (i < M) {
         for (int t = 0; t < 16; ++t) {
           int j = nt * TC_N + c0 + t;
-          if (j < N) epi(u, i, j, ldexp(v[t], erow + fb[(size_t)u * Np + j] - 12));
+          if (j < N) {
+            double w = fma((double)I[t], 0x1p-21, (double)r4[t]);
+            int E2 = erow + fb[(size_t)u * Np + j] - 12;
+            // 2^E2 from its bit pattern while it is a normal number
+            double v = (E2 > -1000 && E2 < 1000)
+                           ? w * __longlong_as_double((long long)(E2 + 1023) << 52)
+                           : ldexp(w, E2);
+            epi(u, i, j, v);
+          }
         }
       }
     }
@@ -409,8 +485,11 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
   unsigned short* Bs = (unsigned short*)(w + L.a_bytes);
   int* ea = (int*)(w + L.a_bytes + L.b_bytes);
   int* fb = (int*)(w + L.a_bytes + L.b_bytes + L.e_bytes);
-  k_slice_rows<<<dim3(L.MT, batch), 256, 0, s>>>(M, K, S, A, lda, sA, As, ea);
-  k_slice_cols<<<dim3(L.NT, batch), 512, 0, s>>>(N, K, S, B, ldb, sB, Bs, fb);
+#define VRTE_SLICE_AB(SS)                                                                  \
+  k_slice_rows<SS><<<dim3(L.MT, batch), 256, 0, s>>>(M, K, A, lda, sA, As, ea, status);  \
+  k_slice_cols<SS><<<dim3(L.NT, batch), 512, 0, s>>>(N, K, B, ldb, sB, Bs, fb, status)
+  VRTE_SLICE_DISPATCH(S, VRTE_SLICE_AB)
+#undef VRTE_SLICE_AB
   int smem = tc_smem_bytes(S);
   cudaFuncSetAttribute(k_tc_gemm<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_tc_gemm<Epi><<<dim3(L.MT, L.NT, batch), 128, smem, s>>>(M, N, K, S, As, ea, Bs, fb, epi,
@@ -436,9 +515,9 @@ void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, 
 }
 
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
-                  const double* B, long long sB, const double* T1, const double* pts,
+                  const double* B, long long sB, const double* T1, const double* g0tab,
                   double* Isyn, int S, void* work, cudaStream_t s) {
-  EpiPart e{T1, Isyn, pts, b.N, b.n_in, b.n_out, b.m0, b.tau};
+  EpiPart e{T1, Isyn, g0tab, b.N, b.n_in, b.n_out, b.m0};
   tc_gemm(4 * b.n_out, 4 * b.n_in, K, A, lda, sA, B, 4 * b.n_in, sB, e, b.n_units, S, work,
           b.status, s);
 }
@@ -449,43 +528,41 @@ void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long lon
 // rows). Each class is one GEMM: rows (pair, element) gathered from I^m, K = orders,
 // columns = azimuths of the cos or sin weight table.
 __constant__ int c_synth_elem[2][8] = {{0, 1, 4, 5, 10, 11, 14, 15}, {2, 3, 6, 7, 8, 9, 12, 13}};
-__constant__ double c_synth_sign[2][8] = {{1, 1, 1, 1, 1, 1, 1, 1},
-                                          {-1, -1, -1, -1, 1, 1, 1, 1}};
+__constant__ int c_synth_neg[2][8] = {{0, 0, 0, 0, 0, 0, 0, 0}, {1, 1, 1, 1, 0, 0, 0, 0}};
 
-// rows r = 8 (pair - pair0) + e, A(r, m) = Isyn[m][pair][elem(e)]; one thread per row
-__global__ void k_slice_synth_rows(int n_rows, int pair0, long long pairs_total, int M, int S,
+// rows r = 8 (pair - pair0) + e, A(r, m) = Isyn[m][pair][elem(e)]; one thread per row,
+// 8 orders per 16-byte chunk of every slice
+template <int S>
+__global__ void k_slice_synth_rows(int n_rows, int pair0, long long pairs_total, int M,
                                    int cls, const double* __restrict__ Isyn,
-                                   unsigned short* out, int* e_out) {
+                                   unsigned short* out, int* e_out, unsigned* status) {
   int mt = blockIdx.x;
   int r = threadIdx.x;
   int row = mt * TC_M + r;
   int Mp = pad_to(n_rows, TC_M), Kp = pad_to(M, TC_KB), KB = Kp / TC_KB, MT = Mp / TC_M;
-  bool valid = row < n_rows;
+  bool valid = row < n_rows, bad = false;
   size_t base_addr = 0;
   if (valid) {
     long long pair = pair0 + row / 8;
     base_addr = (size_t)pair * 16 + c_synth_elem[cls][row & 7];
   }
-  double mx = 0.0;
+  const size_t mstride = (size_t)pairs_total * 16;
+  int Em = 0;
   if (valid)
-    for (int m = 0; m < M; ++m) mx = fmax(mx, fabs(Isyn[(size_t)m * pairs_total * 16 + base_addr]));
-  int ee = 0;
-  if (mx > 0.0 && isfinite(mx)) frexp(mx, &ee);
+    for (int m = 0; m < M; ++m) Em = max(Em, exp_field(Isyn[(size_t)m * mstride + base_addr], &bad));
+  int ee = scale_exp(Em);
   if (valid) e_out[row] = ee;
-  size_t tile_elems = (size_t)TC_M * TC_KB;
-  for (int k = 0; k < Kp; ++k) {
-    double x = 0.0;
-    if (valid && k < M) x = ldexp(Isyn[(size_t)k * pairs_total * 16 + base_addr], -ee);
-    if (!isfinite(x)) x = 0.0;
-    float sl[TC_MAXS];
-    slice_value(x, S, sl);
-    int kb = k / TC_KB, kk = k - kb * TC_KB;
-    int off = swz_offset(r, kk) >> 1;
-    for (int p = 0; p < S; ++p) {
-      size_t base = ((((size_t)p) * MT + mt) * KB + kb) * tile_elems;
-      out[base + off] = (unsigned short)(__float_as_uint(sl[p]) >> 16);
-    }
+  const size_t tile_elems = (size_t)TC_M * TC_KB;
+  const size_t slice_stride = (size_t)MT * KB * tile_elems;
+  for (int k0 = 0; k0 < Kp; k0 += 8) {
+    double v[8];
+    for (int t = 0; t < 8; ++t)
+      v[t] = (valid && k0 + t < M) ? Isyn[(size_t)(k0 + t) * mstride + base_addr] : 0.0;
+    int kb = k0 / TC_KB;
+    size_t base = ((size_t)mt * KB + kb) * tile_elems;
+    put_chunk<S>(v, ee, out + base + (swz_offset(r, k0 - kb * TC_KB) >> 1), slice_stride);
   }
+  if (bad) atomicOr(status, ST_NONFINITE);
 }
 
 template <typename T>
@@ -496,7 +573,7 @@ struct EpiSynth {
   __device__ void operator()(int, int i, int j, double v) const {
     long long pair = pair0 + i / 8;
     int e = i & 7;
-    double w = c_synth_sign[cls][e] * v;
+    double w = c_synth_neg[cls][e] ? -v : v;
     if (!isfinite(w)) atomicOr(status, ST_NONFINITE);
     out[((size_t)pair * n_phi + j) * 16 + c_synth_elem[cls][e]] = (T)w;
   }
@@ -523,8 +600,13 @@ void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, con
     int* fb = (int*)(w + L.a_bytes + L.b_bytes + L.e_bytes);
     int smem = tc_smem_bytes(S);
     for (int cls = 0; cls < 2; ++cls) {
-      k_slice_synth_rows<<<L.MT, TC_M, 0, s>>>(rows, pair0, pairs_total, M, S, cls, Isyn, As, ea);
-      k_slice_cols<<<dim3(L.NT, 1), 512, 0, s>>>(n_phi, M, S, cls ? ws : wc, n_phi, 0, Bs, fb);
+#define VRTE_SLICE_SYN(SS)                                                                 \
+  k_slice_synth_rows<SS><<<L.MT, TC_M, 0, s>>>(rows, pair0, pairs_total, M, cls, Isyn, As, ea, \
+                                               status);                                      \
+  k_slice_cols<SS><<<dim3(L.NT, 1), 512, 0, s>>>(n_phi, M, cls ? ws : wc, n_phi, 0, Bs, fb,   \
+                                                 status)
+      VRTE_SLICE_DISPATCH(S, VRTE_SLICE_SYN)
+#undef VRTE_SLICE_SYN
       if (out_dtype == VRTE_OUT_F64) {
         EpiSynth<double> e{(double*)out, pair0, n_phi, cls, status};
         cudaFuncSetAttribute(k_tc_gemm<EpiSynth<double>>,

@@ -79,6 +79,7 @@ struct vrte_plan {
   int2* rlist = nullptr;
   int kdir = 0;  // extra K of the direct term in the mixed form (4 L_max)
   double* Isyn = nullptr;  // [M_max][n_in][n_out][16]
+  double* g0tab = nullptr;  // [n_out][n_in] depth factors of the current layer
   // host-API staging
   double* d_coef_stage = nullptr;
   size_t coef_stage_bytes = 0;
@@ -278,7 +279,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   cudaMemGetInfo(&free_b, &total_b);
   // the order radiances must fit; the per-order workspace takes at most 35% of what is
   // left (capped at 48 GiB) so that the caller's output table still fits beside it
-  size_t need_fixed = isyn * sizeof(double) + ((size_t)64 << 20);
+  size_t need_fixed = (isyn + (size_t)p->n_in * p->n_out) * sizeof(double) + ((size_t)64 << 20);
   if (need_fixed >= free_b) return VRTE_ERR_OOM;
   size_t budget = std::min((size_t)(0.35 * (double)(free_b - need_fixed)), (size_t)48 << 30);
   size_t units = budget / (per_unit * sizeof(double));
@@ -302,7 +303,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   VRTE_ALLOC(Pb, U * n * R) VRTE_ALLOC(Rb, U * n * R) VRTE_ALLOC(Wv, U * n * R) VRTE_ALLOC(Yv, U * n * R) VRTE_ALLOC(Es, U * n * R)
   VRTE_ALLOC(SD, U * (2 * n + kd) * R) VRTE_ALLOC(RHS, U * 2 * n * R) VRTE_ALLOC(C, U * 2 * n * R)
   VRTE_ALLOC(Upm, U * Ro * (2 * n + kd)) VRTE_ALLOC(P1, U * Ro * n) VRTE_ALLOC(P2, U * Ro * n) VRTE_ALLOC(Hhat, U * Ro * 2 * n)
-  VRTE_ALLOC(T1, U * Ro * R)
+  VRTE_ALLOC(T1, U * Ro * R) VRTE_ALLOC(g0tab, (size_t)p->n_in * p->n_out)
   VRTE_ALLOC(FY, U * n * n) VRTE_ALLOC(mode_res, U) VRTE_ALLOC(mode_flag, U)
   VRTE_ALLOC(Bm, U * 4 * n * n) VRTE_ALLOC(Hb, U * 4 * n * n) VRTE_ALLOC(Zb, U * 4 * n * n)
   VRTE_ALLOC(Vb, U * 4 * n * n) VRTE_ALLOC(Xb, U * 4 * n * n)
@@ -340,10 +341,11 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
     const int P = N + p->n_in + p->n_out;
     const double* coef = coeffs + (size_t)lb * p->desc.n_coef_max * 6;
     {
-      StageScope sc(p, ST_TABLES, s, 2, 0.0, 0.0);
+      StageScope sc(p, ST_TABLES, s, 3, 0.0, 0.0);
       launch_gauss_nodes(N, p->d_mu_nodes, p->d_w_nodes, p->d_status, s);
       launch_interface(N, p->n_in, p->n_out, ly.n_interface, p->d_mu_nodes, p->d_mu_in,
                        p->d_mu_out, p->d_pts, p->d_min4, p->d_mout4, p->d_rtop4, s);
+      launch_depth_table(N, p->n_in, p->n_out, ly.tau, p->d_pts, p->g0tab, s);
     }
     for (int m0 = 0; m0 < Meff; m0 += p->chunk) {
       const int U = std::min(p->chunk, Meff - m0);
@@ -459,13 +461,13 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         gemm(Ro, R, 2 * n, p->Hhat, 2 * n, 2 * Ron, p->C, R, 2 * nR, mixed ? 0.0 : 1.0, p->T1, R,
              (long long)Ro * R);
         if (mixed) {
-          tc_gemm_part(ob, 2 * n + kdir, p->Upm, ldU, sU_part, p->SD, ob.sSD, p->T1, p->d_pts,
+          tc_gemm_part(ob, 2 * n + kdir, p->Upm, ldU, sU_part, p->SD, ob.sSD, p->T1, p->g0tab,
                        p->Isyn, kSlices, p->tcw, s);
           refine_columns(ob, 2 * n + kdir, p->Kinv, p->RHS, p->C, p->Hhat, p->Upm, p->SD,
-                         p->d_pts, kSliceEps, kRefineTol, p->rscratch, p->rcount, p->rlist,
+                         p->g0tab, kSliceEps, kRefineTol, p->rscratch, p->rcount, p->rlist,
                          U * p->n_in, p->Isyn, s);
         } else
-          dgemm_part_epilogue(ob, p->Upm, p->SD, p->T1, p->d_pts, p->Isyn, s);
+          dgemm_part_epilogue(ob, p->Upm, p->SD, p->T1, p->g0tab, p->Isyn, s);
       }
     }
     char* outb = (char*)d_brdf + (size_t)lb * table * esz;

@@ -35,22 +35,25 @@ struct OrderBatch {
   long long sSD;       // unit stride of [s; d; direct beams] (2n R, or (2n + 4L) R when mixed)
 };
 
+// Depth integral of exp(-t/mu0) exp(-t/mu_o) / mu_o over the layer (Eq. 38, Q term).
+__host__ __device__ inline double depth_factor(double tau, double mu_o, double mu0) {
+  double xs = 1.0 / mu_o + 1.0 / mu0;
+  return -expm1(-tau * xs) / (mu_o * xs);
+}
+
 // Reconstruction epilogue (row i = 4o + a: outgoing o, exiting component a; column
 // j = 4k + s: incident k, basis s): Isyn[m][k][o][a][s] = T1[i][j] + g0(o, k) acc with
-// g0 the depth integral of exp(-t/mu0) exp(-t/mu_o) / mu_o over the layer.
+// g0 = depth_factor from the per-layer table g0tab[o][k].
 struct EpiPart {
   const double* T1;
   double* Isyn;
-  const double* pts;
+  const double* g0tab;
   int N, n_in, n_out, m0;
-  double tau;
   __device__ void operator()(int u, int i, int j, double acc) const {
     int R = 4 * n_in;
     int o = i >> 2, a = i & 3, k = j >> 2, s = j & 3;
-    double mu_o = pts[N + n_in + o], mu0 = pts[N + k];
-    double xs = 1.0 / mu_o + 1.0 / mu0;
-    double g0 = -expm1(-tau * xs) / (mu_o * xs);
-    double v = T1[(size_t)u * (4 * n_out) * R + (size_t)i * R + j] + g0 * acc;
+    double g0 = g0tab[(size_t)o * n_in + k];
+    double v = fma(g0, acc, T1[(size_t)u * (4 * n_out) * R + (size_t)i * R + j]);
     size_t dst = (((size_t)(m0 + u) * n_in + k) * n_out + o) * 16 + 4 * a + s;
     Isyn[dst] = v;
   }
@@ -82,6 +85,9 @@ void launch_assemble_direct(const OrderBatch& b, const double* p, const double* 
 // Direct (once-scattered) term as a contraction over (l, component): writes
 // Adir = M_out P_l(mu_o) B_l into columns 2n.. of the [U+ | U- | Adir] rows and
 // Bdir = (omega/2pi) (-1)^(l-m) D P_l(mu0) D b_k into rows 2n.. of [s; d; Bdir].
+// Depth factors g0tab[o][k] = depth_factor(tau, mu_o, mu0_k) of one layer.
+void launch_depth_table(int N, int n_in, int n_out, double tau, const double* pts, double* g0tab,
+                        cudaStream_t s);
 void launch_direct_operators(const OrderBatch& b, const double* p, const double* r,
                              const double* t, const double* min4, const double* mout4,
                              double* Uext, double* SDext, cudaStream_t s);
@@ -93,7 +99,7 @@ void dgemm_batched(int M, int N, int K, double alpha, const double* A, int lda, 
                    long long sC, int batch, cudaStream_t s);
 // Reconstruction epilogue: Isyn[m][k][o][a][s] = T1[ro][rc] + g0(o, k) * (A @ B)[ro][rc]
 void dgemm_part_epilogue(const OrderBatch& b, const double* A, const double* B, const double* T1,
-                         const double* pts, double* Isyn, cudaStream_t s);
+                         const double* g0tab, double* Isyn, cudaStream_t s);
 void batched_inverse(int n, double* A, double* Ainv, int batch, unsigned* status, cudaStream_t s);
 void batched_eigen(int n, const double* A, double* H, double* Z, double* V, double* X,
                    double* lam_re, double* lam_im, double* scale, int batch, unsigned* status,
@@ -115,13 +121,13 @@ void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, 
                    int ldb, long long sB, double beta, double* C, int ldc, long long sC,
                    int batch, int S, void* work, unsigned* status, cudaStream_t s);
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
-                  const double* B, long long sB, const double* T1, const double* pts,
+                  const double* B, long long sB, const double* T1, const double* g0tab,
                   double* Isyn, int S, void* work, cudaStream_t s);
 // Mixed form: flags (order, incident) column blocks whose sliced reconstruction error
 // bound eps K max|row| max|column| exceeds tol |I_00| and recomputes them in FP64.
 void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
                     const double* C, const double* Hhat, const double* Uext, const double* SD,
-                    const double* pts, double eps, double tol, double* scratch, int* counters,
+                    const double* g0tab, double eps, double tol, double* scratch, int* counters,
                     int2* list, int cap, double* Isyn, cudaStream_t s);
 size_t refine_scratch_doubles(int U, int n_in, int n_out);
 // Synthesis of the order radiances on the tensor cores, in blocks of incident cosines.
