@@ -265,7 +265,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   const int S = kSlices;
   size_t tc_unit = 0;
   if (mixed) {
-    size_t c[3] = {tc_workspace_bytes((int)(2 * n), (int)R, (int)(2 * n), 1, S),
+    size_t c[4] = {tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
+                   tc_workspace_bytes((int)(2 * n), (int)R, (int)(2 * n), 1, S),
                    tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n), 1, S),
                    tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n + kd), 1, S)};
     for (size_t v : c) tc_unit = std::max(tc_unit, v);
@@ -278,10 +279,10 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
   // the order radiances must fit; the per-order workspace takes at most 35% of what is
-  // left (capped at 48 GiB) so that the caller's output table still fits beside it
+  // left (capped at 96 GiB) so that the caller's output table still fits beside it
   size_t need_fixed = (isyn + (size_t)p->n_in * p->n_out) * sizeof(double) + ((size_t)64 << 20);
   if (need_fixed >= free_b) return VRTE_ERR_OOM;
-  size_t budget = std::min((size_t)(0.35 * (double)(free_b - need_fixed)), (size_t)48 << 30);
+  size_t budget = std::min((size_t)(0.35 * (double)(free_b - need_fixed)), (size_t)96 << 30);
   size_t units = budget / (per_unit * sizeof(double));
   units = std::max<size_t>(1, std::min<size_t>(units, (size_t)Mx));
   p->chunk = (int)units;
@@ -414,18 +415,19 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         batched_inverse(n, p->X, p->Xinv, U, p->d_status, s);
       }
       {
-        StageScope sc(p, ST_PARTICULAR, s, 9,
+        StageScope sc(p, ST_PARTICULAR, s, 5 + 4 * gl,
                       72.0 * N * p->n_in * lsum + 8.0 * dn * dn * dR * dU,
                       8.0 * 10 * dn * dR * dU);
         launch_assemble_beam(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_min4, p->Pb, p->Rb, s);
-        // FP64 in both forms: near a resonance mu0 ~ 1/kappa_j the eigenbasis solve
-        // amplifies rounding by 1/(kappa_j^2 - mu0^-2), and the homogeneous part cancels it
-        dgemm_batched(n, R, n, 1.0, p->F, n, nn, p->Pb, R, nR, 0.0, p->Wv, R, nR, U, s);
+        // near a resonance mu0 ~ 1/kappa_j the eigenbasis solve amplifies rounding by
+        // 1/(kappa_j^2 - mu0^-2) and the homogeneous part cancels it: the mixed form
+        // keeps FP64-level products here (7 slices, ~2e-15 per term)
+        gemm(n, R, n, p->F, n, nn, p->Pb, R, nR, 0.0, p->Wv, R, nR);
         launch_particular_rhs(ob, p->Wv, p->Rb, p->d_pts, p->Wv, s);
-        dgemm_batched(n, R, n, 1.0, p->Xinv, n, nn, p->Wv, R, nR, 0.0, p->Yv, R, nR, U, s);
+        gemm(n, R, n, p->Xinv, n, nn, p->Wv, R, nR, 0.0, p->Yv, R, nR);
         launch_eigen_scale(ob, p->lam_re, p->lam_im, p->d_pts, p->Yv, s);
-        dgemm_batched(n, R, n, 1.0, p->X, n, nn, p->Yv, R, nR, 0.0, p->SD, R, ob.sSD, U, s);
-        dgemm_batched(n, R, n, 1.0, p->E, n, nn, p->SD, R, ob.sSD, 0.0, p->Es, R, nR, U, s);
+        gemm(n, R, n, p->X, n, nn, p->Yv, R, nR, 0.0, p->SD, R, ob.sSD);
+        gemm(n, R, n, p->E, n, nn, p->SD, R, ob.sSD, 0.0, p->Es, R, nR);
         launch_particular_sd(ob, p->Pb, p->Es, p->d_pts, p->SD, s);
         launch_bc_rhs(ob, p->SD, nullptr, p->d_rtop4, p->d_pts, p->RHS, s);
       }
