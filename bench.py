@@ -5,8 +5,11 @@ A step is one full BRDF solve (every pipeline stage: tables, assembly, eigen,
 boundary, particular, reconstruction, synthesis) of the N = 64, M = L = 128 Mie
 layer with a 1024 x 1024 x 360 table. Prints one JSON line (rank 0).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
   python bench.py --impl reference ...     # the FP64 CPU oracle on a bounded sample
+
+The headline is the mixed form (tensor-core contractions); the FP64 form is timed
+beside it on the same layer ("fp64_plain", "speedup_vs_fp64_plain").
 """
 from __future__ import annotations
 
@@ -201,15 +204,85 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_form(vr, torch, cfg, ly, precision, dev, steps, warmup, dist):
+    """Warm up, then time `steps` full solves with CUDA events on the solve stream."""
+    L = ly["n_coef"]
+    plan = vr.Plan(cfg["mu_in"], cfg["mu_out"], cfg["dphi"], ly["n_nodes"], ly["n_orders"], L, 1,
+                   precision, profile=True)
+    coef = vr.pack_coefficients([ly])
+    plan.set_layers([ly], torch.from_numpy(coef).to(dev))
+    out = torch.empty(plan.table_shape, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        plan.solve(out, stream)
+    st = plan.status()
+    if st != 0:
+        raise SystemExit(f"solve failed: {vr.STATUS_NAMES.get(st, st)}")
+    plan.reset_stages()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xFF)                       # evict L2 between timed steps
+        ev[i][0].record(stream)
+        plan.solve(out, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = plan.status()
+    if st != 0:
+        raise SystemExit(f"solve failed: {vr.STATUS_NAMES.get(st, st)}")
+    stages = plan.stages()
+    refined = plan.debug_buffer("refined")[0] if precision == vr.VRTE_MIXED else 0.0
+    del out, flush
+    return plan, coef, total_ms, clk, stages, refined
+
+
+def roofline(stages, clk, precision_name):
+    """Roofline of the dominant stage: tensor-core stages against the measured sustained
+    BF16 peak (their issued slice products), FP64 stages against the derived FP64 peak."""
+    pk, pk_src = peaks()
+    dom = max(stages, key=lambda s: s["ms"])
+    sec = dom["ms"] / 1000.0 if dom["ms"] > 0 else float("nan")
+    if dom.get("tc_flops", 0.0) > 0.0:
+        peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0)))
+        achieved = dom["tc_flops"] / sec / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel_stage": dom["name"],
+                "launches": dom["launches"],
+                "fp64_equivalent_tflops": dom["flops"] / sec / 1e12,
+                "peak_source": f"bf16_tflops_sustained ({pk_src}); achieved counts the BF16 "
+                               "slice products the sliced FP64 contractions issue"}
+    peak = fp64_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+    achieved = dom["flops"] / sec / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None, "kernel_stage": dom["name"],
+            "launches": dom["launches"],
+            "peak_source": "derived FP64: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x max SM clock"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64-plain", action="store_true",
+                    help="skip timing the FP64 form beside the mixed form")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -229,77 +302,31 @@ def main():
     torch.cuda.set_device(dev)
 
     cfg, ly = build_workload()
-    prec = vr.VRTE_FP64 if args.precision == "fp64" else vr.VRTE_MIXED
     L = ly["n_coef"]
-    plan = vr.Plan(cfg["mu_in"], cfg["mu_out"], cfg["dphi"], ly["n_nodes"], ly["n_orders"], L, 1,
-                   prec, profile=True)
-    coef = vr.pack_coefficients([ly])
-    d_coef = torch.from_numpy(coef).to(dev)
-    plan.set_layers([ly], d_coef)
-    out = torch.empty(plan.table_shape, dtype=torch.float32, device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
     M_eff = min(ly["n_orders"], L)
+    prec = vr.VRTE_FP64 if args.precision == "fp64" else vr.VRTE_MIXED
 
-    for _ in range(args.warmup):
-        plan.solve(out, stream)
-    st = plan.status()
-    if st != 0:
-        raise SystemExit(f"solve failed: {vr.STATUS_NAMES.get(st, st)}")
-    plan.reset_stages()
+    fp64_plain = None
+    if args.precision == "mixed" and not args.no_fp64_plain:
+        plan64, _, ms64, clk64, stages64, _ = time_form(vr, torch, cfg, ly, vr.VRTE_FP64, dev,
+                                                        args.steps, args.warmup, dist)
+        plan64.close()
+        torch.cuda.empty_cache()
+        fp64_plain = {"ms_per_step": ms64 / args.steps,
+                      "value": world * M_eff * args.steps / (ms64 / 1000.0), "unit": UNIT,
+                      "clocks": clk64,
+                      "stages_ms": {s["name"]: round(s["ms"] / args.steps, 2) for s in stages64}}
 
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(torch.cuda.current_device())
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)                       # evict L2 between timed steps
-        ev[i][0].record(stream)
-        plan.solve(out, stream)
-        ev[i][1].record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(ms))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    st = plan.status()
-    stages = plan.stages()
-    if st != 0:
-        raise SystemExit(f"solve failed: {vr.STATUS_NAMES.get(st, st)}")
+    plan, coef, total_ms, clk, stages, refined = time_form(vr, torch, cfg, ly, prec, dev,
+                                                           args.steps, args.warmup, dist)
     ms_per_step = total_ms / args.steps
     value = world * M_eff * args.steps / (total_ms / 1000.0)
-
-    # dominant stage -> roofline
-    pk, pk_src = peaks()
-    dom = max(stages, key=lambda s: s["ms"])
-    sm_for_peak = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    if args.precision == "fp64" or dom["name"] in ("eigen", "modes_bc_inverse", "assemble"):
-        peak = fp64_peak_tflops(pk.get("sm_max_mhz", 2070.0))
-        achieved = dom["flops"] / (dom["ms"] / 1000.0) / 1e12 if dom["ms"] > 0 else 0.0
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel_stage": dom["name"],
-                "launches": dom["launches"],
-                "peak_source": "derived FP64: 152 SMs x 4 FLOP/clk x max SM clock (of derived)"}
-        if dom["name"] == "synthesis" and args.precision != "fp64":
-            pass
-    else:
-        peak = pk["hbm_gbs"]
-        achieved = dom["bytes"] / (dom["ms"] / 1000.0) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel_stage": dom["name"],
-                "peak_source": f"hbm_gbs ({pk_src})"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "mixed",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else
+        "f64 via 7 bf16 slices (tcgen05) + f64",
         "data": "synthetic",
         "config": {"workload": cfg["name"], "N": ly["n_nodes"], "M": ly["n_orders"], "L": L,
                    "n_in": int(cfg["mu_in"].size), "n_out": int(cfg["mu_out"].size),
@@ -310,12 +337,18 @@ def main():
         "full_brdf_seconds": ms_per_step / 1000.0,
         "clocks": clk,
         "gpu_launches": int(sum(s["launches"] for s in stages)),
-        "roofline": roof,
+        "roofline": roofline(stages, clk, args.precision),
         "stages": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()}
                    for s in stages],
     }
+    if args.precision == "mixed":
+        line["refined_fp64_column_blocks_per_step"] = refined
+    if fp64_plain:
+        line["fp64_plain"] = fp64_plain
+        line["speedup_vs_fp64_plain"] = fp64_plain["ms_per_step"] / ms_per_step
 
     if not args.no_e2e:
+        stream = torch.cuda.current_stream(dev)
         h_coef = torch.from_numpy(coef).pin_memory()
         h_out = torch.empty(plan.table_shape, dtype=torch.float32, pin_memory=True)
         plan.solve_host(h_coef, h_out, stream)     # warm the staging buffers

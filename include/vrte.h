@@ -93,6 +93,8 @@ typedef struct {
   double ms;            /* summed event time (0 without VRTE_FLAG_PROFILE) */
   double flops;         /* algorithmic floating-point operations of the stage */
   double bytes;         /* algorithmic HBM bytes of the stage (compulsory traffic) */
+  double tc_flops;      /* mixed form: BF16 tensor-core FLOPs the sliced products issue
+                           (S (S + 1) / 2 slice products per FP64 product), else 0 */
 } vrte_stage_stat;
 
 /* Per-layer parameters (host). */

@@ -50,7 +50,8 @@ VRTE_FLAG_PROFILE = 1
 
 class StageStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("launches", ctypes.c_longlong),
-                ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("flops", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("tc_flops", ctypes.c_double)]
 
 
 class Layer(ctypes.Structure):
@@ -189,7 +190,8 @@ class Plan:
         arr = (StageStat * 32)()
         n = self.lib.vrte_profile_stages(self.handle, arr, 32)
         return [dict(name=arr[i].name.decode(), launches=int(arr[i].launches), ms=arr[i].ms,
-                     flops=arr[i].flops, bytes=arr[i].bytes) for i in range(max(n, 0))]
+                     flops=arr[i].flops, bytes=arr[i].bytes, tc_flops=arr[i].tc_flops)
+                for i in range(max(n, 0))]
 
     def debug_buffer(self, name):
         """float64 copy of an internal buffer of the most recent order batch."""

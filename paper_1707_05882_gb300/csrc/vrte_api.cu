@@ -136,6 +136,7 @@ struct StageScope {
     p->stats[st].bytes += bytes;
     if (p->profile && cudaEventCreate(&e0) == cudaSuccess) cudaEventRecord(e0, s);
   }
+  void tensor_flops(double f) { p->stats[st].tc_flops += f; }
   ~StageScope() {
     if (!e0) return;
     cudaEvent_t e1;
@@ -265,7 +266,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   const int S = kSlices;
   size_t tc_unit = 0;
   if (mixed) {
-    size_t c[4] = {tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
+    size_t c[5] = {tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
+                   tc_workspace_bytes((int)Ro, (int)n, (int)n, 1, S),
                    tc_workspace_bytes((int)(2 * n), (int)R, (int)(2 * n), 1, S),
                    tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n), 1, S),
                    tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n + kd), 1, S)};
@@ -365,6 +367,8 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
       const long long nn = (long long)n * n, nR = (long long)n * R, Ron = (long long)Ro * n;
       const long long sU_part = (long long)Ro * ldU;
       const int gl = mixed ? 3 : 1;  // launches per contraction
+      // BF16 FLOPs issued per FP64 multiply-add by the sliced product
+      const double tcf = mixed ? 2.0 * kSlices * (kSlices + 1) / 2 : 0.0;
       // boundary solve and reconstruction contractions: FP64 on the CUDA cores, or the
       // sliced BF16 product on the tensor cores in the mixed form
       auto gemm = [&](int M_, int N_, int K_, const double* A_, int lda_, long long sA_,
@@ -418,6 +422,7 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         StageScope sc(p, ST_PARTICULAR, s, 5 + 4 * gl,
                       72.0 * N * p->n_in * lsum + 8.0 * dn * dn * dR * dU,
                       8.0 * 10 * dn * dR * dU);
+        sc.tensor_flops(tcf * 4.0 * dn * dn * dR * dU);
         launch_assemble_beam(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_min4, p->Pb, p->Rb, s);
         // near a resonance mu0 ~ 1/kappa_j the eigenbasis solve amplifies rounding by
         // 1/(kappa_j^2 - mu0^-2) and the homogeneous part cancels it: the mixed form
@@ -434,18 +439,18 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
       {
         StageScope sc(p, ST_BC_SOLVE, s, gl, 2.0 * 4 * dn * dn * dR * dU,
                       8.0 * (4 * dn * dn + 4 * dn * dR) * dU);
+        sc.tensor_flops(tcf * 4.0 * dn * dn * dR * dU);
         gemm(2 * n, R, 2 * n, p->Kinv, 2 * n, 4 * nn, p->RHS, R, 2 * nR, 0.0, p->C, R, 2 * nR);
       }
       {
-        StageScope sc(p, ST_RECON_OPS, s, 4 + (mixed ? 2 : 1),
+        StageScope sc(p, ST_RECON_OPS, s, 2 + 2 * gl + (mixed ? 2 : 1),
                       72.0 * N * p->n_out * lsum + 4.0 * dRo * dn * dn * dU +
                           72.0 * p->n_in * p->n_out * lsum,
                       8.0 * (6 * dRo * dn + dRo * dR) * dU);
         launch_assemble_U(ob, p->gp, p->gr, p->gt, p->d_w_nodes, p->d_mout4, p->Upm, s);
-        // FP64 in both forms: the refinement of resonant columns reuses Hhat
-        dgemm_batched(Ro, n, n, 1.0, p->Upm, ldU, sU_part, p->X, n, nn, 0.0, p->P1, n, Ron, U, s);
-        dgemm_batched(Ro, n, n, 1.0, p->Upm + n, ldU, sU_part, p->Y, n, nn, 0.0, p->P2, n, Ron,
-                      U, s);
+        sc.tensor_flops(tcf * 2.0 * dRo * dn * dn * dU);
+        gemm(Ro, n, n, p->Upm, ldU, sU_part, p->X, n, nn, 0.0, p->P1, n, Ron);
+        gemm(Ro, n, n, p->Upm + n, ldU, sU_part, p->Y, n, nn, 0.0, p->P2, n, Ron);
         launch_build_Hhat(ob, p->P1, p->P2, p->lam_re, p->lam_im, p->d_pts, p->Hhat, s);
         if (mixed)
           launch_direct_operators(ob, p->gp, p->gr, p->gt, p->d_min4, p->d_mout4, p->Upm, p->SD,
@@ -458,6 +463,7 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         // two contractions [4 n_out x 2n] x [2n x 4 n_in] per order
         StageScope sc(p, ST_RECON_GEMM, s, mixed ? 2 * gl + 6 : 2, 2.0 * 2 * dRo * dR * 2 * dn * dU,
                       8.0 * (2 * dRo * 2 * dn + 2 * 2 * dn * dR + 3 * dRo * dR) * dU);
+        sc.tensor_flops(tcf * dRo * dR * (2.0 * dn + (2.0 * dn + kdir)) * dU);
         // FP64: T1 holds the direct term and gains the homogeneous part; mixed: T1 is the
         // homogeneous part and the direct term is the tail of the particular contraction
         gemm(Ro, R, 2 * n, p->Hhat, 2 * n, 2 * Ron, p->C, R, 2 * nR, mixed ? 0.0 : 1.0, p->T1, R,
@@ -478,6 +484,10 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
       StageScope sc(p, ST_SYNTHESIS, s,
                     mixed ? 6 * ((p->n_in + kSynthBlock - 1) / kSynthBlock) : 1, 2.0 * table * Meff,
                     (double)table * esz + (double)Meff * p->n_in * p->n_out * 16 * 8);
+      if (mixed) {
+        const int Ss = kSlicesSynth;
+        sc.tensor_flops(2.0 * Ss * (Ss + 1) / 2 * 16.0 * p->n_in * p->n_out * p->n_phi * Meff);
+      }
       if (mixed)
         tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, p->Isyn, p->d_wc, p->d_ws, outb, out_dtype,
                      kSlicesSynth, kSynthBlock, p->tcw, p->d_status, s);
