@@ -91,9 +91,14 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def build_workload():
-    from vrte_inputs import make_config
+def build_workload(grid=None):
+    """The N=64, M=L=128 Mie layer; `grid` = (n_in, n_out, n_phi) replaces the 1024 x 1024
+    x 360 table by a smaller one (profiling captures only; never a bench line)."""
+    from vrte_inputs import angle_grids, make_config
     cfg = make_config(WORKLOAD)
+    if grid:
+        cfg["mu_in"], cfg["mu_out"], cfg["dphi"] = angle_grids(*grid)
+        cfg["name"] = cfg["name"].rsplit("-", 2)[0] + "-%dx%dx%d-n1.5" % tuple(grid)
     ly = dict(cfg["layers"][0])
     ly["n_coef"] = ly["coef"].shape[0]
     return cfg, ly
@@ -283,6 +288,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64-plain", action="store_true",
                     help="skip timing the FP64 form beside the mixed form")
+    ap.add_argument("--grid", type=int, nargs=3, metavar=("N_IN", "N_OUT", "N_PHI"),
+                    help="smaller table for profiling captures (not the benchmark workload)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -301,7 +308,7 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    cfg, ly = build_workload()
+    cfg, ly = build_workload(args.grid)
     L = ly["n_coef"]
     M_eff = min(ly["n_orders"], L)
     prec = vr.VRTE_FP64 if args.precision == "fp64" else vr.VRTE_MIXED
