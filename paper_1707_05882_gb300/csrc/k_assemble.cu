@@ -315,4 +315,126 @@ void launch_depth_table(int N, int n_in, int n_out, double tau, const double* pt
   k_depth_table<<<dim3((n_in + 127) / 128, n_out), 128, 0, s>>>(N, n_in, n_out, tau, pts, g0tab);
 }
 
+// ------------------------------------------------------------------ mixed-form operators
+// S+-(x, y) = sum_l [P_l(x) B_l] [(I +- (-1)^(l-m) D) P_l(y)] is a contraction over the 4L
+// pairs (l, component e). The mixed form builds the two factors and lets the sliced
+// tensor-core GEMM do the sum (Sec. 3.A-3.D):
+//   U+-            = Adir (M_out P(mu_o) B, from k_direct_A) x RU+-,
+//   RU+-[(l,e)][(j,c)] = (omega/4) alpha_j ((I +- (-1)^(l-m) D) P_l(mu_j))_ec,
+//   beam p = Ln x Rb+,  beam r = Ln x Rb-,
+//   Ln[(i,a)][(l,e)]   = (omega/2pi) / mu_i (P_l(mu_i) B_l)_ae,
+//   Rb+[(l,e)][(k,s)]  = ((I + (-1)^(l-m) D) P_l(mu0_k) D b_k)_es,
+//   Rb-[(l,e)][(k,s)]  = -((I - (-1)^(l-m) D) P_l(mu0_k) D b_k)_es.
+// All factors vanish for l < m.
+__device__ inline void p_matrix(double p, double r, double t, double P[4][4]) {
+  for (int a = 0; a < 4; ++a)
+    for (int c = 0; c < 4; ++c) P[a][c] = 0.0;
+  P[0][0] = p; P[1][1] = r; P[1][2] = -t; P[2][1] = -t; P[2][2] = r; P[3][3] = p;
+}
+
+__global__ void k_left_nodes(OrderBatch b, const double* pt, const double* rt, const double* tt,
+                             const double* mu_nodes, double* Ln) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.y, u = blockIdx.z;
+  if (l >= b.L) return;
+  int m = b.m0 + u;
+  const int ld = 4 * b.L;
+  double* row0 = Ln + (size_t)u * b.n * ld + (size_t)(4 * i) * ld + 4 * l;
+  double V[4][4];
+  for (int a = 0; a < 4; ++a)
+    for (int e = 0; e < 4; ++e) V[a][e] = 0.0;
+  if (l >= m) {
+    size_t idx = (size_t)u * b.L * b.P + (size_t)l * b.P + i;
+    double P[4][4];
+    p_matrix(pt[idx], rt[idx], tt[idx], P);
+    const double* cf = b.coef + 6 * l;
+    double Bm[4][4] = {{cf[0], cf[4], 0.0, 0.0}, {cf[4], cf[1], 0.0, 0.0},
+                       {0.0, 0.0, cf[2], cf[5]}, {0.0, 0.0, -cf[5], cf[3]}};
+    double f = b.omega / (2.0 * kPi) / mu_nodes[i];
+    for (int a = 0; a < 4; ++a)
+      for (int e = 0; e < 4; ++e) {
+        double v = 0.0;
+        for (int c = 0; c < 4; ++c) v += P[a][c] * Bm[c][e];
+        V[a][e] = f * v;
+      }
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int e = 0; e < 4; ++e) row0[(size_t)a * ld + e] = V[a][e];
+}
+
+__global__ void k_right_nodes(OrderBatch b, const double* pt, const double* rt, const double* tt,
+                              const double* w_nodes, double* RU) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int l = blockIdx.y, u = blockIdx.z;
+  if (j >= b.N) return;
+  int m = b.m0 + u;
+  const int ld = 2 * b.n;
+  double* base = RU + (size_t)u * (4 * b.L) * ld + (size_t)(4 * l) * ld;
+  double Vp[4][4], Vm[4][4];
+  for (int e = 0; e < 4; ++e)
+    for (int c = 0; c < 4; ++c) Vp[e][c] = Vm[e][c] = 0.0;
+  if (l >= m) {
+    size_t idx = (size_t)u * b.L * b.P + (size_t)l * b.P + j;
+    double P[4][4];
+    p_matrix(pt[idx], rt[idx], tt[idx], P);
+    double par = ((l - m) & 1) ? -1.0 : 1.0;
+    double f = 0.25 * b.omega * w_nodes[j];
+    for (int e = 0; e < 4; ++e) {
+      double de = par * (e < 2 ? 1.0 : -1.0);  // (-1)^(l-m) D_ee
+      for (int c = 0; c < 4; ++c) {
+        Vp[e][c] = f * (1.0 + de) * P[e][c];
+        Vm[e][c] = f * (1.0 - de) * P[e][c];
+      }
+    }
+  }
+  for (int e = 0; e < 4; ++e)
+    for (int c = 0; c < 4; ++c) {
+      base[(size_t)e * ld + 4 * j + c] = Vp[e][c];
+      base[(size_t)e * ld + b.n + 4 * j + c] = Vm[e][c];
+    }
+}
+
+__global__ void k_right_beam(OrderBatch b, const double* pt, const double* rt, const double* tt,
+                             const double* min4, double* Rp, double* Rm) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int l = blockIdx.y, u = blockIdx.z;
+  if (k >= b.n_in) return;
+  int m = b.m0 + u;
+  const int R = 4 * b.n_in;
+  size_t off = (size_t)u * (4 * b.L) * R + (size_t)(4 * l) * R + 4 * k;
+  double Vp[4][4], Vm[4][4];
+  for (int e = 0; e < 4; ++e)
+    for (int s = 0; s < 4; ++s) Vp[e][s] = Vm[e][s] = 0.0;
+  if (l >= m) {
+    size_t idx = (size_t)u * b.L * b.P + (size_t)l * b.P + b.N + k;
+    double P[4][4];
+    p_matrix(pt[idx], rt[idx], tt[idx], P);
+    double par = ((l - m) & 1) ? -1.0 : 1.0;
+    const double* q = min4 + 4 * k;
+    for (int e = 0; e < 4; ++e) {
+      double de = par * (e < 2 ? 1.0 : -1.0);
+      for (int s = 0; s < 4; ++s) {
+        double v = 0.0;  // (P D b)_es
+        for (int c = 0; c < 4; ++c) v += P[e][c] * (c < 2 ? 1.0 : -1.0) * blk(q, c, s);
+        Vp[e][s] = (1.0 + de) * v;
+        Vm[e][s] = -(1.0 - de) * v;
+      }
+    }
+  }
+  for (int e = 0; e < 4; ++e)
+    for (int s = 0; s < 4; ++s) {
+      Rp[off + (size_t)e * R + s] = Vp[e][s];
+      Rm[off + (size_t)e * R + s] = Vm[e][s];
+    }
+}
+
+void launch_mixed_operators(const OrderBatch& b, const double* p, const double* r,
+                            const double* t, const double* mu_nodes, const double* w_nodes,
+                            const double* min4, double* Ln, double* RU, double* Rp, double* Rm,
+                            cudaStream_t s) {
+  k_left_nodes<<<dim3((b.L + 63) / 64, b.N, b.n_units), 64, 0, s>>>(b, p, r, t, mu_nodes, Ln);
+  k_right_nodes<<<dim3((b.N + 63) / 64, b.L, b.n_units), 64, 0, s>>>(b, p, r, t, w_nodes, RU);
+  k_right_beam<<<dim3((b.n_in + 63) / 64, b.L, b.n_units), 64, 0, s>>>(b, p, r, t, min4, Rp, Rm);
+}
+
 }  // namespace vrte

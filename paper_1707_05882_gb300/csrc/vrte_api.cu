@@ -75,6 +75,8 @@ struct vrte_plan {
   size_t tcw_bytes = 0;
   // mixed form: FP64 refinement of ill-conditioned columns (maxima, counters, work list)
   double* rscratch = nullptr;
+  // mixed form: factors of the (l, component) contractions for U+- and the beam vectors
+  double *Ln = nullptr, *RU = nullptr, *Rbp = nullptr, *Rbm = nullptr;
   int* rcount = nullptr;  // [flagged in this batch, flagged in this solve]
   int2* rlist = nullptr;
   int kdir = 0;  // extra K of the direct term in the mixed form (4 L_max)
@@ -266,7 +268,9 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   const int S = kSlices;
   size_t tc_unit = 0;
   if (mixed) {
-    size_t c[5] = {tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
+    size_t c[7] = {tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
+                   tc_workspace_bytes((int)n, (int)R, (int)kd, 1, S),
+                   tc_workspace_bytes((int)Ro, (int)(2 * n), (int)kd, 1, S),
                    tc_workspace_bytes((int)Ro, (int)n, (int)n, 1, S),
                    tc_workspace_bytes((int)(2 * n), (int)R, (int)(2 * n), 1, S),
                    tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n), 1, S),
@@ -276,7 +280,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   size_t per_unit = 3 * (size_t)Lx * P + 10 * n * n + 3 * n + 8 * n * n + 5 * n * R +
                     (4 * n + kd) * R + 2 * n * R + 4 * Ro * n + Ro * (2 * n + kd) + Ro * R + n * n +
                     1 + 5 * 4 * n * n + 3 * 2 * n + 1 + (tc_unit + 7) / 8 +
-                    (mixed ? refine_scratch_doubles(1, p->n_in, p->n_out) + p->n_in : 0);
+                    (mixed ? refine_scratch_doubles(1, p->n_in, p->n_out) + p->n_in : 0) +
+                    n * kd + kd * 2 * n + 2 * kd * R;
   size_t isyn = (size_t)Mx * p->n_in * p->n_out * 16;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
@@ -311,6 +316,10 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   VRTE_ALLOC(Bm, U * 4 * n * n) VRTE_ALLOC(Hb, U * 4 * n * n) VRTE_ALLOC(Zb, U * 4 * n * n)
   VRTE_ALLOC(Vb, U * 4 * n * n) VRTE_ALLOC(Xb, U * 4 * n * n)
   VRTE_ALLOC(kb_re, U * 2 * n) VRTE_ALLOC(kb_im, U * 2 * n) VRTE_ALLOC(balb, U * 2 * n)
+  if (mixed) {
+    VRTE_ALLOC(Ln, U * n * kd) VRTE_ALLOC(RU, U * kd * 2 * n)
+    VRTE_ALLOC(Rbp, U * kd * R) VRTE_ALLOC(Rbm, U * kd * R)
+  }
   if (mixed) {
     size_t synth = tc_synthesis_workspace(Mx, p->n_in, p->n_out, p->n_phi, kSlicesSynth,
                                           kSynthBlock);
@@ -419,11 +428,21 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         batched_inverse(n, p->X, p->Xinv, U, p->d_status, s);
       }
       {
-        StageScope sc(p, ST_PARTICULAR, s, 5 + 4 * gl,
+        StageScope sc(p, ST_PARTICULAR, s, mixed ? 7 + 6 * gl : 9,
                       72.0 * N * p->n_in * lsum + 8.0 * dn * dn * dR * dU,
                       8.0 * 10 * dn * dR * dU);
-        sc.tensor_flops(tcf * 4.0 * dn * dn * dR * dU);
-        launch_assemble_beam(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_min4, p->Pb, p->Rb, s);
+        sc.tensor_flops(tcf * (4.0 * dn + 2.0 * kdir) * dn * dR * dU);
+        if (mixed) {
+          // beam vectors as contractions over (l, component) on the tensor cores
+          launch_mixed_operators(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_w_nodes, p->d_min4,
+                                 p->Ln, p->RU, p->Rbp, p->Rbm, s);
+          const long long sL = (long long)n * kdir, sB = (long long)kdir * R;
+          gemm(n, R, kdir, p->Ln, kdir, sL, p->Rbp, R, sB, 0.0, p->Pb, R, nR);
+          gemm(n, R, kdir, p->Ln, kdir, sL, p->Rbm, R, sB, 0.0, p->Rb, R, nR);
+        } else {
+          launch_assemble_beam(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_min4, p->Pb, p->Rb,
+                               s);
+        }
         // near a resonance mu0 ~ 1/kappa_j the eigenbasis solve amplifies rounding by
         // 1/(kappa_j^2 - mu0^-2) and the homogeneous part cancels it: the mixed form
         // keeps FP64-level products here (7 slices, ~2e-15 per term)
@@ -443,19 +462,24 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         gemm(2 * n, R, 2 * n, p->Kinv, 2 * n, 4 * nn, p->RHS, R, 2 * nR, 0.0, p->C, R, 2 * nR);
       }
       {
-        StageScope sc(p, ST_RECON_OPS, s, 2 + 2 * gl + (mixed ? 2 : 1),
+        StageScope sc(p, ST_RECON_OPS, s, mixed ? 3 + 3 * gl : 5,
                       72.0 * N * p->n_out * lsum + 4.0 * dRo * dn * dn * dU +
                           72.0 * p->n_in * p->n_out * lsum,
                       8.0 * (6 * dRo * dn + dRo * dR) * dU);
-        launch_assemble_U(ob, p->gp, p->gr, p->gt, p->d_w_nodes, p->d_mout4, p->Upm, s);
-        sc.tensor_flops(tcf * 2.0 * dRo * dn * dn * dU);
+        sc.tensor_flops(tcf * 2.0 * dRo * dn * (dn + kdir) * dU);
+        if (mixed) {
+          // U+- = [M_out P(mu_o) B] x RU+-: the direct operator's columns are the left factor
+          launch_direct_operators(ob, p->gp, p->gr, p->gt, p->d_min4, p->d_mout4, p->Upm, p->SD,
+                                  s);
+          gemm(Ro, 2 * n, kdir, p->Upm + 2 * n, ldU, sU_part, p->RU, 2 * n,
+               (long long)kdir * 2 * n, 0.0, p->Upm, ldU, sU_part);
+        } else {
+          launch_assemble_U(ob, p->gp, p->gr, p->gt, p->d_w_nodes, p->d_mout4, p->Upm, s);
+        }
         gemm(Ro, n, n, p->Upm, ldU, sU_part, p->X, n, nn, 0.0, p->P1, n, Ron);
         gemm(Ro, n, n, p->Upm + n, ldU, sU_part, p->Y, n, nn, 0.0, p->P2, n, Ron);
         launch_build_Hhat(ob, p->P1, p->P2, p->lam_re, p->lam_im, p->d_pts, p->Hhat, s);
-        if (mixed)
-          launch_direct_operators(ob, p->gp, p->gr, p->gt, p->d_min4, p->d_mout4, p->Upm, p->SD,
-                                  s);
-        else
+        if (!mixed)
           launch_assemble_direct(ob, p->gp, p->gr, p->gt, p->d_pts, p->d_min4, p->d_mout4, p->T1,
                                  s);
       }

@@ -88,6 +88,11 @@ void launch_assemble_direct(const OrderBatch& b, const double* p, const double* 
 // Depth factors g0tab[o][k] = depth_factor(tau, mu_o, mu0_k) of one layer.
 void launch_depth_table(int N, int n_in, int n_out, double tau, const double* pts, double* g0tab,
                         cudaStream_t s);
+// Mixed form: factors of the parity-split sums over (l, component) for U+-, beam p, r.
+void launch_mixed_operators(const OrderBatch& b, const double* p, const double* r,
+                            const double* t, const double* mu_nodes, const double* w_nodes,
+                            const double* min4, double* Ln, double* RU, double* Rp, double* Rm,
+                            cudaStream_t s);
 void launch_direct_operators(const OrderBatch& b, const double* p, const double* r,
                              const double* t, const double* min4, const double* mout4,
                              double* Uext, double* SDext, cudaStream_t s);
