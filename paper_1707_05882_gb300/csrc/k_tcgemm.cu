@@ -18,7 +18,8 @@
 // memory image of 128B-swizzled K-major tiles ([unit][slice][tile][k-block] blocks of
 // 128 x 64 or 64 x 64 BF16), so the GEMM kernel loads each tile with one bulk copy. The
 // GEMM kernel computes a 128 x 64 output tile per CTA with up to five accumulators of 64
-// columns in TMEM, two shared-memory stages while S <= 4 (one above), one thread issuing
+// columns in TMEM, as many shared-memory stages as fit (S = 7: one of 168 KB; S <= 4: two
+// or three; a 32-wide K block with two stages at S = 7 measured slower), one thread issuing
 // bulk copies and MMAs, and four warps draining TMEM in the epilogue. Every mbarrier wait
 // is bounded; on timeout the kernel records ST_TIMEOUT, waits (bounded) for its copies,
 // frees TMEM and returns.
@@ -32,19 +33,20 @@ namespace vrte {
 
 constexpr int TC_M = 128;       // output rows per CTA (MMA M)
 constexpr int TC_N = 64;        // output columns per CTA (MMA N)
-constexpr int TC_KB = 64;       // K per stage (one 128-byte swizzle atom of BF16)
+constexpr int TC_KB = 64;       // K per stage (one 128-byte swizzle row of BF16)
 constexpr int TC_MAXS = 8;      // maximum number of slices
 constexpr int TC_NACC = 5;      // TMEM accumulators: diagonals 0 .. 3 and 4 .. S-1
-constexpr int TC_STAGES = 2;    // shared-memory stages (at most)
+constexpr int TC_STAGES = 3;    // shared-memory stages (at most)
 constexpr int TC_SMEM_MAX = 227 * 1024;
 constexpr int A_TILE_BYTES = TC_M * TC_KB * 2;   // 16 KiB
 constexpr int B_TILE_BYTES = TC_N * TC_KB * 2;   // 8 KiB
 constexpr long long WAIT_LIMIT = 1ll << 22;      // polls before a wait is declared stuck
 
 __device__ __host__ inline int pad_to(int x, int m) { return (x + m - 1) / m * m; }
-// two stages of S slices of A and B tiles while they fit in shared memory, else one
+// as many stages (up to three) of S slices of A and B tiles as fit in shared memory
 __device__ __host__ inline int tc_stages(int S) {
-  return 2 * S * (A_TILE_BYTES + B_TILE_BYTES) + 1024 <= TC_SMEM_MAX ? 2 : 1;
+  int n = (TC_SMEM_MAX - 1024) / (S * (A_TILE_BYTES + B_TILE_BYTES));
+  return n < 1 ? 1 : (n > TC_STAGES ? TC_STAGES : n);
 }
 __device__ __host__ inline int tc_smem_bytes(int S) {
   return tc_stages(S) * S * (A_TILE_BYTES + B_TILE_BYTES) + 1024;
@@ -330,12 +332,12 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
       }
     };
     int issued = 0;
-    bool pending[TC_STAGES] = {false, false};
+    bool pending[TC_STAGES] = {};
     for (; issued < KB && issued < nst; ++issued) {
       issue_copies(issued, issued);
       pending[issued] = true;
     }
-    uint32_t full_phase[TC_STAGES] = {0, 0}, empty_phase[TC_STAGES] = {0, 0};
+    uint32_t full_phase[TC_STAGES] = {}, empty_phase[TC_STAGES] = {};
     unsigned written = 0;  // accumulators that hold a value (the first MMA overwrites)
     for (int kb = 0; kb < KB && ok; ++kb) {
       int s = kb % nst;
@@ -344,33 +346,39 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
       pending[s] = false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       unsigned char* st = smem + (size_t)s * stage_bytes;
+      // descriptors differ only in the start-address field (bits 0-13, 16-byte units)
+      const uint64_t abase = smem_desc_sw128(st);
+      const uint64_t bbase = smem_desc_sw128(st + S * A_TILE_BYTES);
       for (int p = 0; p < S; ++p)
         for (int q = 0; p + q < S; ++q) {
           int a = p + q < TC_NACC ? p + q : TC_NACC - 1;
           uint32_t dt = tmem + (uint32_t)(a * TC_N);
+#pragma unroll
           for (int k16 = 0; k16 < TC_KB / 16; ++k16) {
-            uint64_t ad = smem_desc_sw128(st + p * A_TILE_BYTES) + (uint64_t)(k16 * 2);
-            uint64_t bd = smem_desc_sw128(st + S * A_TILE_BYTES + q * B_TILE_BYTES) +
-                          (uint64_t)(k16 * 2);
+            uint64_t ad = abase + (uint64_t)(p * (A_TILE_BYTES >> 4) + k16 * 2);
+            uint64_t bd = bbase + (uint64_t)(q * (B_TILE_BYTES >> 4) + k16 * 2);
             uint32_t acc = (k16 == 0 && !((written >> a) & 1u)) ? 0u : 1u;
             mma_bf16(dt, ad, bd, idesc, acc);
           }
           written |= 1u << a;
         }
       mma_commit(&empty_bar[s]);
-      if (issued < KB) {
-        // reuse stage s once the MMAs that read it have completed
-        if (!mbar_wait(&empty_bar[s], empty_phase[s])) { ok = false; break; }
-        empty_phase[s] ^= 1;
-        issue_copies(issued, s);
-        pending[s] = true;
+      // refill the previous block's stage once its MMAs are done, so that the MMAs just
+      // issued keep the tensor pipe busy meanwhile (with one stage: this block's stage)
+      const int lag = nst > 1 ? 1 : 0;
+      if (kb >= lag && issued < KB) {
+        int ps = (kb - lag) % nst;
+        if (!mbar_wait(&empty_bar[ps], empty_phase[ps])) { ok = false; break; }
+        empty_phase[ps] ^= 1;
+        issue_copies(issued, ps);
+        pending[ps] = true;
         ++issued;
       }
     }
-    if (ok) {
-      mma_commit(&done_bar);
-      if (!mbar_wait(&done_bar, 0)) ok = false;
-    }
+    // all MMAs issued by this thread have completed once done_bar fires (also on the abort
+    // path, before TMEM is released)
+    mma_commit(&done_bar);
+    if (!mbar_wait(&done_bar, 0)) ok = false;
     if (!ok) {
       abort_flag = 1;
       atomicOr(status, ST_TIMEOUT);
@@ -389,43 +397,66 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
     const int i = mt * TC_M + r;
     const int erow = (i < M) ? ea[(size_t)u * Mp + i] : 0;
     for (int c0 = 0; c0 < TC_N; c0 += 16) {
-      // acc_0 .. acc_3 hold integers in units of 2^-7a: combine them exactly in an int64
-      // in units of 2^-21, then one FP64 fma adds the (rounded) fifth accumulator
-      long long I[16];
-      float r4[16];
+      uint32_t regs[TC_NACC][16];
 #pragma unroll
-      for (int t = 0; t < 16; ++t) {
-        I[t] = 0;
-        r4[t] = 0.0f;
-      }
-      for (int a = 0; a < nacc; ++a) {
-        uint32_t regs[16];
+      for (int a = 0; a < TC_NACC; ++a) {
+        if (a >= nacc) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) regs[a][t] = 0u;  // +0.0f
+          continue;
+        }
         uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * TC_N + c0);
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
             "%13,%14,%15}, [%16];\n"
-            : "=r"(regs[0]), "=r"(regs[1]), "=r"(regs[2]), "=r"(regs[3]), "=r"(regs[4]),
-              "=r"(regs[5]), "=r"(regs[6]), "=r"(regs[7]), "=r"(regs[8]), "=r"(regs[9]),
-              "=r"(regs[10]), "=r"(regs[11]), "=r"(regs[12]), "=r"(regs[13]), "=r"(regs[14]),
-              "=r"(regs[15])
+            : "=r"(regs[a][0]), "=r"(regs[a][1]), "=r"(regs[a][2]), "=r"(regs[a][3]),
+              "=r"(regs[a][4]), "=r"(regs[a][5]), "=r"(regs[a][6]), "=r"(regs[a][7]),
+              "=r"(regs[a][8]), "=r"(regs[a][9]), "=r"(regs[a][10]), "=r"(regs[a][11]),
+              "=r"(regs[a][12]), "=r"(regs[a][13]), "=r"(regs[a][14]), "=r"(regs[a][15])
             : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (a < TC_NACC - 1) {
-          const float up = (float)(1 << (7 * a));
-          const int sh = 7 * (TC_NACC - 2 - a);
-#pragma unroll
-          for (int t = 0; t < 16; ++t)
-            I[t] += (long long)__float2int_rn(__uint_as_float(regs[t]) * up) << sh;
-        } else {
-#pragma unroll
-          for (int t = 0; t < 16; ++t) r4[t] = __uint_as_float(regs[t]);
-        }
       }
-      if (i < M) {
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (i >= M) continue;
+      if constexpr (Epi::kF32) {
+        // FP32 output: an error-free FP32 sum (hi + lo) of the accumulators, largest first,
+        // rounded once; no FP64 instruction
+#pragma unroll
         for (int t = 0; t < 16; ++t) {
+          float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+          for (int a = 0; a < TC_NACC; ++a) {
+            float x = __uint_as_float(regs[a][t]);
+            float sm = hi + x, bb = sm - hi;
+            lo += (hi - (sm - bb)) + (x - bb);
+            hi = sm;
+          }
           int j = nt * TC_N + c0 + t;
           if (j < N) {
-            double w = fma((double)I[t], 0x1p-21, (double)r4[t]);
+            int E2 = erow + fb[(size_t)u * Np + j] - 12;
+            float w = hi + lo;
+            float v = (E2 > -120 && E2 < 120) ? w * __int_as_float((E2 + 127) << 23)
+                                              : ldexpf(w, E2);
+            epi.put32(u, i, j, v);
+          }
+        }
+      } else {
+        // acc_0 .. acc_3 hold integers in units of 2^-7a: combine them exactly in an int64
+        // in units of 2^-21, then one FP64 fma adds the (rounded) fifth accumulator
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          long long I = 0;
+          float r4 = 0.0f;
+#pragma unroll
+          for (int a = 0; a < TC_NACC; ++a) {
+            float x = __uint_as_float(regs[a][t]);
+            if (a < TC_NACC - 1)
+              I += (long long)__float2int_rn(x * (float)(1 << (7 * a))) << (7 * (TC_NACC - 2 - a));
+            else
+              r4 = x;
+          }
+          int j = nt * TC_N + c0 + t;
+          if (j < N) {
+            double w = fma((double)I, 0x1p-21, (double)r4);
             int E2 = erow + fb[(size_t)u * Np + j] - 12;
             // 2^E2 from its bit pattern while it is a normal number
             double v = (E2 > -1000 && E2 < 1000)
@@ -497,6 +528,7 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
 }
 
 struct TcEpiStore {
+  static constexpr bool kF32 = false;
   double* C;
   int ldc;
   long long sC;
@@ -567,6 +599,7 @@ __global__ void k_slice_synth_rows(int n_rows, int pair0, long long pairs_total,
 
 template <typename T>
 struct EpiSynth {
+  static constexpr bool kF32 = sizeof(T) == 4;
   T* out;
   int pair0, n_phi, cls;
   unsigned* status;
@@ -574,6 +607,13 @@ struct EpiSynth {
     long long pair = pair0 + i / 8;
     int e = i & 7;
     double w = c_synth_neg[cls][e] ? -v : v;
+    if (!isfinite(w)) atomicOr(status, ST_NONFINITE);
+    out[((size_t)pair * n_phi + j) * 16 + c_synth_elem[cls][e]] = (T)w;
+  }
+  __device__ void put32(int, int i, int j, float v) const {
+    long long pair = pair0 + i / 8;
+    int e = i & 7;
+    float w = c_synth_neg[cls][e] ? -v : v;
     if (!isfinite(w)) atomicOr(status, ST_NONFINITE);
     out[((size_t)pair * n_phi + j) * 16 + c_synth_elem[cls][e]] = (T)w;
   }
