@@ -123,79 +123,180 @@ void dgemm_part_epilogue(const OrderBatch& b, const double* A, const double* B, 
             b.n_units, s);
 }
 
-// In-place Gauss-Jordan inversion with partial (row) pivoting, one CTA per matrix.
-// Step k: pick the largest |W[i][k]|, i >= k; swap rows; scale the pivot row; subtract
-// multiples of it from every other row (the pivot column takes the inverse's column).
-// Row swaps are undone at the end by swapping columns in reverse order.
+// Gauss-Jordan inversion with partial (row) pivoting, blocked, one CTA per matrix.
+// The unblocked algorithm's step k picks the largest |W[i][k]|, i >= k, swaps rows,
+// scales the pivot row and subtracts multiples of it from every other row, the pivot
+// column taking the inverse's column; row swaps are undone at the end by swapping
+// columns in reverse order. Here the steps run BI columns at a time: the panel of BI
+// columns is eliminated in shared memory (recording each step's column C_c and the
+// swaps), and the other columns receive the BI steps at once. With the swaps applied
+// first, an outside column v maps to v + Z v[blk], where over the block rows
+// (pivots D, strictly lower part Lw and strictly upper part Up of C[blk])
+//   Q = (D + Lw)^-1,  Z[blk] = (I - Up) Q - I,  Z[other] = -C[other] Q,
+// a rank-BI update read from and written to global memory once per block (the
+// unblocked form reads and writes the whole matrix at every step).
 // A zero or non-finite pivot sets ST_SINGULAR (the matrix is still processed).
+constexpr int BI = 16;   // panel width
+constexpr int TJ = 32;   // column tile of the outside update
+
 __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict__ A,
                                                  double* __restrict__ Ainv, unsigned* status) {
   extern __shared__ double sh[];
-  double* colk = sh;            // [n]
-  double* rowk = sh + n;        // [n]
-  int* perm = (int*)(sh + 2 * n);
-  __shared__ double red_v[32];
-  __shared__ int red_i[32];
-  int u = blockIdx.x;
+  double* P = sh;                  // [n][BI] panel
+  double* Cb = P + (size_t)n * BI; // [n][BI] step columns, then Z
+  double* Wb = Cb + (size_t)n * BI;// [BI][TJ] block rows of a column tile
+  int* perm = (int*)(Wb + BI * TJ);
+  __shared__ double red_v[16];
+  __shared__ int red_i[16];
+  __shared__ double rk[BI];
+  __shared__ double Q[BI][BI], G[BI][BI];
+  const int u = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
   const double* Ab = A + (size_t)u * n * n;
   double* W = Ainv + (size_t)u * n * n;
-  int tid = threadIdx.x, nt = blockDim.x;
   for (size_t e = tid; e < (size_t)n * n; e += nt) W[e] = Ab[e];
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    // pivot search
-    double best = -1.0;
-    int bi = k;
-    for (int i = k + tid; i < n; i += nt) {
-      double v = fabs(W[(size_t)i * n + k]);
-      if (v > best) { best = v; bi = i; }
+  for (int k0 = 0; k0 < n; k0 += BI) {
+    const int bb = min(BI, n - k0);
+    for (int e = tid; e < n * bb; e += nt) {
+      int i = e / bb, c = e - i * bb;
+      P[i * BI + c] = W[(size_t)i * n + k0 + c];
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      double ov = __shfl_down_sync(0xffffffffu, best, off);
-      int oi = __shfl_down_sync(0xffffffffu, bi, off);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
     __syncthreads();
-    if (tid < 32) {
-      int nw = (nt + 31) >> 5;
-      best = tid < nw ? red_v[tid] : -1.0;
-      bi = tid < nw ? red_i[tid] : k;
+    // ---- panel elimination
+    for (int c = 0; c < bb; ++c) {
+      const int k = k0 + c;
+      double best = -1.0;
+      int bi = k;
+      for (int i = k + tid; i < n; i += nt) {
+        double v = fabs(P[i * BI + c]);
+        if (v > best) { best = v; bi = i; }
+      }
       for (int off = 16; off > 0; off >>= 1) {
         double ov = __shfl_down_sync(0xffffffffu, best, off);
         int oi = __shfl_down_sync(0xffffffffu, bi, off);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
-      if (tid == 0) { red_i[0] = bi; perm[k] = bi; }
+      if ((tid & 31) == 0) { red_v[tid >> 5] = best; red_i[tid >> 5] = bi; }
+      __syncthreads();
+      if (tid < 32) {
+        int nw = (nt + 31) >> 5;
+        best = tid < nw ? red_v[tid] : -1.0;
+        bi = tid < nw ? red_i[tid] : k;
+        for (int off = 16; off > 0; off >>= 1) {
+          double ov = __shfl_down_sync(0xffffffffu, best, off);
+          int oi = __shfl_down_sync(0xffffffffu, bi, off);
+          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (tid == 0) { red_i[0] = bi; perm[k] = bi; }
+      }
+      __syncthreads();
+      const int p = red_i[0];
+      if (p != k && tid < BI) {
+        // the panel row, and the recorded columns of earlier steps, follow the swap
+        double t = P[k * BI + tid];
+        P[k * BI + tid] = P[p * BI + tid];
+        P[p * BI + tid] = t;
+        if (tid < c) {
+          t = Cb[k * BI + tid];
+          Cb[k * BI + tid] = Cb[p * BI + tid];
+          Cb[p * BI + tid] = t;
+        }
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += nt) Cb[i * BI + c] = P[i * BI + c];
+      __syncthreads();
+      const double piv = P[k * BI + c];
+      if (tid == 0 && (piv == 0.0 || !isfinite(piv))) atomicOr(status, ST_SINGULAR);
+      const double pinv = 1.0 / piv;
+      if (tid < bb) rk[tid] = (tid == c) ? pinv : P[k * BI + tid] * pinv;
+      __syncthreads();
+      for (int e = tid; e < n * bb; e += nt) {
+        int i = e / bb, cc = e - i * bb;
+        if (i == k) {
+          P[i * BI + cc] = rk[cc];
+        } else {
+          double w = (cc == c) ? 0.0 : P[i * BI + cc];
+          P[i * BI + cc] = w - Cb[i * BI + c] * rk[cc];
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    int p = red_i[0];
-    if (p != k) {
-      for (int j = tid; j < n; j += nt) {
-        double t = W[(size_t)k * n + j];
-        W[(size_t)k * n + j] = W[(size_t)p * n + j];
-        W[(size_t)p * n + j] = t;
+    for (int e = tid; e < n * bb; e += nt) {
+      int i = e / bb, c = e - i * bb;
+      W[(size_t)i * n + k0 + c] = P[i * BI + c];
+    }
+    // ---- the block's swaps on the outside columns, in order
+    for (int c = 0; c < bb; ++c) {
+      const int k = k0 + c, p = perm[k];
+      if (p != k)
+        for (int j = tid; j < n; j += nt) {
+          if (j >= k0 && j < k0 + bb) continue;
+          double t = W[(size_t)k * n + j];
+          W[(size_t)k * n + j] = W[(size_t)p * n + j];
+          W[(size_t)p * n + j] = t;
+        }
+      __syncthreads();
+    }
+    // ---- Q = (D + Lw)^-1 (forward substitution per column), G = (I - Up) Q
+    if (tid < bb) {
+      const int col = tid;
+      for (int r = 0; r < bb; ++r) {
+        double acc = (r == col) ? 1.0 : 0.0;
+        for (int c2 = 0; c2 < r; ++c2) acc -= Cb[(k0 + r) * BI + c2] * Q[c2][col];
+        Q[r][col] = acc / Cb[(k0 + r) * BI + r];
       }
     }
     __syncthreads();
-    double piv = W[(size_t)k * n + k];
-    if (tid == 0 && (piv == 0.0 || !isfinite(piv))) atomicOr(status, ST_SINGULAR);
-    double pinv = 1.0 / piv;
-    for (int i = tid; i < n; i += nt) colk[i] = W[(size_t)i * n + k];
-    __syncthreads();
-    for (int j = tid; j < n; j += nt) {
-      double v = (j == k) ? pinv : W[(size_t)k * n + j] * pinv;
-      rowk[j] = v;
-      W[(size_t)k * n + j] = v;
+    if (tid < bb * bb) {
+      const int r = tid / bb, c = tid - r * bb;
+      double g = Q[r][c];
+      for (int c2 = r + 1; c2 < bb; ++c2) g -= Cb[(k0 + r) * BI + c2] * Q[c2][c];
+      G[r][c] = g;
     }
     __syncthreads();
-    for (size_t e = tid; e < (size_t)n * n; e += nt) {
-      int i = (int)(e / n), j = (int)(e - (size_t)i * n);
-      if (i == k) continue;
-      double w = (j == k) ? 0.0 : W[e];
-      W[e] = w - colk[i] * rowk[j];
+    // Z overwrites C row by row (each row only reads its own entries)
+    for (int i = tid; i < n; i += nt) {
+      double z[BI];
+      if (i >= k0 && i < k0 + bb) {
+        const int r = i - k0;
+#pragma unroll
+        for (int c = 0; c < BI; ++c) z[c] = (c < bb) ? G[r][c] - (r == c ? 1.0 : 0.0) : 0.0;
+      } else {
+        double ci[BI];
+#pragma unroll
+        for (int c = 0; c < BI; ++c) ci[c] = (c < bb) ? Cb[i * BI + c] : 0.0;
+#pragma unroll
+        for (int c = 0; c < BI; ++c) {
+          double acc = 0.0;
+#pragma unroll
+          for (int c2 = c; c2 < BI; ++c2)
+            if (c2 < bb) acc -= ci[c2] * Q[c2][c];
+          z[c] = acc;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < BI; ++c)
+        if (c < bb) Cb[i * BI + c] = z[c];
     }
     __syncthreads();
+    // ---- W[:, out] += Z W[blk, out], one tile of TJ columns at a time
+    for (int j0 = 0; j0 < n; j0 += TJ) {
+      for (int e = tid; e < bb * TJ; e += nt) {
+        int c = e / TJ, jj = e - c * TJ;
+        int j = j0 + jj;
+        Wb[c * TJ + jj] = (j < n) ? W[(size_t)(k0 + c) * n + j] : 0.0;
+      }
+      __syncthreads();
+      for (int e = tid; e < n * TJ; e += nt) {
+        int i = e / TJ, jj = e - i * TJ;
+        int j = j0 + jj;
+        if (j >= n || (j >= k0 && j < k0 + bb)) continue;
+        double acc = W[(size_t)i * n + j];
+        for (int c = 0; c < bb; ++c) acc = fma(Cb[i * BI + c], Wb[c * TJ + jj], acc);
+        W[(size_t)i * n + j] = acc;
+      }
+      __syncthreads();
+    }
   }
   for (int k = n - 1; k >= 0; --k) {
     int p = perm[k];
@@ -211,9 +312,9 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
 }
 
 void batched_inverse(int n, double* A, double* Ainv, int batch, unsigned* status, cudaStream_t s) {
-  size_t smem = 2 * n * sizeof(double) + n * sizeof(int);
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // static shared memory (reductions, Q, G) comes on top: always raise the dynamic limit
+  size_t smem = (2 * (size_t)n * BI + BI * TJ) * sizeof(double) + n * sizeof(int);
+  cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_inverse<<<batch, 512, smem, s>>>(n, A, Ainv, status);
 }
 

@@ -502,6 +502,11 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
           dgemm_part_epilogue(ob, p->Upm, p->SD, p->T1, p->g0tab, p->Isyn, s);
       }
     }
+    // a launch that could not start (resources, configuration) fails the solve here
+    if (cudaPeekAtLastError() != cudaSuccess) {
+      cudaGetLastError();
+      return VRTE_ERR_CUDA;
+    }
     char* outb = (char*)d_brdf + (size_t)lb * table * esz;
     {
       const bool mixed = p->desc.precision == VRTE_MIXED;
