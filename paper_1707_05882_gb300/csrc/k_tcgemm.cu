@@ -5,19 +5,20 @@
 // likewise every column j of B with 2^-f_j and slices b_kjq. Each slice is a 7-bit integer
 // times a power of two, which BF16 represents exactly, and every product a_ikp b_kjq is an
 // integer of magnitude <= 2^12 times 2^(-7(p+q)). Products on one diagonal d = p + q share
-// a scale, so a FP32 accumulator that collects only diagonal d sums them exactly as long
-// as the integer total stays within 2^24: diagonals 0 .. 3 (at most 4 pairs, K <= 1024)
-// get one TMEM accumulator each. The diagonals 4 .. S-1 share a fifth accumulator whose
-// FP32 rounding sits 2^-28 below the leading term (~1e-15 of it). Pairs with p + q >= S
-// are dropped. The epilogue adds the accumulators in FP64 and scales by
-//   C_ij = 2^(e_i + f_j - 12) (acc_0 + ... + acc_4),
-// so the error is the dropped slices (and the fifth accumulator's rounding): relative to
-// max|A_i| max|B_j| per term ~3e-9 at S = 4, ~3e-13 at S = 6, ~2e-15 at S = 7.
+// a scale, so a FP32 accumulator that collects them sums them exactly as long as its
+// integer total stays within 2^24, i.e. at most 4 pairs for K <= 1024: diagonals 0 .. 3
+// get one TMEM accumulator each, diagonal 4 two (3 + 2 pairs), and the diagonals
+// 5 .. S-1 share a seventh whose rounding sits 2^-35 below the leading term. Pairs with
+// p + q >= S are dropped. The epilogue combines the exact accumulators in an int64,
+// adds the last in FP64 and scales by 2^(e_i + f_j - 12):
+//   C_ij = 2^(e_i + f_j - 12) (acc_0 + ... + acc_6),
+// so the error is the slices dropped: relative to max|A_i| max|B_j| per term ~3e-9 at
+// S = 4, ~3e-13 at S = 6, ~2e-15 at S = 7.
 //
 // Data flow: `k_slice_rows` / `k_slice_cols` write the slices directly as the shared-
 // memory image of 128B-swizzled K-major tiles ([unit][slice][tile][k-block] blocks of
 // 128 x 64 or 64 x 64 BF16), so the GEMM kernel loads each tile with one bulk copy. The
-// GEMM kernel computes a 128 x 64 output tile per CTA with up to five accumulators of 64
+// GEMM kernel computes a 128 x 64 output tile per CTA with up to seven accumulators of 64
 // columns in TMEM, as many shared-memory stages as fit (S = 7: one of 168 KB; S <= 4: two
 // or three; a 32-wide K block with two stages at S = 7 measured slower), one thread issuing
 // bulk copies and MMAs, and four warps draining TMEM in the epilogue. Every mbarrier wait
@@ -35,7 +36,7 @@ constexpr int TC_M = 128;       // output rows per CTA (MMA M)
 constexpr int TC_N = 64;        // output columns per CTA (MMA N)
 constexpr int TC_KB = 64;       // K per stage (one 128-byte swizzle row of BF16)
 constexpr int TC_MAXS = 8;      // maximum number of slices
-constexpr int TC_NACC = 5;      // TMEM accumulators: diagonals 0 .. 3 and 4 .. S-1
+constexpr int TC_NACC = 7;      // TMEM accumulators (see acc_index)
 constexpr int TC_STAGES = 3;    // shared-memory stages (at most)
 constexpr int TC_SMEM_MAX = 227 * 1024;
 constexpr int A_TILE_BYTES = TC_M * TC_KB * 2;   // 16 KiB
@@ -43,6 +44,16 @@ constexpr int B_TILE_BYTES = TC_N * TC_KB * 2;   // 8 KiB
 constexpr long long WAIT_LIMIT = 1ll << 22;      // polls before a wait is declared stuck
 
 __device__ __host__ inline int pad_to(int x, int m) { return (x + m - 1) / m * m; }
+// Accumulator of slice pair (p, q): diagonals d = p + q < 4 one each; diagonal 4 split by
+// p <= 2 (3 pairs) and p >= 3 (2 pairs) so that each stays exact for K <= 1024; the
+// diagonals 5 .. S-1 share the last one (rounded; 2^-35 below the leading term).
+__device__ __host__ inline int acc_index(int p, int q) {
+  int d = p + q;
+  return d < 4 ? d : (d == 4 ? (p <= 2 ? 4 : 5) : 6);
+}
+// diagonal (scale 2^-7d) of exact accumulator a
+__device__ __host__ inline int acc_diag(int a) { return a < 4 ? a : 4; }
+__device__ __host__ inline int acc_count(int S) { return S <= 4 ? S : (S == 5 ? 6 : 7); }
 // as many stages (up to three) of S slices of A and B tiles as fit in shared memory
 __device__ __host__ inline int tc_stages(int S) {
   int n = (TC_SMEM_MAX - 1024) / (S * (A_TILE_BYTES + B_TILE_BYTES));
@@ -285,7 +296,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
   const int KB = Kp / TC_KB, MT = Mp / TC_M, NT = Np / TC_N;
   const int stage_bytes = S * (A_TILE_BYTES + B_TILE_BYTES);
   const int nst = tc_stages(S);
-  const int nacc = S < TC_NACC ? S : TC_NACC;
+  const int nacc = acc_count(S);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t ncols = (nacc * TC_N <= 128) ? 128 : (nacc * TC_N <= 256 ? 256 : 512);
 
@@ -351,7 +362,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
       const uint64_t bbase = smem_desc_sw128(st + S * A_TILE_BYTES);
       for (int p = 0; p < S; ++p)
         for (int q = 0; p + q < S; ++q) {
-          int a = p + q < TC_NACC ? p + q : TC_NACC - 1;
+          int a = acc_index(p, q);
           uint32_t dt = tmem + (uint32_t)(a * TC_N);
 #pragma unroll
           for (int k16 = 0; k16 < TC_KB / 16; ++k16) {
@@ -440,8 +451,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
           }
         }
       } else {
-        // acc_0 .. acc_3 hold integers in units of 2^-7a: combine them exactly in an int64
-        // in units of 2^-21, then one FP64 fma adds the (rounded) fifth accumulator
+        // the exact accumulators hold integers in units of 2^-7d: combine them in an int64
+        // in units of 2^-28 (|I| < 2^53), then one FP64 fma adds the rounded last one
 #pragma unroll
         for (int t = 0; t < 16; ++t) {
           long long I = 0;
@@ -449,14 +460,15 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
 #pragma unroll
           for (int a = 0; a < TC_NACC; ++a) {
             float x = __uint_as_float(regs[a][t]);
-            if (a < TC_NACC - 1)
-              I += (long long)__float2int_rn(x * (float)(1 << (7 * a))) << (7 * (TC_NACC - 2 - a));
+            if (a < TC_NACC - 1)  // exact: an integer times 2^-7d, d = acc_diag(a)
+              I += (long long)__float2int_rn(x * (float)(1 << (7 * acc_diag(a))))
+                   << (7 * (4 - acc_diag(a)));
             else
               r4 = x;
           }
           int j = nt * TC_N + c0 + t;
           if (j < N) {
-            double w = fma((double)I, 0x1p-21, (double)r4);
+            double w = fma((double)I, 0x1p-28, (double)r4);
             int E2 = erow + fb[(size_t)u * Np + j] - 12;
             // 2^E2 from its bit pattern while it is a normal number
             double v = (E2 > -1000 && E2 < 1000)

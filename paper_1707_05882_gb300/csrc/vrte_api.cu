@@ -31,10 +31,10 @@ enum Stage {
 constexpr int kSlices = 7;
 constexpr int kSlicesSynth = 5;
 constexpr int kSynthBlock = 64;
-// per-term error of the 7-slice product relative to max|A_i| max|B_j| (measured ~2e-15),
+// per-term error of the 7-slice product relative to max|A_i| max|B_j| (measured 6e-16),
 // and the bound, relative to the order-0 I_00 of the same (incident, outgoing) pair,
 // above which a column block is recomputed in FP64
-constexpr double kSliceEps = 1e-14;
+constexpr double kSliceEps = 2e-15;
 constexpr double kRefineTol = 1e-7;
 
 const char* kStageNames[kStages] = {"tables", "assemble", "eigen", "modes_bc_inverse",
