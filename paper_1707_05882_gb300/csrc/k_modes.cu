@@ -266,23 +266,19 @@ void launch_bc_rhs(const OrderBatch& b, const double* SD, const double* d, const
 __global__ void k_build_Hhat(int N, int n, int n_in, int n_out, double tau, const double* P1,
                              const double* P2, const double* lam_re, const double* lam_im,
                              const double* pts, double* Hhat) {
+  // one thread per (outgoing o, mode j): the depth factors depend on (o, j) only and are
+  // applied to the four rows 4o .. 4o+3
   int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int ro = blockIdx.y, u = blockIdx.z;
+  int o = blockIdx.y, u = blockIdx.z;
   if (j >= n) return;
   const double* lr = lam_re + (size_t)u * n;
   const double* li = lam_im + (size_t)u * n;
   if (li[j] < 0.0) return;
   bool cplx = li[j] > 0.0;
-  double mu = pts[N + n_in + (ro >> 2)];
+  double mu = pts[N + n_in + o];
   double x = 1.0 / mu;
   int Ro = 4 * n_out;
-  size_t rowp = (size_t)u * Ro * n + (size_t)ro * n;
-  double* Hb = Hhat + (size_t)u * Ro * 2 * n + (size_t)ro * 2 * n;
   cd kap = kappa_of(lr, li, j);
-  cd p1{P1[rowp + j], cplx ? P1[rowp + j + 1] : 0.0};
-  cd p2{P2[rowp + j], cplx ? P2[rowp + j + 1] : 0.0};
-  cd hD{p1.r - p2.r, p1.i - p2.i};
-  cd hG{p1.r + p2.r, p1.i + p2.i};
   // decaying
   cd a{x + kap.r, kap.i};
   cd em = cexpm1v(cd{-a.r * tau, -a.i * tau});
@@ -300,19 +296,28 @@ __global__ void k_build_Hhat(int N, int n, int n_in, int n_out, double tau, cons
     cd ek = cexpv(cd{-kap.r * tau, -kap.i * tau});
     gG = cdivv(cd{ex - ek.r, -ek.i}, cd{mu * bb.r, mu * bb.i});
   }
-  cd vD = cmul(hD, gD), vG = cmul(hG, gG);
-  Hb[j] = vD.r;
-  Hb[n + j] = vG.r;
-  if (cplx) {
-    Hb[j + 1] = vD.i;
-    Hb[n + j + 1] = vG.i;
+  for (int ar = 0; ar < 4; ++ar) {
+    const int ro = 4 * o + ar;
+    size_t rowp = (size_t)u * Ro * n + (size_t)ro * n;
+    double* Hb = Hhat + (size_t)u * Ro * 2 * n + (size_t)ro * 2 * n;
+    cd p1{P1[rowp + j], cplx ? P1[rowp + j + 1] : 0.0};
+    cd p2{P2[rowp + j], cplx ? P2[rowp + j + 1] : 0.0};
+    cd hD{p1.r - p2.r, p1.i - p2.i};
+    cd hG{p1.r + p2.r, p1.i + p2.i};
+    cd vD = cmul(hD, gD), vG = cmul(hG, gG);
+    Hb[j] = vD.r;
+    Hb[n + j] = vG.r;
+    if (cplx) {
+      Hb[j + 1] = vD.i;
+      Hb[n + j + 1] = vG.i;
+    }
   }
 }
 
 void launch_build_Hhat(const OrderBatch& b, const double* P1, const double* P2,
                        const double* lam_re, const double* lam_im, const double* pts,
                        double* Hhat, cudaStream_t s) {
-  dim3 grid((b.n + 127) / 128, 4 * b.n_out, b.n_units);
+  dim3 grid((b.n + 127) / 128, b.n_out, b.n_units);
   k_build_Hhat<<<grid, 128, 0, s>>>(b.N, b.n, b.n_in, b.n_out, b.tau, P1, P2, lam_re, lam_im, pts,
                                     Hhat);
 }
