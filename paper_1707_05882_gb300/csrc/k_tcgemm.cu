@@ -283,7 +283,10 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
                                                  const int* __restrict__ ea,
                                                  const unsigned short* __restrict__ Bs,
                                                  const int* __restrict__ fb, Epi epi,
-                                                 unsigned* status) {
+                                                 unsigned* status, int batch) {
+  // Persistent: CTA b takes tiles b, b + gridDim.x, ... (tile t = mt + MT (nt + NT u)).
+  // Thread 0 issues bulk copies and MMAs; once a tile's MMAs are done it starts the next
+  // tile's first copies, which land while the four warps drain TMEM.
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
   __shared__ uint32_t tmem_slot;
@@ -291,9 +294,9 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
   // align the dynamic region to 1024 bytes (128B swizzle atoms)
   unsigned char* smem =
       (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int u = blockIdx.z, mt = blockIdx.x, nt = blockIdx.y;
   const int Mp = pad_to(M, TC_M), Np = pad_to(N, TC_N), Kp = pad_to(K, TC_KB);
   const int KB = Kp / TC_KB, MT = Mp / TC_M, NT = Np / TC_N;
+  const int tiles = MT * NT * batch;
   const int stage_bytes = S * (A_TILE_BYTES + B_TILE_BYTES);
   const int nst = tc_stages(S);
   const int nacc = acc_count(S);
@@ -326,83 +329,92 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
   const size_t a_unit = (size_t)S * MT * KB * (A_TILE_BYTES / 2);
   const size_t b_unit = (size_t)S * NT * KB * (B_TILE_BYTES / 2);
 
-  if (threadIdx.x == 0) {
-    bool ok = true;
-    auto issue_copies = [&](int kb, int s) {
-      unsigned char* st = smem + (size_t)s * stage_bytes;
-      mbar_expect_tx(&full_bar[s], (unsigned)stage_bytes);
-      for (int p = 0; p < S; ++p) {
-        const unsigned short* src =
-            As + (size_t)u * a_unit + (((size_t)p * MT + mt) * KB + kb) * (A_TILE_BYTES / 2);
-        bulk_g2s(st + p * A_TILE_BYTES, src, A_TILE_BYTES, &full_bar[s]);
-      }
-      for (int q = 0; q < S; ++q) {
-        const unsigned short* src =
-            Bs + (size_t)u * b_unit + (((size_t)q * NT + nt) * KB + kb) * (B_TILE_BYTES / 2);
-        bulk_g2s(st + S * A_TILE_BYTES + q * B_TILE_BYTES, src, B_TILE_BYTES, &full_bar[s]);
-      }
-    };
-    int issued = 0;
-    bool pending[TC_STAGES] = {};
-    for (; issued < KB && issued < nst; ++issued) {
-      issue_copies(issued, issued);
-      pending[issued] = true;
+  // thread-0 pipeline state (barrier phases carry over from tile to tile)
+  bool pending[TC_STAGES] = {};
+  bool unwaited[TC_STAGES] = {};
+  uint32_t full_phase[TC_STAGES] = {}, empty_phase[TC_STAGES] = {}, done_phase = 0;
+  int issued = 0;
+  auto issue_copies = [&](int t, int kb, int s) {
+    const int tmt = t % MT, tnt = (t / MT) % NT, tu = t / (MT * NT);
+    unsigned char* st = smem + (size_t)s * stage_bytes;
+    mbar_expect_tx(&full_bar[s], (unsigned)stage_bytes);
+    for (int p = 0; p < S; ++p) {
+      const unsigned short* src =
+          As + (size_t)tu * a_unit + (((size_t)p * MT + tmt) * KB + kb) * (A_TILE_BYTES / 2);
+      bulk_g2s(st + p * A_TILE_BYTES, src, A_TILE_BYTES, &full_bar[s]);
     }
-    uint32_t full_phase[TC_STAGES] = {}, empty_phase[TC_STAGES] = {};
-    unsigned written = 0;  // accumulators that hold a value (the first MMA overwrites)
-    for (int kb = 0; kb < KB && ok; ++kb) {
-      int s = kb % nst;
-      if (!mbar_wait(&full_bar[s], full_phase[s])) { ok = false; break; }
-      full_phase[s] ^= 1;
-      pending[s] = false;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      unsigned char* st = smem + (size_t)s * stage_bytes;
-      // descriptors differ only in the start-address field (bits 0-13, 16-byte units)
-      const uint64_t abase = smem_desc_sw128(st);
-      const uint64_t bbase = smem_desc_sw128(st + S * A_TILE_BYTES);
-      for (int p = 0; p < S; ++p)
-        for (int q = 0; p + q < S; ++q) {
-          int a = acc_index(p, q);
-          uint32_t dt = tmem + (uint32_t)(a * TC_N);
-#pragma unroll
-          for (int k16 = 0; k16 < TC_KB / 16; ++k16) {
-            uint64_t ad = abase + (uint64_t)(p * (A_TILE_BYTES >> 4) + k16 * 2);
-            uint64_t bd = bbase + (uint64_t)(q * (B_TILE_BYTES >> 4) + k16 * 2);
-            uint32_t acc = (k16 == 0 && !((written >> a) & 1u)) ? 0u : 1u;
-            mma_bf16(dt, ad, bd, idesc, acc);
-          }
-          written |= 1u << a;
-        }
-      mma_commit(&empty_bar[s]);
-      // refill the previous block's stage once its MMAs are done, so that the MMAs just
-      // issued keep the tensor pipe busy meanwhile (with one stage: this block's stage)
-      const int lag = nst > 1 ? 1 : 0;
-      if (kb >= lag && issued < KB) {
-        int ps = (kb - lag) % nst;
-        if (!mbar_wait(&empty_bar[ps], empty_phase[ps])) { ok = false; break; }
-        empty_phase[ps] ^= 1;
-        issue_copies(issued, ps);
-        pending[ps] = true;
-        ++issued;
-      }
+    for (int q = 0; q < S; ++q) {
+      const unsigned short* src =
+          Bs + (size_t)tu * b_unit + (((size_t)q * NT + tnt) * KB + kb) * (B_TILE_BYTES / 2);
+      bulk_g2s(st + S * A_TILE_BYTES + q * B_TILE_BYTES, src, B_TILE_BYTES, &full_bar[s]);
     }
-    // all MMAs issued by this thread have completed once done_bar fires (also on the abort
-    // path, before TMEM is released)
-    mma_commit(&done_bar);
-    if (!mbar_wait(&done_bar, 0)) ok = false;
-    if (!ok) {
-      abort_flag = 1;
-      atomicOr(status, ST_TIMEOUT);
-      // let the copies still in flight land before the CTA exits (bounded)
-      for (int s = 0; s < TC_STAGES; ++s)
-        if (pending[s]) mbar_wait(&full_bar[s], full_phase[s]);
-    }
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    pending[s] = true;
+  };
+  auto prologue = [&](int t) {
+    for (issued = 0; issued < KB && issued < nst; ++issued) issue_copies(t, issued, issued);
+  };
+  if (threadIdx.x == 0 && (int)blockIdx.x < tiles) prologue(blockIdx.x);
 
-  if (!abort_flag) {
+  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int mt = tile % MT, nt = (tile / MT) % NT, u = tile / (MT * NT);
+    if (threadIdx.x == 0) {
+      bool ok = true;
+      unsigned written = 0;  // accumulators that hold a value (the first MMA overwrites)
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        int s = kb % nst;
+        if (!mbar_wait(&full_bar[s], full_phase[s])) { ok = false; break; }
+        full_phase[s] ^= 1;
+        pending[s] = false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        unsigned char* st = smem + (size_t)s * stage_bytes;
+        // descriptors differ only in the start-address field (bits 0-13, 16-byte units)
+        const uint64_t abase = smem_desc_sw128(st);
+        const uint64_t bbase = smem_desc_sw128(st + S * A_TILE_BYTES);
+        for (int p = 0; p < S; ++p)
+          for (int q = 0; p + q < S; ++q) {
+            int a = acc_index(p, q);
+            uint32_t dt = tmem + (uint32_t)(a * TC_N);
+#pragma unroll
+            for (int k16 = 0; k16 < TC_KB / 16; ++k16) {
+              uint64_t ad = abase + (uint64_t)(p * (A_TILE_BYTES >> 4) + k16 * 2);
+              uint64_t bd = bbase + (uint64_t)(q * (B_TILE_BYTES >> 4) + k16 * 2);
+              uint32_t acc = (k16 == 0 && !((written >> a) & 1u)) ? 0u : 1u;
+              mma_bf16(dt, ad, bd, idesc, acc);
+            }
+            written |= 1u << a;
+          }
+        mma_commit(&empty_bar[s]);
+        unwaited[s] = true;
+        // refill the previous block's stage once its MMAs are done, so that the MMAs just
+        // issued keep the tensor pipe busy meanwhile (with one stage: this block's stage)
+        const int lag = nst > 1 ? 1 : 0;
+        if (kb >= lag && issued < KB) {
+          int ps = (kb - lag) % nst;
+          if (!mbar_wait(&empty_bar[ps], empty_phase[ps])) { ok = false; break; }
+          empty_phase[ps] ^= 1;
+          unwaited[ps] = false;
+          issue_copies(tile, issued, ps);
+          ++issued;
+        }
+      }
+      // every MMA issued so far has completed once done_bar fires (also before an abort)
+      mma_commit(&done_bar);
+      if (!mbar_wait(&done_bar, done_phase)) ok = false;
+      done_phase ^= 1;
+      // the stage releases not waited for have completed too: keep the phases in step
+      for (int s2 = 0; s2 < TC_STAGES; ++s2)
+        if (unwaited[s2]) { empty_phase[s2] ^= 1; unwaited[s2] = false; }
+      if (ok && tile + (int)gridDim.x < tiles) prologue(tile + gridDim.x);
+      if (!ok) {
+        abort_flag = 1;
+        atomicOr(status, ST_TIMEOUT);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (abort_flag) break;
+
     // epilogue: warp w drains TMEM lanes 32w..32w+31 (output rows), 16 columns at a time
     const int r = warp * 32 + lane;
     const int i = mt * TC_M + r;
@@ -479,6 +491,15 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
         }
       }
     }
+    // TMEM is free for the next tile's MMAs once every warp has read it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  }
+  if (threadIdx.x == 0 && abort_flag) {
+    // let the copies still in flight land before the CTA exits (bounded)
+    for (int s = 0; s < TC_STAGES; ++s)
+      if (pending[s]) mbar_wait(&full_bar[s], full_phase[s]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -488,6 +509,18 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
                  : "memory");
 }
 
+
+// one persistent CTA per SM (each holds up to 512 TMEM columns and most of shared memory)
+static int tc_grid(long long tiles) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  return (int)std::min<long long>(tiles, sms);
+}
 
 struct TcLayout {
   int Mp, Np, Kp, MT, NT, KB;
@@ -535,8 +568,8 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
 #undef VRTE_SLICE_AB
   int smem = tc_smem_bytes(S);
   cudaFuncSetAttribute(k_tc_gemm<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_tc_gemm<Epi><<<dim3(L.MT, L.NT, batch), 128, smem, s>>>(M, N, K, S, As, ea, Bs, fb, epi,
-                                                              status);
+  k_tc_gemm<Epi><<<tc_grid((long long)L.MT * L.NT * batch), 128, smem, s>>>(
+      M, N, K, S, As, ea, Bs, fb, epi, status, batch);
 }
 
 struct TcEpiStore {
@@ -663,14 +696,14 @@ void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, con
         EpiSynth<double> e{(double*)out, pair0, n_phi, cls, status};
         cudaFuncSetAttribute(k_tc_gemm<EpiSynth<double>>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_tc_gemm<EpiSynth<double>><<<dim3(L.MT, L.NT, 1), 128, smem, s>>>(rows, n_phi, M, S, As,
-                                                                         ea, Bs, fb, e, status);
+        k_tc_gemm<EpiSynth<double>><<<tc_grid((long long)L.MT * L.NT), 128, smem, s>>>(
+            rows, n_phi, M, S, As, ea, Bs, fb, e, status, 1);
       } else {
         EpiSynth<float> e{(float*)out, pair0, n_phi, cls, status};
         cudaFuncSetAttribute(k_tc_gemm<EpiSynth<float>>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_tc_gemm<EpiSynth<float>><<<dim3(L.MT, L.NT, 1), 128, smem, s>>>(rows, n_phi, M, S, As,
-                                                                        ea, Bs, fb, e, status);
+        k_tc_gemm<EpiSynth<float>><<<tc_grid((long long)L.MT * L.NT), 128, smem, s>>>(
+            rows, n_phi, M, S, As, ea, Bs, fb, e, status, 1);
       }
     }
   }
