@@ -599,6 +599,28 @@ void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long lon
           b.status, s);
 }
 
+// First half of a reconstruction contraction too deep for one exact accumulation
+// (K > 1024): T1[u][i][j] += g0(o, k) acc, the second half then goes through EpiPart.
+struct EpiPartAccum {
+  static constexpr bool kF32 = false;
+  double* T1;
+  const double* g0tab;
+  int n_in, n_out;
+  __device__ void operator()(int u, int i, int j, double acc) const {
+    int R = 4 * n_in;
+    double* t = T1 + (size_t)u * (4 * n_out) * R + (size_t)i * R + j;
+    *t = fma(g0tab[(size_t)(i >> 2) * n_in + (j >> 2)], acc, *t);
+  }
+};
+
+void tc_gemm_part_accum(const OrderBatch& b, int K, const double* A, int lda, long long sA,
+                        const double* B, long long sB, double* T1, const double* g0tab, int S,
+                        void* work, cudaStream_t s) {
+  EpiPartAccum e{T1, g0tab, b.n_in, b.n_out};
+  tc_gemm(4 * b.n_out, 4 * b.n_in, K, A, lda, sA, B, 4 * b.n_in, sB, e, b.n_units, S, work,
+          b.status, s);
+}
+
 // ------------------------------------------------------------------ synthesis
 // The 16 Mueller elements split into two classes by their Fourier factor (Eq. 7):
 // cos for (IQ, IQ) and (UV, UV), sin for the off-diagonal blocks (+ for UV rows, - for IQ

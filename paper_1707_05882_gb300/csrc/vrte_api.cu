@@ -243,10 +243,9 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
         l.n_nodes < 1 || l.n_nodes > p->desc.n_nodes_max || l.n_orders < 1 ||
         l.n_orders > p->desc.n_orders_max || l.n_coef < 1 || l.n_coef > p->desc.n_coef_max)
       return VRTE_ERR_INVALID_ARG;
-    // the mixed form folds the direct term into the particular contraction: K = 2n + 4L
-    // must stay within the exact-accumulation limit of the sliced tensor-core GEMM
-    if (p->desc.precision == VRTE_MIXED && 8 * l.n_nodes + 4 * l.n_coef > 1024)
-      return VRTE_ERR_UNSUPPORTED;
+    // the mixed form contracts over the 4L (l, component) pairs with the sliced
+    // tensor-core GEMM, whose exact accumulation holds for K <= 1024
+    if (p->desc.precision == VRTE_MIXED && 4 * l.n_coef > 1024) return VRTE_ERR_UNSUPPORTED;
   }
   cudaDeviceSynchronize();
   free_workspace(p, kPlanAllocs);
@@ -485,7 +484,8 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
       }
       {
         // two contractions [4 n_out x 2n] x [2n x 4 n_in] per order
-        StageScope sc(p, ST_RECON_GEMM, s, mixed ? 2 * gl + 6 : 2, 2.0 * 2 * dRo * dR * 2 * dn * dU,
+        StageScope sc(p, ST_RECON_GEMM, s,
+                      mixed ? (2 * n + kdir <= 1024 ? 2 : 3) * gl + 6 : 2, 2.0 * 2 * dRo * dR * 2 * dn * dU,
                       8.0 * (2 * dRo * 2 * dn + 2 * 2 * dn * dR + 3 * dRo * dR) * dU);
         sc.tensor_flops(tcf * dRo * dR * (2.0 * dn + (2.0 * dn + kdir)) * dU);
         // FP64: T1 holds the direct term and gains the homogeneous part; mixed: T1 is the
@@ -493,8 +493,16 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         gemm(Ro, R, 2 * n, p->Hhat, 2 * n, 2 * Ron, p->C, R, 2 * nR, mixed ? 0.0 : 1.0, p->T1, R,
              (long long)Ro * R);
         if (mixed) {
-          tc_gemm_part(ob, 2 * n + kdir, p->Upm, ldU, sU_part, p->SD, ob.sSD, p->T1, p->g0tab,
-                       p->Isyn, kSlices, p->tcw, s);
+          if (2 * n + kdir <= 1024) {
+            tc_gemm_part(ob, 2 * n + kdir, p->Upm, ldU, sU_part, p->SD, ob.sSD, p->T1,
+                         p->g0tab, p->Isyn, kSlices, p->tcw, s);
+          } else {
+            // too deep for one exact accumulation: [U+ U-][s; d] into T1, then the direct part
+            tc_gemm_part_accum(ob, 2 * n, p->Upm, ldU, sU_part, p->SD, ob.sSD, p->T1, p->g0tab,
+                               kSlices, p->tcw, s);
+            tc_gemm_part(ob, kdir, p->Upm + 2 * n, ldU, sU_part, p->SD + (size_t)2 * n * R,
+                         ob.sSD, p->T1, p->g0tab, p->Isyn, kSlices, p->tcw, s);
+          }
           refine_columns(ob, 2 * n + kdir, p->Kinv, p->RHS, p->C, p->Hhat, p->Upm, p->SD,
                          p->g0tab, kSliceEps, kRefineTol, p->rscratch, p->rcount, p->rlist,
                          U * p->n_in, p->Isyn, s);

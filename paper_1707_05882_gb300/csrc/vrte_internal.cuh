@@ -136,6 +136,10 @@ void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const do
                     const double* g0tab, double eps, double tol, double* scratch, int* counters,
                     int2* list, int cap, double* Isyn, cudaStream_t s);
 size_t refine_scratch_doubles(int U, int n_in, int n_out);
+// T1 += g0 (A @ B): the first part of a reconstruction contraction split in K.
+void tc_gemm_part_accum(const OrderBatch& b, int K, const double* A, int lda, long long sA,
+                        const double* B, long long sB, double* T1, const double* g0tab, int S,
+                        void* work, cudaStream_t s);
 // Synthesis of the order radiances on the tensor cores, in blocks of incident cosines.
 size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int S, int k_block);
 void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, const double* wc,

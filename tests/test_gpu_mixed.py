@@ -122,15 +122,22 @@ def test_mixed_fp32_output_rounds_the_mixed_result():
 
 
 def test_mixed_rejects_contraction_beyond_exact_limit():
-    """2 * 4N + 4L > 1024 leaves the exact-accumulation range of the sliced product."""
+    """4L > 1024 leaves the exact-accumulation range of the sliced product."""
     mu = np.array([0.5])
-    plan = vr.Plan(mu, mu, mu, 96, 200, 200, precision=vr.VRTE_MIXED)
-    coef = torch.zeros((1, 200, 6), dtype=torch.float64, device="cuda")
-    ly = dict(tau=1.0, omega=0.5, n_interface=1.0, n_nodes=96, n_orders=8, n_coef=200)
+    plan = vr.Plan(mu, mu, mu, 8, 300, 300, precision=vr.VRTE_MIXED)
+    coef = torch.zeros((1, 300, 6), dtype=torch.float64, device="cuda")
+    ly = dict(tau=1.0, omega=0.5, n_interface=1.0, n_nodes=8, n_orders=8, n_coef=300)
     with pytest.raises(vr.VrteError) as e:
         plan.set_layers([ly], coef)
     assert e.value.code == 8
     plan.close()
+
+
+def test_mixed_reconstruction_split_in_k():
+    """2 * 4N + 4L = 320 + 800 > 1024: the reconstruction contraction runs in two parts."""
+    coef = polydisperse_coefficients(1.5 + 0.001j, 25.0, 0.1, 200)
+    ly = dict(tau=2.0, omega=0.95, n_interface=1.5, n_nodes=40, n_orders=5, coef=coef)
+    check(ly, *angle_grids(7, 6, 9))
 
 
 def test_mixed_matches_fp64_form_on_the_same_plan_shape():
