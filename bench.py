@@ -254,6 +254,67 @@ def time_form(vr, torch, cfg, ly, precision, dev, steps, warmup, dist):
     return plan, coef, total_ms, clk, stages, refined
 
 
+def run_batched(args):
+    """Workload 4: 256 layers of uneven N, L, tau, omega and interface (8 materials x 32
+    wavelengths) on a 64 x 64 x 90 table each, all in one plan and one solve call per
+    step; the FP64 form is timed beside the mixed form. Prints its own JSON line."""
+    import torch
+    import paper_1707_05882_gb300 as vr
+    from vrte_inputs import make_config
+    cfg = make_config(4)
+    layers = [dict(l, n_coef=l["coef"].shape[0]) for l in cfg["layers"]]
+    coef = vr.pack_coefficients(layers)
+    dev = torch.device("cuda", 0)
+    d_coef = torch.from_numpy(coef).to(dev)
+    M_total = sum(min(l["n_orders"], l["n_coef"]) for l in layers)
+    res = {}
+    for name, prec in (("mixed", vr.VRTE_MIXED), ("fp64", vr.VRTE_FP64)):
+        if name == "fp64" and args.no_fp64_plain:
+            continue
+        plan = vr.Plan(cfg["mu_in"], cfg["mu_out"], cfg["dphi"],
+                       max(l["n_nodes"] for l in layers), max(l["n_orders"] for l in layers),
+                       coef.shape[1], len(layers), prec, profile=True)
+        plan.set_layers(layers, d_coef)
+        out = torch.empty(plan.table_shape, dtype=torch.float32, device=dev)
+        stream = torch.cuda.current_stream(dev)
+        for _ in range(args.warmup):
+            plan.solve(out, stream)
+        if plan.status() != 0:
+            raise SystemExit("batched solve failed")
+        plan.reset_stages()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(torch.cuda.current_device())
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            plan.solve(out, stream)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+        res[name] = {"ms_per_step": ms, "value": M_total / (ms / 1000.0), "clocks": clk,
+                     "stages_ms": {st["name"]: round(st["ms"] / args.steps, 2)
+                                   for st in plan.stages()},
+                     "gpu_launches": int(sum(st["launches"] for st in plan.stages())) // args.steps}
+        plan.close()
+        del out
+        torch.cuda.empty_cache()
+    line = {"metric": "Fourier-order VRTE solves/s, batched uneven layers", "unit": UNIT,
+            "value": res["mixed"]["value"], "ms_per_step": res["mixed"]["ms_per_step"],
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 via 7 bf16 slices (tcgen05) + f64",
+            "data": "synthetic",
+            "config": {"workload": cfg["name"], "layers": len(layers), "order_solves": M_total,
+                       "n_in": 64, "n_out": 64, "n_phi": 90, "out_dtype": "f32",
+                       "structure": "one plan, one vrte_solve_brdf call per step; layers run "
+                                    "one after another, all orders of a layer batched"},
+            "mixed": res["mixed"], "fp64_plain": res.get("fp64"),
+            "speedup_vs_fp64_plain": (res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]
+                                      if "fp64" in res else None)}
+    print(json.dumps(line), flush=True)
+
+
 def roofline(stages, clk, precision_name):
     """Roofline of the dominant stage: tensor-core stages against the measured sustained
     BF16 peak (their issued slice products), FP64 stages against the derived FP64 peak."""
@@ -290,9 +351,14 @@ def main():
                     help="skip timing the FP64 form beside the mixed form")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("N_IN", "N_OUT", "N_PHI"),
                     help="smaller table for profiling captures (not the benchmark workload)")
+    ap.add_argument("--workload", default="brdf", choices=["brdf", "batched"],
+                    help="brdf: the N=64, M=128 layer (the benchmark line); batched: 256 "
+                         "uneven layers, its own JSON line")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import torch
     import paper_1707_05882_gb300 as vr
