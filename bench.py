@@ -315,17 +315,24 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes per launch of a stage's dominant kernel from one ncu capture of the same
+# kernel (profiles/eigen_mie-N64-M128.md: k_eigen, 128 orders of the N = 64 layer; the
+# stage does not depend on the angular grid). Stages without a current capture: None.
+DRAM_TRAFFIC = {"eigen": 7.643186e9 + 21.738669e9}
+
+
 def roofline(stages, clk, precision_name):
     """Roofline of the dominant stage: tensor-core stages against the measured sustained
     BF16 peak (their issued slice products), FP64 stages against the derived FP64 peak."""
     pk, pk_src = peaks()
     dom = max(stages, key=lambda s: s["ms"])
+    traffic = DRAM_TRAFFIC.get(dom["name"]) if WORKLOAD == 3 else None
     sec = dom["ms"] / 1000.0 if dom["ms"] > 0 else float("nan")
     if dom.get("tc_flops", 0.0) > 0.0:
         peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0)))
         achieved = dom["tc_flops"] / sec / 1e12
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel_stage": dom["name"],
+                "frac": achieved / peak, "traffic": traffic, "kernel_stage": dom["name"],
                 "launches": dom["launches"],
                 "fp64_equivalent_tflops": dom["flops"] / sec / 1e12,
                 "peak_source": f"bf16_tflops_sustained ({pk_src}); achieved counts the BF16 "
@@ -333,7 +340,7 @@ def roofline(stages, clk, precision_name):
     peak = fp64_peak_tflops(pk.get("sm_max_mhz", 2070.0))
     achieved = dom["flops"] / sec / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None, "kernel_stage": dom["name"],
+            "frac": achieved / peak, "traffic": traffic, "kernel_stage": dom["name"],
             "launches": dom["launches"],
             "peak_source": "derived FP64: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x max SM clock"}
 

@@ -24,9 +24,9 @@ using namespace vrte;
 namespace {
 enum Stage {
   ST_TABLES, ST_ASSEMBLE, ST_EIGEN, ST_MODES, ST_PARTICULAR, ST_BC_SOLVE, ST_RECON_OPS,
-  ST_RECON_GEMM, ST_SYNTHESIS, kStages
+  ST_RECON_HOM, ST_RECON_PART, ST_REFINE, ST_SYNTHESIS, kStages
 };
-// mixed form: BF16 slices per FP64 operand (exact products, ~1e-12 relative per term) and
+// mixed form: BF16 slices per FP64 operand (exact products, ~6e-16 relative per term) and
 // incident cosines per tensor-core synthesis block
 constexpr int kSlices = 7;
 constexpr int kSlicesSynth = 5;
@@ -37,9 +37,10 @@ constexpr int kSynthBlock = 64;
 constexpr double kSliceEps = 2e-15;
 constexpr double kRefineTol = 1e-7;
 
-const char* kStageNames[kStages] = {"tables", "assemble", "eigen", "modes_bc_inverse",
-                                    "particular", "bc_solve", "recon_ops", "recon_gemm",
-                                    "synthesis"};
+const char* kStageNames[kStages] = {"tables",     "assemble",   "eigen",
+                                    "modes_bc_inverse", "particular", "bc_solve",
+                                    "recon_ops",  "recon_hom",  "recon_part",
+                                    "refine",     "synthesis"};
 }  // namespace
 
 struct vrte_plan {
@@ -483,15 +484,21 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
                                  s);
       }
       {
-        // two contractions [4 n_out x 2n] x [2n x 4 n_in] per order
-        StageScope sc(p, ST_RECON_GEMM, s,
-                      mixed ? (2 * n + kdir <= 1024 ? 2 : 3) * gl + 6 : 2, 2.0 * 2 * dRo * dR * 2 * dn * dU,
-                      8.0 * (2 * dRo * 2 * dn + 2 * 2 * dn * dR + 3 * dRo * dR) * dU);
-        sc.tensor_flops(tcf * dRo * dR * (2.0 * dn + (2.0 * dn + kdir)) * dU);
-        // FP64: T1 holds the direct term and gains the homogeneous part; mixed: T1 is the
-        // homogeneous part and the direct term is the tail of the particular contraction
+        // homogeneous part: [4 n_out x 2n] x [2n x 4 n_in] per order. FP64: T1 holds the
+        // direct term and gains the homogeneous part; mixed: T1 is the homogeneous part and
+        // the direct term is the tail of the particular contraction
+        StageScope sc(p, ST_RECON_HOM, s, gl, 2.0 * dRo * dR * 2 * dn * dU,
+                      8.0 * (dRo * 2 * dn + 2 * dn * dR + 2 * dRo * dR) * dU);
+        sc.tensor_flops(tcf * dRo * dR * 2.0 * dn * dU);
         gemm(Ro, R, 2 * n, p->Hhat, 2 * n, 2 * Ron, p->C, R, 2 * nR, mixed ? 0.0 : 1.0, p->T1, R,
              (long long)Ro * R);
+      }
+      {
+        // particular (+ direct, mixed) part with the depth factor, into I^m
+        const double kp = 2.0 * dn + kdir;
+        StageScope sc(p, ST_RECON_PART, s, mixed ? (2 * n + kdir <= 1024 ? 1 : 2) * gl : 1,
+                      2.0 * dRo * dR * kp * dU, 8.0 * (dRo * kp + kp * dR + 2 * dRo * dR) * dU);
+        sc.tensor_flops(tcf * dRo * dR * kp * dU);
         if (mixed) {
           if (2 * n + kdir <= 1024) {
             tc_gemm_part(ob, 2 * n + kdir, p->Upm, ldU, sU_part, p->SD, ob.sSD, p->T1,
@@ -503,11 +510,15 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
             tc_gemm_part(ob, kdir, p->Upm + 2 * n, ldU, sU_part, p->SD + (size_t)2 * n * R,
                          ob.sSD, p->T1, p->g0tab, p->Isyn, kSlices, p->tcw, s);
           }
-          refine_columns(ob, 2 * n + kdir, p->Kinv, p->RHS, p->C, p->Hhat, p->Upm, p->SD,
-                         p->g0tab, kSliceEps, kRefineTol, p->rscratch, p->rcount, p->rlist,
-                         U * p->n_in, p->Isyn, s);
-        } else
+        } else {
           dgemm_part_epilogue(ob, p->Upm, p->SD, p->T1, p->g0tab, p->Isyn, s);
+        }
+      }
+      if (mixed) {
+        StageScope sc(p, ST_REFINE, s, 6, 0.0, 0.0);
+        refine_columns(ob, 2 * n + kdir, p->Kinv, p->RHS, p->C, p->Hhat, p->Upm, p->SD,
+                       p->g0tab, kSliceEps, kRefineTol, p->rscratch, p->rcount, p->rlist,
+                       U * p->n_in, p->Isyn, s);
       }
     }
     // a launch that could not start (resources, configuration) fails the solve here
