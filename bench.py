@@ -255,7 +255,7 @@ def time_form(vr, torch, cfg, ly, precision, dev, steps, warmup, dist):
 
 
 def run_batched(args):
-    """Workload 4: 256 layers of uneven N, L, tau, omega and interface (8 materials x 32
+    """Batched workload: 256 layers of uneven N, L, tau, omega and interface (8 materials x 32
     wavelengths) on a 64 x 64 x 90 table each, all in one plan and one solve call per
     step; the FP64 form is timed beside the mixed form. Prints its own JSON line."""
     import torch

@@ -50,7 +50,7 @@ def check(layer, mu_in, mu_out, dphi):
     return ei, eq
 
 
-def test_mixed_config1_rayleigh():
+def test_mixed_rayleigh_N8_M3_8x8x16():
     cfg = make_config(1)
     check(cfg["layers"][0], cfg["mu_in"], cfg["mu_out"], cfg["dphi"])
 
@@ -63,7 +63,7 @@ def test_mixed_ragged_multi_tile_mie(n_if):
     check(ly, *angle_grids(17, 19, 11))
 
 
-def test_mixed_config2_full():
+def test_mixed_mie_N32_M64_64x64x90():
     cfg = make_config(2)
     check(cfg["layers"][0], cfg["mu_in"], cfg["mu_out"], cfg["dphi"])
 

@@ -37,7 +37,7 @@ def oracle_brdf(layer, mu_in, mu_out, dphi):
                   layer["n_nodes"], layer["n_orders"], mu_in, mu_out, dphi)
 
 
-def test_config1_rayleigh():
+def test_rayleigh_N8_M3_8x8x16():
     cfg = make_config(1)
     ly = cfg["layers"][0]
     F = gpu_brdf(ly, cfg["mu_in"], cfg["mu_out"], cfg["dphi"])
@@ -57,7 +57,7 @@ def test_ragged_multi_tile_mie(n_if):
     assert normalised_error(F, G) < TOL_FP64
 
 
-def test_config2_full():
+def test_mie_N32_M64_64x64x90():
     cfg = make_config(2)
     ly = cfg["layers"][0]
     F = gpu_brdf(ly, cfg["mu_in"], cfg["mu_out"], cfg["dphi"])

@@ -69,7 +69,7 @@ def test_normalisation_and_asymmetry():
     assert abs(c[1, 0] / 3.0 - g) < 1e-12
 
 
-def test_grids_and_config1():
+def test_grids_and_rayleigh_workload():
     mu = uniform_zenith_grid(8)
     assert np.all(np.diff(mu) < 0) and mu.min() > 0 and mu.max() < 1
     cfg = make_config(1)

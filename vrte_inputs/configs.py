@@ -68,7 +68,7 @@ def make_config(index: int, small: bool = False) -> dict:
         layers = [_layer(1.0, 0.9, 1.0, 8, 3, rayleigh_coefficients())]
         grids = angle_grids(8, 8, 16)
     elif index in (2, 3):
-        # config 3 is the config-2 particle layer with larger particles, L = 128
+        # the N = 64 layer is the N = 32 particle layer with larger particles, L = 128
         x_eff = rng.uniform(2.0, 20.0) if index == 2 else rng.uniform(2.0, 40.0)
         omega = rng.uniform(0.8, 0.999)
         L = 64 if index == 2 else 128
