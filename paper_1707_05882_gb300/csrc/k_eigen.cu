@@ -58,8 +58,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
                                                        double* lam_re, double* lam_im,
                                                        double* scale, const int* mask,
                                                        unsigned* status) {
-  extern __shared__ double vsh[];  // Householder vector, n entries
+  extern __shared__ double vsh[];  // Householder vector, n entries; then the sweep's
+                                   // reflectors (tau, v1, v2), n entries each
   __shared__ double red[32];
+  __shared__ int ired[32];
+  __shared__ double xyz[3];  // next bulge column, forwarded from the right update
   int u = blockIdx.x;
   if (mask && !mask[u]) return;
   int tid = threadIdx.x, nt = blockDim.x;
@@ -67,6 +70,9 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
   double* H = Hbuf + (size_t)u * n * n;
   double* Z = Zbuf + (size_t)u * n * n;
   double* V = Vbuf + (size_t)u * n * n;
+  double* rtau = vsh + n;
+  double* rv1 = rtau + n;
+  double* rv2 = rv1 + n;
   double* wr = lam_re + (size_t)u * n;
   double* wi = lam_im + (size_t)u * n;
   double* dsc = scale + (size_t)u * n;
@@ -171,15 +177,20 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
   long total = 0;
   const long max_total = 60L * n;
   while (hi >= 0) {
-    // deflation scan (every thread reads the same values)
-    int l = hi;
-    while (l > 0) {
-      double sub = fabs(H[(size_t)l * n + l - 1]);
-      double tst = fabs(H[(size_t)(l - 1) * n + l - 1]) + fabs(H[(size_t)l * n + l]);
+    // deflation scan: the largest l in [1, hi] with a negligible H[l][l-1] (0 if none),
+    // every thread testing its own positions from the top, then a block max
+    int lf = 0;
+    for (int l2 = hi - tid; l2 > 0; l2 -= nt) {
+      double sub = fabs(H[(size_t)l2 * n + l2 - 1]);
+      double tst = fabs(H[(size_t)(l2 - 1) * n + l2 - 1]) + fabs(H[(size_t)l2 * n + l2]);
       if (tst == 0.0) tst = hn;
-      if (sub <= fmax(smlnum, EPS * tst)) break;
-      --l;
+      if (sub <= fmax(smlnum, EPS * tst)) { lf = l2; break; }
     }
+    lf = __reduce_max_sync(0xffffffffu, lf);
+    if (lane == 0) ired[warp] = lf;
+    __syncthreads();
+    int l = 0;
+    for (int i = 0; i < nwarps; ++i) l = max(l, ired[i]);
     __syncthreads();
     if (l > 0 && tid == 0) H[(size_t)l * n + l - 1] = 0.0;
     __syncthreads();
@@ -301,17 +312,31 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
     double x = h21s * H[(size_t)l * n + l + 1] + (hll - r1r) * ((hll - r2r) / s3) - r1i * (r2i / s3);
     double y = h21s * (hll + H[(size_t)(l + 1) * n + l + 1] - r1r - r2r);
     double z = h21s * H[(size_t)(l + 2) * n + l + 1];
+    bool fwd = false;  // xyz holds the bulge column written by the previous right update
     for (int k = l; k <= hi - 1; ++k) {
       int nr = (k < hi - 1) ? 3 : 2;
       if (k > l) {
-        x = H[(size_t)k * n + k - 1];
-        y = H[(size_t)(k + 1) * n + k - 1];
-        z = (nr == 3) ? H[(size_t)(k + 2) * n + k - 1] : 0.0;
+        if (fwd) {
+          x = xyz[0];
+          y = xyz[1];
+          z = (nr == 3) ? xyz[2] : 0.0;
+        } else {
+          x = H[(size_t)k * n + k - 1];
+          y = H[(size_t)(k + 1) * n + k - 1];
+          z = (nr == 3) ? H[(size_t)(k + 2) * n + k - 1] : 0.0;
+        }
       }
       double tau, v1, v2;
       house3(x, y, nr == 3 ? z : 0.0, tau, v1, v2);
       if (nr == 2) v2 = 0.0;
-      __syncthreads();
+      if (tid == 0) {
+        rtau[k - l] = tau;
+        rv1[k - l] = v1;
+        rv2[k - l] = v2;
+      }
+      // the left update below overwrites H values this step read from global memory; with
+      // the bulge column forwarded in shared memory nothing is read from H before it
+      if (!(k > l && fwd)) __syncthreads();
       if (tau != 0.0) {
         int c0 = (k > l) ? k - 1 : l;
         // left: rows k..k+nr-1, columns c0..n-1
@@ -335,20 +360,38 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
           double h2 = (nr == 3) ? H[(size_t)i * n + k + 2] : 0.0;
           double w = tau * (h0 + v1 * h1 + v2 * h2);
           H[(size_t)i * n + k] = h0 - w;
+          if (i > k) xyz[i - k - 1] = h0 - w;  // column k of rows k+1..k+3: the next bulge
           H[(size_t)i * n + k + 1] = h1 - w * v1;
           if (nr == 3) H[(size_t)i * n + k + 2] = h2 - w * v2;
         }
-        for (int i = tid; i < n; i += nt) {
-          double z0 = Z[(size_t)k * n + i], z1 = Z[(size_t)(k + 1) * n + i];
-          double z2 = (nr == 3) ? Z[(size_t)(k + 2) * n + i] : 0.0;
-          double w = tau * (z0 + v1 * z1 + v2 * z2);
-          Z[(size_t)k * n + i] = z0 - w;
-          Z[(size_t)(k + 1) * n + i] = z1 - w * v1;
-          if (nr == 3) Z[(size_t)(k + 2) * n + i] = z2 - w * v2;
-        }
       }
+      fwd = (tau != 0.0);
       __syncthreads();
     }
+    // Schur vectors: Z <- Z P_l ... P_{hi-1}, deferred to the end of the sweep. Each row of
+    // Z transforms on its own, so a thread carries its row through all reflectors with a
+    // sliding window of three columns (the same arithmetic, in the same order, as
+    // applying each reflector at its step).
+    for (int i = tid; i < n; i += nt) {
+      double za = Z[(size_t)l * n + i], zb = Z[(size_t)(l + 1) * n + i];
+      for (int k = l; k <= hi - 1; ++k) {
+        const int nr = (k < hi - 1) ? 3 : 2;
+        double zc = (nr == 3) ? Z[(size_t)(k + 2) * n + i] : 0.0;
+        const double tau = rtau[k - l];
+        if (tau != 0.0) {
+          const double v1 = rv1[k - l], v2 = rv2[k - l];
+          double w = tau * (za + v1 * zb + v2 * zc);
+          za = za - w;
+          zb = zb - w * v1;
+          if (nr == 3) zc = zc - w * v2;
+        }
+        Z[(size_t)k * n + i] = za;
+        za = zb;
+        zb = zc;
+      }
+      Z[(size_t)hi * n + i] = za;
+    }
+    __syncthreads();
   }
   __syncthreads();
 
@@ -488,7 +531,9 @@ void dgemm_batched_mask(bool tA, bool tB, int M, int N, int K, double alpha, con
 void batched_eigen(int n, const double* A, double* H, double* Z, double* V, double* X,
                    double* lam_re, double* lam_im, double* scale, int batch, unsigned* status,
                    cudaStream_t s, const int* mask) {
-  size_t smem = (size_t)n * sizeof(double);
+  size_t smem = 4 * (size_t)n * sizeof(double);
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_eigen<<<batch, EIG_THREADS, smem, s>>>(n, A, H, Z, V, lam_re, lam_im, scale, mask, status);
   // X = Z V with Z, V column-major: in row-major terms X = Zc^T Vc^T
   dgemm_batched_mask(true, true, n, n, n, 1.0, Z, n, (long long)n * n, V, n, (long long)n * n, 0.0,
