@@ -316,17 +316,19 @@ def run_batched(args):
 
 
 # DRAM bytes per launch of a stage's dominant kernel from one ncu capture of the same
-# kernel (profiles/eigen_mie-N64-M128.md: k_eigen, 128 orders of the N = 64 layer; the
-# stage does not depend on the angular grid). Stages without a current capture: None.
-DRAM_TRAFFIC = {"eigen": 7.643186e9 + 21.738669e9}
+# kernel (profiles/eigen_mie-N64-M128.md: k_eigen, 128 orders of the N = 64 layer, the
+# stage does not depend on the angular grid; profiles/tc_gemm_part_traffic_mie-N64-M128-
+# 1024x1024x360.md: the particular + direct reconstruction GEMM at this workload).
+# Stages without a current capture: None.
+DRAM_TRAFFIC = {"eigen": 7.643186e9 + 21.738669e9, "recon_part": 112.70e9 + 17.18e9}
 
 
-def roofline(stages, clk, precision_name):
+def roofline(stages, clk, precision_name, grid=None):
     """Roofline of the dominant stage: tensor-core stages against the measured sustained
     BF16 peak (their issued slice products), FP64 stages against the derived FP64 peak."""
     pk, pk_src = peaks()
     dom = max(stages, key=lambda s: s["ms"])
-    traffic = DRAM_TRAFFIC.get(dom["name"]) if WORKLOAD == 3 else None
+    traffic = DRAM_TRAFFIC.get(dom["name"]) if WORKLOAD == 3 and not grid else None
     sec = dom["ms"] / 1000.0 if dom["ms"] > 0 else float("nan")
     if dom.get("tc_flops", 0.0) > 0.0:
         peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0)))
@@ -417,7 +419,7 @@ def main():
         "full_brdf_seconds": ms_per_step / 1000.0,
         "clocks": clk,
         "gpu_launches": int(sum(s["launches"] for s in stages)),
-        "roofline": roofline(stages, clk, args.precision),
+        "roofline": roofline(stages, clk, args.precision, args.grid),
         "stages": [{k: (round(v, 4) if isinstance(v, float) else v) for k, v in s.items()}
                    for s in stages],
     }
