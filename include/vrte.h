@@ -118,7 +118,9 @@ vrte_status vrte_plan_create(const vrte_plan_desc* desc, vrte_plan** out);
  * d_coeffs: device FP64 [n_layers][n_coef_max][6] expansion coefficients
  * (alpha1, alpha2, alpha3, alpha4, beta1, beta2) per l, zero-padded beyond each
  * layer's n_coef; the pointer is kept and read by each solve (the caller keeps
- * it alive). Allocates the solve workspace for these layers. */
+ * it alive). Allocates the solve workspace for these layers. A VRTE_MIXED plan
+ * contracts over the 4 n_coef (l, component) pairs on the tensor cores and returns
+ * VRTE_ERR_UNSUPPORTED when 4 n_coef > 1024 (before touching the workspace). */
 vrte_status vrte_set_layer(vrte_plan* plan, int n_layers, const vrte_layer* host_params,
                            const double* d_coeffs);
 
@@ -126,7 +128,13 @@ vrte_status vrte_set_layer(vrte_plan* plan, int n_layers, const vrte_layer* host
  *   d_brdf[n_layers][n_mu_in][n_mu_out][n_phi][4][4]   (row r = exiting Stokes
  *   component, column s = incident Stokes basis vector),
  * FP32 or FP64 per out_dtype, on `stream` (a cudaStream_t; NULL = legacy default
- * stream). Asynchronous: no host synchronization and no allocation inside. */
+ * stream). Asynchronous: no host synchronization and no allocation inside.
+ * Accuracy against the exact DOM solution of the given N: VRTE_FP64 ~1e-10 of F_00 at
+ * the same point (more near a resonance mu0 kappa_j ~ 1 of the particular solution,
+ * where every FP64 formulation loses digits); VRTE_MIXED 1e-6 on the I row and 1e-5 on
+ * the Q, U, V rows of F_00 (column blocks whose sliced-product error bound is large
+ * are recomputed in FP64). An FP32 table is the result rounded to FP32 (VRTE_MIXED:
+ * within one unit in the last place). */
 vrte_status vrte_solve_brdf(vrte_plan* plan, void* d_brdf, int out_dtype, void* stream);
 
 /* Same solve with host buffers: copies h_coeffs (host FP64, layout as d_coeffs
