@@ -308,7 +308,9 @@ def run_batched(args):
             "config": {"workload": cfg["name"], "layers": len(layers), "order_solves": M_total,
                        "n_in": 64, "n_out": 64, "n_phi": 90, "out_dtype": "f32",
                        "structure": "one plan, one vrte_solve_brdf call per step; layers run "
-                                    "one after another, all orders of a layer batched"},
+                                    "on up to 4 concurrent streams (one workspace slot each), "
+                                    "all orders of a layer batched",
+                       "stages_ms": "summed over the concurrent streams, so above ms_per_step"},
             "mixed": res["mixed"], "fp64_plain": res.get("fp64"),
             "speedup_vs_fp64_plain": (res["fp64"]["ms_per_step"] / res["mixed"]["ms_per_step"]
                                       if "fp64" in res else None)}

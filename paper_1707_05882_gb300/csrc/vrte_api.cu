@@ -43,22 +43,14 @@ const char* kStageNames[kStages] = {"tables",     "assemble",   "eigen",
                                     "refine",     "synthesis"};
 }  // namespace
 
-struct vrte_plan {
-  vrte_plan_desc desc{};
-  int n_in = 0, n_out = 0, n_phi = 0;
-  double *d_mu_in = nullptr, *d_mu_out = nullptr, *d_phi = nullptr;
-  double *d_wc = nullptr, *d_ws = nullptr;  // [M_max][n_phi]
-  unsigned* d_status = nullptr;
-  cudaStream_t last_stream = nullptr;
-  // layers
-  std::vector<vrte_layer> layers;
-  const double* d_coeffs = nullptr;
-  int n_layers = 0;
+// Buffers of one order batch of one layer. A plan holds up to kMaxSlots of them so that
+// the layers of a multi-layer solve run on concurrent streams (a layer's orders occupy
+// only as many SMs as it has orders in the FP64 stages).
+struct Work {
   // per-layer tables (sized for N_max)
   double *d_mu_nodes = nullptr, *d_w_nodes = nullptr, *d_pts = nullptr, *d_min4 = nullptr,
          *d_mout4 = nullptr, *d_rtop4 = nullptr;
   // order-batch workspace (sized for the largest layer)
-  int chunk = 0;
   double *gp = nullptr, *gr = nullptr, *gt = nullptr;
   double *E = nullptr, *F = nullptr, *FE = nullptr, *X = nullptr, *EX = nullptr, *Y = nullptr,
          *Xinv = nullptr, *Hs = nullptr, *Zs = nullptr, *Vs = nullptr;
@@ -73,16 +65,37 @@ struct vrte_plan {
   int* mode_flag = nullptr;
   // mixed form: slice workspace of the tensor-core GEMMs (shared with the synthesis)
   void* tcw = nullptr;
-  size_t tcw_bytes = 0;
   // mixed form: FP64 refinement of ill-conditioned columns (maxima, counters, work list)
   double* rscratch = nullptr;
   // mixed form: factors of the (l, component) contractions for U+- and the beam vectors
   double *Ln = nullptr, *RU = nullptr, *Rbp = nullptr, *Rbm = nullptr;
   int* rcount = nullptr;  // [flagged in this batch, flagged in this solve]
   int2* rlist = nullptr;
+  double* Isyn = nullptr;   // [M_max][n_in][n_out][16]
+  double* g0tab = nullptr;  // [n_out][n_in] depth factors of the layer
+  cudaStream_t stream = nullptr;  // own stream when the plan runs several slots
+  cudaEvent_t done = nullptr;
+};
+constexpr int kMaxSlots = 4;
+
+struct vrte_plan {
+  vrte_plan_desc desc{};
+  int n_in = 0, n_out = 0, n_phi = 0;
+  double *d_mu_in = nullptr, *d_mu_out = nullptr, *d_phi = nullptr;
+  double *d_wc = nullptr, *d_ws = nullptr;  // [M_max][n_phi]
+  unsigned* d_status = nullptr;
+  cudaStream_t last_stream = nullptr;
+  // layers
+  std::vector<vrte_layer> layers;
+  const double* d_coeffs = nullptr;
+  int n_layers = 0;
+  // order-batch workspaces, one per concurrent layer slot
+  Work ws[kMaxSlots];
+  int nslots = 1;
+  int chunk = 0;
+  size_t tcw_bytes = 0;
   int kdir = 0;  // extra K of the direct term in the mixed form (4 L_max)
-  double* Isyn = nullptr;  // [M_max][n_in][n_out][16]
-  double* g0tab = nullptr;  // [n_out][n_in] depth factors of the current layer
+  cudaEvent_t fork = nullptr;
   // host-API staging
   double* d_coef_stage = nullptr;
   size_t coef_stage_bytes = 0;
@@ -95,7 +108,7 @@ struct vrte_plan {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> events;
   bool profile = false;
   // geometry of the most recent order batch (for vrte_debug_copy)
-  int last_n = 0, last_U = 0, last_P = 0, last_Meff = 0, last_ldU = 0;
+  int last_n = 0, last_U = 0, last_P = 0, last_Meff = 0, last_ldU = 0, last_slot = 0;
 };
 
 namespace {
@@ -250,7 +263,14 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   }
   cudaDeviceSynchronize();
   free_workspace(p, kPlanAllocs);
-  p->Isyn = nullptr;
+  for (Work& x : p->ws) {
+    cudaStream_t st_ = x.stream;
+    cudaEvent_t ev_ = x.done;
+    x = Work();
+    x.stream = st_;
+    x.done = ev_;
+  }
+  p->last_U = 0;
   p->layers.assign(hp, hp + n_layers);
   p->n_layers = n_layers;
   p->d_coeffs = d_coeffs;
@@ -285,22 +305,37 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   size_t isyn = (size_t)Mx * p->n_in * p->n_out * 16;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
-  // the order radiances must fit; the per-order workspace takes at most 35% of what is
-  // left (capped at 96 GiB) so that the caller's output table still fits beside it
-  size_t need_fixed = (isyn + (size_t)p->n_in * p->n_out) * sizeof(double) + ((size_t)64 << 20);
-  if (need_fixed >= free_b) return VRTE_ERR_OOM;
-  size_t budget = std::min((size_t)(0.35 * (double)(free_b - need_fixed)), (size_t)96 << 30);
-  size_t units = budget / (per_unit * sizeof(double));
-  units = std::max<size_t>(1, std::min<size_t>(units, (size_t)Mx));
-  p->chunk = (int)units;
-  size_t U = units;
+  // Several layers run in up to kMaxSlots concurrent slots, each with its own order
+  // radiances and workspace, as long as every slot still takes all of a layer's orders in
+  // one batch. The order radiances must fit; the per-order workspace takes at most 35% of
+  // what is left (capped at 96 GiB) so that the caller's output table still fits beside it.
+  const size_t fixed_slot = (isyn + (size_t)p->n_in * p->n_out) * sizeof(double);
+  int nslots = std::max(1, std::min(n_layers, kMaxSlots));
+  size_t U = 0;
+  for (;; --nslots) {
+    size_t need_fixed = nslots * fixed_slot + ((size_t)64 << 20);
+    if (need_fixed >= free_b) {
+      if (nslots == 1) return VRTE_ERR_OOM;
+      continue;
+    }
+    size_t budget = std::min((size_t)(0.35 * (double)(free_b - need_fixed)), (size_t)96 << 30);
+    size_t units = budget / nslots / (per_unit * sizeof(double));
+    units = std::max<size_t>(1, std::min<size_t>(units, (size_t)Mx));
+    U = units;
+    if (nslots == 1 || units == (size_t)Mx) break;
+  }
+  p->nslots = nslots;
+  p->chunk = (int)U;
   vrte_status st = VRTE_OK;
+  Work* w = nullptr;
 #define VRTE_ALLOC(ptr, cnt)                        \
-  if ((st = allocd(p, &p->ptr, (cnt))) != VRTE_OK) { \
+  if ((st = allocd(p, &w->ptr, (cnt))) != VRTE_OK) { \
     free_workspace(p, kPlanAllocs);                  \
-    p->Isyn = nullptr;                               \
+    for (Work& x : p->ws) x.Isyn = nullptr;          \
     return st;                                       \
   }
+  for (int slot = 0; slot < nslots; ++slot) {
+  w = &p->ws[slot];
   VRTE_ALLOC(d_mu_nodes, Nx) VRTE_ALLOC(d_w_nodes, Nx) VRTE_ALLOC(d_pts, P) VRTE_ALLOC(d_min4, 4 * (size_t)p->n_in)
   VRTE_ALLOC(d_mout4, 4 * (size_t)p->n_out) VRTE_ALLOC(d_rtop4, 4 * (size_t)Nx)
   VRTE_ALLOC(gp, U * Lx * P) VRTE_ALLOC(gr, U * Lx * P) VRTE_ALLOC(gt, U * Lx * P)
@@ -324,29 +359,53 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
     size_t synth = tc_synthesis_workspace(Mx, p->n_in, p->n_out, p->n_phi, kSlicesSynth,
                                           kSynthBlock);
     p->tcw_bytes = std::max(tc_unit * U, synth);
-    if ((st = alloc(p, &p->tcw, p->tcw_bytes)) != VRTE_OK ||
-        (st = allocd(p, &p->rscratch, refine_scratch_doubles((int)U, p->n_in, p->n_out))) !=
+    if ((st = alloc(p, &w->tcw, p->tcw_bytes)) != VRTE_OK ||
+        (st = allocd(p, &w->rscratch, refine_scratch_doubles((int)U, p->n_in, p->n_out))) !=
             VRTE_OK ||
-        (st = allocd(p, &p->rcount, 2)) != VRTE_OK ||
-        (st = allocd(p, &p->rlist, U * p->n_in)) != VRTE_OK) {
+        (st = allocd(p, &w->rcount, 2)) != VRTE_OK ||
+        (st = allocd(p, &w->rlist, U * p->n_in)) != VRTE_OK) {
       free_workspace(p, kPlanAllocs);
-      p->Isyn = nullptr;
+      for (Work& x : p->ws) x.Isyn = nullptr;
       return st;
     }
   }
   VRTE_ALLOC(Isyn, isyn)
+  if (nslots > 1) {
+    if (!w->stream && cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return VRTE_ERR_CUDA;
+    if (!w->done && cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming) != cudaSuccess)
+      return VRTE_ERR_CUDA;
+  }
+  }
 #undef VRTE_ALLOC
+  if (nslots > 1 && !p->fork &&
+      cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess)
+    return VRTE_ERR_CUDA;
   return VRTE_OK;
 }
 
 static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, int out_dtype,
-                             cudaStream_t s) {
+                             cudaStream_t s0) {
   const size_t table = (size_t)p->n_in * p->n_out * p->n_phi * 16;
   const size_t esz = out_dtype == VRTE_OUT_F64 ? sizeof(double) : sizeof(float);
   const int R = 4 * p->n_in, Ro = 4 * p->n_out;
-  if (p->desc.precision == VRTE_MIXED && cudaMemsetAsync(p->rcount, 0, 2 * sizeof(int), s))
-    return VRTE_ERR_CUDA;
-  for (int lb = 0; lb < p->n_layers; ++lb) {
+  // layer lb runs on slot lb % nslots; with several slots each has its own stream, forked
+  // from and joined back into the caller's stream
+  const int ns = p->nslots;
+  if (ns > 1) {
+    if (cudaEventRecord(p->fork, s0) != cudaSuccess) return VRTE_ERR_CUDA;
+    for (int k = 0; k < ns; ++k)
+      if (cudaStreamWaitEvent(p->ws[k].stream, p->fork, 0) != cudaSuccess) return VRTE_ERR_CUDA;
+  }
+  vrte_status result = VRTE_OK;
+  for (int k = 0; k < ns && result == VRTE_OK; ++k)
+    if (p->desc.precision == VRTE_MIXED &&
+        cudaMemsetAsync(p->ws[k].rcount, 0, 2 * sizeof(int), ns > 1 ? p->ws[k].stream : s0))
+      result = VRTE_ERR_CUDA;
+  for (int lb = 0; lb < p->n_layers && result == VRTE_OK; ++lb) {
+    Work* w = &p->ws[lb % ns];
+    cudaStream_t s = ns > 1 ? w->stream : s0;
+    p->last_slot = lb % ns;
     const vrte_layer& ly = p->layers[lb];
     const int N = ly.n_nodes, n = 4 * N, L = ly.n_coef;
     const int Meff = std::min(ly.n_orders, ly.n_coef);
@@ -354,10 +413,10 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
     const double* coef = coeffs + (size_t)lb * p->desc.n_coef_max * 6;
     {
       StageScope sc(p, ST_TABLES, s, 3, 0.0, 0.0);
-      launch_gauss_nodes(N, p->d_mu_nodes, p->d_w_nodes, p->d_status, s);
-      launch_interface(N, p->n_in, p->n_out, ly.n_interface, p->d_mu_nodes, p->d_mu_in,
-                       p->d_mu_out, p->d_pts, p->d_min4, p->d_mout4, p->d_rtop4, s);
-      launch_depth_table(N, p->n_in, p->n_out, ly.tau, p->d_pts, p->g0tab, s);
+      launch_gauss_nodes(N, w->d_mu_nodes, w->d_w_nodes, p->d_status, s);
+      launch_interface(N, p->n_in, p->n_out, ly.n_interface, w->d_mu_nodes, p->d_mu_in,
+                       p->d_mu_out, w->d_pts, w->d_min4, w->d_mout4, w->d_rtop4, s);
+      launch_depth_table(N, p->n_in, p->n_out, ly.tau, w->d_pts, w->g0tab, s);
     }
     for (int m0 = 0; m0 < Meff; m0 += p->chunk) {
       const int U = std::min(p->chunk, Meff - m0);
@@ -385,7 +444,7 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
                       int ldc_, long long sC_) {
         if (mixed)
           tc_gemm_store(M_, N_, K_, A_, lda_, sA_, B_, ldb_, sB_, beta_, C_, ldc_, sC_, U,
-                        kSlices, p->tcw, p->d_status, s);
+                        kSlices, w->tcw, p->d_status, s);
         else
           dgemm_batched(M_, N_, K_, 1.0, A_, lda_, sA_, B_, ldb_, sB_, beta_, C_, ldc_, sC_, U,
                         s);
@@ -395,37 +454,37 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
       for (int u = 0; u < U; ++u) lsum += L - (m0 + u);
       {
         StageScope sc(p, ST_TABLES, s, 1, 30.0 * P * lsum, 24.0 * P * lsum);
-        launch_gsf_tables(ob, p->d_pts, p->gp, p->gr, p->gt, s);
+        launch_gsf_tables(ob, w->d_pts, w->gp, w->gr, w->gt, s);
       }
       {
         StageScope sc(p, ST_ASSEMBLE, s, 2, 72.0 * N * N * lsum + 2.0 * dn * dn * dn * dU,
                       8.0 * 3 * dn * dn * dU);
-        launch_assemble_EF(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_w_nodes, p->E, p->F, s);
-        dgemm_batched(n, n, n, 1.0, p->F, n, nn, p->E, n, nn, 0.0, p->FE, n, nn, U, s);
+        launch_assemble_EF(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, w->E, w->F, s);
+        dgemm_batched(n, n, n, 1.0, w->F, n, nn, w->E, n, nn, 0.0, w->FE, n, nn, U, s);
       }
       {
         // nominal cost of a real Schur decomposition with eigenvectors: 25 n^3, plus
         // E'X, Y = E'X / kappa and the mode residual F'Y - X kappa
         StageScope sc(p, ST_EIGEN, s, 10, (25.0 + 4.0) * dn * dn * dn * dU,
                       8.0 * 6 * dn * dn * dU);
-        batched_eigen(n, p->FE, p->Hs, p->Zs, p->Vs, p->X, p->lam_re, p->lam_im, p->bal, U,
+        batched_eigen(n, w->FE, w->Hs, w->Zs, w->Vs, w->X, w->lam_re, w->lam_im, w->bal, U,
                       p->d_status, s);
-        dgemm_batched(n, n, n, 1.0, p->E, n, nn, p->X, n, nn, 0.0, p->EX, n, nn, U, s);
-        launch_pack_Y(ob, p->EX, p->lam_re, p->lam_im, p->Y, s);
-        dgemm_batched(n, n, n, 1.0, p->F, n, nn, p->Y, n, nn, 0.0, p->FY, n, nn, U, s);
+        dgemm_batched(n, n, n, 1.0, w->E, n, nn, w->X, n, nn, 0.0, w->EX, n, nn, U, s);
+        launch_pack_Y(ob, w->EX, w->lam_re, w->lam_im, w->Y, s);
+        dgemm_batched(n, n, n, 1.0, w->F, n, nn, w->Y, n, nn, 0.0, w->FY, n, nn, U, s);
         // the FP64 form re-solves order 0 (diffusion mode) and any order with a poor mode
         // residual in the 2n block form; the mixed form only catastrophic ones
         const bool fp64 = p->desc.precision == VRTE_FP64;
-        eigen_block_fallback(n, m0, p->E, p->F, p->FY, p->X, p->Y, p->lam_re, p->lam_im,
-                             fp64 ? 1e-4 : 1e-1, fp64 ? 1 : 0, p->mode_res, p->mode_flag, p->Bm,
-                             p->Hb, p->Zb, p->Vb, p->Xb, p->kb_re, p->kb_im, p->balb, U,
+        eigen_block_fallback(n, m0, w->E, w->F, w->FY, w->X, w->Y, w->lam_re, w->lam_im,
+                             fp64 ? 1e-4 : 1e-1, fp64 ? 1 : 0, w->mode_res, w->mode_flag, w->Bm,
+                             w->Hb, w->Zb, w->Vb, w->Xb, w->kb_re, w->kb_im, w->balb, U,
                              p->d_status, s);
       }
       {
         StageScope sc(p, ST_MODES, s, 3, 16.0 * dn * dn * dn * dU, 8.0 * 12 * dn * dn * dU);
-        launch_build_K(ob, p->X, p->Y, p->lam_re, p->lam_im, p->d_rtop4, p->K, s);
-        batched_inverse(2 * n, p->K, p->Kinv, U, p->d_status, s);
-        batched_inverse(n, p->X, p->Xinv, U, p->d_status, s);
+        launch_build_K(ob, w->X, w->Y, w->lam_re, w->lam_im, w->d_rtop4, w->K, s);
+        batched_inverse(2 * n, w->K, w->Kinv, U, p->d_status, s);
+        batched_inverse(n, w->X, w->Xinv, U, p->d_status, s);
       }
       {
         StageScope sc(p, ST_PARTICULAR, s, mixed ? 7 + 6 * gl : 9,
@@ -434,32 +493,32 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         sc.tensor_flops(tcf * (4.0 * dn + 2.0 * kdir) * dn * dR * dU);
         if (mixed) {
           // beam vectors as contractions over (l, component) on the tensor cores
-          launch_mixed_operators(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_w_nodes, p->d_min4,
-                                 p->Ln, p->RU, p->Rbp, p->Rbm, s);
+          launch_mixed_operators(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, w->d_min4,
+                                 w->Ln, w->RU, w->Rbp, w->Rbm, s);
           const long long sL = (long long)n * kdir, sB = (long long)kdir * R;
-          gemm(n, R, kdir, p->Ln, kdir, sL, p->Rbp, R, sB, 0.0, p->Pb, R, nR);
-          gemm(n, R, kdir, p->Ln, kdir, sL, p->Rbm, R, sB, 0.0, p->Rb, R, nR);
+          gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbp, R, sB, 0.0, w->Pb, R, nR);
+          gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbm, R, sB, 0.0, w->Rb, R, nR);
         } else {
-          launch_assemble_beam(ob, p->gp, p->gr, p->gt, p->d_mu_nodes, p->d_min4, p->Pb, p->Rb,
+          launch_assemble_beam(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_min4, w->Pb, w->Rb,
                                s);
         }
         // near a resonance mu0 ~ 1/kappa_j the eigenbasis solve amplifies rounding by
         // 1/(kappa_j^2 - mu0^-2) and the homogeneous part cancels it: the mixed form
         // keeps FP64-level products here (7 slices, ~2e-15 per term)
-        gemm(n, R, n, p->F, n, nn, p->Pb, R, nR, 0.0, p->Wv, R, nR);
-        launch_particular_rhs(ob, p->Wv, p->Rb, p->d_pts, p->Wv, s);
-        gemm(n, R, n, p->Xinv, n, nn, p->Wv, R, nR, 0.0, p->Yv, R, nR);
-        launch_eigen_scale(ob, p->lam_re, p->lam_im, p->d_pts, p->Yv, s);
-        gemm(n, R, n, p->X, n, nn, p->Yv, R, nR, 0.0, p->SD, R, ob.sSD);
-        gemm(n, R, n, p->E, n, nn, p->SD, R, ob.sSD, 0.0, p->Es, R, nR);
-        launch_particular_sd(ob, p->Pb, p->Es, p->d_pts, p->SD, s);
-        launch_bc_rhs(ob, p->SD, nullptr, p->d_rtop4, p->d_pts, p->RHS, s);
+        gemm(n, R, n, w->F, n, nn, w->Pb, R, nR, 0.0, w->Wv, R, nR);
+        launch_particular_rhs(ob, w->Wv, w->Rb, w->d_pts, w->Wv, s);
+        gemm(n, R, n, w->Xinv, n, nn, w->Wv, R, nR, 0.0, w->Yv, R, nR);
+        launch_eigen_scale(ob, w->lam_re, w->lam_im, w->d_pts, w->Yv, s);
+        gemm(n, R, n, w->X, n, nn, w->Yv, R, nR, 0.0, w->SD, R, ob.sSD);
+        gemm(n, R, n, w->E, n, nn, w->SD, R, ob.sSD, 0.0, w->Es, R, nR);
+        launch_particular_sd(ob, w->Pb, w->Es, w->d_pts, w->SD, s);
+        launch_bc_rhs(ob, w->SD, nullptr, w->d_rtop4, w->d_pts, w->RHS, s);
       }
       {
         StageScope sc(p, ST_BC_SOLVE, s, gl, 2.0 * 4 * dn * dn * dR * dU,
                       8.0 * (4 * dn * dn + 4 * dn * dR) * dU);
         sc.tensor_flops(tcf * 4.0 * dn * dn * dR * dU);
-        gemm(2 * n, R, 2 * n, p->Kinv, 2 * n, 4 * nn, p->RHS, R, 2 * nR, 0.0, p->C, R, 2 * nR);
+        gemm(2 * n, R, 2 * n, w->Kinv, 2 * n, 4 * nn, w->RHS, R, 2 * nR, 0.0, w->C, R, 2 * nR);
       }
       {
         StageScope sc(p, ST_RECON_OPS, s, mixed ? 3 + 3 * gl : 5,
@@ -469,18 +528,18 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         sc.tensor_flops(tcf * 2.0 * dRo * dn * (dn + kdir) * dU);
         if (mixed) {
           // U+- = [M_out P(mu_o) B] x RU+-: the direct operator's columns are the left factor
-          launch_direct_operators(ob, p->gp, p->gr, p->gt, p->d_min4, p->d_mout4, p->Upm, p->SD,
+          launch_direct_operators(ob, w->gp, w->gr, w->gt, w->d_min4, w->d_mout4, w->Upm, w->SD,
                                   s);
-          gemm(Ro, 2 * n, kdir, p->Upm + 2 * n, ldU, sU_part, p->RU, 2 * n,
-               (long long)kdir * 2 * n, 0.0, p->Upm, ldU, sU_part);
+          gemm(Ro, 2 * n, kdir, w->Upm + 2 * n, ldU, sU_part, w->RU, 2 * n,
+               (long long)kdir * 2 * n, 0.0, w->Upm, ldU, sU_part);
         } else {
-          launch_assemble_U(ob, p->gp, p->gr, p->gt, p->d_w_nodes, p->d_mout4, p->Upm, s);
+          launch_assemble_U(ob, w->gp, w->gr, w->gt, w->d_w_nodes, w->d_mout4, w->Upm, s);
         }
-        gemm(Ro, n, n, p->Upm, ldU, sU_part, p->X, n, nn, 0.0, p->P1, n, Ron);
-        gemm(Ro, n, n, p->Upm + n, ldU, sU_part, p->Y, n, nn, 0.0, p->P2, n, Ron);
-        launch_build_Hhat(ob, p->P1, p->P2, p->lam_re, p->lam_im, p->d_pts, p->Hhat, s);
+        gemm(Ro, n, n, w->Upm, ldU, sU_part, w->X, n, nn, 0.0, w->P1, n, Ron);
+        gemm(Ro, n, n, w->Upm + n, ldU, sU_part, w->Y, n, nn, 0.0, w->P2, n, Ron);
+        launch_build_Hhat(ob, w->P1, w->P2, w->lam_re, w->lam_im, w->d_pts, w->Hhat, s);
         if (!mixed)
-          launch_assemble_direct(ob, p->gp, p->gr, p->gt, p->d_pts, p->d_min4, p->d_mout4, p->T1,
+          launch_assemble_direct(ob, w->gp, w->gr, w->gt, w->d_pts, w->d_min4, w->d_mout4, w->T1,
                                  s);
       }
       {
@@ -490,7 +549,7 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         StageScope sc(p, ST_RECON_HOM, s, gl, 2.0 * dRo * dR * 2 * dn * dU,
                       8.0 * (dRo * 2 * dn + 2 * dn * dR + 2 * dRo * dR) * dU);
         sc.tensor_flops(tcf * dRo * dR * 2.0 * dn * dU);
-        gemm(Ro, R, 2 * n, p->Hhat, 2 * n, 2 * Ron, p->C, R, 2 * nR, mixed ? 0.0 : 1.0, p->T1, R,
+        gemm(Ro, R, 2 * n, w->Hhat, 2 * n, 2 * Ron, w->C, R, 2 * nR, mixed ? 0.0 : 1.0, w->T1, R,
              (long long)Ro * R);
       }
       {
@@ -501,30 +560,31 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         sc.tensor_flops(tcf * dRo * dR * kp * dU);
         if (mixed) {
           if (2 * n + kdir <= 1024) {
-            tc_gemm_part(ob, 2 * n + kdir, p->Upm, ldU, sU_part, p->SD, ob.sSD, p->T1,
-                         p->g0tab, p->Isyn, kSlices, p->tcw, s);
+            tc_gemm_part(ob, 2 * n + kdir, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1,
+                         w->g0tab, w->Isyn, kSlices, w->tcw, s);
           } else {
             // too deep for one exact accumulation: [U+ U-][s; d] into T1, then the direct part
-            tc_gemm_part_accum(ob, 2 * n, p->Upm, ldU, sU_part, p->SD, ob.sSD, p->T1, p->g0tab,
-                               kSlices, p->tcw, s);
-            tc_gemm_part(ob, kdir, p->Upm + 2 * n, ldU, sU_part, p->SD + (size_t)2 * n * R,
-                         ob.sSD, p->T1, p->g0tab, p->Isyn, kSlices, p->tcw, s);
+            tc_gemm_part_accum(ob, 2 * n, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1, w->g0tab,
+                               kSlices, w->tcw, s);
+            tc_gemm_part(ob, kdir, w->Upm + 2 * n, ldU, sU_part, w->SD + (size_t)2 * n * R,
+                         ob.sSD, w->T1, w->g0tab, w->Isyn, kSlices, w->tcw, s);
           }
         } else {
-          dgemm_part_epilogue(ob, p->Upm, p->SD, p->T1, p->g0tab, p->Isyn, s);
+          dgemm_part_epilogue(ob, w->Upm, w->SD, w->T1, w->g0tab, w->Isyn, s);
         }
       }
       if (mixed) {
         StageScope sc(p, ST_REFINE, s, 6, 0.0, 0.0);
-        refine_columns(ob, 2 * n + kdir, p->Kinv, p->RHS, p->C, p->Hhat, p->Upm, p->SD,
-                       p->g0tab, kSliceEps, kRefineTol, p->rscratch, p->rcount, p->rlist,
-                       U * p->n_in, p->Isyn, s);
+        refine_columns(ob, 2 * n + kdir, w->Kinv, w->RHS, w->C, w->Hhat, w->Upm, w->SD,
+                       w->g0tab, kSliceEps, kRefineTol, w->rscratch, w->rcount, w->rlist,
+                       U * p->n_in, w->Isyn, s);
       }
     }
     // a launch that could not start (resources, configuration) fails the solve here
     if (cudaPeekAtLastError() != cudaSuccess) {
       cudaGetLastError();
-      return VRTE_ERR_CUDA;
+      result = VRTE_ERR_CUDA;
+      break;
     }
     char* outb = (char*)d_brdf + (size_t)lb * table * esz;
     {
@@ -537,21 +597,27 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         sc.tensor_flops(2.0 * Ss * (Ss + 1) / 2 * 16.0 * p->n_in * p->n_out * p->n_phi * Meff);
       }
       if (mixed)
-        tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, p->Isyn, p->d_wc, p->d_ws, outb, out_dtype,
-                     kSlicesSynth, kSynthBlock, p->tcw, p->d_status, s);
+        tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws, outb, out_dtype,
+                     kSlicesSynth, kSynthBlock, w->tcw, p->d_status, s);
       else
-        launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, p->Isyn, p->d_wc, p->d_ws, outb,
+        launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws, outb,
                               out_dtype, p->d_status, s);
     }
   }
+  // join: the caller's stream waits for every slot, also after a failed launch
+  if (ns > 1)
+    for (int k = 0; k < ns; ++k)
+      if (cudaEventRecord(p->ws[k].done, p->ws[k].stream) != cudaSuccess ||
+          cudaStreamWaitEvent(s0, p->ws[k].done, 0) != cudaSuccess)
+        result = VRTE_ERR_CUDA;
   if (cudaGetLastError() != cudaSuccess) return VRTE_ERR_CUDA;
-  return VRTE_OK;
+  return result;
 }
 
 vrte_status vrte_solve_brdf(vrte_plan* p, void* d_brdf, int out_dtype, void* stream) {
   if (!p || !d_brdf) return VRTE_ERR_INVALID_ARG;
   if (out_dtype != VRTE_OUT_F32 && out_dtype != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
-  if (p->n_layers < 1 || !p->d_coeffs || !p->Isyn) return VRTE_ERR_STATE;
+  if (p->n_layers < 1 || !p->d_coeffs || !p->ws[0].Isyn) return VRTE_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   p->last_stream = s;
   return run_solve(p, p->d_coeffs, d_brdf, out_dtype, s);
@@ -561,7 +627,7 @@ vrte_status vrte_solve_brdf_host(vrte_plan* p, const double* h_coeffs, void* h_b
                                  int out_dtype, void* stream) {
   if (!p || !h_coeffs || !h_brdf) return VRTE_ERR_INVALID_ARG;
   if (out_dtype != VRTE_OUT_F32 && out_dtype != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
-  if (p->n_layers < 1 || !p->Isyn) return VRTE_ERR_STATE;
+  if (p->n_layers < 1 || !p->ws[0].Isyn) return VRTE_ERR_STATE;
   cudaStream_t s = (cudaStream_t)stream;
   size_t cbytes = (size_t)p->n_layers * p->desc.n_coef_max * 6 * sizeof(double);
   size_t obytes = (size_t)p->n_layers * p->n_in * p->n_out * p->n_phi * 16 *
@@ -624,46 +690,50 @@ vrte_status vrte_debug_copy(vrte_plan* p, const char* name, void* dst, size_t by
     return VRTE_OK;
   }
   if (strcmp(name, "refined") == 0) {  // mixed form: column blocks recomputed in FP64
-    int h = 0;
-    if (p->rcount && (cudaStreamSynchronize(p->last_stream) != cudaSuccess ||
-                      cudaMemcpy(&h, p->rcount + 1, sizeof(int), cudaMemcpyDeviceToHost) !=
-                          cudaSuccess))
-      return VRTE_ERR_CUDA;
-    double v = (double)h;
+    if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return VRTE_ERR_CUDA;
+    double v = 0.0;
+    for (const Work& x : p->ws) {
+      int h = 0;
+      if (x.rcount &&
+          cudaMemcpy(&h, x.rcount + 1, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return VRTE_ERR_CUDA;
+      v += h;
+    }
     if (size_out) *size_out = sizeof(double);
     if (dst && bytes >= sizeof(double)) memcpy(dst, &v, sizeof(double));
     return VRTE_OK;
   }
   if (p->last_U == 0) return VRTE_ERR_STATE;
+  const Work* w = &p->ws[p->last_slot];  // the slot of the last layer solved
   size_t n = p->last_n, U = p->last_U, R = 4 * (size_t)p->n_in, Ro = 4 * (size_t)p->n_out;
   const void* src = nullptr;
   size_t cnt = 0;
   struct Entry { const char* nm; const double* ptr; size_t count; };
   const Entry tab[] = {
-      {"pts", p->d_pts, (size_t)p->last_P},
-      {"nodes", p->d_mu_nodes, n / 4},
-      {"weights", p->d_w_nodes, n / 4},
-      {"E", p->E, U * n * n},
-      {"F", p->F, U * n * n},
-      {"FE", p->FE, U * n * n},
-      {"schur", p->Hs, U * n * n},
-      {"X", p->X, U * n * n},
-      {"Y", p->Y, U * n * n},
-      {"lam_re", p->lam_re, U * n},
-      {"lam_im", p->lam_im, U * n},
-      {"K", p->K, U * 4 * n * n},
-      {"Kinv", p->Kinv, U * 4 * n * n},
-      {"Xinv", p->Xinv, U * n * n},
-      {"beam_p", p->Pb, U * n * R},
-      {"beam_r", p->Rb, U * n * R},
-      {"SD", p->SD, U * (size_t)p->last_ldU * R},
-      {"RHS", p->RHS, U * 2 * n * R},
-      {"C", p->C, U * 2 * n * R},
-      {"Upm", p->Upm, U * Ro * (size_t)p->last_ldU},
-      {"Hhat", p->Hhat, U * Ro * 2 * n},
-      {"T1", p->T1, U * Ro * R},
-      {"Isyn", p->Isyn, (size_t)p->last_Meff * p->n_in * p->n_out * 16},
-      {"mode_res", p->mode_res, U},
+      {"pts", w->d_pts, (size_t)p->last_P},
+      {"nodes", w->d_mu_nodes, n / 4},
+      {"weights", w->d_w_nodes, n / 4},
+      {"E", w->E, U * n * n},
+      {"F", w->F, U * n * n},
+      {"FE", w->FE, U * n * n},
+      {"schur", w->Hs, U * n * n},
+      {"X", w->X, U * n * n},
+      {"Y", w->Y, U * n * n},
+      {"lam_re", w->lam_re, U * n},
+      {"lam_im", w->lam_im, U * n},
+      {"K", w->K, U * 4 * n * n},
+      {"Kinv", w->Kinv, U * 4 * n * n},
+      {"Xinv", w->Xinv, U * n * n},
+      {"beam_p", w->Pb, U * n * R},
+      {"beam_r", w->Rb, U * n * R},
+      {"SD", w->SD, U * (size_t)p->last_ldU * R},
+      {"RHS", w->RHS, U * 2 * n * R},
+      {"C", w->C, U * 2 * n * R},
+      {"Upm", w->Upm, U * Ro * (size_t)p->last_ldU},
+      {"Hhat", w->Hhat, U * Ro * 2 * n},
+      {"T1", w->T1, U * Ro * R},
+      {"Isyn", w->Isyn, (size_t)p->last_Meff * p->n_in * p->n_out * 16},
+      {"mode_res", w->mode_res, U},
   };
   for (const Entry& e : tab)
     if (strcmp(e.nm, name) == 0) { src = e.ptr; cnt = e.count; }
@@ -712,6 +782,11 @@ void vrte_destroy(vrte_plan* p) {
   cudaDeviceSynchronize();
   reset_stats(p);
   free_workspace(p, 0);
+  for (Work& x : p->ws) {
+    if (x.stream) cudaStreamDestroy(x.stream);
+    if (x.done) cudaEventDestroy(x.done);
+  }
+  if (p->fork) cudaEventDestroy(p->fork);
   if (p->d_coef_stage) cudaFree(p->d_coef_stage);
   if (p->d_out_stage) cudaFree(p->d_out_stage);
   delete p;
