@@ -28,7 +28,7 @@
 
 #include <algorithm>
 
-#include "vrte_internal.cuh"
+#include "tc_common.cuh"
 
 namespace vrte {
 
@@ -41,9 +41,7 @@ constexpr int TC_STAGES = 3;    // shared-memory stages (at most)
 constexpr int TC_SMEM_MAX = 227 * 1024;
 constexpr int A_TILE_BYTES = TC_M * TC_KB * 2;   // 16 KiB
 constexpr int B_TILE_BYTES = TC_N * TC_KB * 2;   // 8 KiB
-constexpr long long WAIT_LIMIT = 1ll << 22;      // polls before a wait is declared stuck
 
-__device__ __host__ inline int pad_to(int x, int m) { return (x + m - 1) / m * m; }
 // Accumulator of slice pair (p, q): diagonals d = p + q < 4 one each; diagonal 4 split by
 // p <= 2 (3 pairs) and p >= 3 (2 pairs) so that each stays exact for K <= 1024; the
 // diagonals 5 .. S-1 share the last one (rounded; 2^-35 below the leading term).
@@ -68,66 +66,6 @@ __device__ __host__ inline int tc_smem_bytes(int S) {
 __device__ inline int swz_offset(int r, int k) {
   int chunk = k >> 3, within = k & 7;
   return (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4) + within * 2;
-}
-
-// Exponent field of a float64 for the scale search: 0 for zero and subnormals; a
-// non-finite value counts as zero and sets *bad.
-__device__ inline int exp_field(double x, bool* bad) {
-  int E = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
-  if (E == 0x7FF) {
-    *bad = true;
-    return 0;
-  }
-  return E;
-}
-// Scale exponent from the largest exponent field of a row or column: max |x| < 2^e.
-__device__ inline int scale_exp(int Emax) { return Emax ? Emax - 1022 : 0; }
-
-// Slices of v 2^-e in (-1, 1) in integer arithmetic: X = round(v 2^(6 + 7(S-1) - e)) is
-// cut into signed base-128 digits q_p in [-64, 64] (most significant first), and slice p
-// is q_p 2^-7p, written as its (exact) BF16 bit pattern. Subnormals and non-finite
-// values give zero slices.
-template <int S>
-__device__ inline void slice_bits(double v, int e, unsigned short* bf) {
-  long long b = __double_as_longlong(v);
-  int E = (int)((b >> 52) & 0x7FF);
-  long long X = 0;
-  if (E != 0 && E != 0x7FF) {
-    long long mant = (b & 0xFFFFFFFFFFFFFll) | (1ll << 52);
-    int sh = E - 1075 + 6 + 7 * (S - 1) - e;  // |v| < 2^e keeps X below 2^(6 + 7(S-1))
-    if (sh >= 0) X = mant << sh;
-    else if (sh > -63) X = (mant + (1ll << (-sh - 1))) >> (-sh);
-    if (b < 0) X = -X;
-  }
-  float scale = 1.0f;
-#pragma unroll
-  for (int p = 1; p < S; ++p) scale *= 1.0f / 128.0f;
-#pragma unroll
-  for (int p = S - 1; p >= 1; --p) {
-    int d = (int)(((X + 64) & 127) - 64);
-    X = (X - d) >> 7;  // exact: X - d is a multiple of 128
-    bf[p] = (unsigned short)(__float_as_uint((float)d * scale) >> 16);
-    scale *= 128.0f;
-  }
-  bf[0] = (unsigned short)(__float_as_uint((float)X) >> 16);
-}
-
-// Writes the S slices of 8 consecutive K entries (one 16-byte chunk per slice).
-template <int S>
-__device__ inline void put_chunk(const double* v, int e, unsigned short* dst0,
-                                 size_t slice_stride) {
-  uint32_t w[S][4];
-#pragma unroll
-  for (int t = 0; t < 8; t += 2) {
-    unsigned short lo[S], hi[S];
-    slice_bits<S>(v[t], e, lo);
-    slice_bits<S>(v[t + 1], e, hi);
-#pragma unroll
-    for (int p = 0; p < S; ++p) w[p][t >> 1] = (uint32_t)lo[p] | ((uint32_t)hi[p] << 16);
-  }
-#pragma unroll
-  for (int p = 0; p < S; ++p)
-    *(uint4*)(dst0 + p * slice_stride) = make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
 }
 
 // A rows: A[u][i][k] (row-major, lda, unit stride sA), M x K. Writes
@@ -227,55 +165,6 @@ __global__ void k_slice_cols(int N, int K, const double* __restrict__ B, int ldb
     case 7: CALL(7); break;          \
     default: CALL(8); break;         \
   }
-
-// ------------------------------------------------------------------ PTX helpers
-__device__ inline uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ inline void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ inline void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes) : "memory");
-}
-__device__ inline bool mbar_try_wait(uint64_t* bar, unsigned phase) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok) : "r"(smem_u32(bar)), "r"(phase) : "memory");
-  return ok != 0;
-}
-// bounded wait: returns false if the barrier did not complete within WAIT_LIMIT polls
-__device__ inline bool mbar_wait(uint64_t* bar, unsigned phase) {
-  for (long long it = 0; it < WAIT_LIMIT; ++it)
-    if (mbar_try_wait(bar, phase)) return true;
-  return false;
-}
-__device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ inline uint64_t smem_desc_sw128(const void* p) {
-  uint64_t a = (uint64_t)(smem_u32(p) >> 4) & 0x3FFF;
-  return a | ((uint64_t)1 << 16)          // leading byte offset (unused for swizzled K-major)
-         | ((uint64_t)(1024 >> 4) << 32)  // stride byte offset: 8 rows x 128 bytes
-         | ((uint64_t)1 << 46)            // descriptor version for sm_100-family
-         | ((uint64_t)2 << 61);           // 128-byte swizzle
-}
-__device__ inline void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-}
-__device__ inline void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::
-                   "r"(smem_u32(bar)) : "memory");
-}
 
 template <class Epi>
 __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
@@ -619,116 +508,6 @@ void tc_gemm_part_accum(const OrderBatch& b, int K, const double* A, int lda, lo
   EpiPartAccum e{T1, g0tab, b.n_in, b.n_out};
   tc_gemm(4 * b.n_out, 4 * b.n_in, K, A, lda, sA, B, 4 * b.n_in, sB, e, b.n_units, S, work,
           b.status, s);
-}
-
-// ------------------------------------------------------------------ synthesis
-// The 16 Mueller elements split into two classes by their Fourier factor (Eq. 7):
-// cos for (IQ, IQ) and (UV, UV), sin for the off-diagonal blocks (+ for UV rows, - for IQ
-// rows). Each class is one GEMM: rows (pair, element) gathered from I^m, K = orders,
-// columns = azimuths of the cos or sin weight table.
-__constant__ int c_synth_elem[2][8] = {{0, 1, 4, 5, 10, 11, 14, 15}, {2, 3, 6, 7, 8, 9, 12, 13}};
-__constant__ int c_synth_neg[2][8] = {{0, 0, 0, 0, 0, 0, 0, 0}, {1, 1, 1, 1, 0, 0, 0, 0}};
-
-// rows r = 8 (pair - pair0) + e, A(r, m) = Isyn[m][pair][elem(e)]; one thread per row,
-// 8 orders per 16-byte chunk of every slice
-template <int S>
-__global__ void k_slice_synth_rows(int n_rows, int pair0, long long pairs_total, int M,
-                                   int cls, const double* __restrict__ Isyn,
-                                   unsigned short* out, int* e_out, unsigned* status) {
-  int mt = blockIdx.x;
-  int r = threadIdx.x;
-  int row = mt * TC_M + r;
-  int Mp = pad_to(n_rows, TC_M), Kp = pad_to(M, TC_KB), KB = Kp / TC_KB, MT = Mp / TC_M;
-  bool valid = row < n_rows, bad = false;
-  size_t base_addr = 0;
-  if (valid) {
-    long long pair = pair0 + row / 8;
-    base_addr = (size_t)pair * 16 + c_synth_elem[cls][row & 7];
-  }
-  const size_t mstride = (size_t)pairs_total * 16;
-  int Em = 0;
-  if (valid)
-    for (int m = 0; m < M; ++m) Em = max(Em, exp_field(Isyn[(size_t)m * mstride + base_addr], &bad));
-  int ee = scale_exp(Em);
-  if (valid) e_out[row] = ee;
-  const size_t tile_elems = (size_t)TC_M * TC_KB;
-  const size_t slice_stride = (size_t)MT * KB * tile_elems;
-  for (int k0 = 0; k0 < Kp; k0 += 8) {
-    double v[8];
-    for (int t = 0; t < 8; ++t)
-      v[t] = (valid && k0 + t < M) ? Isyn[(size_t)(k0 + t) * mstride + base_addr] : 0.0;
-    int kb = k0 / TC_KB;
-    size_t base = ((size_t)mt * KB + kb) * tile_elems;
-    put_chunk<S>(v, ee, out + base + (swz_offset(r, k0 - kb * TC_KB) >> 1), slice_stride);
-  }
-  if (bad) atomicOr(status, ST_NONFINITE);
-}
-
-template <typename T>
-struct EpiSynth {
-  static constexpr bool kF32 = sizeof(T) == 4;
-  T* out;
-  int pair0, n_phi, cls;
-  unsigned* status;
-  __device__ void operator()(int, int i, int j, double v) const {
-    long long pair = pair0 + i / 8;
-    int e = i & 7;
-    double w = c_synth_neg[cls][e] ? -v : v;
-    if (!isfinite(w)) atomicOr(status, ST_NONFINITE);
-    out[((size_t)pair * n_phi + j) * 16 + c_synth_elem[cls][e]] = (T)w;
-  }
-  __device__ void put32(int, int i, int j, float v) const {
-    long long pair = pair0 + i / 8;
-    int e = i & 7;
-    float w = c_synth_neg[cls][e] ? -v : v;
-    if (!isfinite(w)) atomicOr(status, ST_NONFINITE);
-    out[((size_t)pair * n_phi + j) * 16 + c_synth_elem[cls][e]] = (T)w;
-  }
-};
-
-size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int S, int k_block) {
-  int rows = 8 * std::min(k_block, n_in) * n_out;
-  return tc_workspace_bytes(rows, n_phi, M, 1, S);
-}
-
-void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, const double* wc,
-                  const double* ws, void* out, int out_dtype, int S, int k_block, void* work,
-                  unsigned* status, cudaStream_t s) {
-  long long pairs_total = (long long)n_in * n_out;
-  for (int k0 = 0; k0 < n_in; k0 += k_block) {
-    int kb = std::min(k_block, n_in - k0);
-    int rows = 8 * kb * n_out;
-    int pair0 = k0 * n_out;
-    TcLayout L = tc_layout(rows, n_phi, M, 1, S);
-    unsigned char* w = (unsigned char*)work;
-    unsigned short* As = (unsigned short*)w;
-    unsigned short* Bs = (unsigned short*)(w + L.a_bytes);
-    int* ea = (int*)(w + L.a_bytes + L.b_bytes);
-    int* fb = (int*)(w + L.a_bytes + L.b_bytes + L.e_bytes);
-    int smem = tc_smem_bytes(S);
-    for (int cls = 0; cls < 2; ++cls) {
-#define VRTE_SLICE_SYN(SS)                                                                 \
-  k_slice_synth_rows<SS><<<L.MT, TC_M, 0, s>>>(rows, pair0, pairs_total, M, cls, Isyn, As, ea, \
-                                               status);                                      \
-  k_slice_cols<SS><<<dim3(L.NT, 1), 512, 0, s>>>(n_phi, M, cls ? ws : wc, n_phi, 0, Bs, fb,   \
-                                                 status)
-      VRTE_SLICE_DISPATCH(S, VRTE_SLICE_SYN)
-#undef VRTE_SLICE_SYN
-      if (out_dtype == VRTE_OUT_F64) {
-        EpiSynth<double> e{(double*)out, pair0, n_phi, cls, status};
-        cudaFuncSetAttribute(k_tc_gemm<EpiSynth<double>>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_tc_gemm<EpiSynth<double>><<<tc_grid((long long)L.MT * L.NT), 128, smem, s>>>(
-            rows, n_phi, M, S, As, ea, Bs, fb, e, status, 1);
-      } else {
-        EpiSynth<float> e{(float*)out, pair0, n_phi, cls, status};
-        cudaFuncSetAttribute(k_tc_gemm<EpiSynth<float>>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        k_tc_gemm<EpiSynth<float>><<<tc_grid((long long)L.MT * L.NT), 128, smem, s>>>(
-            rows, n_phi, M, S, As, ea, Bs, fb, e, status, 1);
-      }
-    }
-  }
 }
 
 }  // namespace vrte

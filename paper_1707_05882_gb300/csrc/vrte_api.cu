@@ -356,8 +356,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
     VRTE_ALLOC(Rbp, U * kd * R) VRTE_ALLOC(Rbm, U * kd * R)
   }
   if (mixed) {
-    size_t synth = tc_synthesis_workspace(Mx, p->n_in, p->n_out, p->n_phi, kSlicesSynth,
-                                          kSynthBlock);
+    size_t synth = tc_synthesis_workspace(Mx, p->n_in, p->n_out, p->n_phi, kSynthBlock);
     p->tcw_bytes = std::max(tc_unit * U, synth);
     if ((st = alloc(p, &w->tcw, p->tcw_bytes)) != VRTE_OK ||
         (st = allocd(p, &w->rscratch, refine_scratch_doubles((int)U, p->n_in, p->n_out))) !=
@@ -590,7 +589,8 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
     {
       const bool mixed = p->desc.precision == VRTE_MIXED;
       StageScope sc(p, ST_SYNTHESIS, s,
-                    mixed ? 6 * ((p->n_in + kSynthBlock - 1) / kSynthBlock) : 1, 2.0 * table * Meff,
+                    mixed ? 1 + 2 * ((p->n_in + kSynthBlock - 1) / kSynthBlock) : 1,
+                    2.0 * table * Meff,
                     (double)table * esz + (double)Meff * p->n_in * p->n_out * 16 * 8);
       if (mixed) {
         const int Ss = kSlicesSynth;
@@ -598,7 +598,7 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
       }
       if (mixed)
         tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws, outb, out_dtype,
-                     kSlicesSynth, kSynthBlock, w->tcw, p->d_status, s);
+                     kSynthBlock, w->tcw, p->d_status, s);
       else
         launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws, outb,
                               out_dtype, p->d_status, s);

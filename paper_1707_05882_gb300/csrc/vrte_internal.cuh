@@ -140,10 +140,11 @@ size_t refine_scratch_doubles(int U, int n_in, int n_out);
 void tc_gemm_part_accum(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                         const double* B, long long sB, double* T1, const double* g0tab, int S,
                         void* work, cudaStream_t s);
-// Synthesis of the order radiances on the tensor cores, in blocks of incident cosines.
-size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int S, int k_block);
+// Synthesis of the order radiances on the tensor cores (five slices), in blocks of k_block
+// incident cosines (k_synth_tc.cu).
+size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int k_block);
 void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, const double* wc,
-                  const double* ws, void* out, int out_dtype, int S, int k_block, void* work,
+                  const double* ws, void* out, int out_dtype, int k_block, void* work,
                   unsigned* status, cudaStream_t s);
 
 // ---------------------------------------------------------------- mode algebra (k_modes.cu)
