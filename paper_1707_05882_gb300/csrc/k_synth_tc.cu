@@ -53,25 +53,6 @@ __constant__ int c_class_el[2][8] = {{0, 1, 4, 5, 10, 11, 14, 15}, {2, 3, 6, 7, 
 // accumulator of slice pair (p, q)
 __device__ inline int sy_acc(int p, int q) { return min(p + q, SY_NACC - 1); }
 
-// Byte offset of element (row r, k) in a 64B-swizzled K-major tile of 32 BF16 per row:
-// 8-row groups of 512 bytes, 64 bytes per row, 16-byte chunk index XOR ((row / 2) mod 4).
-__device__ inline int swz64_offset(int r, int k) {
-  int chunk = k >> 3, within = k & 7;
-  return (r >> 3) * 512 + (r & 7) * 64 + ((chunk ^ ((r >> 1) & 3)) << 4) + within * 2;
-}
-
-__device__ inline uint64_t smem_desc_sw64(const void* p) {
-  uint64_t a = (uint64_t)(smem_u32(p) >> 4) & 0x3FFF;
-  return a | ((uint64_t)1 << 16)         // leading byte offset (unused for swizzled K-major)
-         | ((uint64_t)(512 >> 4) << 32)  // stride byte offset: 8 rows x 64 bytes
-         | ((uint64_t)1 << 46)           // descriptor version for sm_100-family
-         | ((uint64_t)4 << 61);          // 64-byte swizzle
-}
-
-__device__ inline void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 struct SynthLayout {
   int P, MT, NT, Kp, KB;
   size_t a_bytes, e_bytes, b_bytes, f_bytes;

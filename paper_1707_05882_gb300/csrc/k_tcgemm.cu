@@ -16,14 +16,15 @@
 // S = 4, ~3e-13 at S = 6, ~2e-15 at S = 7.
 //
 // Data flow: `k_slice_rows` / `k_slice_cols` write the slices directly as the shared-
-// memory image of 128B-swizzled K-major tiles ([unit][slice][tile][k-block] blocks of
-// 128 x 64 or 64 x 64 BF16), so the GEMM kernel loads each tile with one bulk copy. The
-// GEMM kernel computes a 128 x 64 output tile per CTA with up to seven accumulators of 64
-// columns in TMEM, as many shared-memory stages as fit (S = 7: one of 168 KB; S <= 4: two
-// or three; a 32-wide K block with two stages at S = 7 measured slower), one thread issuing
-// bulk copies and MMAs, and four warps draining TMEM in the epilogue. Every mbarrier wait
-// is bounded; on timeout the kernel records ST_TIMEOUT, waits (bounded) for its copies,
-// frees TMEM and returns.
+// memory image of 64B-swizzled K-major tiles ([unit][slice][tile][k-block] blocks of
+// 128 x 32 or 64 x 32 BF16), so the GEMM kernel loads each tile with one bulk copy. The
+// persistent GEMM kernel computes 128 x 64 output tiles with up to seven accumulators of
+// 64 columns in TMEM. It is warp-specialised: one warp keeps a ring of shared-memory
+// stages (S = 7: two of 84 KB; S <= 5: three or four) filled with bulk copies, one warp
+// issues the MMAs as stages fill, and four warps drain the accumulators; with S <= 4 two
+// TMEM buffers let the next tile's MMAs run during the epilogue. Every mbarrier wait is
+// bounded; on timeout the kernel records ST_TIMEOUT, waits (bounded) for its copies and
+// MMAs, frees TMEM and returns.
 #include <stdint.h>
 
 #include <algorithm>
@@ -34,13 +35,15 @@ namespace vrte {
 
 constexpr int TC_M = 128;       // output rows per CTA (MMA M)
 constexpr int TC_N = 64;        // output columns per CTA (MMA N)
-constexpr int TC_KB = 64;       // K per stage (one 128-byte swizzle row of BF16)
+constexpr int TC_KB = 32;       // K per stage (one 64-byte swizzle row of BF16)
 constexpr int TC_MAXS = 8;      // maximum number of slices
 constexpr int TC_NACC = 7;      // TMEM accumulators (see acc_index)
-constexpr int TC_STAGES = 3;    // shared-memory stages (at most)
+constexpr int TC_STAGES = 4;    // shared-memory stages (at most)
+constexpr int TC_THREADS = 192; // warp 0 copies, warp 1 MMAs, warps 2-5 epilogue
+constexpr int TC_GROUP_M = 8;   // row tiles per group of the tile order
 constexpr int TC_SMEM_MAX = 227 * 1024;
-constexpr int A_TILE_BYTES = TC_M * TC_KB * 2;   // 16 KiB
-constexpr int B_TILE_BYTES = TC_N * TC_KB * 2;   // 8 KiB
+constexpr int A_TILE_BYTES = TC_M * TC_KB * 2;   // 8 KiB
+constexpr int B_TILE_BYTES = TC_N * TC_KB * 2;   // 4 KiB
 
 // Accumulator of slice pair (p, q): diagonals d = p + q < 4 one each; diagonal 4 split by
 // p <= 2 (3 pairs) and p >= 3 (2 pairs) so that each stays exact for K <= 1024; the
@@ -52,20 +55,13 @@ __device__ __host__ inline int acc_index(int p, int q) {
 // diagonal (scale 2^-7d) of exact accumulator a
 __device__ __host__ inline int acc_diag(int a) { return a < 4 ? a : 4; }
 __device__ __host__ inline int acc_count(int S) { return S <= 4 ? S : (S == 5 ? 6 : 7); }
-// as many stages (up to three) of S slices of A and B tiles as fit in shared memory
+// as many stages (up to four) of S slices of A and B tiles as fit in shared memory
 __device__ __host__ inline int tc_stages(int S) {
-  int n = (TC_SMEM_MAX - 1024) / (S * (A_TILE_BYTES + B_TILE_BYTES));
+  int n = (TC_SMEM_MAX - 2048) / (S * (A_TILE_BYTES + B_TILE_BYTES));
   return n < 1 ? 1 : (n > TC_STAGES ? TC_STAGES : n);
 }
 __device__ __host__ inline int tc_smem_bytes(int S) {
   return tc_stages(S) * S * (A_TILE_BYTES + B_TILE_BYTES) + 1024;
-}
-
-// Byte offset of element (row r, k) inside a 128B-swizzled K-major tile of 64 BF16 per row:
-// 8-row groups of 1024 bytes, 128 bytes per row, 16-byte chunk index XOR (row mod 8).
-__device__ inline int swz_offset(int r, int k) {
-  int chunk = k >> 3, within = k & 7;
-  return (r >> 3) * 1024 + (r & 7) * 128 + ((chunk ^ (r & 7)) << 4) + within * 2;
 }
 
 // A rows: A[u][i][k] (row-major, lda, unit stride sA), M x K. Writes
@@ -104,7 +100,7 @@ __global__ void k_slice_rows(int M, int K, const double* __restrict__ A, int lda
       v[t] = (i < M && k0 + t < K) ? Ab[(size_t)i * lda + k0 + t] : 0.0;
     int kb = k0 / TC_KB;
     size_t base = ((((size_t)u * S) * MT + mt) * KB + kb) * tile_elems;
-    put_chunk<S>(v, ex[r], out + base + (swz_offset(r, k0 - kb * TC_KB) >> 1), slice_stride);
+    put_chunk<S>(v, ex[r], out + base + (swz64_offset(r, k0 - kb * TC_KB) >> 1), slice_stride);
   }
   if (bad) atomicOr(status, ST_NONFINITE);
 }
@@ -148,7 +144,7 @@ __global__ void k_slice_cols(int N, int K, const double* __restrict__ B, int ldb
       v[t] = (jj < N && k0 + t < K) ? Bb[(size_t)(k0 + t) * ldb + jj] : 0.0;
     int kb = k0 / TC_KB;
     size_t base = ((((size_t)u * S) * NT + nt) * KB + kb) * tile_elems;
-    put_chunk<S>(v, ex[cc], out + base + (swz_offset(cc, k0 - kb * TC_KB) >> 1), slice_stride);
+    put_chunk<S>(v, ex[cc], out + base + (swz64_offset(cc, k0 - kb * TC_KB) >> 1), slice_stride);
   }
   if (bad) atomicOr(status, ST_NONFINITE);
 }
@@ -166,42 +162,70 @@ __global__ void k_slice_cols(int N, int K, const double* __restrict__ B, int ldb
     default: CALL(8); break;         \
   }
 
+// TMEM columns of one accumulator buffer, buffers per CTA, and the allocation
+__device__ __host__ inline int tc_buf_cols(int S) { return acc_count(S) * TC_N; }
+__device__ __host__ inline int tc_nbuf(int S) { return 2 * tc_buf_cols(S) <= 512 ? 2 : 1; }
+__device__ __host__ inline uint32_t tc_tmem_cols(int S) {
+  int c = tc_nbuf(S) * tc_buf_cols(S);
+  return c <= 32 ? 32 : (c <= 64 ? 64 : (c <= 128 ? 128 : (c <= 256 ? 256 : 512)));
+}
+
+// tile t of the persistent sequence -> (unit, row tile, column tile): per unit, groups of
+// TC_GROUP_M row tiles with every column tile, row tile fastest inside a group, so that
+// the tiles in flight at one time share few slice panels (L2 reuse)
+__device__ inline void tc_decode(int t, int MT, int NT, int& u, int& mt, int& nt) {
+  const int per_unit = MT * NT;
+  u = t / per_unit;
+  const int tl = t - u * per_unit;
+  const int gsz = TC_GROUP_M * NT;
+  const int g = tl / gsz, idx = tl - g * gsz;
+  const int gm = min(TC_GROUP_M, MT - g * TC_GROUP_M);
+  mt = g * TC_GROUP_M + idx % gm;
+  nt = idx / gm;
+}
+
 template <class Epi>
-__global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
-                                                 const unsigned short* __restrict__ As,
-                                                 const int* __restrict__ ea,
-                                                 const unsigned short* __restrict__ Bs,
-                                                 const int* __restrict__ fb, Epi epi,
-                                                 unsigned* status, int batch) {
-  // Persistent: CTA b takes tiles b, b + gridDim.x, ... (tile t = mt + MT (nt + NT u)).
-  // Thread 0 issues bulk copies and MMAs; once a tile's MMAs are done it starts the next
-  // tile's first copies, which land while the four warps drain TMEM.
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_gemm(int M, int N, int K, int S, const unsigned short* __restrict__ As,
+              const int* __restrict__ ea, const unsigned short* __restrict__ Bs,
+              const int* __restrict__ fb, Epi epi, unsigned* status, int batch) {
+  // Persistent: CTA b takes tiles b, b + gridDim.x, ... Warp 0 bulk-copies the slice
+  // tiles of each 32-wide K block into a ring of shared-memory stages, warp 1 (owner of
+  // the TMEM allocation) issues the slice-pair MMAs as the stages fill, and warps 2-5
+  // drain the finished accumulators; with two TMEM buffers (S <= 4) the next tile's MMAs
+  // run during the epilogue, with one the copies for it do.
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  __shared__ uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], done_bar;
+  __shared__ uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], tfull_bar[2], tempty_bar[2],
+      fin_bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
-  // align the dynamic region to 1024 bytes (128B swizzle atoms)
-  unsigned char* smem =
-      (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ volatile int abort_flag;
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int Mp = pad_to(M, TC_M), Np = pad_to(N, TC_N), Kp = pad_to(K, TC_KB);
   const int KB = Kp / TC_KB, MT = Mp / TC_M, NT = Np / TC_N;
   const int tiles = MT * NT * batch;
   const int stage_bytes = S * (A_TILE_BYTES + B_TILE_BYTES);
   const int nst = tc_stages(S);
   const int nacc = acc_count(S);
+  const int buf_cols = tc_buf_cols(S), nbuf = tc_nbuf(S);
+  const uint32_t ncols = tc_tmem_cols(S);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t ncols = (nacc * TC_N <= 128) ? 128 : (nacc * TC_N <= 256 ? 256 : 512);
+  const size_t a_unit = (size_t)S * MT * KB * (A_TILE_BYTES / 2);
+  const size_t b_unit = (size_t)S * NT * KB * (B_TILE_BYTES / 2);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < TC_STAGES; ++s) {
       mbar_init(&full_bar[s], 1);
       mbar_init(&empty_bar[s], 1);
     }
-    mbar_init(&done_bar, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull_bar[b], 1);
+      mbar_init(&tempty_bar[b], 4);
+    }
+    mbar_init(&fin_bar, 1);
     abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tmem_slot)),
                  "r"(ncols) : "memory");
@@ -211,165 +235,139 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_slot;
-
-  // instruction descriptor: D = F32, A = B = BF16, K-major, N = 64, M = 128
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
-                         ((uint32_t)(TC_M >> 4) << 24);
-  const size_t a_unit = (size_t)S * MT * KB * (A_TILE_BYTES / 2);
-  const size_t b_unit = (size_t)S * NT * KB * (B_TILE_BYTES / 2);
-
-  // thread-0 pipeline state (barrier phases carry over from tile to tile)
-  bool pending[TC_STAGES] = {};
-  bool unwaited[TC_STAGES] = {};
-  uint32_t full_phase[TC_STAGES] = {}, empty_phase[TC_STAGES] = {}, done_phase = 0;
-  int issued = 0;
-  auto issue_copies = [&](int t, int kb, int s) {
-    const int tmt = t % MT, tnt = (t / MT) % NT, tu = t / (MT * NT);
-    unsigned char* st = smem + (size_t)s * stage_bytes;
-    mbar_expect_tx(&full_bar[s], (unsigned)stage_bytes);
-    for (int p = 0; p < S; ++p) {
-      const unsigned short* src =
-          As + (size_t)tu * a_unit + (((size_t)p * MT + tmt) * KB + kb) * (A_TILE_BYTES / 2);
-      bulk_g2s(st + p * A_TILE_BYTES, src, A_TILE_BYTES, &full_bar[s]);
-    }
-    for (int q = 0; q < S; ++q) {
-      const unsigned short* src =
-          Bs + (size_t)tu * b_unit + (((size_t)q * NT + tnt) * KB + kb) * (B_TILE_BYTES / 2);
-      bulk_g2s(st + S * A_TILE_BYTES + q * B_TILE_BYTES, src, B_TILE_BYTES, &full_bar[s]);
-    }
-    pending[s] = true;
+  auto fail = [&]() {
+    abort_flag = 1;
+    atomicOr(status, ST_TIMEOUT);
   };
-  auto prologue = [&](int t) {
-    for (issued = 0; issued < KB && issued < nst; ++issued) issue_copies(t, issued, issued);
-  };
-  if (threadIdx.x == 0 && (int)blockIdx.x < tiles) prologue(blockIdx.x);
 
-  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int mt = tile % MT, nt = (tile / MT) % NT, u = tile / (MT * NT);
-    if (threadIdx.x == 0) {
-      bool ok = true;
-      unsigned written = 0;  // accumulators that hold a value (the first MMA overwrites)
-      for (int kb = 0; kb < KB && ok; ++kb) {
-        int s = kb % nst;
-        if (!mbar_wait(&full_bar[s], full_phase[s])) { ok = false; break; }
-        full_phase[s] ^= 1;
-        pending[s] = false;
+  bool issued[TC_STAGES] = {};  // producer: stages with copies issued, and their round
+  int round_of[TC_STAGES] = {};
+  if (warp == 0) {
+    // ---- producer
+    if (lane == 0) {
+      int g = 0;
+      for (int t = blockIdx.x; t < tiles && !abort_flag; t += gridDim.x) {
+        int u, mt, nt;
+        tc_decode(t, MT, NT, u, mt, nt);
+        const unsigned short* a0 = As + (size_t)u * a_unit + (size_t)mt * KB * (A_TILE_BYTES / 2);
+        const unsigned short* b0 = Bs + (size_t)u * b_unit + (size_t)nt * KB * (B_TILE_BYTES / 2);
+        const size_t a_slice = (size_t)MT * KB * (A_TILE_BYTES / 2);
+        const size_t b_slice = (size_t)NT * KB * (B_TILE_BYTES / 2);
+        bool ok = true;
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % nst, r = g / nst;
+          if (!mbar_wait(&empty_bar[s], (r & 1) ^ 1)) { ok = false; break; }
+          unsigned char* st = smem + (size_t)s * stage_bytes;
+          mbar_expect_tx(&full_bar[s], (unsigned)stage_bytes);
+          for (int p = 0; p < S; ++p)
+            bulk_g2s(st + p * A_TILE_BYTES, a0 + p * a_slice + (size_t)kb * (A_TILE_BYTES / 2),
+                     A_TILE_BYTES, &full_bar[s]);
+          for (int q = 0; q < S; ++q)
+            bulk_g2s(st + S * A_TILE_BYTES + q * B_TILE_BYTES,
+                     b0 + q * b_slice + (size_t)kb * (B_TILE_BYTES / 2), B_TILE_BYTES,
+                     &full_bar[s]);
+          issued[s] = true;
+          round_of[s] = r;
+        }
+        if (!ok) { fail(); break; }
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issue
+    if (lane == 0) {
+      // D = F32, A = B = BF16, both K-major, N = 64, M = 128
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                             ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+      int g = 0, lt = 0;
+      for (int t = blockIdx.x; t < tiles && !abort_flag; t += gridDim.x, ++lt) {
+        const int b = nbuf == 2 ? (lt & 1) : 0, use = nbuf == 2 ? (lt >> 1) : lt;
+        if (!mbar_wait(&tempty_bar[b], (use & 1) ^ 1)) { fail(); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        unsigned char* st = smem + (size_t)s * stage_bytes;
-        // descriptors differ only in the start-address field (bits 0-13, 16-byte units)
-        const uint64_t abase = smem_desc_sw128(st);
-        const uint64_t bbase = smem_desc_sw128(st + S * A_TILE_BYTES);
-        for (int p = 0; p < S; ++p)
-          for (int q = 0; p + q < S; ++q) {
-            int a = acc_index(p, q);
-            uint32_t dt = tmem + (uint32_t)(a * TC_N);
+        const uint32_t dbase = tmem + (uint32_t)(b * buf_cols);
+        unsigned written = 0;  // accumulators that hold a value (the first MMA overwrites)
+        bool ok = true;
+        for (int kb = 0; kb < KB; ++kb, ++g) {
+          const int s = g % nst, r = g / nst;
+          if (!mbar_wait(&full_bar[s], r & 1)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          unsigned char* st = smem + (size_t)s * stage_bytes;
+          // descriptors differ only in the start-address field (bits 0-13, 16-byte units)
+          const uint64_t abase = smem_desc_sw64(st);
+          const uint64_t bbase = smem_desc_sw64(st + S * A_TILE_BYTES);
+          for (int p = 0; p < S; ++p)
+            for (int q = 0; p + q < S; ++q) {
+              const int a = acc_index(p, q);
 #pragma unroll
-            for (int k16 = 0; k16 < TC_KB / 16; ++k16) {
-              uint64_t ad = abase + (uint64_t)(p * (A_TILE_BYTES >> 4) + k16 * 2);
-              uint64_t bd = bbase + (uint64_t)(q * (B_TILE_BYTES >> 4) + k16 * 2);
-              uint32_t acc = (k16 == 0 && !((written >> a) & 1u)) ? 0u : 1u;
-              mma_bf16(dt, ad, bd, idesc, acc);
+              for (int k16 = 0; k16 < TC_KB / 16; ++k16) {
+                uint64_t ad = abase + (uint64_t)(p * (A_TILE_BYTES >> 4) + k16 * 2);
+                uint64_t bd = bbase + (uint64_t)(q * (B_TILE_BYTES >> 4) + k16 * 2);
+                uint32_t acc = (k16 == 0 && !((written >> a) & 1u)) ? 0u : 1u;
+                mma_bf16(dbase + (uint32_t)(a * TC_N), ad, bd, idesc, acc);
+              }
+              written |= 1u << a;
             }
-            written |= 1u << a;
-          }
-        mma_commit(&empty_bar[s]);
-        unwaited[s] = true;
-        // refill the previous block's stage once its MMAs are done, so that the MMAs just
-        // issued keep the tensor pipe busy meanwhile (with one stage: this block's stage)
-        const int lag = nst > 1 ? 1 : 0;
-        if (kb >= lag && issued < KB) {
-          int ps = (kb - lag) % nst;
-          if (!mbar_wait(&empty_bar[ps], empty_phase[ps])) { ok = false; break; }
-          empty_phase[ps] ^= 1;
-          unwaited[ps] = false;
-          issue_copies(tile, issued, ps);
-          ++issued;
+          mma_commit(&empty_bar[s]);  // the stage is free once these MMAs have read it
         }
+        if (!ok) { fail(); break; }
+        mma_commit(&tfull_bar[b]);    // the accumulators are final once every MMA is done
       }
-      // every MMA issued so far has completed once done_bar fires (also before an abort)
-      mma_commit(&done_bar);
-      if (!mbar_wait(&done_bar, done_phase)) ok = false;
-      done_phase ^= 1;
-      // the stage releases not waited for have completed too: keep the phases in step
-      for (int s2 = 0; s2 < TC_STAGES; ++s2)
-        if (unwaited[s2]) { empty_phase[s2] ^= 1; unwaited[s2] = false; }
-      if (ok && tile + (int)gridDim.x < tiles) prologue(tile + gridDim.x);
-      if (!ok) {
-        abort_flag = 1;
-        atomicOr(status, ST_TIMEOUT);
-      }
+      // every MMA issued has completed before TMEM is released (bounded)
+      mma_commit(&fin_bar);
+      if (!mbar_wait(&fin_bar, 0)) fail();
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (abort_flag) break;
-
-    // epilogue: warp w drains TMEM lanes 32w..32w+31 (output rows), 16 columns at a time
-    const int r = warp * 32 + lane;
-    const int i = mt * TC_M + r;
-    const int erow = (i < M) ? ea[(size_t)u * Mp + i] : 0;
-    for (int c0 = 0; c0 < TC_N; c0 += 16) {
-      uint32_t regs[TC_NACC][16];
+  } else {
+    // ---- epilogue: warp w drains TMEM lanes 32 (w mod 4) .. + 31 (output rows)
+    const int quad = warp & 3;
+    int lt = 0;
+    for (int t = blockIdx.x; t < tiles && !abort_flag; t += gridDim.x, ++lt) {
+      const int b = nbuf == 2 ? (lt & 1) : 0, use = nbuf == 2 ? (lt >> 1) : lt;
+      if (!mbar_wait(&tfull_bar[b], use & 1)) { fail(); break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int u, mt, nt;
+      tc_decode(t, MT, NT, u, mt, nt);
+      const int i = mt * TC_M + quad * 32 + lane;
+      const int erow = (i < M) ? ea[(size_t)u * Mp + i] : 0;
+      const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * buf_cols);
+      for (int c0 = 0; c0 < TC_N; c0 += 16) {
+        __syncwarp();
+        uint32_t regs[TC_NACC][16];
 #pragma unroll
-      for (int a = 0; a < TC_NACC; ++a) {
-        if (a >= nacc) {
+        for (int a = 0; a < TC_NACC; ++a) {
+          if (a >= nacc) {
 #pragma unroll
-          for (int t = 0; t < 16; ++t) regs[a][t] = 0u;  // +0.0f
-          continue;
-        }
-        uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * TC_N + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-            "%13,%14,%15}, [%16];\n"
-            : "=r"(regs[a][0]), "=r"(regs[a][1]), "=r"(regs[a][2]), "=r"(regs[a][3]),
-              "=r"(regs[a][4]), "=r"(regs[a][5]), "=r"(regs[a][6]), "=r"(regs[a][7]),
-              "=r"(regs[a][8]), "=r"(regs[a][9]), "=r"(regs[a][10]), "=r"(regs[a][11]),
-              "=r"(regs[a][12]), "=r"(regs[a][13]), "=r"(regs[a][14]), "=r"(regs[a][15])
-            : "r"(taddr));
-      }
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (i >= M) continue;
-      if constexpr (Epi::kF32) {
-        // FP32 output: an error-free FP32 sum (hi + lo) of the accumulators, largest first,
-        // rounded once; no FP64 instruction
-#pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          float hi = 0.0f, lo = 0.0f;
-#pragma unroll
-          for (int a = 0; a < TC_NACC; ++a) {
-            float x = __uint_as_float(regs[a][t]);
-            float sm = hi + x, bb = sm - hi;
-            lo += (hi - (sm - bb)) + (x - bb);
-            hi = sm;
+            for (int t2 = 0; t2 < 16; ++t2) regs[a][t2] = 0u;  // +0.0f
+            continue;
           }
-          int j = nt * TC_N + c0 + t;
-          if (j < N) {
-            int E2 = erow + fb[(size_t)u * Np + j] - 12;
-            float w = hi + lo;
-            float v = (E2 > -120 && E2 < 120) ? w * __int_as_float((E2 + 127) << 23)
-                                              : ldexpf(w, E2);
-            epi.put32(u, i, j, v);
-          }
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,"
+              "%12,%13,%14,%15}, [%16];\n"
+              : "=r"(regs[a][0]), "=r"(regs[a][1]), "=r"(regs[a][2]), "=r"(regs[a][3]),
+                "=r"(regs[a][4]), "=r"(regs[a][5]), "=r"(regs[a][6]), "=r"(regs[a][7]),
+                "=r"(regs[a][8]), "=r"(regs[a][9]), "=r"(regs[a][10]), "=r"(regs[a][11]),
+                "=r"(regs[a][12]), "=r"(regs[a][13]), "=r"(regs[a][14]), "=r"(regs[a][15])
+              : "r"(tbase + (uint32_t)(a * TC_N + c0)));
         }
-      } else {
-        // the exact accumulators hold integers in units of 2^-7d: combine them in an int64
-        // in units of 2^-28 (|I| < 2^53), then one FP64 fma adds the rounded last one
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (c0 + 16 >= TC_N) {
+          // the last reads of this buffer are done: hand it back to the MMA warp
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tempty_bar[b]);
+        }
+        if (i < M) {
+          // the exact accumulators hold integers in units of 2^-7d: combine them in an
+          // int64 in units of 2^-28 (|I| < 2^53), then one FP64 fma adds the rounded last one
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          long long I = 0;
-          float r4 = 0.0f;
+          for (int t2 = 0; t2 < 16; ++t2) {
+            const int j = nt * TC_N + c0 + t2;
+            if (j >= N) continue;
+            long long I = 0;
 #pragma unroll
-          for (int a = 0; a < TC_NACC; ++a) {
-            float x = __uint_as_float(regs[a][t]);
-            if (a < TC_NACC - 1)  // exact: an integer times 2^-7d, d = acc_diag(a)
-              I += (long long)__float2int_rn(x * (float)(1 << (7 * acc_diag(a))))
+            for (int a = 0; a < TC_NACC - 1; ++a)
+              I += (long long)__float2int_rn(__uint_as_float(regs[a][t2]) *
+                                             (float)(1 << (7 * acc_diag(a))))
                    << (7 * (4 - acc_diag(a)));
-            else
-              r4 = x;
-          }
-          int j = nt * TC_N + c0 + t;
-          if (j < N) {
-            double w = fma((double)I, 0x1p-28, (double)r4);
+            double w = fma((double)I, 0x1p-28, (double)__uint_as_float(regs[TC_NACC - 1][t2]));
             int E2 = erow + fb[(size_t)u * Np + j] - 12;
             // 2^E2 from its bit pattern while it is a normal number
             double v = (E2 > -1000 && E2 < 1000)
@@ -380,20 +378,15 @@ __global__ void __launch_bounds__(128) k_tc_gemm(int M, int N, int K, int S,
         }
       }
     }
-    // TMEM is free for the next tile's MMAs once every warp has read it
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  }
-  if (threadIdx.x == 0 && abort_flag) {
-    // let the copies still in flight land before the CTA exits (bounded)
-    for (int s = 0; s < TC_STAGES; ++s)
-      if (pending[s]) mbar_wait(&full_bar[s], full_phase[s]);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0)
+  // after an abort, let the copies still in flight land before the CTA exits (bounded)
+  if (warp == 0 && lane == 0 && abort_flag)
+    for (int s = 0; s < TC_STAGES; ++s)
+      if (issued[s]) mbar_wait(&full_bar[s], round_of[s] & 1);
+  if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
                  : "memory");
 }
@@ -457,7 +450,7 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
 #undef VRTE_SLICE_AB
   int smem = tc_smem_bytes(S);
   cudaFuncSetAttribute(k_tc_gemm<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_tc_gemm<Epi><<<tc_grid((long long)L.MT * L.NT * batch), 128, smem, s>>>(
+  k_tc_gemm<Epi><<<tc_grid((long long)L.MT * L.NT * batch), TC_THREADS, smem, s>>>(
       M, N, K, S, As, ea, Bs, fb, epi, status, batch);
 }
 
