@@ -267,28 +267,29 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
         if (!mbar_wait(&tempty_bar[b], (use & 1) ^ 1)) { fail(); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dbase = tmem + (uint32_t)(b * SY_NACC * SY_N);
-        unsigned written = 0;
         bool ok = true;
         for (int kb = 0; kb < KB; ++kb, ++g) {
           const int s = g % SY_STAGES, r = g / SY_STAGES;
           if (!mbar_wait(&full_bar[s], r & 1)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           unsigned char* st = smem + (size_t)s * SY_STAGE_BYTES;
-          const uint64_t abase = smem_desc_sw64(st);
-          const uint64_t bbase = smem_desc_sw64(st + SY_S * SY_A_TILE);
+          const uint64_t adesc = smem_desc_sw64(st);
+          const uint32_t alo = (uint32_t)adesc, dhi = (uint32_t)(adesc >> 32);
+          const uint32_t blo = (uint32_t)smem_desc_sw64(st + SY_S * SY_A_TILE);
+          const uint32_t later = kb > 0 ? 1u : 0u;
 #pragma unroll
           for (int p = 0; p < SY_S; ++p)
 #pragma unroll
             for (int q = 0; p + q < SY_S; ++q) {
               const int a = sy_acc(p, q);
+              // first pair (in this order) of its accumulator: overwrite in K block 0
+              const bool first = p == 0 && q < SY_NACC;
 #pragma unroll
-              for (int k16 = 0; k16 < SY_KB / 16; ++k16) {
-                uint64_t ad = abase + (uint64_t)(p * (SY_A_TILE >> 4) + k16 * 2);
-                uint64_t bd = bbase + (uint64_t)(q * (SY_B_TILE >> 4) + k16 * 2);
-                uint32_t acc = (k16 == 0 && !((written >> a) & 1u)) ? 0u : 1u;
-                mma_bf16(dbase + (uint32_t)(a * SY_N), ad, bd, idesc, acc);
-              }
-              written |= 1u << a;
+              for (int k16 = 0; k16 < SY_KB / 16; ++k16)
+                mma_bf16_w(dbase + (uint32_t)(a * SY_N),
+                           alo + (uint32_t)(p * (SY_A_TILE >> 4) + k16 * 2), dhi,
+                           blo + (uint32_t)(q * (SY_B_TILE >> 4) + k16 * 2), dhi, idesc,
+                           (k16 > 0 || !first) ? 1u : later);
             }
           mma_commit(&empty_bar[s]);  // the stage is free once these MMAs have read it
         }
