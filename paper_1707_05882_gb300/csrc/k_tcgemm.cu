@@ -188,7 +188,8 @@ template <class Epi>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(int M, int N, int K, int S, const unsigned short* __restrict__ As,
               const int* __restrict__ ea, const unsigned short* __restrict__ Bs,
-              const int* __restrict__ fb, Epi epi, unsigned* status, int batch) {
+              const int* __restrict__ fb, float* scratch, Epi epi, unsigned* status,
+              int batch) {
   // Persistent: CTA b takes tiles b, b + gridDim.x, ... Warp 0 bulk-copies the slice
   // tiles of each 32-wide K block into a ring of shared-memory stages, warp 1 (owner of
   // the TMEM allocation) issues the slice-pair MMAs as the stages fill, and warps 2-5
@@ -333,9 +334,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int i = mt * TC_M + quad * 32 + lane;
       const int erow = (i < M) ? ea[(size_t)u * Mp + i] : 0;
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * buf_cols);
-      for (int c0 = 0; c0 < TC_N; c0 += 16) {
-        __syncwarp();
-        uint32_t regs[TC_NACC][16];
+      // the exact accumulators hold integers in units of 2^-7d: combine them in an int64
+      // in units of 2^-28 (|I| < 2^53), then one FP64 fma adds the rounded last one
+      auto finish = [&](int c0, const uint32_t (&regs)[TC_NACC][16]) {
+#pragma unroll
+        for (int t2 = 0; t2 < 16; ++t2) {
+          const int j = nt * TC_N + c0 + t2;
+          if (j >= N) continue;
+          long long I = 0;
+#pragma unroll
+          for (int a = 0; a < TC_NACC - 1; ++a)
+            I += (long long)__float2int_rn(__uint_as_float(regs[a][t2]) *
+                                           (float)(1 << (7 * acc_diag(a))))
+                 << (7 * (4 - acc_diag(a)));
+          double w = fma((double)I, 0x1p-28, (double)__uint_as_float(regs[TC_NACC - 1][t2]));
+          int E2 = erow + fb[(size_t)u * Np + j] - 12;
+          // 2^E2 from its bit pattern while it is a normal number
+          double v = (E2 > -1000 && E2 < 1000)
+                         ? w * __longlong_as_double((long long)(E2 + 1023) << 52)
+                         : ldexp(w, E2);
+          epi(u, i, j, v);
+        }
+      };
+      auto load_tmem = [&](int c0, uint32_t (&regs)[TC_NACC][16]) {
 #pragma unroll
         for (int a = 0; a < TC_NACC; ++a) {
           if (a >= nacc) {
@@ -359,28 +380,54 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty_bar[b]);
         }
-        if (i < M) {
-          // the exact accumulators hold integers in units of 2^-7d: combine them in an
-          // int64 in units of 2^-28 (|I| < 2^53), then one FP64 fma adds the rounded last one
+      };
+      if (nbuf == 2) {
+        // two TMEM buffers: the next tile's MMAs already run in the other one
+        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+          __syncwarp();
+          uint32_t regs[TC_NACC][16];
+          load_tmem(c0, regs);
+          if (i < M) finish(c0, regs);
+        }
+      } else {
+        // one TMEM buffer: park the raw accumulators in this CTA's (L2-resident) scratch,
+        // layout [acc][column / 4][row] of float4 so that every warp store is coalesced,
+        // hand TMEM back at once, and combine from the scratch while the MMAs of the next
+        // tile run (each thread reads back only what it wrote)
+        float4* sc = (float4*)scratch + (size_t)blockIdx.x * (TC_NACC * (TC_N / 4) * TC_M);
+        const int row = quad * 32 + lane;
+        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+          __syncwarp();
+          uint32_t regs[TC_NACC][16];
+          load_tmem(c0, regs);
 #pragma unroll
-          for (int t2 = 0; t2 < 16; ++t2) {
-            const int j = nt * TC_N + c0 + t2;
-            if (j >= N) continue;
-            long long I = 0;
+          for (int a = 0; a < TC_NACC; ++a) {
+            if (a >= nacc) continue;
 #pragma unroll
-            for (int a = 0; a < TC_NACC - 1; ++a)
-              I += (long long)__float2int_rn(__uint_as_float(regs[a][t2]) *
-                                             (float)(1 << (7 * acc_diag(a))))
-                   << (7 * (4 - acc_diag(a)));
-            double w = fma((double)I, 0x1p-28, (double)__uint_as_float(regs[TC_NACC - 1][t2]));
-            int E2 = erow + fb[(size_t)u * Np + j] - 12;
-            // 2^E2 from its bit pattern while it is a normal number
-            double v = (E2 > -1000 && E2 < 1000)
-                           ? w * __longlong_as_double((long long)(E2 + 1023) << 52)
-                           : ldexp(w, E2);
-            epi(u, i, j, v);
+            for (int g4 = 0; g4 < 4; ++g4)
+              sc[((size_t)a * (TC_N / 4) + c0 / 4 + g4) * TC_M + row] =
+                  make_float4(__uint_as_float(regs[a][4 * g4]), __uint_as_float(regs[a][4 * g4 + 1]),
+                              __uint_as_float(regs[a][4 * g4 + 2]),
+                              __uint_as_float(regs[a][4 * g4 + 3]));
           }
         }
+        if (i < M)
+          for (int c0 = 0; c0 < TC_N; c0 += 16) {
+            uint32_t regs[TC_NACC][16];
+#pragma unroll
+            for (int a = 0; a < TC_NACC; ++a) {
+#pragma unroll
+              for (int g4 = 0; g4 < 4; ++g4) {
+                float4 v4 = a < nacc ? sc[((size_t)a * (TC_N / 4) + c0 / 4 + g4) * TC_M + row]
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                regs[a][4 * g4] = __float_as_uint(v4.x);
+                regs[a][4 * g4 + 1] = __float_as_uint(v4.y);
+                regs[a][4 * g4 + 2] = __float_as_uint(v4.z);
+                regs[a][4 * g4 + 3] = __float_as_uint(v4.w);
+              }
+            }
+            finish(c0, regs);
+          }
       }
     }
   }
@@ -411,8 +458,11 @@ static int tc_grid(long long tiles) {
 
 struct TcLayout {
   int Mp, Np, Kp, MT, NT, KB;
-  size_t a_bytes, b_bytes, e_bytes, f_bytes;
+  size_t a_bytes, b_bytes, e_bytes, f_bytes, s_bytes;
 };
+
+// epilogue scratch of one persistent CTA: the raw accumulators of one tile
+constexpr size_t TC_SCRATCH_PER_CTA = (size_t)TC_NACC * TC_M * TC_N * sizeof(float);
 
 static TcLayout tc_layout(int M, int N, int K, int batch, int S) {
   TcLayout L;
@@ -427,12 +477,15 @@ static TcLayout tc_layout(int M, int N, int K, int batch, int S) {
   L.b_bytes = al((size_t)batch * S * L.Np * L.Kp * 2);
   L.e_bytes = al((size_t)batch * L.Mp * 4);
   L.f_bytes = al((size_t)batch * L.Np * 4);
+  L.s_bytes = tc_scratch_bytes();
   return L;
 }
 
+size_t tc_scratch_bytes() { return (size_t)tc_grid(1ll << 40) * TC_SCRATCH_PER_CTA; }
+
 size_t tc_workspace_bytes(int M, int N, int K, int batch, int S) {
   TcLayout L = tc_layout(M, N, K, batch, S);
-  return L.a_bytes + L.b_bytes + L.e_bytes + L.f_bytes;
+  return L.a_bytes + L.b_bytes + L.e_bytes + L.f_bytes + L.s_bytes;
 }
 
 bool tc_shape_ok(int K, int S) { return S >= 1 && S <= TC_MAXS && K >= 1 && K <= 1024; }
@@ -448,6 +501,7 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
   unsigned short* Bs = (unsigned short*)(w + L.a_bytes);
   int* ea = (int*)(w + L.a_bytes + L.b_bytes);
   int* fb = (int*)(w + L.a_bytes + L.b_bytes + L.e_bytes);
+  float* scratch = (float*)(w + L.a_bytes + L.b_bytes + L.e_bytes + L.f_bytes);
 #define VRTE_SLICE_AB(SS)                                                                  \
   k_slice_rows<SS><<<dim3(L.MT, batch), 256, 0, s>>>(M, K, A, lda, sA, As, ea, status);  \
   k_slice_cols<SS><<<dim3(L.NT, batch), 512, 0, s>>>(N, K, B, ldb, sB, Bs, fb, status)
@@ -456,7 +510,7 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
   int smem = tc_smem_bytes(S);
   cudaFuncSetAttribute(k_tc_gemm<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_tc_gemm<Epi><<<tc_grid((long long)L.MT * L.NT * batch), TC_THREADS, smem, s>>>(
-      M, N, K, S, As, ea, Bs, fb, epi, status, batch);
+      M, N, K, S, As, ea, Bs, fb, scratch, epi, status, batch);
 }
 
 struct TcEpiStore {

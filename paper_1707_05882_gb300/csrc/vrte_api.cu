@@ -295,7 +295,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
                    tc_workspace_bytes((int)(2 * n), (int)R, (int)(2 * n), 1, S),
                    tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n), 1, S),
                    tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n + kd), 1, S)};
-    for (size_t v : c) tc_unit = std::max(tc_unit, v);
+    for (size_t v : c) tc_unit = std::max(tc_unit, v - tc_scratch_bytes());
   }
   size_t per_unit = 3 * (size_t)Lx * P + 10 * n * n + 3 * n + 8 * n * n + 5 * n * R +
                     (4 * n + kd) * R + 2 * n * R + 4 * Ro * n + Ro * (2 * n + kd) + Ro * R + n * n +
@@ -357,7 +357,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   }
   if (mixed) {
     size_t synth = tc_synthesis_workspace(Mx, p->n_in, p->n_out, p->n_phi, kSynthBlock);
-    p->tcw_bytes = std::max(tc_unit * U, synth);
+    p->tcw_bytes = std::max(tc_unit * U + tc_scratch_bytes(), synth);
     if ((st = alloc(p, &w->tcw, p->tcw_bytes)) != VRTE_OK ||
         (st = allocd(p, &w->rscratch, refine_scratch_doubles((int)U, p->n_in, p->n_out))) !=
             VRTE_OK ||

@@ -122,6 +122,8 @@ void eigen_block_fallback(int n, int m0, const double* E, const double* F, const
 // C = A B (+ beta C) with A, B FP64 sliced into S exact 7-bit BF16 slices (relative
 // accuracy ~2^-7S per term); K <= 1024, 1 <= S <= 4. `work` holds tc_workspace_bytes.
 size_t tc_workspace_bytes(int M, int N, int K, int batch, int S);
+// the part of tc_workspace_bytes that does not grow with the batch (epilogue scratch)
+size_t tc_scratch_bytes();
 bool tc_shape_ok(int K, int S);
 void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, const double* B,
                    int ldb, long long sB, double beta, double* C, int ldc, long long sC,
