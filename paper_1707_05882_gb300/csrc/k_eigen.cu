@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
                                    // reflectors (tau, v1, v2), n entries each
   __shared__ double red[32];
   __shared__ int ired[32];
-  __shared__ double xyz[3];  // next bulge column, forwarded from the right update
+  __shared__ double refl[2][3];  // reflectors of the current and the next sweep step
   int u = blockIdx.x;
   if (mask && !mask[u]) return;
   int tid = threadIdx.x, nt = blockDim.x;
@@ -266,77 +266,72 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
       }
       break;
     }
-    double h11, h12, h21, h22;
-    if (its % 20 == 10) {
-      double s = fabs(H[(size_t)(l + 1) * n + l]) + fabs(H[(size_t)(l + 2) * n + l + 1]);
-      h11 = 0.75 * s + H[(size_t)l * n + l]; h12 = -0.4375 * s; h21 = s; h22 = h11;
-    } else if (its % 20 == 0) {
-      double s = fabs(H[(size_t)hi * n + hi - 1]) + fabs(H[(size_t)(hi - 1) * n + hi - 2]);
-      h11 = 0.75 * s + H[(size_t)hi * n + hi]; h12 = -0.4375 * s; h21 = s; h22 = h11;
-    } else {
-      h11 = H[(size_t)(hi - 1) * n + hi - 1]; h12 = H[(size_t)(hi - 1) * n + hi];
-      h21 = H[(size_t)hi * n + hi - 1]; h22 = H[(size_t)hi * n + hi];
-    }
-    // Shifts: the eigenvalues of the 2x2 block (computed on a scaled copy). A complex pair
-    // is used as a double shift; real shifts are replaced by the one closer to h22 taken
-    // twice. The first column of (H - s1)(H - s2) e1 is formed from differences
-    // (h_ll - s1)(h_ll - s2) + h_{l,l+1} h_{l+1,l}, scaled by 1/s3: expanding it into
-    // h_ll^2 - (s1 + s2) h_ll + s1 s2 cancels catastrophically when the shifts sit inside
-    // a tight eigenvalue cluster and the sweeps then stall.
-    double r1r, r1i, r2r, r2i;
-    {
-      double sc = fabs(h11) + fabs(h12) + fabs(h21) + fabs(h22);
-      if (sc == 0.0) {
-        r1r = r1i = r2r = r2i = 0.0;
+    // The reflectors of the sweep are computed by warp 0 alone (FP64 square roots and
+    // divisions are scarce) and passed through shared memory, double-buffered by step
+    // parity: refl[k & 1] = (tau, v1, v2) of step k.
+    if (warp == 0) {
+      double h11, h12, h21, h22;
+      if (its % 20 == 10) {
+        double s = fabs(H[(size_t)(l + 1) * n + l]) + fabs(H[(size_t)(l + 2) * n + l + 1]);
+        h11 = 0.75 * s + H[(size_t)l * n + l]; h12 = -0.4375 * s; h21 = s; h22 = h11;
+      } else if (its % 20 == 0) {
+        double s = fabs(H[(size_t)hi * n + hi - 1]) + fabs(H[(size_t)(hi - 1) * n + hi - 2]);
+        h11 = 0.75 * s + H[(size_t)hi * n + hi]; h12 = -0.4375 * s; h21 = s; h22 = h11;
       } else {
-        double a11 = h11 / sc, a12 = h12 / sc, a21 = h21 / sc, a22 = h22 / sc;
-        double tr = 0.5 * (a11 + a22);
-        double det = (a11 - tr) * (a22 - tr) - a12 * a21;
-        double rt = sqrt(fabs(det));
-        if (det >= 0.0) {
-          r1r = r2r = tr * sc;
-          r1i = rt * sc;
-          r2i = -r1i;
+        h11 = H[(size_t)(hi - 1) * n + hi - 1]; h12 = H[(size_t)(hi - 1) * n + hi];
+        h21 = H[(size_t)hi * n + hi - 1]; h22 = H[(size_t)hi * n + hi];
+      }
+      // Shifts: the eigenvalues of the 2x2 block (computed on a scaled copy). A complex
+      // pair is used as a double shift; real shifts are replaced by the one closer to h22
+      // taken twice. The first column of (H - s1)(H - s2) e1 is formed from differences
+      // (h_ll - s1)(h_ll - s2) + h_{l,l+1} h_{l+1,l}, scaled by 1/s3: expanding it into
+      // h_ll^2 - (s1 + s2) h_ll + s1 s2 cancels catastrophically when the shifts sit inside
+      // a tight eigenvalue cluster and the sweeps then stall.
+      double r1r, r1i, r2r, r2i;
+      {
+        double sc = fabs(h11) + fabs(h12) + fabs(h21) + fabs(h22);
+        if (sc == 0.0) {
+          r1r = r1i = r2r = r2i = 0.0;
         } else {
-          r1r = tr + rt;
-          r2r = tr - rt;
-          if (fabs(r1r - a22) <= fabs(r2r - a22)) { r1r *= sc; r2r = r1r; }
-          else { r2r *= sc; r1r = r2r; }
-          r1i = r2i = 0.0;
+          double a11 = h11 / sc, a12 = h12 / sc, a21 = h21 / sc, a22 = h22 / sc;
+          double tr = 0.5 * (a11 + a22);
+          double det = (a11 - tr) * (a22 - tr) - a12 * a21;
+          double rt = sqrt(fabs(det));
+          if (det >= 0.0) {
+            r1r = r2r = tr * sc;
+            r1i = rt * sc;
+            r2i = -r1i;
+          } else {
+            r1r = tr + rt;
+            r2r = tr - rt;
+            if (fabs(r1r - a22) <= fabs(r2r - a22)) { r1r *= sc; r2r = r1r; }
+            else { r2r *= sc; r1r = r2r; }
+            r1i = r2i = 0.0;
+          }
         }
       }
-    }
-    double hll = H[(size_t)l * n + l], hl1l = H[(size_t)(l + 1) * n + l];
-    double s3 = fabs(hll - r2r) + fabs(r2i) + fabs(hl1l);
-    double h21s = hl1l / s3;
-    double x = h21s * H[(size_t)l * n + l + 1] + (hll - r1r) * ((hll - r2r) / s3) - r1i * (r2i / s3);
-    double y = h21s * (hll + H[(size_t)(l + 1) * n + l + 1] - r1r - r2r);
-    double z = h21s * H[(size_t)(l + 2) * n + l + 1];
-    bool fwd = false;  // xyz holds the bulge column written by the previous right update
-    for (int k = l; k <= hi - 1; ++k) {
-      int nr = (k < hi - 1) ? 3 : 2;
-      if (k > l) {
-        if (fwd) {
-          x = xyz[0];
-          y = xyz[1];
-          z = (nr == 3) ? xyz[2] : 0.0;
-        } else {
-          x = H[(size_t)k * n + k - 1];
-          y = H[(size_t)(k + 1) * n + k - 1];
-          z = (nr == 3) ? H[(size_t)(k + 2) * n + k - 1] : 0.0;
-        }
-      }
+      double hll = H[(size_t)l * n + l], hl1l = H[(size_t)(l + 1) * n + l];
+      double s3 = fabs(hll - r2r) + fabs(r2i) + fabs(hl1l);
+      double h21s = hl1l / s3;
+      double x = h21s * H[(size_t)l * n + l + 1] + (hll - r1r) * ((hll - r2r) / s3) - r1i * (r2i / s3);
+      double y = h21s * (hll + H[(size_t)(l + 1) * n + l + 1] - r1r - r2r);
+      double z = h21s * H[(size_t)(l + 2) * n + l + 1];
+      const int nr = (l < hi - 1) ? 3 : 2;
       double tau, v1, v2;
       house3(x, y, nr == 3 ? z : 0.0, tau, v1, v2);
       if (nr == 2) v2 = 0.0;
-      if (tid == 0) {
-        rtau[k - l] = tau;
-        rv1[k - l] = v1;
-        rv2[k - l] = v2;
+      if (lane == 0) {
+        refl[l & 1][0] = tau; refl[l & 1][1] = v1; refl[l & 1][2] = v2;
+        rtau[0] = tau; rv1[0] = v1; rv2[0] = v2;
       }
-      // the left update below overwrites H values this step read from global memory; with
-      // the bulge column forwarded in shared memory nothing is read from H before it
-      if (!(k > l && fwd)) __syncthreads();
+    }
+    __syncthreads();
+    for (int k = l; k <= hi - 1; ++k) {
+      const int nr = (k < hi - 1) ? 3 : 2;
+      const double tau = refl[k & 1][0], v1 = refl[k & 1][1], v2 = refl[k & 1][2];
+      // right-update rows rotate so that rows k+1 .. k+3 (the next bulge column) fall on
+      // lanes 0 .. 2 of warp 0
+      double nb = 0.0;
       if (tau != 0.0) {
         int c0 = (k > l) ? k - 1 : l;
         // left: rows k..k+nr-1, columns c0..n-1
@@ -353,19 +348,41 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
           H[(size_t)(k + 1) * n + k - 1] = 0.0;
           if (nr == 3) H[(size_t)(k + 2) * n + k - 1] = 0.0;
         }
-        // right: columns k..k+nr-1, rows 0..min(k+3, hi); Z columns k..k+nr-1
-        int rmax = min(k + 3, hi);
-        for (int i = tid; i <= rmax; i += nt) {
+        // right: columns k..k+nr-1, rows 0..min(k+3, hi)
+        const int rows = min(k + 3, hi) + 1;
+        for (int t = tid; t < rows; t += nt) {
+          int i = k + 1 + t;
+          if (i >= rows) i -= rows;
           double h0 = H[(size_t)i * n + k], h1 = H[(size_t)i * n + k + 1];
           double h2 = (nr == 3) ? H[(size_t)i * n + k + 2] : 0.0;
           double w = tau * (h0 + v1 * h1 + v2 * h2);
           H[(size_t)i * n + k] = h0 - w;
-          if (i > k) xyz[i - k - 1] = h0 - w;  // column k of rows k+1..k+3: the next bulge
+          if (t == tid) nb = h0 - w;
           H[(size_t)i * n + k + 1] = h1 - w * v1;
           if (nr == 3) H[(size_t)i * n + k + 2] = h2 - w * v2;
         }
       }
-      fwd = (tau != 0.0);
+      // reflector of step k + 1 from column k of rows k+1 .. k+3 (warp 0)
+      if (k + 1 <= hi - 1 && warp == 0) {
+        const int nr1 = (k + 1 < hi - 1) ? 3 : 2;
+        double x, y, z;
+        if (tau != 0.0) {
+          x = __shfl_sync(0xffffffffu, nb, 0);
+          y = __shfl_sync(0xffffffffu, nb, 1);
+          z = __shfl_sync(0xffffffffu, nb, 2);
+        } else {
+          x = H[(size_t)(k + 1) * n + k];
+          y = H[(size_t)(k + 2) * n + k];
+          z = (nr1 == 3) ? H[(size_t)(k + 3) * n + k] : 0.0;
+        }
+        double t1, w1, w2;
+        house3(x, y, nr1 == 3 ? z : 0.0, t1, w1, w2);
+        if (nr1 == 2) w2 = 0.0;
+        if (lane == 0) {
+          refl[(k + 1) & 1][0] = t1; refl[(k + 1) & 1][1] = w1; refl[(k + 1) & 1][2] = w2;
+          rtau[k + 1 - l] = t1; rv1[k + 1 - l] = w1; rv2[k + 1 - l] = w2;
+        }
+      }
       __syncthreads();
     }
     // Schur vectors: Z <- Z P_l ... P_{hi-1}, deferred to the end of the sweep. Each row of
