@@ -11,13 +11,14 @@
 // pairs of 2^12-bounded integers, K <= 1365), the diagonals 3 and 4 sharing a fourth whose
 // FP32 rounding lies about 2^-37 below the leading term.
 //
-// Kernel structure (one persistent CTA per SM, 192 threads):
+// Kernel structure (one persistent CTA per SM, 320 threads):
 //   warp 0    bulk-copies the slice tiles of A (rows) and B (azimuths) for one 32-order K
 //             block into one of three 60 KB shared-memory stages;
 //   warp 1    owns the TMEM allocation (512 columns = two buffers of 4 x 64) and issues
 //             the 15 slice-pair MMAs of every K block into the tile's buffer;
-//   warps 2-5 drain a finished buffer (TMEM -> registers -> error-free FP32 sum ->
-//             scaled store) while warp 1 already fills the other one.
+//   warps 2-9 drain a finished buffer (TMEM -> registers -> error-free FP32 sum ->
+//             scaled store; two warps per TMEM lane quarter, 32 columns each) while
+//             warp 1 already fills the other one.
 // Tiles run azimuth-tile fastest, so the six azimuth tiles of one row tile are in flight
 // together and its slices come from L2 after the first read. Every wait is bounded: on
 // timeout the kernel records ST_TIMEOUT, waits (bounded) for its copies and MMAs, frees
@@ -41,7 +42,8 @@ constexpr int SY_A_TILE = SY_M * SY_KB * 2;                      // 8 KiB
 constexpr int SY_B_TILE = SY_N * SY_KB * 2;                      // 4 KiB
 constexpr int SY_STAGE_BYTES = SY_S * (SY_A_TILE + SY_B_TILE);   // 60 KiB
 constexpr int SY_SMEM = SY_STAGES * SY_STAGE_BYTES + 1024;
-constexpr int SY_THREADS = 192;
+constexpr int SY_EPI_WARPS = 8;  // two per TMEM lane quarter, each draining 32 columns
+constexpr int SY_THREADS = 64 + 32 * SY_EPI_WARPS;
 constexpr uint32_t SY_TMEM_COLS = 2 * SY_NACC * SY_N;            // 512
 constexpr int SY_PAIRS_PER_TILE = SY_M / 8;
 
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull_bar[b], 1);
-      mbar_init(&tempty_bar[b], 4);
+      mbar_init(&tempty_bar[b], SY_EPI_WARPS);
     }
     mbar_init(&fin_bar, 1);
     abort_flag = 0;
@@ -301,8 +303,10 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
       if (!mbar_wait(&fin_bar, 0)) fail();
     }
   } else {
-    // ---- epilogue: warp w drains TMEM lanes 32 (w mod 4) .. + 31 (tile rows)
+    // ---- epilogue: warp w drains TMEM lanes 32 (w mod 4) .. + 31 (tile rows), columns
+    // 32 h .. 32 h + 31 with h = (w - 2) / 4
     const int quad = warp & 3;
+    const int cbeg = ((warp - 2) >> 2) * (SY_N / 2);
     const int r = quad * 32 + lane;
     const int pl = r >> 3, e = r & 7;
     int lt = 0;
@@ -319,7 +323,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
       const int* fcol = fb + (size_t)cls * NT * SY_N + nt * SY_N;
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * SY_NACC * SY_N);
       bool bad = false;
-      for (int c0 = 0; c0 < SY_N; c0 += 16) {
+      for (int c0 = cbeg; c0 < cbeg + SY_N / 2; c0 += 16) {
         __syncwarp();
         uint32_t x[SY_NACC][16];
 #pragma unroll
@@ -334,8 +338,8 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
               : "r"(tbase + (uint32_t)(a * SY_N + c0)));
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (c0 + 16 >= SY_N) {
-          // the last reads of this buffer are done: hand it back to the MMA warp
+        if (c0 + 16 >= cbeg + SY_N / 2) {
+          // this warp's last reads of the buffer are done: hand its share back
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty_bar[b]);
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
             for (int a = 0; a < SY_NACC; ++a) xs[a] = x[a][t16];
             T v = synth_value(xs, erow + fcol[c0 + t16], (T*)nullptr);
             bad |= !isfinite((double)v);
-            orow[(size_t)j * 16] = v;
+            __stcs(orow + (size_t)j * 16, v);  // the table streams out (evict-first)
           }
         }
       }
