@@ -21,7 +21,7 @@
 // persistent GEMM kernel computes 128 x 64 output tiles with up to seven accumulators of
 // 64 columns in TMEM. It is warp-specialised: one warp keeps a ring of shared-memory
 // stages (S = 7: two of 84 KB; S <= 5: three or four) filled with bulk copies, one warp
-// issues the MMAs as stages fill, and four warps drain the accumulators; with S <= 4 two
+// issues the MMAs as stages fill, and eight warps drain the accumulators; with S <= 4 two
 // TMEM buffers let the next tile's MMAs run during the epilogue. Every mbarrier wait is
 // bounded; on timeout the kernel records ST_TIMEOUT, waits (bounded) for its copies and
 // MMAs, frees TMEM and returns.
@@ -39,7 +39,8 @@ constexpr int TC_KB = 32;       // K per stage (one 64-byte swizzle row of BF16)
 constexpr int TC_MAXS = 8;      // maximum number of slices
 constexpr int TC_NACC = 7;      // TMEM accumulators (see acc_index)
 constexpr int TC_STAGES = 4;    // shared-memory stages (at most)
-constexpr int TC_THREADS = 192; // warp 0 copies, warp 1 MMAs, warps 2-5 epilogue
+constexpr int TC_EPI_WARPS = 8; // epilogue warps: two per TMEM lane quarter, 32 columns each
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;  // warp 0 copies, warp 1 MMAs
 constexpr int TC_GROUP_M = 8;   // row tiles per group of the tile order
 constexpr int TC_SMEM_MAX = 227 * 1024;
 constexpr int A_TILE_BYTES = TC_M * TC_KB * 2;   // 8 KiB
@@ -192,8 +193,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               int batch) {
   // Persistent: CTA b takes tiles b, b + gridDim.x, ... Warp 0 bulk-copies the slice
   // tiles of each 32-wide K block into a ring of shared-memory stages, warp 1 (owner of
-  // the TMEM allocation) issues the slice-pair MMAs as the stages fill, and warps 2-5
-  // drain the finished accumulators; with two TMEM buffers (S <= 4) the next tile's MMAs
+  // the TMEM allocation) issues the slice-pair MMAs as the stages fill, and warps 2-9
+  // drain the finished accumulators (two per TMEM lane quarter); with two TMEM buffers (S <= 4) the next tile's MMAs
   // run during the epilogue, with one the copies for it do.
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES], tfull_bar[2], tempty_bar[2],
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull_bar[b], 1);
-      mbar_init(&tempty_bar[b], 4);
+      mbar_init(&tempty_bar[b], TC_EPI_WARPS);
     }
     mbar_init(&fin_bar, 1);
     abort_flag = 0;
@@ -322,8 +323,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!mbar_wait(&fin_bar, 0)) fail();
     }
   } else {
-    // ---- epilogue: warp w drains TMEM lanes 32 (w mod 4) .. + 31 (output rows)
+    // ---- epilogue: warp w drains TMEM lanes 32 (w mod 4) .. + 31 (output rows), columns
+    // 32 h .. 32 h + 31 with h = (w - 2) / 4
     const int quad = warp & 3;
+    const int cbeg = ((warp - 2) >> 2) * (TC_N / 2), cend = cbeg + TC_N / 2;
     int lt = 0;
     for (int t = blockIdx.x; t < tiles && !abort_flag; t += gridDim.x, ++lt) {
       const int b = nbuf == 2 ? (lt & 1) : 0, use = nbuf == 2 ? (lt >> 1) : lt;
@@ -374,8 +377,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
               : "r"(tbase + (uint32_t)(a * TC_N + c0)));
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (c0 + 16 >= TC_N) {
-          // the last reads of this buffer are done: hand it back to the MMA warp
+        if (c0 + 16 >= cend) {
+          // this warp's last reads of the buffer are done: hand its share back
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(&tempty_bar[b]);
@@ -383,7 +386,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       };
       if (nbuf == 2) {
         // two TMEM buffers: the next tile's MMAs already run in the other one
-        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
           __syncwarp();
           uint32_t regs[TC_NACC][16];
           load_tmem(c0, regs);
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // tile run (each thread reads back only what it wrote)
         float4* sc = (float4*)scratch + (size_t)blockIdx.x * (TC_NACC * (TC_N / 4) * TC_M);
         const int row = quad * 32 + lane;
-        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
           __syncwarp();
           uint32_t regs[TC_NACC][16];
           load_tmem(c0, regs);
@@ -412,7 +415,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           }
         }
         if (i < M)
-          for (int c0 = 0; c0 < TC_N; c0 += 16) {
+          for (int c0 = cbeg; c0 < cend; c0 += 16) {
             uint32_t regs[TC_NACC][16];
 #pragma unroll
             for (int a = 0; a < TC_NACC; ++a) {
