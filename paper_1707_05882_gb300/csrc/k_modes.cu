@@ -263,53 +263,75 @@ void launch_bc_rhs(const OrderBatch& b, const double* SD, const double* d, const
 //   g_D = int_0^tau0 exp(-kappa t) exp(-t/mu) dt / mu = (1 - e^{-a tau0}) / (mu a), a = 1/mu + kappa
 //   g_G = int_0^tau0 exp(-kappa (tau0 - t)) exp(-t/mu) dt / mu
 //       = e^{-tau0/mu} (1 - e^{-b tau0}) / (mu b), b = kappa - 1/mu (limit tau0 e^{-tau0/mu}/mu).
+constexpr int HHAT_OB = 16;  // outgoing cosines per block of k_build_Hhat
+
 __global__ void k_build_Hhat(int N, int n, int n_in, int n_out, double tau, const double* P1,
                              const double* P2, const double* lam_re, const double* lam_im,
                              const double* pts, double* Hhat) {
-  // one thread per (outgoing o, mode j): the depth factors depend on (o, j) only and are
-  // applied to the four rows 4o .. 4o+3
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  int o = blockIdx.y, u = blockIdx.z;
+  // one thread per mode j for HHAT_OB outgoing cosines o: the depth factors depend on (o, j)
+  // only and are applied to the four rows 4o .. 4o+3. The exponentials factor,
+  // e^{-a tau0} = e^{-tau0/mu} e^{-kappa tau0}: e^{-kappa tau0} once per thread and
+  // e^{-tau0/mu} once per block (FP64 transcendentals are expensive on this part); the
+  // expm1 forms stay where 1 - e^{-x} would cancel.
+  __shared__ double s_mu[HHAT_OB], s_x[HHAT_OB], s_ex[HHAT_OB];
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int o0 = blockIdx.y * HHAT_OB, u = blockIdx.z;
+  if (threadIdx.x < HHAT_OB && o0 + (int)threadIdx.x < n_out) {
+    const double mu = pts[N + n_in + o0 + threadIdx.x];
+    s_mu[threadIdx.x] = mu;
+    s_x[threadIdx.x] = 1.0 / mu;
+    s_ex[threadIdx.x] = exp(-tau / mu);
+  }
+  __syncthreads();
   if (j >= n) return;
   const double* lr = lam_re + (size_t)u * n;
   const double* li = lam_im + (size_t)u * n;
   if (li[j] < 0.0) return;
-  bool cplx = li[j] > 0.0;
-  double mu = pts[N + n_in + o];
-  double x = 1.0 / mu;
-  int Ro = 4 * n_out;
-  cd kap = kappa_of(lr, li, j);
-  // decaying
-  cd a{x + kap.r, kap.i};
-  cd em = cexpm1v(cd{-a.r * tau, -a.i * tau});
-  cd gD = cdivv(cd{-em.r, -em.i}, cd{mu * a.r, mu * a.i});
-  // growing
-  cd bb{kap.r - x, kap.i};
-  cd gG;
-  double ex = exp(-tau * x);
-  if (bb.r == 0.0 && bb.i == 0.0) {
-    gG = cd{tau * ex / mu, 0.0};
-  } else if (fabs(bb.r * tau) + fabs(bb.i * tau) < 1e-2) {
-    cd e2 = cexpm1v(cd{-bb.r * tau, -bb.i * tau});
-    gG = cdivv(cd{-e2.r * ex, -e2.i * ex}, cd{mu * bb.r, mu * bb.i});
-  } else {
-    cd ek = cexpv(cd{-kap.r * tau, -kap.i * tau});
-    gG = cdivv(cd{ex - ek.r, -ek.i}, cd{mu * bb.r, mu * bb.i});
-  }
-  for (int ar = 0; ar < 4; ++ar) {
-    const int ro = 4 * o + ar;
-    size_t rowp = (size_t)u * Ro * n + (size_t)ro * n;
-    double* Hb = Hhat + (size_t)u * Ro * 2 * n + (size_t)ro * 2 * n;
-    cd p1{P1[rowp + j], cplx ? P1[rowp + j + 1] : 0.0};
-    cd p2{P2[rowp + j], cplx ? P2[rowp + j + 1] : 0.0};
-    cd hD{p1.r - p2.r, p1.i - p2.i};
-    cd hG{p1.r + p2.r, p1.i + p2.i};
-    cd vD = cmul(hD, gD), vG = cmul(hG, gG);
-    Hb[j] = vD.r;
-    Hb[n + j] = vG.r;
-    if (cplx) {
-      Hb[j + 1] = vD.i;
-      Hb[n + j + 1] = vG.i;
+  const bool cplx = li[j] > 0.0;
+  const int Ro = 4 * n_out;
+  const cd kap = kappa_of(lr, li, j);
+  const cd ek = cexpv(cd{-kap.r * tau, -kap.i * tau});
+  for (int oo = 0; oo < HHAT_OB; ++oo) {
+    const int o = o0 + oo;
+    if (o >= n_out) break;
+    const double mu = s_mu[oo], x = s_x[oo], ex = s_ex[oo];
+    // decaying: 1 - e^{-a tau0} = 1 - e^{-tau0/mu} e^{-kappa tau0} without cancellation once
+    // Re(a) tau0 > 1/2 (|e^{-a tau0}| < 0.61)
+    const cd a{x + kap.r, kap.i};
+    cd one_m;
+    if (a.r * tau > 0.5) {
+      one_m = cd{1.0 - ex * ek.r, -ex * ek.i};
+    } else {
+      cd em = cexpm1v(cd{-a.r * tau, -a.i * tau});
+      one_m = cd{-em.r, -em.i};
+    }
+    const cd gD = cdivv(one_m, cd{mu * a.r, mu * a.i});
+    // growing
+    const cd bb{kap.r - x, kap.i};
+    cd gG;
+    if (bb.r == 0.0 && bb.i == 0.0) {
+      gG = cd{tau * ex / mu, 0.0};
+    } else if (fabs(bb.r * tau) + fabs(bb.i * tau) < 1e-2) {
+      cd e2 = cexpm1v(cd{-bb.r * tau, -bb.i * tau});
+      gG = cdivv(cd{-e2.r * ex, -e2.i * ex}, cd{mu * bb.r, mu * bb.i});
+    } else {
+      gG = cdivv(cd{ex - ek.r, -ek.i}, cd{mu * bb.r, mu * bb.i});
+    }
+    for (int ar = 0; ar < 4; ++ar) {
+      const int ro = 4 * o + ar;
+      size_t rowp = (size_t)u * Ro * n + (size_t)ro * n;
+      double* Hb = Hhat + (size_t)u * Ro * 2 * n + (size_t)ro * 2 * n;
+      cd p1{P1[rowp + j], cplx ? P1[rowp + j + 1] : 0.0};
+      cd p2{P2[rowp + j], cplx ? P2[rowp + j + 1] : 0.0};
+      cd hD{p1.r - p2.r, p1.i - p2.i};
+      cd hG{p1.r + p2.r, p1.i + p2.i};
+      cd vD = cmul(hD, gD), vG = cmul(hG, gG);
+      Hb[j] = vD.r;
+      Hb[n + j] = vG.r;
+      if (cplx) {
+        Hb[j + 1] = vD.i;
+        Hb[n + j + 1] = vG.i;
+      }
     }
   }
 }
@@ -317,7 +339,7 @@ __global__ void k_build_Hhat(int N, int n, int n_in, int n_out, double tau, cons
 void launch_build_Hhat(const OrderBatch& b, const double* P1, const double* P2,
                        const double* lam_re, const double* lam_im, const double* pts,
                        double* Hhat, cudaStream_t s) {
-  dim3 grid((b.n + 127) / 128, b.n_out, b.n_units);
+  dim3 grid((b.n + 127) / 128, (b.n_out + HHAT_OB - 1) / HHAT_OB, b.n_units);
   k_build_Hhat<<<grid, 128, 0, s>>>(b.N, b.n, b.n_in, b.n_out, b.tau, P1, P2, lam_re, lam_im, pts,
                                     Hhat);
 }

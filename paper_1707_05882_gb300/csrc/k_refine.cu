@@ -78,9 +78,13 @@ __global__ void k_flag_columns(OrderBatch b, const double* __restrict__ rmH,
   }
 }
 
-// Persistent grid over the flagged (u, k): FP64 C' = K^-1 RHS[:, 4k..4k+3] in shared
-// memory, then one warp per output row r = 4o + a:
+// Persistent grid over (flagged (u, k), block of FIX_ROWS output rows), so that the FP64
+// work spreads evenly over the SMs however few columns are flagged: FP64
+// C' = K^-1 RHS[:, 4k..4k+3] in shared memory (recomputed per row block), then one warp per
+// output row r = 4o + a:
 //   I^m[k][o][a][s] = sum_i Hhat[r][i] C'[i][s] + g0(o, k) sum_i U[r][i] SD[i][4k + s].
+constexpr int FIX_ROWS = 512;  // output rows per work item of k_fix_columns
+
 __global__ void __launch_bounds__(256) k_fix_columns(
     OrderBatch b, const double* __restrict__ Kinv, const double* __restrict__ RHS,
     const double* __restrict__ Hhat, const double* __restrict__ Uext,
@@ -90,8 +94,10 @@ __global__ void __launch_bounds__(256) k_fix_columns(
   extern __shared__ double Cs[];  // [2n][4]
   const int n2 = 2 * b.n, R = 4 * b.n_in, Ro = 4 * b.n_out;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int items = min(*count, cap);
-  for (int it = blockIdx.x; it < items; it += gridDim.x) {
+  const int items = min(*count, cap);
+  const int nblk = (Ro + FIX_ROWS - 1) / FIX_ROWS;
+  for (int wi = blockIdx.x; wi < items * nblk; wi += gridDim.x) {
+    const int it = wi / nblk, r0 = (wi - it * nblk) * FIX_ROWS;
     int2 e = list[it];
     int u = e.x, k = e.y;
     const double* Ki = Kinv + (size_t)u * n2 * n2;
@@ -113,7 +119,7 @@ __global__ void __launch_bounds__(256) k_fix_columns(
     const double* H = Hhat + (size_t)u * Ro * n2;
     const double* Ub = Uext + (size_t)u * Ro * b.ldU;
     const double* sd = SD + (size_t)u * b.sSD + 4 * k;
-    for (int r = warp; r < Ro; r += nw) {
+    for (int r = r0 + warp; r < min(Ro, r0 + FIX_ROWS); r += nw) {
       double h[4] = {0.0, 0.0, 0.0, 0.0}, q[4] = {0.0, 0.0, 0.0, 0.0};
       for (int i = lane; i < n2; i += 32) {
         double hv = H[(size_t)r * n2 + i];
