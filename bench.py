@@ -303,7 +303,7 @@ def run_batched(args):
     line = {"metric": "Fourier-order VRTE solves/s, batched uneven layers", "unit": UNIT,
             "value": res["mixed"]["value"], "ms_per_step": res["mixed"]["ms_per_step"],
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64 via 7 bf16 slices (tcgen05) + f64",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 via 7-slice (synthesis 5-slice) bf16 products on tcgen05 + f64",
             "data": "synthetic",
             "config": {"workload": cfg["name"], "layers": len(layers), "order_solves": M_total,
                        "n_in": 64, "n_out": 64, "n_phi": 90, "out_dtype": "f32",
@@ -319,10 +319,8 @@ def run_batched(args):
 
 # DRAM bytes per launch of a stage's dominant kernel from one ncu capture of the same
 # kernel (profiles/eigen_mie-N64-M128.md: k_eigen, 128 orders of the N = 64 layer, the
-# stage does not depend on the angular grid; profiles/tc_gemm_part_traffic_mie-N64-M128-
-# 1024x1024x360.md: the particular + direct reconstruction GEMM at this workload).
-# Stages without a current capture: None.
-DRAM_TRAFFIC = {"eigen": 7.643186e9 + 21.738669e9, "recon_part": 112.70e9 + 17.18e9}
+# stage does not depend on the angular grid). Stages without a current capture: None.
+DRAM_TRAFFIC = {"eigen": 7.489435648e9 + 21.57342464e9}
 
 
 def roofline(stages, clk, precision_name, grid=None):
@@ -410,7 +408,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else
-        "f64 via 7 bf16 slices (tcgen05) + f64",
+        "f64 via 7-slice (synthesis 5-slice) bf16 products on tcgen05 + f64",
         "data": "synthetic",
         "config": {"workload": cfg["name"], "N": ly["n_nodes"], "M": ly["n_orders"], "L": L,
                    "n_in": int(cfg["mu_in"].size), "n_out": int(cfg["mu_out"].size),
