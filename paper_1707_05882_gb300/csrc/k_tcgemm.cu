@@ -16,7 +16,7 @@
 // S = 4, ~3e-13 at S = 6, ~2e-15 at S = 7.
 //
 // Data flow: `k_slice_rows` / `k_slice_cols` write the slices directly as the shared-
-// memory image of 64B-swizzled K-major tiles ([unit][slice][tile][k-block] blocks of
+// memory image of 64B-swizzled K-major tiles ([unit][tile][k-block][slice] blocks of
 // 128 x 32 or 64 x 32 BF16), so the GEMM kernel loads each tile with one bulk copy. The
 // persistent GEMM kernel computes 128 x 64 output tiles with up to seven accumulators of
 // 64 columns in TMEM. It is warp-specialised: one warp keeps a ring of shared-memory
@@ -91,7 +91,7 @@ __global__ void k_slice_rows(int M, int K, const double* __restrict__ A, int lda
   }
   __syncthreads();
   const size_t tile_elems = (size_t)TC_M * TC_KB;
-  const size_t slice_stride = (size_t)MT * KB * tile_elems;
+  const size_t slice_stride = tile_elems;  // the S slices of a tile block are adjacent
   const int chunks = Kp / 8;
   for (int idx = threadIdx.x; idx < TC_M * chunks; idx += blockDim.x) {
     int r = idx / chunks, k0 = 8 * (idx - r * chunks);
@@ -100,7 +100,7 @@ __global__ void k_slice_rows(int M, int K, const double* __restrict__ A, int lda
     for (int t = 0; t < 8; ++t)
       v[t] = (i < M && k0 + t < K) ? Ab[(size_t)i * lda + k0 + t] : 0.0;
     int kb = k0 / TC_KB;
-    size_t base = ((((size_t)u * S) * MT + mt) * KB + kb) * tile_elems;
+    size_t base = ((((size_t)u * MT + mt) * KB + kb) * S) * tile_elems;
     put_chunk<S>(v, ex[r], out + base + (swz64_offset(r, k0 - kb * TC_KB) >> 1), slice_stride);
   }
   if (bad) atomicOr(status, ST_NONFINITE);
@@ -135,7 +135,7 @@ __global__ void k_slice_cols(int N, int K, const double* __restrict__ B, int ldb
   }
   __syncthreads();
   const size_t tile_elems = (size_t)TC_N * TC_KB;
-  const size_t slice_stride = (size_t)NT * KB * tile_elems;
+  const size_t slice_stride = tile_elems;  // the S slices of a tile block are adjacent
   const int chunks = Kp / 8;
   for (int idx = threadIdx.x; idx < TC_N * chunks; idx += blockDim.x) {
     int k0 = 8 * (idx / TC_N), cc = idx % TC_N;
@@ -144,7 +144,7 @@ __global__ void k_slice_cols(int N, int K, const double* __restrict__ B, int ldb
     for (int t = 0; t < 8; ++t)
       v[t] = (jj < N && k0 + t < K) ? Bb[(size_t)(k0 + t) * ldb + jj] : 0.0;
     int kb = k0 / TC_KB;
-    size_t base = ((((size_t)u * S) * NT + nt) * KB + kb) * tile_elems;
+    size_t base = ((((size_t)u * NT + nt) * KB + kb) * S) * tile_elems;
     put_chunk<S>(v, ex[cc], out + base + (swz64_offset(cc, k0 - kb * TC_KB) >> 1), slice_stride);
   }
   if (bad) atomicOr(status, ST_NONFINITE);
@@ -251,23 +251,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       for (int t = blockIdx.x; t < tiles && !abort_flag; t += gridDim.x) {
         int u, mt, nt;
         tc_decode(t, MT, NT, u, mt, nt);
-        const unsigned short* a0 = As + (size_t)u * a_unit + (size_t)mt * KB * (A_TILE_BYTES / 2);
-        const unsigned short* b0 = Bs + (size_t)u * b_unit + (size_t)nt * KB * (B_TILE_BYTES / 2);
-        const size_t a_slice = (size_t)MT * KB * (A_TILE_BYTES / 2);
-        const size_t b_slice = (size_t)NT * KB * (B_TILE_BYTES / 2);
+        // the S slice tiles of a (tile, K block) are adjacent: one bulk copy per operand
+        const unsigned short* a0 =
+            As + (size_t)u * a_unit + (size_t)mt * KB * S * (A_TILE_BYTES / 2);
+        const unsigned short* b0 =
+            Bs + (size_t)u * b_unit + (size_t)nt * KB * S * (B_TILE_BYTES / 2);
         bool ok = true;
         for (int kb = 0; kb < KB; ++kb, ++g) {
           const int s = g % nst, r = g / nst;
           if (!mbar_wait(&empty_bar[s], (r & 1) ^ 1)) { ok = false; break; }
           unsigned char* st = smem + (size_t)s * stage_bytes;
           mbar_expect_tx(&full_bar[s], (unsigned)stage_bytes);
-          for (int p = 0; p < S; ++p)
-            bulk_g2s(st + p * A_TILE_BYTES, a0 + p * a_slice + (size_t)kb * (A_TILE_BYTES / 2),
-                     A_TILE_BYTES, &full_bar[s]);
-          for (int q = 0; q < S; ++q)
-            bulk_g2s(st + S * A_TILE_BYTES + q * B_TILE_BYTES,
-                     b0 + q * b_slice + (size_t)kb * (B_TILE_BYTES / 2), B_TILE_BYTES,
-                     &full_bar[s]);
+          bulk_g2s(st, a0 + (size_t)kb * S * (A_TILE_BYTES / 2), S * A_TILE_BYTES, &full_bar[s]);
+          bulk_g2s(st + S * A_TILE_BYTES, b0 + (size_t)kb * S * (B_TILE_BYTES / 2),
+                   S * B_TILE_BYTES, &full_bar[s]);
           issued[s] = true;
           round_of[s] = r;
         }
