@@ -96,6 +96,10 @@ struct vrte_plan {
   size_t tcw_bytes = 0;
   int kdir = 0;  // extra K of the direct term in the mixed form (4 L_max)
   cudaEvent_t fork = nullptr;
+  // host-API output copy: split over four streams (several copy engines)
+  cudaStream_t cstream[4] = {};
+  cudaEvent_t cdone[4] = {};
+  cudaEvent_t solved = nullptr;
   // host-API staging
   double* d_coef_stage = nullptr;
   size_t coef_stage_bytes = 0;
@@ -650,8 +654,30 @@ vrte_status vrte_solve_brdf_host(vrte_plan* p, const double* h_coeffs, void* h_b
   p->last_stream = s;
   vrte_status st = run_solve(p, p->d_coef_stage, p->d_out_stage, out_dtype, s);
   if (st != VRTE_OK) return st;
-  if (cudaMemcpyAsync(h_brdf, p->d_out_stage, obytes, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return VRTE_ERR_CUDA;
+  // the table leaves in kCopyStreams chunks on their own streams (one copy engine each),
+  // forked from and joined back into the caller's stream
+  constexpr int kCopyStreams = 4;
+  if (!p->solved) {
+    if (cudaEventCreateWithFlags(&p->solved, cudaEventDisableTiming) != cudaSuccess)
+      return VRTE_ERR_CUDA;
+    for (int c = 0; c < kCopyStreams; ++c)
+      if (cudaStreamCreateWithFlags(&p->cstream[c], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->cdone[c], cudaEventDisableTiming) != cudaSuccess)
+        return VRTE_ERR_CUDA;
+  }
+  if (cudaEventRecord(p->solved, s) != cudaSuccess) return VRTE_ERR_CUDA;
+  const size_t chunk = ((obytes + kCopyStreams - 1) / kCopyStreams + 4095) / 4096 * 4096;
+  for (int c = 0; c < kCopyStreams; ++c) {
+    const size_t off = (size_t)c * chunk;
+    const size_t len = off < obytes ? std::min(chunk, obytes - off) : 0;
+    if (cudaStreamWaitEvent(p->cstream[c], p->solved, 0) != cudaSuccess) return VRTE_ERR_CUDA;
+    if (len && cudaMemcpyAsync((char*)h_brdf + off, (const char*)p->d_out_stage + off, len,
+                               cudaMemcpyDeviceToHost, p->cstream[c]) != cudaSuccess)
+      return VRTE_ERR_CUDA;
+    if (cudaEventRecord(p->cdone[c], p->cstream[c]) != cudaSuccess ||
+        cudaStreamWaitEvent(s, p->cdone[c], 0) != cudaSuccess)
+      return VRTE_ERR_CUDA;
+  }
   if (cudaStreamSynchronize(s) != cudaSuccess) return VRTE_ERR_CUDA;
   return VRTE_OK;
 }
@@ -787,6 +813,11 @@ void vrte_destroy(vrte_plan* p) {
     if (x.done) cudaEventDestroy(x.done);
   }
   if (p->fork) cudaEventDestroy(p->fork);
+  for (int c = 0; c < 4; ++c) {
+    if (p->cstream[c]) cudaStreamDestroy(p->cstream[c]);
+    if (p->cdone[c]) cudaEventDestroy(p->cdone[c]);
+  }
+  if (p->solved) cudaEventDestroy(p->solved);
   if (p->d_coef_stage) cudaFree(p->d_coef_stage);
   if (p->d_out_stage) cudaFree(p->d_out_stage);
   delete p;
