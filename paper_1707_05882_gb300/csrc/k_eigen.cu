@@ -42,13 +42,17 @@ __device__ inline double block_sum(double v, double* red) {
   return t;
 }
 
-// Householder reflector P = I - tau v v^T with v[0] = 1 mapping (x, y, z) to (beta, 0, 0).
+// Householder reflector P = I - tau v v^T with v[0] = 1 mapping (x, y, z) to (beta, 0, 0),
+// beta = -sign(x) |(x, y, z)|: tau = (beta - x) / beta = 1 + |x| / |(x, y, z)| and
+// v = (y, z) / (x - beta) = sign(x) (y, z) / (|x| + |(x, y, z)|), from one reciprocal square
+// root and one division (FP64 instructions are scarce on this part).
 __device__ inline void house3(double x, double y, double z, double& tau, double& v1, double& v2) {
-  double nrm = sqrt(x * x + y * y + z * z);
-  if (nrm == 0.0 || (y == 0.0 && z == 0.0)) { tau = 0.0; v1 = 0.0; v2 = 0.0; return; }
-  double beta = -copysign(nrm, x);
-  tau = (beta - x) / beta;
-  double sc = 1.0 / (x - beta);
+  const double s2 = fma(z, z, fma(y, y, x * x));
+  if (s2 == 0.0 || (y == 0.0 && z == 0.0)) { tau = 0.0; v1 = 0.0; v2 = 0.0; return; }
+  const double r = rsqrt(s2);
+  const double nrm = s2 * r;
+  tau = fma(fabs(x), r, 1.0);
+  const double sc = copysign(1.0, x) / (fabs(x) + nrm);
   v1 = y * sc;
   v2 = z * sc;
 }
@@ -59,10 +63,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
                                                        double* scale, const int* mask,
                                                        unsigned* status) {
   extern __shared__ double vsh[];  // Householder vector, n entries; then the sweep's
-                                   // reflectors (tau, v1, v2), n entries each
+                                   // reflectors (tau, v1, v2, tau v1, tau v2), n entries each
   __shared__ double red[32];
   __shared__ int ired[32];
-  __shared__ double refl[2][3];  // reflectors of the current and the next sweep step
+  __shared__ double refl[2][5];  // reflectors (tau, v1, v2, tau v1, tau v2) of the current
+                                 // and the next sweep step
   int u = blockIdx.x;
   if (mask && !mask[u]) return;
   int tid = threadIdx.x, nt = blockDim.x;
@@ -73,6 +78,8 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
   double* rtau = vsh + n;
   double* rv1 = rtau + n;
   double* rv2 = rv1 + n;
+  double* rtv1 = rv2 + n;  // tau v1 and tau v2 of each step (five-operation updates)
+  double* rtv2 = rtv1 + n;
   double* wr = lam_re + (size_t)u * n;
   double* wi = lam_im + (size_t)u * n;
   double* dsc = scale + (size_t)u * n;
@@ -321,14 +328,19 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
       house3(x, y, nr == 3 ? z : 0.0, tau, v1, v2);
       if (nr == 2) v2 = 0.0;
       if (lane == 0) {
+        const double tv1 = tau * v1, tv2 = tau * v2;
         refl[l & 1][0] = tau; refl[l & 1][1] = v1; refl[l & 1][2] = v2;
-        rtau[0] = tau; rv1[0] = v1; rv2[0] = v2;
+        refl[l & 1][3] = tv1; refl[l & 1][4] = tv2;
+        rtau[0] = tau; rv1[0] = v1; rv2[0] = v2; rtv1[0] = tv1; rtv2[0] = tv2;
       }
     }
     __syncthreads();
     for (int k = l; k <= hi - 1; ++k) {
       const int nr = (k < hi - 1) ? 3 : 2;
       const double tau = refl[k & 1][0], v1 = refl[k & 1][1], v2 = refl[k & 1][2];
+      const double tv1 = refl[k & 1][3], tv2 = refl[k & 1][4];
+      // each update: w = h0 + v1 h1 + v2 h2, then h -= (tau, tau v1, tau v2) w (five FP64
+      // operations per element)
       // right-update rows rotate so that rows k+1 .. k+3 (the next bulge column) fall on
       // lanes 0 .. 2 of warp 0
       double nb = 0.0;
@@ -338,10 +350,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
         for (int j = c0 + tid; j < n; j += nt) {
           double h0 = H[(size_t)k * n + j], h1 = H[(size_t)(k + 1) * n + j];
           double h2 = (nr == 3) ? H[(size_t)(k + 2) * n + j] : 0.0;
-          double w = tau * (h0 + v1 * h1 + v2 * h2);
-          H[(size_t)k * n + j] = h0 - w;
-          H[(size_t)(k + 1) * n + j] = h1 - w * v1;
-          if (nr == 3) H[(size_t)(k + 2) * n + j] = h2 - w * v2;
+          const double w = fma(v2, h2, fma(v1, h1, h0));
+          H[(size_t)k * n + j] = fma(-tau, w, h0);
+          H[(size_t)(k + 1) * n + j] = fma(-tv1, w, h1);
+          if (nr == 3) H[(size_t)(k + 2) * n + j] = fma(-tv2, w, h2);
         }
         __syncthreads();
         if (k > l && tid == 0) {
@@ -355,11 +367,12 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
           if (i >= rows) i -= rows;
           double h0 = H[(size_t)i * n + k], h1 = H[(size_t)i * n + k + 1];
           double h2 = (nr == 3) ? H[(size_t)i * n + k + 2] : 0.0;
-          double w = tau * (h0 + v1 * h1 + v2 * h2);
-          H[(size_t)i * n + k] = h0 - w;
-          if (t == tid) nb = h0 - w;
-          H[(size_t)i * n + k + 1] = h1 - w * v1;
-          if (nr == 3) H[(size_t)i * n + k + 2] = h2 - w * v2;
+          const double w = fma(v2, h2, fma(v1, h1, h0));
+          const double g0 = fma(-tau, w, h0);
+          H[(size_t)i * n + k] = g0;
+          if (t == tid) nb = g0;
+          H[(size_t)i * n + k + 1] = fma(-tv1, w, h1);
+          if (nr == 3) H[(size_t)i * n + k + 2] = fma(-tv2, w, h2);
         }
       }
       // reflector of step k + 1 from column k of rows k+1 .. k+3 (warp 0)
@@ -379,8 +392,11 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
         house3(x, y, nr1 == 3 ? z : 0.0, t1, w1, w2);
         if (nr1 == 2) w2 = 0.0;
         if (lane == 0) {
+          const double tw1 = t1 * w1, tw2 = t1 * w2;
           refl[(k + 1) & 1][0] = t1; refl[(k + 1) & 1][1] = w1; refl[(k + 1) & 1][2] = w2;
+          refl[(k + 1) & 1][3] = tw1; refl[(k + 1) & 1][4] = tw2;
           rtau[k + 1 - l] = t1; rv1[k + 1 - l] = w1; rv2[k + 1 - l] = w2;
+          rtv1[k + 1 - l] = tw1; rtv2[k + 1 - l] = tw2;
         }
       }
       __syncthreads();
@@ -396,11 +412,10 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
         double zc = (nr == 3) ? Z[(size_t)(k + 2) * n + i] : 0.0;
         const double tau = rtau[k - l];
         if (tau != 0.0) {
-          const double v1 = rv1[k - l], v2 = rv2[k - l];
-          double w = tau * (za + v1 * zb + v2 * zc);
-          za = za - w;
-          zb = zb - w * v1;
-          if (nr == 3) zc = zc - w * v2;
+          const double w = fma(rv2[k - l], zc, fma(rv1[k - l], zb, za));
+          za = fma(-tau, w, za);
+          zb = fma(-rtv1[k - l], w, zb);
+          if (nr == 3) zc = fma(-rtv2[k - l], w, zc);
         }
         Z[(size_t)k * n + i] = za;
         za = zb;
@@ -548,7 +563,7 @@ void dgemm_batched_mask(bool tA, bool tB, int M, int N, int K, double alpha, con
 void batched_eigen(int n, const double* A, double* H, double* Z, double* V, double* X,
                    double* lam_re, double* lam_im, double* scale, int batch, unsigned* status,
                    cudaStream_t s, const int* mask) {
-  size_t smem = 4 * (size_t)n * sizeof(double);
+  size_t smem = 6 * (size_t)n * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_eigen<<<batch, EIG_THREADS, smem, s>>>(n, A, H, Z, V, lam_re, lam_im, scale, mask, status);
