@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
   extern __shared__ double vsh[];  // Householder vector, n entries; then the sweep's
                                    // reflectors (tau, v1, v2, tau v1, tau v2), n entries each
   __shared__ double red[32];
+  __shared__ double bal[2][2];  // balancing decision (f, 1/f) of row i, at bal[i & 1]
   __shared__ int ired[32];
   __shared__ double refl[2][5];  // reflectors (tau, v1, v2, tau v1, tau v2) of the current
                                  // and the next sweep step
@@ -93,25 +94,36 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
   for (int i = tid; i < n; i += nt) dsc[i] = 1.0;
   __syncthreads();
 
-  // ---- 1. balancing: D^-1 H D with power-of-two entries, Gauss-Seidel sweeps
+  // ---- 1. balancing: D^-1 H D with power-of-two entries, Gauss-Seidel sweeps. The row and
+  // column norms and the scaling decision come from warp 0 alone (FP64 instructions cost the
+  // same for one active warp as for every warp repeating them).
   for (int sweep = 0; sweep < 32; ++sweep) {
     int changed = 0;
     for (int i = 0; i < n; ++i) {
-      double c = 0.0, r = 0.0;
-      for (int j = tid; j < n; j += nt) {
-        if (j == i) continue;
-        c += fabs(H[(size_t)j * n + i]);
-        r += fabs(H[(size_t)i * n + j]);
+      if (warp == 0) {
+        double c = 0.0, r = 0.0;
+        for (int j = lane; j < n; j += 32) {
+          if (j == i) continue;
+          c += fabs(H[(size_t)j * n + i]);
+          r += fabs(H[(size_t)i * n + j]);
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          c += __shfl_xor_sync(0xffffffffu, c, off);
+          r += __shfl_xor_sync(0xffffffffu, r, off);
+        }
+        double f = 0.0, finv = 0.0;  // f = 0: row i stays
+        if (c > 0.0 && r > 0.0 && isfinite(c) && isfinite(r)) {
+          const int e2 = (int)rint(0.5 * log2(r / c));
+          if (e2 != 0) {
+            const double ff = ldexp(1.0, e2);
+            if (!(c * ff + r / ff >= 0.95 * (c + r))) { f = ff; finv = ldexp(1.0, -e2); }
+          }
+        }
+        if (lane == 0) { bal[i & 1][0] = f; bal[i & 1][1] = finv; }
       }
-      c = block_sum(c, red);
-      r = block_sum(r, red);
-      if (!(c > 0.0) || !(r > 0.0) || !isfinite(c) || !isfinite(r)) continue;
-      int e2 = (int)rint(0.5 * log2(r / c));
-      if (e2 == 0) continue;
-      double f = ldexp(1.0, e2);
-      if (c * f + r / f >= 0.95 * (c + r)) continue;
-      double finv = 1.0 / f;
       __syncthreads();
+      const double f = bal[i & 1][0], finv = bal[i & 1][1];
+      if (f == 0.0) continue;  // uniform: nothing changed, the next row reads the same H
       for (int j = tid; j < n; j += nt) {
         H[(size_t)i * n + j] *= finv;
         H[(size_t)j * n + i] *= f;
@@ -467,21 +479,28 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
           if (cplx) si0 += t0 * vi[j];
         }
       }
+      // reduce only the sums this row needs (warp-uniform conditions)
       for (int off = 16; off > 0; off >>= 1) {
-        sr0 += __shfl_xor_sync(0xffffffffu, sr0, off);
-        si0 += __shfl_xor_sync(0xffffffffu, si0, off);
         sr1 += __shfl_xor_sync(0xffffffffu, sr1, off);
-        si1 += __shfl_xor_sync(0xffffffffu, si1, off);
+        if (cplx) si1 += __shfl_xor_sync(0xffffffffu, si1, off);
+        if (blk2) {
+          sr0 += __shfl_xor_sync(0xffffffffu, sr0, off);
+          if (cplx) si0 += __shfl_xor_sync(0xffffffffu, si0, off);
+        }
       }
       if (lane == 0) {
         if (!blk2) {
           // (T_ii - lam) v_i = -r
           double dr = H[(size_t)i * n + i] - lr, di = -li;
           if (fabs(dr) + fabs(di) < smin) { dr = smin; di = 0.0; }
-          double den = dr * dr + di * di;
-          // v = -(sr + i si) / (dr + i di)
-          vr[i] = -(sr1 * dr + si1 * di) / den;
-          if (cplx) vi[i] = -(si1 * dr - sr1 * di) / den;
+          // v = -(sr + i si) / (dr + i di), with one division
+          if (!cplx) {
+            vr[i] = -sr1 / dr;
+          } else {
+            const double inv = 1.0 / (dr * dr + di * di);
+            vr[i] = -(sr1 * dr + si1 * di) * inv;
+            vi[i] = -(si1 * dr - sr1 * di) * inv;
+          }
         } else {
           // [[a - lam, b], [c, d - lam]] [v0; v1] = -[r0; r1]
           double a = H[(size_t)i0 * n + i0] - lr, b = H[(size_t)i0 * n + i];
@@ -490,14 +509,14 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
           double ar = a, ai = -li, dr = d, di = -li;
           double detr = ar * dr - ai * di - b * c, deti = ar * di + ai * dr;
           if (fabs(detr) + fabs(deti) < smin) { detr = smin; deti = 0.0; }
-          double den = detr * detr + deti * deti;
+          const double inv = 1.0 / (detr * detr + deti * deti);
           // Cramer with negated right-hand side: v0 = (b r1 - r0 d') / det, v1 = (c r0 - a' r1) / det
           double n0r = -(sr0 * dr - si0 * di) + b * sr1;
           double n0i = -(sr0 * di + si0 * dr) + b * si1;
           double n1r = c * sr0 - (ar * sr1 - ai * si1);
           double n1i = c * si0 - (ar * si1 + ai * sr1);
-          double v0r = (n0r * detr + n0i * deti) / den, v0i = (n0i * detr - n0r * deti) / den;
-          double v1r = (n1r * detr + n1i * deti) / den, v1i = (n1i * detr - n1r * deti) / den;
+          double v0r = (n0r * detr + n0i * deti) * inv, v0i = (n0i * detr - n0r * deti) * inv;
+          double v1r = (n1r * detr + n1i * deti) * inv, v1i = (n1i * detr - n1r * deti) * inv;
           vr[i0] = v0r; vr[i] = v1r;
           if (cplx) { vi[i0] = v0i; vi[i] = v1i; }
         }
