@@ -30,18 +30,6 @@ constexpr int EIG_THREADS = 256;
 constexpr double EPS = 2.220446049250313e-16;
 constexpr double SAFMIN = 2.2250738585072014e-308;
 
-__device__ inline double block_sum(double v, double* red) {
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) t += red[i];
-  return t;
-}
-
 // Householder reflector P = I - tau v v^T with v[0] = 1 mapping (x, y, z) to (beta, 0, 0),
 // beta = -sign(x) |(x, y, z)|: tau = (beta - x) / beta = 1 + |x| / |(x, y, z)| and
 // v = (y, z) / (x - beta) = sign(x) (y, z) / (|x| + |(x, y, z)|), from one reciprocal square
@@ -66,6 +54,7 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
                                    // reflectors (tau, v1, v2, tau v1, tau v2), n entries each
   __shared__ double red[32];
   __shared__ double bal[2][2];  // balancing decision (f, 1/f) of row i, at bal[i & 1]
+  __shared__ double hred[4];    // Hessenberg step: (|x|^2 below the subdiagonal, beta, tau, 1/(alpha - beta))
   __shared__ int ired[32];
   __shared__ double refl[2][5];  // reflectors (tau, v1, v2, tau v1, tau v2) of the current
                                  // and the next sweep step
@@ -137,18 +126,31 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
   __syncthreads();
 
   // ---- 2. Householder reduction to Hessenberg form, Z <- Z (I - tau v v^T)
+  // The reflector of each column comes from warp 0 alone; the right update runs a thread
+  // per row (a sequential dot product, no shuffle reductions), like the Z update.
   for (int k = 0; k + 2 < n; ++k) {
-    double xs = 0.0;
-    for (int i = k + 2 + tid; i < n; i += nt) {
-      double v = H[(size_t)i * n + k];
-      xs += v * v;
+    if (warp == 0) {
+      double xs = 0.0;
+      for (int i = k + 2 + lane; i < n; i += 32) {
+        const double v = H[(size_t)i * n + k];
+        xs = fma(v, v, xs);
+      }
+      for (int off = 16; off > 0; off >>= 1) xs += __shfl_xor_sync(0xffffffffu, xs, off);
+      double beta = 0.0, tau = 0.0, sc = 0.0;
+      if (xs != 0.0) {
+        const double alpha = H[(size_t)(k + 1) * n + k];
+        beta = -copysign(sqrt(fma(alpha, alpha, xs)), alpha);
+        tau = (beta - alpha) / beta;
+        sc = 1.0 / (alpha - beta);
+      }
+      if (lane == 0) { hred[0] = xs; hred[1] = beta; hred[2] = tau; hred[3] = sc; }
     }
-    xs = block_sum(xs, red);
-    double alpha = H[(size_t)(k + 1) * n + k];
-    if (xs == 0.0) continue;
-    double beta = -copysign(sqrt(alpha * alpha + xs), alpha);
-    double tau = (beta - alpha) / beta;
-    double sc = 1.0 / (alpha - beta);
+    __syncthreads();
+    if (hred[0] == 0.0) {  // uniform: the column is already reduced
+      __syncthreads();     // hred is rewritten for the next column only after every read
+      continue;
+    }
+    const double beta = hred[1], tau = hred[2], sc = hred[3];
     int len = n - k - 1;
     for (int i = tid; i < len; i += nt) vsh[i] = (i == 0) ? 1.0 : H[(size_t)(k + 1 + i) * n + k] * sc;
     __syncthreads();
@@ -161,13 +163,13 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
       for (int i = 0; i < len; ++i) H[(size_t)(k + 1 + i) * n + j] -= vsh[i] * w;
     }
     __syncthreads();
-    // right: every row of H (warp per row), and Z (thread per row, column-major)
-    for (int i = warp; i < n; i += nwarps) {
+    // right: every row of H and of Z (thread per row; Z column-major)
+    for (int i = tid; i < n; i += nt) {
+      double* Hi = H + (size_t)i * n + k + 1;
       double w = 0.0;
-      for (int j = lane; j < len; j += 32) w += H[(size_t)i * n + k + 1 + j] * vsh[j];
-      for (int off = 16; off > 0; off >>= 1) w += __shfl_xor_sync(0xffffffffu, w, off);
+      for (int j = 0; j < len; ++j) w += Hi[j] * vsh[j];
       w *= tau;
-      for (int j = lane; j < len; j += 32) H[(size_t)i * n + k + 1 + j] -= w * vsh[j];
+      for (int j = 0; j < len; ++j) Hi[j] -= w * vsh[j];
     }
     for (int i = tid; i < n; i += nt) {
       double w = 0.0;
