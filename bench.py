@@ -320,7 +320,7 @@ def run_batched(args):
 # DRAM bytes per launch of a stage's dominant kernel from one ncu capture of the same
 # kernel (profiles/eigen_mie-N64-M128.md: k_eigen, 128 orders of the N = 64 layer, the
 # stage does not depend on the angular grid). Stages without a current capture: None.
-DRAM_TRAFFIC = {"eigen": 7.950195712e9 + 22.129113088e9}
+DRAM_TRAFFIC = {"eigen": 7.330067712e9 + 21.217310208e9}
 
 
 def roofline(stages, clk, precision_name, grid=None):
