@@ -292,7 +292,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   const int S = kSlices;
   size_t tc_unit = 0;
   if (mixed) {
-    size_t c[7] = {tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
+    size_t c[8] = {tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
+                   tc_workspace_bytes((int)n, (int)n, (int)n, 1, S),
                    tc_workspace_bytes((int)n, (int)R, (int)kd, 1, S),
                    tc_workspace_bytes((int)Ro, (int)(2 * n), (int)kd, 1, S),
                    tc_workspace_bytes((int)Ro, (int)n, (int)n, 1, S),
@@ -468,13 +469,16 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
       {
         // nominal cost of a real Schur decomposition with eigenvectors: 25 n^3, plus
         // E'X, Y = E'X / kappa and the mode residual F'Y - X kappa
-        StageScope sc(p, ST_EIGEN, s, 10, (25.0 + 4.0) * dn * dn * dn * dU,
-                      8.0 * 6 * dn * dn * dU);
+        // (the mixed form takes E'X and F'Y, whose operands are row- and column-scaled
+        // eigenvectors, on the tensor cores; F'E' itself stays an FP64 GEMM). The stage is
+        // bound by the FP64 eigen-decomposition, so its work is counted as FP64 work only.
+        StageScope sc(p, ST_EIGEN, s, mixed ? 10 + 2 * (gl - 1) : 10,
+                      (25.0 + 4.0) * dn * dn * dn * dU, 8.0 * 6 * dn * dn * dU);
         batched_eigen(n, w->FE, w->Hs, w->Zs, w->Vs, w->X, w->lam_re, w->lam_im, w->bal, U,
                       p->d_status, s);
-        dgemm_batched(n, n, n, 1.0, w->E, n, nn, w->X, n, nn, 0.0, w->EX, n, nn, U, s);
+        gemm(n, n, n, w->E, n, nn, w->X, n, nn, 0.0, w->EX, n, nn);
         launch_pack_Y(ob, w->EX, w->lam_re, w->lam_im, w->Y, s);
-        dgemm_batched(n, n, n, 1.0, w->F, n, nn, w->Y, n, nn, 0.0, w->FY, n, nn, U, s);
+        gemm(n, n, n, w->F, n, nn, w->Y, n, nn, 0.0, w->FY, n, nn);
         // the FP64 form re-solves order 0 (diffusion mode) and any order with a poor mode
         // residual in the 2n block form; the mixed form only catastrophic ones
         const bool fp64 = p->desc.precision == VRTE_FP64;
