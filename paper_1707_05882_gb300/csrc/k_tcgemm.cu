@@ -66,7 +66,7 @@ __device__ __host__ inline int tc_smem_bytes(int S) {
 }
 
 // A rows: A[u][i][k] (row-major, lda, unit stride sA), M x K. Writes
-//   out[u][p][mt][kb] tiles (128 x 64 BF16 images) and e[u][i] (int exponent).
+//   out[u][mt][kb][p] tiles (128 x 32 BF16 images) and e[u][i] (int exponent).
 // One CTA per (row block of 128, unit); each thread slices 8 consecutive k of one row.
 template <int S>
 __global__ void k_slice_rows(int M, int K, const double* __restrict__ A, int lda,
@@ -107,7 +107,7 @@ __global__ void k_slice_rows(int M, int K, const double* __restrict__ A, int lda
 }
 
 // B columns: B[u][k][j] (row-major, ldb, unit stride sB), K x N, sliced per column j
-// into K-major tiles out[u][q][nt][kb] (64 x 64 BF16 images, row = j) and f[u][j].
+// into K-major tiles out[u][nt][kb][q] (64 x 32 BF16 images, row = j) and f[u][j].
 // Each thread slices 8 consecutive k of one column (consecutive threads: consecutive
 // columns, so every global load is coalesced).
 template <int S>
