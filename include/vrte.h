@@ -128,7 +128,10 @@ vrte_status vrte_set_layer(vrte_plan* plan, int n_layers, const vrte_layer* host
  *   d_brdf[n_layers][n_mu_in][n_mu_out][n_phi][4][4]   (row r = exiting Stokes
  *   component, column s = incident Stokes basis vector),
  * FP32 or FP64 per out_dtype, on `stream` (a cudaStream_t; NULL = legacy default
- * stream). Asynchronous: no host synchronization and no allocation inside.
+ * stream). Asynchronous: no host synchronization and no allocation inside. With several
+ * layers the plan runs up to four layers at a time on streams of its own, forked from
+ * `stream` by an event and joined back into it, so the call stays ordered on `stream`
+ * (and capturable into a CUDA graph from it).
  * Accuracy against the exact DOM solution of the given N: VRTE_FP64 ~1e-10 of F_00 at
  * the same point (more near a resonance mu0 kappa_j ~ 1 of the particular solution,
  * where every FP64 formulation loses digits); VRTE_MIXED 1e-6 on the I row and 1e-5 on
@@ -139,8 +142,9 @@ vrte_status vrte_solve_brdf(vrte_plan* plan, void* d_brdf, int out_dtype, void* 
 
 /* Same solve with host buffers: copies h_coeffs (host FP64, layout as d_coeffs
  * of vrte_set_layer) to the plan's staging buffer, solves, copies the table to
- * h_brdf (host, layout as d_brdf) and synchronizes `stream` before returning.
- * Pinned host memory gives full copy bandwidth. */
+ * h_brdf (host, layout as d_brdf) and synchronizes `stream` before returning. The table
+ * is copied in four chunks on four streams of the plan (several copy engines), forked
+ * from and joined back into `stream`. Pinned host memory gives full copy bandwidth. */
 vrte_status vrte_solve_brdf_host(vrte_plan* plan, const double* h_coeffs, void* h_brdf,
                                  int out_dtype, void* stream);
 
