@@ -130,7 +130,8 @@ vrte_status vrte_set_layer(vrte_plan* plan, int n_layers, const vrte_layer* host
  * FP32 or FP64 per out_dtype, on `stream` (a cudaStream_t; NULL = legacy default
  * stream). Asynchronous: no host synchronization and no allocation inside. With several
  * layers the plan runs up to four layers at a time on streams of its own, forked from
- * `stream` by an event and joined back into it, so the call stays ordered on `stream`.
+ * `stream` by an event and joined back into it, so the call stays ordered on `stream`
+ * and can be captured into a CUDA graph from it.
  * Accuracy against the exact DOM solution of the given N: VRTE_FP64 ~1e-10 of F_00 at
  * the same point (more near a resonance mu0 kappa_j ~ 1 of the particular solution,
  * where every FP64 formulation loses digits); VRTE_MIXED 1e-6 on the I row and 1e-5 on
