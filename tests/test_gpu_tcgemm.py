@@ -1,6 +1,6 @@
 """The tensor-core GEMM with exact fixed-point slicing (vrte_gemm_sliced) against FP64.
 
-Sizes span several 128 x 64 output tiles and 64-wide K blocks with ragged tails; rows of A
+Sizes span several 128 x 64 output tiles and 32-wide K blocks with ragged tails; rows of A
 and columns of B carry widely different scales (the slicing is per row / per column).
 Error bound: |C - A B| <= c 2^(-7S) max|A_i| max|B_j| K (measured in a CPU simulation of
 the same arithmetic: 2.1e-3, 3.1e-5, 3.5e-7, 3.2e-9 for S = 1..4; on the GPU 9.1e-10,
