@@ -53,3 +53,23 @@ def test_plan_descriptor_layout_matches_header():
     # 7 ints, 3 pointers, int + unsigned: offsets follow the C struct in vrte.h
     assert vr.PlanDesc.mu_in.offset == 32
     assert ctypes.sizeof(vr.Layer) == 40
+
+
+def test_sliced_gemm_workspace_sizes_without_gpu():
+    """Host-side sizing of the sliced GEMM's workspace: rejected shapes give 0 (K outside
+    1..1024, slices outside 1..8, empty M, N or batch); valid ones grow with the batch by
+    the slice images of one more unit (the epilogue scratch does not grow)."""
+    lib = vr.load_library()
+    ws = lib.vrte_gemm_sliced_workspace
+    assert ws(128, 64, 0, 1, 7) == 0
+    assert ws(128, 64, 1025, 1, 7) == 0
+    assert ws(128, 64, 64, 1, 0) == 0
+    assert ws(128, 64, 64, 1, 9) == 0
+    assert ws(0, 64, 64, 1, 7) == 0 and ws(128, 0, 64, 1, 7) == 0 and ws(128, 64, 64, 0, 7) == 0
+    one, two, three = ws(200, 100, 300, 1, 7), ws(200, 100, 300, 2, 7), ws(200, 100, 300, 3, 7)
+    assert 0 < one < two < three
+    # one unit of slices: (256 rows + 128 columns) x 320 K (padded to 32) x 7 slices x 2 bytes,
+    # plus the per-row and per-column exponents, each part rounded up to 1 KiB
+    unit = 2 * 7 * 320 * (256 + 128) + 4 * (256 + 128)
+    assert abs((three - two) - unit) <= 4 * 1024
+    assert ws(200, 100, 300, 1, 4) < one
