@@ -123,8 +123,18 @@ __global__ void k_slice_cols(int N, int K, const double* __restrict__ B, int ldb
   int c = threadIdx.x % TC_N, g = threadIdx.x / TC_N;  // blockDim = 512 -> 8 groups
   int j = nt * TC_N + c;
   int Em = 0;
-  if (j < N)
-    for (int k = g; k < K; k += 8) Em = max(Em, exp_field(Bb[(size_t)k * ldb + j], &bad));
+  if (j < N) {
+    // eight independent loads in flight per thread
+    int k = g;
+    for (; k + 56 < K; k += 64) {
+      double v[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) v[t] = Bb[(size_t)(k + 8 * t) * ldb + j];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) Em = max(Em, exp_field(v[t], &bad));
+    }
+    for (; k < K; k += 8) Em = max(Em, exp_field(Bb[(size_t)k * ldb + j], &bad));
+  }
   red[g][c] = Em;
   __syncthreads();
   if (g == 0) {
