@@ -209,6 +209,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, dist, device):
+    """Maximum of the float x over the ranks of the process group (x itself without one)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, steps, seconds):
+    """Units per second of the whole job: every rank processed units_per_rank per step, and the
+    job took the slowest rank's time."""
+    return world * units_per_rank * steps / seconds
+
+
 def time_form(vr, torch, cfg, ly, precision, dev, steps, warmup, dist):
     """Warm up, then time `steps` full solves with CUDA events on the solve stream."""
     L = ly["n_coef"]
@@ -240,11 +256,7 @@ def time_form(vr, torch, cfg, ly, precision, dev, steps, warmup, dist):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = float(sum(a.elapsed_time(b) for a, b in ev))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(a.elapsed_time(b) for a, b in ev)), dist, dev)
     st = plan.status()
     if st != 0:
         raise SystemExit(f"solve failed: {vr.STATUS_NAMES.get(st, st)}")
@@ -395,14 +407,14 @@ def main():
         plan64.close()
         torch.cuda.empty_cache()
         fp64_plain = {"ms_per_step": ms64 / args.steps,
-                      "value": world * M_eff * args.steps / (ms64 / 1000.0), "unit": UNIT,
+                      "value": whole_job_rate(world, M_eff, args.steps, ms64 / 1000.0), "unit": UNIT,
                       "clocks": clk64,
                       "stages_ms": {s["name"]: round(s["ms"] / args.steps, 2) for s in stages64}}
 
     plan, coef, total_ms, clk, stages, refined = time_form(vr, torch, cfg, ly, prec, dev,
                                                            args.steps, args.warmup, dist)
     ms_per_step = total_ms / args.steps
-    value = world * M_eff * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(world, M_eff, args.steps, total_ms / 1000.0)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -439,12 +451,8 @@ def main():
         t0 = time.perf_counter()
         for i in range(args.steps):
             plan.solve_host(h_coef, h_out, stream)
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        line["e2e"] = {"value": world * M_eff * args.steps / e2e_s, "unit": UNIT,
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        line["e2e"] = {"value": whole_job_rate(world, M_eff, args.steps, e2e_s), "unit": UNIT,
                        "h2d_bytes_per_step": int(h_coef.numel() * 8),
                        "d2h_bytes_per_step": int(h_out.numel() * 4),
                        "api": "vrte_solve_brdf_host (pinned host buffers)"}
