@@ -524,7 +524,6 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
 }
 
 struct TcEpiStore {
-  static constexpr bool kF32 = false;
   double* C;
   int ldc;
   long long sC;
@@ -553,7 +552,6 @@ void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long lon
 // First half of a reconstruction contraction too deep for one exact accumulation
 // (K > 1024): T1[u][i][j] += g0(o, k) acc, the second half then goes through EpiPart.
 struct EpiPartAccum {
-  static constexpr bool kF32 = false;
   double* T1;
   const double* g0tab;
   int n_in, n_out;

@@ -102,21 +102,9 @@ __device__ inline void bulk_g2s(void* dst, const void* src, unsigned bytes, uint
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
           "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
 }
-__device__ inline uint64_t smem_desc_sw128(const void* p) {
-  uint64_t a = (uint64_t)(smem_u32(p) >> 4) & 0x3FFF;
-  return a | ((uint64_t)1 << 16)          // leading byte offset (unused for swizzled K-major)
-         | ((uint64_t)(1024 >> 4) << 32)  // stride byte offset: 8 rows x 128 bytes
-         | ((uint64_t)1 << 46)            // descriptor version for sm_100-family
-         | ((uint64_t)2 << 61);           // 128-byte swizzle
-}
-__device__ inline void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
-}
-// The same MMA with each shared-memory descriptor given as its (low, high) 32-bit words:
+// D (+)= A B, BF16 in, FP32 accumulate in TMEM, one M = 128 x N tile per the instruction
+// descriptor (cta_group::1, kind::f16); the shared-memory descriptors are given as their
+// (low, high) 32-bit words:
 // the address field sits in the low word and shared-memory offsets never carry out of it,
 // so unrolled issue loops step descriptors with 32-bit adds of constants.
 __device__ __forceinline__ void mma_bf16_w(uint32_t dtmem, uint32_t alo, uint32_t ahi,
@@ -146,21 +134,6 @@ __device__ inline uint64_t smem_desc_sw64(const void* p) {
          | ((uint64_t)(512 >> 4) << 32)  // stride byte offset: 8 rows x 64 bytes
          | ((uint64_t)1 << 46)           // descriptor version for sm_100-family
          | ((uint64_t)4 << 61);          // 64-byte swizzle
-}
-
-// Byte offset of element (row r, k) in a 32B-swizzled K-major tile of 16 BF16 per row:
-// 8-row groups of 256 bytes, 32 bytes per row, 16-byte chunk index XOR ((row / 4) mod 2).
-__device__ inline int swz32_offset(int r, int k) {
-  int chunk = k >> 3, within = k & 7;
-  return (r >> 3) * 256 + (r & 7) * 32 + ((chunk ^ ((r >> 2) & 1)) << 4) + within * 2;
-}
-
-__device__ inline uint64_t smem_desc_sw32(const void* p) {
-  uint64_t a = (uint64_t)(smem_u32(p) >> 4) & 0x3FFF;
-  return a | ((uint64_t)1 << 16)         // leading byte offset (unused for swizzled K-major)
-         | ((uint64_t)(256 >> 4) << 32)  // stride byte offset: 8 rows x 32 bytes
-         | ((uint64_t)1 << 46)           // descriptor version for sm_100-family
-         | ((uint64_t)6 << 61);          // 32-byte swizzle
 }
 
 __device__ inline void mbar_arrive(uint64_t* bar) {

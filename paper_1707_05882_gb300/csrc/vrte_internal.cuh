@@ -45,7 +45,6 @@ __host__ __device__ inline double depth_factor(double tau, double mu_o, double m
 // j = 4k + s: incident k, basis s): Isyn[m][k][o][a][s] = T1[i][j] + g0(o, k) acc with
 // g0 = depth_factor from the per-layer table g0tab[o][k].
 struct EpiPart {
-  static constexpr bool kF32 = false;
   const double* T1;
   double* Isyn;
   const double* g0tab;
