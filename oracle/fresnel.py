@@ -26,8 +26,12 @@ equations:
 For n <= 1 the interface is absent: M_in = M_out = identity, no reflection.
 
 Pinned by tests: R + T = 1 per polarization on both sides, |r| = 1 beyond the
-critical angle, n -> 1 limits, and the end-to-end invariants of the BRDF with an
-interface (energy balance inside, reciprocity outside, n = 1 equals no interface).
+critical angle, the total-internal-reflection retardance against its closed form
+tan(delta/2) = cos(theta) sqrt(sin^2(theta) - 1/n^2) / sin^2(theta) (Born & Wolf) and
+its sign against the evanescent decay of the transmitted field under exp(-i w t), the
+Mueller map against Stokes vectors formed from explicit fields, n -> 1 limits, and the
+end-to-end invariants of the BRDF with an interface (energy balance inside,
+reciprocity outside, n = 1 equals no interface).
 """
 from __future__ import annotations
 

@@ -1,5 +1,5 @@
-"""Gradient of the BRDF loss with respect to the layer parameters (the target of the adjoint,
-SURVEY row a9), by central differences of the FP64 oracle.
+"""Gradient of the BRDF loss with respect to the layer parameters (the target of the adjoint),
+by central differences of the FP64 oracle.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring): the CUDA library never calls it.
 

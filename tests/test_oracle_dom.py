@@ -229,3 +229,69 @@ def test_fresnel_energy_and_limits():
         r = (n - 1) / (n + 1)
         assert np.allclose(R1, np.diag([r * r, r * r, -r * r, -r * r]), atol=1e-15)
     assert np.allclose(O.fresnel_beam_in(mu, 1.0), np.eye(4)) and np.allclose(O.fresnel_exit(mu, 1.0), np.eye(4))
+
+
+def test_fresnel_tir_retardance_magnitude():
+    """Beyond the critical angle |r_p| = |r_s| = 1 and the p-s phase difference delta obeys
+    the closed form of total internal reflection (Born & Wolf, Sec. 1.5.4):
+        tan(delta/2) = cos(theta) sqrt(sin^2(theta) - 1/n^2) / sin^2(theta).
+    The internal-reflection Mueller matrix carries delta in its U/V block as the rotation
+    [[cos delta, sin delta], [-sin delta, cos delta]]; its magnitude is independent of the
+    p-axis convention (r_p = -r_s at normal incidence) and of the time convention."""
+    for n in (1.3, 1.5, 1.7):
+        mu_c = math.sqrt(1 - 1 / n**2)
+        mu = np.linspace(0.01, mu_c - 1e-6, 40)
+        R = O.fresnel_internal_reflection(mu, n)
+        # unit reflectance of both polarizations: R = diag(1, 1, .) and no I-Q coupling
+        assert np.allclose(R[:, 0, 0], 1.0, atol=1e-14) and np.allclose(R[:, 0, 1], 0.0, atol=1e-14)
+        delta = np.arctan2(R[:, 2, 3], R[:, 2, 2])
+        assert np.allclose(R[:, 3, 3], R[:, 2, 2], atol=1e-15)
+        assert np.allclose(R[:, 3, 2], -R[:, 2, 3], atol=1e-15)
+        sin2 = 1.0 - mu**2
+        closed = mu * np.sqrt(sin2 - 1.0 / n**2) / sin2
+        # 1e-10: the closed form itself loses digits in sin^2 - 1/n^2 next to critical
+        assert np.allclose(np.abs(np.tan(0.5 * delta)), closed, rtol=1e-10, atol=1e-15)
+
+
+def test_fresnel_tir_retardance_sign_follows_time_convention():
+    """The sign of the TIR retardance is fixed by the branch of the transmitted-side
+    cosine c2 = +-i sqrt(n^2 sin^2 - 1). Under the exp(-i w t) time factor of the Mie code
+    the transmitted field is exp(i k0 c2 z) for z > 0 away from the interface, which decays
+    only for Im c2 > 0. With that branch r_s = exp(-2i atan(beta/(n c1))) and
+    r_p = exp(-2i atan(n beta/c1)), so delta = arg(r_p r_s*) is negative: the U -> V
+    element of the Mueller matrix, sin(delta) = Im(r_p r_s*), is negative at every cosine
+    below critical. The Mueller matrix itself follows the project's Stokes definition
+    (U = 2 Re(E1 E2*), V = -2 Im(E1 E2*)), checked here on explicit fields, and it is the
+    same map from a diagonal Jones matrix that the Mie code uses for its amplitude
+    matrix diag(S2, S1) (b2 = Im(S2 S1*))."""
+    from oracle.fresnel import _fresnel_amplitudes, _mueller_diag_jones
+    from vrte_inputs.mie import amplitude_functions, mie_coefficients_ab, scattering_matrix_elements
+    for n in (1.3, 1.5, 1.7):
+        mu_c = math.sqrt(1 - 1 / n**2)
+        mu = np.linspace(0.01, mu_c - 1e-6, 40)
+        rp, rs, _, _, c2 = _fresnel_amplitudes(mu, n, 1.0)
+        k0z = np.linspace(0.0, 5.0, 11)
+        field = np.exp(1j * np.outer(c2, k0z))   # exp(i k0 c2 z) at z >= 0
+        assert np.all(c2.imag > 0.0)
+        assert np.all(np.diff(np.abs(field), axis=1) < 0.0)   # evanescent: decays away
+        R = O.fresnel_internal_reflection(mu, n)
+        assert np.all(R[:, 2, 3] < 0.0)
+        assert np.allclose(R[:, 2, 3], (rp * np.conj(rs)).imag, atol=1e-15)
+    # Mueller map of a diagonal Jones matrix against Stokes vectors formed from fields
+    rng = np.random.default_rng(5)
+    jp, js = rng.normal(size=2) + 1j * rng.normal(size=2)
+    M = _mueller_diag_jones(np.array([jp]), np.array([js]))[0]
+    for _ in range(4):
+        E1, E2 = rng.normal(size=2) + 1j * rng.normal(size=2)
+
+        def stokes(a, b):
+            return np.array([abs(a)**2 + abs(b)**2, abs(a)**2 - abs(b)**2,
+                             2 * (a * np.conj(b)).real, -2 * (a * np.conj(b)).imag])
+        assert np.allclose(M @ stokes(E1, E2), stokes(jp * E1, js * E2), atol=1e-13)
+    # the Mie code's scattering matrix is the same map from its amplitude matrix diag(S2, S1)
+    a, b = mie_coefficients_ab(1.5 + 0.01j, 3.0)
+    S1, S2 = amplitude_functions(a, b, np.array([0.3, -0.5]))
+    el = scattering_matrix_elements(S1, S2)
+    Mm = _mueller_diag_jones(S2, S1)
+    assert np.allclose(Mm[:, 0, 0], el[0]) and np.allclose(Mm[:, 0, 1], el[4])
+    assert np.allclose(Mm[:, 2, 2], el[2]) and np.allclose(Mm[:, 2, 3], el[5])
