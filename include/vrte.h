@@ -181,8 +181,8 @@ vrte_status vrte_debug_copy(vrte_plan* plan, const char* name, void* host_dst, s
 /* Batched eigen-decomposition of `batch` real n x n matrices (row-major, device
  * d_A[batch][n][n], read only) without allocating any device memory, for callers that
  * cannot call cudaMalloc: code whose device memory is owned by another allocator or a
- * fixed pool, code where an allocation would synchronize the device or is not allowed,
- * and code recorded into a CUDA graph by a capture it does not control. The paper has
+ * fixed pool, and code where an allocation would synchronize the device or is not
+ * allowed. The paper has
  * no counterpart; this is the library's homogeneous-step eigensolver (balancing,
  * Hessenberg, Francis double-shift QR, back-substitution) run on scratch space taken
  * from a file-scope device array of 2^21 doubles (16 MiB) that every GPU loading the
@@ -193,9 +193,11 @@ vrte_status vrte_debug_copy(vrte_plan* plan, const char* name, void* host_dst, s
  *   to a largest component modulus of one.
  *   d_status: optional device word (caller zeroes it) that receives the device-detected
  *   error bits (1 = no convergence, 4 = non-finite); NULL discards them.
- * Limits: 1 <= n <= 768 and (3 n^2 + n) * batch <= 2^21 - 8, else VRTE_ERR_INVALID_ARG
- * before any launch. The first call on each device resolves the scratch array's device
- * address (with that device current); make that first call before any stream capture.
+ * Limits: 1 <= n <= 768, 1 <= batch <= 65535 and (3 n^2 + n) * batch <= 2^21 - 8, else
+ * VRTE_ERR_INVALID_ARG before any launch. A launch error pending from earlier work on the
+ * calling thread is cleared on entry, so VRTE_ERR_CUDA reports this call's launches only.
+ * The first call on each device resolves the scratch array's device address (with that
+ * device current); make that first call before any stream capture.
  * All calls share the one array and it keeps the previous call's contents (the kernels
  * initialise what they read): calls that overlap on the GPU, on any streams, race.
  * Asynchronous on `stream`. */

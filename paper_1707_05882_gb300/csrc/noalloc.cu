@@ -2,9 +2,8 @@
 //
 // Some callers cannot call cudaMalloc: code that runs while another component owns
 // the device memory budget (a framework's caching allocator, a fixed-size pool on a
-// shared GPU), code on a path where an allocation would synchronize the device or is
-// forbidden (stream-ordered callbacks, latency-critical loops), and code that wants to
-// be recorded into a CUDA graph by a capture it does not control. For them this entry
+// shared GPU), and code on a path where an allocation would synchronize the device or is
+// forbidden (stream-ordered callbacks, latency-critical loops). For them this entry
 // point runs the library's eigensolver with its Hessenberg/Schur/eigenvector scratch
 // taken from a file-scope device array instead of a plan workspace.
 #include <mutex>
@@ -55,10 +54,14 @@ vrte_status scratch_for_current_device(double** out) {
 extern "C" vrte_status vrte_eigen_noalloc(const double* d_A, int n, int batch, double* d_lam_re,
                                           double* d_lam_im, double* d_X, unsigned* d_status,
                                           void* stream) {
-  if (!d_A || !d_lam_re || !d_lam_im || !d_X || n < 1 || n > 768 || batch < 1)
+  // batch <= 65535: the eigenvector kernels take the batch in a grid y or z dimension
+  if (!d_A || !d_lam_re || !d_lam_im || !d_X || n < 1 || n > 768 || batch < 1 || batch > 65535)
     return VRTE_ERR_INVALID_ARG;
   size_t per = 3 * (size_t)n * n + (size_t)n;
   if (per * (size_t)batch > kNoAllocUsable) return VRTE_ERR_INVALID_ARG;
+  // a launch error left pending by earlier, unrelated work is not this call's failure:
+  // it is cleared here so that the check after the launches sees only this call's own
+  cudaGetLastError();
   double* base = nullptr;
   vrte_status st = scratch_for_current_device(&base);
   if (st != VRTE_OK) return st;
