@@ -169,6 +169,8 @@ def cpu_baseline(ly, cfg):
         "value": 1.0 / t_order,
         "unit": UNIT,
         "cores": blas_threads(),
+        "cpu_model": cpu_model(),
+        "nproc": os.cpu_count(),
         "kind": "oracle",
         "sample": ("FP64 numpy oracle (full 8N formulation) on orders m=0 and m=64 of the "
                    "N=64, L=128 layer for sub-grids (2,8), (8,8), (2,24), (8,24) incident x "
@@ -201,7 +203,8 @@ def run_reference(args):
         "config": {"workload": "mie-N64-M128-L128-1024x1024x360-n1.5", "N": 64, "M": 128, "L": 128,
                    "n_in": 1024, "n_out": 1024, "n_phi": 360,
                    "step": "bounded oracle sample (4 sub-grids x 2 orders), extrapolated"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(),
+                         "cpu_model": cpu_model(), "nproc": os.cpu_count(), "kind": "oracle",
                          "sample": "each step: oracle on orders 0 and 64, sub-grids (2,8),(8,8),"
                                    "(2,24),(8,24) x 360 azimuths, linear fit to 1024 x 1024"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -329,34 +332,78 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-# DRAM bytes per launch of a stage's dominant kernel from one ncu capture of the same
-# kernel (profiles/eigen_mie-N64-M128.md: k_eigen, 128 orders of the N = 64 layer, the
-# stage does not depend on the angular grid). Stages without a current capture: None.
-DRAM_TRAFFIC = {"eigen": 7.330067712e9 + 21.217310208e9}
+# Committed ncu summaries that give the DRAM bytes per launch of a stage's dominant kernel
+# (the stage's kernel, not the grid, decides them: k_eigen does not depend on the angular
+# grid). A stage without a summary of its current kernel reports traffic null.
+TRAFFIC_PROFILES = {"eigen": "profiles/eigen_mie-N64-M128.md"}
+
+
+def profile_traffic(stage):
+    """dram__bytes_read + dram__bytes_write (bytes per launch) from the stage's committed ncu
+    summary table rows "| dram__bytes_read | X GB |", or None."""
+    path = TRAFFIC_PROFILES.get(stage)
+    if not path:
+        return None
+    try:
+        total, seen = 0.0, set()
+        for line in open(os.path.join(ROOT, path)):
+            f = [x.strip() for x in line.strip().strip("|").split("|")]
+            if len(f) >= 2 and f[0] in ("dram__bytes_read", "dram__bytes_write"):
+                v, unit = f[1].split()[:2]
+                total += float(v) * {"GB": 1e9, "MB": 1e6, "KB": 1e3, "B": 1.0}[unit]
+                seen.add(f[0])
+        return total if len(seen) == 2 else None
+    except Exception:
+        return None
+
+
+def stage_roofline(st, pk, pk_src):
+    """One stage against its bounding unit: tensor-core stages against the measured sustained
+    BF16 peak (the slice products they issue), FP64 stages against the derived FP64 peak."""
+    sec = st["ms"] / 1000.0 if st["ms"] > 0 else float("nan")
+    if st.get("tc_flops", 0.0) > 0.0:
+        peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0)))
+        achieved = st["tc_flops"] / sec / 1e12
+        return {"stage": st["name"], "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak,
+                "fp64_equivalent_tflops": st["flops"] / sec / 1e12,
+                "peak_source": f"bf16_tflops_sustained ({pk_src}) of measured; achieved counts "
+                               "the BF16 slice products the sliced FP64 contractions issue"}
+    peak = fp64_peak_tflops(pk.get("sm_max_mhz", 2070.0))
+    achieved = st["flops"] / sec / 1e12
+    return {"stage": st["name"], "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": "derived FP64: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x max SM clock"}
 
 
 def roofline(stages, clk, precision_name, grid=None):
-    """Roofline of the dominant stage: tensor-core stages against the measured sustained
-    BF16 peak (their issued slice products), FP64 stages against the derived FP64 peak."""
+    """Roofline of the dominant stage (the headline), with its DRAM traffic per launch from
+    the committed ncu summary; `per_stage` holds every timed stage against its own unit."""
     pk, pk_src = peaks()
+    timed = [s for s in stages if s["ms"] > 0 and s["flops"] > 0]
     dom = max(stages, key=lambda s: s["ms"])
-    traffic = DRAM_TRAFFIC.get(dom["name"]) if WORKLOAD == 3 and not grid else None
-    sec = dom["ms"] / 1000.0 if dom["ms"] > 0 else float("nan")
-    if dom.get("tc_flops", 0.0) > 0.0:
-        peak = float(pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0)))
-        achieved = dom["tc_flops"] / sec / 1e12
-        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel_stage": dom["name"],
-                "launches": dom["launches"],
-                "fp64_equivalent_tflops": dom["flops"] / sec / 1e12,
-                "peak_source": f"bf16_tflops_sustained ({pk_src}); achieved counts the BF16 "
-                               "slice products the sliced FP64 contractions issue"}
-    peak = fp64_peak_tflops(pk.get("sm_max_mhz", 2070.0))
-    achieved = dom["flops"] / sec / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel_stage": dom["name"],
-            "launches": dom["launches"],
-            "peak_source": "derived FP64: 152 SMs x 2 FP64 FMA/clk x 2 FLOP x max SM clock"}
+    head = stage_roofline(dom, pk, pk_src)
+    head["traffic"] = profile_traffic(dom["name"]) if WORKLOAD == 3 and not grid else None
+    head["kernel_stage"] = head.pop("stage")
+    head["launches"] = dom["launches"]
+    head["per_stage"] = [{k: (round(v, 4) if isinstance(v, float) else v)
+                          for k, v in stage_roofline(s, pk, pk_src).items() if k != "peak_source"}
+                         for s in timed]
+    return head
+
+
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
 def main():
@@ -452,11 +499,24 @@ def main():
         for i in range(args.steps):
             plan.solve_host(h_coef, h_out, stream)
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        # the device-to-host link alone: the same table copied from device to pinned host
+        d_tab = torch.empty(plan.table_shape, dtype=torch.float32, device=dev)
+        h_out.copy_(d_tab)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h_out.copy_(d_tab)
+        torch.cuda.synchronize()
+        link_s = time.perf_counter() - t0
+        d2h = int(h_out.numel() * 4)
         line["e2e"] = {"value": whole_job_rate(world, M_eff, args.steps, e2e_s), "unit": UNIT,
                        "h2d_bytes_per_step": int(h_coef.numel() * 8),
-                       "d2h_bytes_per_step": int(h_out.numel() * 4),
-                       "api": "vrte_solve_brdf_host (pinned host buffers)"}
-        del h_out
+                       "d2h_bytes_per_step": d2h,
+                       "seconds_per_step": e2e_s / args.steps,
+                       "d2h_gbs_in_step": d2h / (e2e_s / args.steps) / 1e9,
+                       "d2h_link_gbs_alone": d2h / link_s / 1e9,
+                       "api": "vrte_solve_brdf_host (pinned host buffers; the table leaves in "
+                              "blocks of 64 incident cosines as the synthesis completes them)"}
+        del h_out, d_tab
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ly, cfg)

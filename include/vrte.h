@@ -143,8 +143,10 @@ vrte_status vrte_solve_brdf(vrte_plan* plan, void* d_brdf, int out_dtype, void* 
 /* Same solve with host buffers: copies h_coeffs (host FP64, layout as d_coeffs
  * of vrte_set_layer) to the plan's staging buffer, solves, copies the table to
  * h_brdf (host, layout as d_brdf) and synchronizes `stream` before returning. The table
- * is copied in four chunks on four streams of the plan (several copy engines), forked
- * from and joined back into `stream`. Pinned host memory gives full copy bandwidth. */
+ * leaves in blocks of incident cosines, each copied as soon as the synthesis kernels that
+ * complete it have run, on four streams of the plan (several copy engines) that wait on
+ * `stream` by events and are joined back into it, so the copies overlap the rest of the
+ * solve. Pinned host memory gives full copy bandwidth. */
 vrte_status vrte_solve_brdf_host(vrte_plan* plan, const double* h_coeffs, void* h_brdf,
                                  int out_dtype, void* stream);
 

@@ -392,7 +392,7 @@ size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int k_block
 
 void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, const double* wc,
                   const double* ws, void* out, int out_dtype, int k_block, void* work,
-                  unsigned* status, cudaStream_t s) {
+                  unsigned* status, cudaStream_t s, const SynthHook* hook) {
   const long long pairs_total = (long long)n_in * n_out;
   const SynthLayout Lmax = synth_layout(std::min(k_block, n_in) * n_out, M, n_phi);
   unsigned char* w = (unsigned char*)work;
@@ -421,6 +421,7 @@ void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, con
     else
       k_synth_mma<float><<<grid, SY_THREADS, SY_SMEM, s>>>(L.P, pair0, n_phi, L.MT, L.NT, L.KB, As,
                                                            ea, Bs, fb, (float*)out, status);
+    if (hook) hook->fn(hook->user, hook->layer, k0, k0 + kb, s);
   }
 }
 

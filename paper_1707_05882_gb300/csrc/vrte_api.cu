@@ -96,9 +96,9 @@ struct vrte_plan {
   size_t tcw_bytes = 0;
   int kdir = 0;  // extra K of the direct term in the mixed form (4 L_max)
   cudaEvent_t fork = nullptr;
-  // host-API output copy: split over four streams (several copy engines)
+  // host-API output copy: blocks of incident cosines on four streams (several copy engines)
   cudaStream_t cstream[4] = {};
-  cudaEvent_t cdone[4] = {};
+  cudaEvent_t cdone[4] = {}, cready[4] = {};
   cudaEvent_t solved = nullptr;
   // host-API staging
   double* d_coef_stage = nullptr;
@@ -389,7 +389,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
 }
 
 static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, int out_dtype,
-                             cudaStream_t s0) {
+                             cudaStream_t s0, void (*hook_fn)(void*, int, int, int, cudaStream_t) = nullptr,
+                             void* hook_user = nullptr) {
   const size_t table = (size_t)p->n_in * p->n_out * p->n_phi * 16;
   const size_t esz = out_dtype == VRTE_OUT_F64 ? sizeof(double) : sizeof(float);
   const int R = 4 * p->n_in, Ro = 4 * p->n_out;
@@ -467,13 +468,12 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         dgemm_batched(n, n, n, 1.0, w->F, n, nn, w->E, n, nn, 0.0, w->FE, n, nn, U, s);
       }
       {
-        // nominal cost of a real Schur decomposition with eigenvectors: 25 n^3, plus
-        // E'X, Y = E'X / kappa and the mode residual F'Y - X kappa
-        // (the mixed form takes E'X and F'Y, whose operands are row- and column-scaled
-        // eigenvectors, on the tensor cores; F'E' itself stays an FP64 GEMM). The stage is
-        // bound by the FP64 eigen-decomposition, so its work is counted as FP64 work only.
-        StageScope sc(p, ST_EIGEN, s, mixed ? 10 + 2 * (gl - 1) : 10,
-                      (25.0 + 4.0) * dn * dn * dn * dU, 8.0 * 6 * dn * dn * dU);
+        // algorithmic work counted: the nominal 25 n^3 of a real Schur decomposition with
+        // eigenvectors, the stage's dominant kernel. E'X, Y = E'X / kappa and the mode
+        // residual F'Y - X kappa (4 n^3 more; on the tensor cores in the mixed form) are
+        // not counted, so the stage's FP64 rate is that of the eigen-decomposition.
+        StageScope sc(p, ST_EIGEN, s, mixed ? 10 + 2 * (gl - 1) : 10, 25.0 * dn * dn * dn * dU,
+                      8.0 * 6 * dn * dn * dU);
         batched_eigen(n, w->FE, w->Hs, w->Zs, w->Vs, w->X, w->lam_re, w->lam_im, w->bal, U,
                       p->d_status, s);
         gemm(n, n, n, w->E, n, nn, w->X, n, nn, 0.0, w->EX, n, nn);
@@ -604,12 +604,15 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         const int Ss = kSlicesSynth;
         sc.tensor_flops(2.0 * Ss * (Ss + 1) / 2 * 16.0 * p->n_in * p->n_out * p->n_phi * Meff);
       }
-      if (mixed)
+      SynthHook hook{hook_fn, hook_user, lb};
+      if (mixed) {
         tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws, outb, out_dtype,
-                     kSynthBlock, w->tcw, p->d_status, s);
-      else
+                     kSynthBlock, w->tcw, p->d_status, s, hook_fn ? &hook : nullptr);
+      } else {
         launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws, outb,
                               out_dtype, p->d_status, s);
+        if (hook_fn) hook_fn(hook_user, lb, 0, p->n_in, s);
+      }
     }
   }
   // join: the caller's stream waits for every slot, also after a failed launch
@@ -656,34 +659,50 @@ vrte_status vrte_solve_brdf_host(vrte_plan* p, const double* h_coeffs, void* h_b
   if (cudaMemcpyAsync(p->d_coef_stage, h_coeffs, cbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return VRTE_ERR_CUDA;
   p->last_stream = s;
-  vrte_status st = run_solve(p, p->d_coef_stage, p->d_out_stage, out_dtype, s);
-  if (st != VRTE_OK) return st;
-  // the table leaves in kCopyStreams chunks on their own streams (one copy engine each),
-  // forked from and joined back into the caller's stream
+  // The table leaves in blocks of incident cosines, each as soon as the synthesis kernels that
+  // complete it have run: the solve stream records an event after them and one of four copy
+  // streams (several copy engines) waits on it and copies the block, so the copies overlap
+  // the rest of the solve. The copy streams join back into the caller's stream at the end.
   constexpr int kCopyStreams = 4;
   if (!p->solved) {
     if (cudaEventCreateWithFlags(&p->solved, cudaEventDisableTiming) != cudaSuccess)
       return VRTE_ERR_CUDA;
     for (int c = 0; c < kCopyStreams; ++c)
       if (cudaStreamCreateWithFlags(&p->cstream[c], cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&p->cdone[c], cudaEventDisableTiming) != cudaSuccess)
+          cudaEventCreateWithFlags(&p->cdone[c], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&p->cready[c], cudaEventDisableTiming) != cudaSuccess)
         return VRTE_ERR_CUDA;
   }
-  if (cudaEventRecord(p->solved, s) != cudaSuccess) return VRTE_ERR_CUDA;
-  const size_t chunk = ((obytes + kCopyStreams - 1) / kCopyStreams + 4095) / 4096 * 4096;
-  for (int c = 0; c < kCopyStreams; ++c) {
-    const size_t off = (size_t)c * chunk;
-    const size_t len = off < obytes ? std::min(chunk, obytes - off) : 0;
-    if (cudaStreamWaitEvent(p->cstream[c], p->solved, 0) != cudaSuccess) return VRTE_ERR_CUDA;
-    if (len && cudaMemcpyAsync((char*)h_brdf + off, (const char*)p->d_out_stage + off, len,
-                               cudaMemcpyDeviceToHost, p->cstream[c]) != cudaSuccess)
-      return VRTE_ERR_CUDA;
+  struct CopyCtx {
+    vrte_plan* p;
+    char* h;
+    size_t row_bytes, layer_bytes;
+    int next;
+    bool failed;
+  } ctx{p, (char*)h_brdf,
+        (size_t)p->n_out * p->n_phi * 16 * (out_dtype == VRTE_OUT_F64 ? sizeof(double) : sizeof(float)),
+        0, 0, false};
+  ctx.layer_bytes = ctx.row_bytes * p->n_in;
+  auto copy_block = [](void* user, int layer, int k0, int k1, cudaStream_t sl) {
+    CopyCtx* c = (CopyCtx*)user;
+    const int q = c->next++ % kCopyStreams;
+    const size_t off = (size_t)layer * c->layer_bytes + (size_t)k0 * c->row_bytes;
+    const size_t len = (size_t)(k1 - k0) * c->row_bytes;
+    if (cudaEventRecord(c->p->cready[q], sl) != cudaSuccess ||
+        cudaStreamWaitEvent(c->p->cstream[q], c->p->cready[q], 0) != cudaSuccess ||
+        cudaMemcpyAsync(c->h + off, (const char*)c->p->d_out_stage + off, len,
+                        cudaMemcpyDeviceToHost, c->p->cstream[q]) != cudaSuccess)
+      c->failed = true;
+  };
+  vrte_status st = run_solve(p, p->d_coef_stage, p->d_out_stage, out_dtype, s, copy_block, &ctx);
+  // join the copy streams (also after a failure, so that no copy outlives the call)
+  for (int c = 0; c < kCopyStreams; ++c)
     if (cudaEventRecord(p->cdone[c], p->cstream[c]) != cudaSuccess ||
         cudaStreamWaitEvent(s, p->cdone[c], 0) != cudaSuccess)
-      return VRTE_ERR_CUDA;
-  }
+      st = st == VRTE_OK ? VRTE_ERR_CUDA : st;
   if (cudaStreamSynchronize(s) != cudaSuccess) return VRTE_ERR_CUDA;
-  return VRTE_OK;
+  if (st != VRTE_OK) return st;
+  return ctx.failed ? VRTE_ERR_CUDA : VRTE_OK;
 }
 
 vrte_status vrte_brdf_backward(vrte_plan* p, const void* g, int gd, double* d_grad, void* stream) {
@@ -820,6 +839,7 @@ void vrte_destroy(vrte_plan* p) {
   for (int c = 0; c < 4; ++c) {
     if (p->cstream[c]) cudaStreamDestroy(p->cstream[c]);
     if (p->cdone[c]) cudaEventDestroy(p->cdone[c]);
+    if (p->cready[c]) cudaEventDestroy(p->cready[c]);
   }
   if (p->solved) cudaEventDestroy(p->solved);
   if (p->d_coef_stage) cudaFree(p->d_coef_stage);

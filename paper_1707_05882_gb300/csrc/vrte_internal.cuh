@@ -141,12 +141,20 @@ size_t refine_scratch_doubles(int U, int n_in, int n_out);
 void tc_gemm_part_accum(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                         const double* B, long long sB, double* T1, const double* g0tab, int S,
                         void* work, cudaStream_t s);
+// Called on the host after the kernels that complete the table rows of incident cosines
+// k0 .. k1-1 of one layer have been enqueued on `s` (the host-buffer solve starts the copy
+// of those rows there).
+struct SynthHook {
+  void (*fn)(void* user, int layer, int k0, int k1, cudaStream_t s);
+  void* user;
+  int layer;
+};
 // Synthesis of the order radiances on the tensor cores (five slices), in blocks of k_block
 // incident cosines (k_synth_tc.cu).
 size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int k_block);
 void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, const double* wc,
                   const double* ws, void* out, int out_dtype, int k_block, void* work,
-                  unsigned* status, cudaStream_t s);
+                  unsigned* status, cudaStream_t s, const SynthHook* hook = nullptr);
 
 // ---------------------------------------------------------------- mode algebra (k_modes.cu)
 void launch_pack_Y(const OrderBatch& b, const double* EX, const double* lam_re,
