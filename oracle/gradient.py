@@ -9,10 +9,13 @@ with the coefficients in input order (alpha1, alpha2, alpha3, alpha4, beta1, bet
 Loss L(p) = 1/2 sum over the table (F(p) - F_target)^2, so
     dL/dp_k = sum (F - F_target) dF/dp_k
 (the chain rule through the table), with dF/dp_k a central difference of step
-h_k = h |p_k| (h where p_k = 0), Richardson-extrapolated from the steps h_k and h_k / 2,
+h_k = h max(1, |p_k|), Richardson-extrapolated from the steps h_k and h_k / 2,
 (4 D(h_k / 2) - D(h_k)) / 3, so that the truncation error is O(h^4) and the rounding error
-O(u / h) of the table. A relative step keeps tau0 - h_k > 0 for thin layers; the interface
-index must sit away from n = 1, where the interface switches off.
+O(u / h) of the table. The floor of one keeps the step, and so the rounding error, bounded
+for the small high-order coefficients (a step relative to a coefficient of 1e-5 would leave
+only rounding); a thin layer (tau0 below h) takes h_k = h |tau0| instead so that tau0 - h_k
+stays positive. The interface index must sit away from n = 1, where the interface switches
+off.
 
 Pinned by tests/test_oracle_gradient.py: in the thin-layer limit F tends to the closed-form
 single-scattering BRDF, which is linear in omega and in every coefficient and has a closed
@@ -46,7 +49,9 @@ def table_derivative(p, k: int, L, N, M, mu_in, mu_out, dphi, h: float = 1e-6,
                      richardson: bool = True) -> np.ndarray:
     """dF/dp_k by central differences (Richardson-extrapolated unless richardson=False)."""
     p = np.asarray(p, dtype=float)
-    hk = h * (abs(p[k]) if p[k] != 0.0 else 1.0)
+    hk = h * max(1.0, abs(p[k]))
+    if k == 1 and hk >= 0.5 * p[k]:   # thin layer: keep tau0 - h_k > 0
+        hk = h * abs(p[k])
 
     def central(step):
         pp = p.copy()
