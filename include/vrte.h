@@ -86,6 +86,12 @@ typedef struct {
  * with vrte_profile_stages. Adds two event records per stage and order batch. */
 #define VRTE_FLAG_PROFILE 1u
 
+/* Allocates, in vrte_set_layer, the workspace of the adjoint (vrte_brdf_backward), which
+ * vrte_brdf_backward requires. The adjoint recomputes each order batch's eigen-decomposition
+ * and boundary factors in FP64 from the layer parameters instead of keeping them, so the
+ * workspace grows with the batch of orders processed at once, not with all orders. */
+#define VRTE_FLAG_ADJOINT 2u
+
 /* Per-stage statistics accumulated since the last vrte_profile_reset. */
 typedef struct {
   char name[24];        /* stage name, e.g. "eigen", "recon_gemm", "synthesis" */
@@ -150,8 +156,26 @@ vrte_status vrte_solve_brdf(vrte_plan* plan, void* d_brdf, int out_dtype, void* 
 vrte_status vrte_solve_brdf_host(vrte_plan* plan, const double* h_coeffs, void* h_brdf,
                                  int out_dtype, void* stream);
 
-/* Gradient of a scalar loss through the BRDF table (not implemented in this
- * version: returns VRTE_ERR_UNSUPPORTED). */
+/* Adjoint of the BRDF table (the paper has no adjoint; it is the differentiation target of
+ * the inverse material-fitting use): given d_grad_brdf = dL/dF for a scalar loss L of the
+ * table F that vrte_solve_brdf writes for the plan's current layers (device, layout as
+ * d_brdf, FP32 or FP64 per grad_dtype), writes
+ *   d_grad_params[n_layers][3 + 6 n_coef_max]  (device FP64, caller-owned)
+ * = dL/d(omega, tau0, n_interface, coefficients), the coefficients in the order of
+ * d_coeffs ((alpha1, alpha2, alpha3, alpha4, beta1, beta2) per l), zero beyond a layer's
+ * n_coef. The interface entry is zero for a layer without interface (n_interface <= 1).
+ * The derivative is that of the FP64 solution (the VRTE_FP64 table; a VRTE_MIXED table
+ * agrees with it to the mixed form's accuracy). Every order batch is solved again in FP64
+ * (eigen-decomposition, boundary system, particular solution) and then reversed: the
+ * reverse of Secs. 2.D / 3.D (synthesis, reconstruction), Sec. 3.C (boundary system) and
+ * Sec. 3.B (particular solution) with the eigenpairs held fixed, plus the dependence of the
+ * homogeneous modes on F'E' (Sec. 3.A) through the adjoint two-point problem of the order,
+ * whose mode integrals are closed-form divided differences (finite at degenerate and complex
+ * eigenvalues). Requires a plan created with VRTE_FLAG_ADJOINT and vrte_set_layer, else
+ * VRTE_ERR_STATE; VRTE_ERR_INVALID_ARG for NULL pointers or an unknown grad_dtype.
+ * Asynchronous on `stream`; no allocation; layers run on the plan's streams as in
+ * vrte_solve_brdf. Accuracy: ~1e-8 relative in the gradient's largest entries (the FP64
+ * solution's rounding, amplified near a resonance mu kappa_j ~ 1 as in the solve). */
 vrte_status vrte_brdf_backward(vrte_plan* plan, const void* d_grad_brdf, int grad_dtype,
                                double* d_grad_params, void* stream);
 

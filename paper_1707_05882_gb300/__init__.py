@@ -46,6 +46,7 @@ class PlanDesc(ctypes.Structure):
 
 
 VRTE_FLAG_PROFILE = 1
+VRTE_FLAG_ADJOINT = 2
 
 
 class StageStat(ctypes.Structure):
@@ -133,7 +134,7 @@ class Plan:
     """A solver plan (vrte_plan_create / vrte_set_layer / vrte_solve_brdf / vrte_destroy)."""
 
     def __init__(self, mu_in, mu_out, dphi, n_nodes_max, n_orders_max, n_coef_max,
-                 n_layers_max=1, precision=VRTE_FP64, profile=False):
+                 n_layers_max=1, precision=VRTE_FP64, profile=False, adjoint=False):
         self.lib = load_library()
         self._mu_in = np.ascontiguousarray(mu_in, dtype=np.float64)
         self._mu_out = np.ascontiguousarray(mu_out, dtype=np.float64)
@@ -141,7 +142,7 @@ class Plan:
         d = PlanDesc(int(n_nodes_max), int(n_orders_max), int(n_coef_max), int(n_layers_max),
                      self._mu_in.size, self._mu_out.size, self._phi.size, _dptr(self._mu_in),
                      _dptr(self._mu_out), _dptr(self._phi), int(precision),
-                     VRTE_FLAG_PROFILE if profile else 0)
+                     (VRTE_FLAG_PROFILE if profile else 0) | (VRTE_FLAG_ADJOINT if adjoint else 0))
         h = ctypes.c_void_p()
         _check(self.lib.vrte_plan_create(ctypes.byref(d), ctypes.byref(h)), "vrte_plan_create")
         self.handle = h
@@ -181,6 +182,21 @@ class Plan:
                                              ctypes.c_void_p(h_out.data_ptr()), dt,
                                              _stream_handle(stream)), "vrte_solve_brdf_host")
         return h_out
+
+    def backward(self, grad_table, out=None, stream=None):
+        """dL/d(omega, tau0, n, coefficients) for the table gradient `grad_table` (CUDA float32
+        or float64, the table's shape) through vrte_brdf_backward: CUDA float64 tensor
+        [n_layers, 3 + 6 n_coef_max]. Needs a plan created with adjoint=True."""
+        import torch
+        g = grad_table.contiguous()
+        dt = VRTE_OUT_F64 if g.dtype == torch.float64 else VRTE_OUT_F32
+        if out is None:
+            out = torch.empty((self.n_layers, 3 + 6 * self.n_coef_max), dtype=torch.float64,
+                              device=g.device)
+        _check(self.lib.vrte_brdf_backward(self.handle, ctypes.c_void_p(g.data_ptr()), dt,
+                                           ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+               "vrte_brdf_backward")
+        return out
 
     def status(self):
         return self.lib.vrte_plan_status(self.handle)
@@ -280,3 +296,52 @@ def brdf(layers, mu_in, mu_out, dphi, precision=VRTE_FP64, out_dtype=None, strea
         return out
     finally:
         plan.close()
+
+
+def _autograd_function():
+    import torch
+
+    class BRDFFunction(torch.autograd.Function):
+        """The BRDF table as a differentiable function of the layer parameters: forward is
+        vrte_solve_brdf, backward is vrte_brdf_backward (argument marshalling only)."""
+
+        @staticmethod
+        def forward(ctx, params, coeffs, plan, sizes, out_dtype):
+            # params [n_layers, 3] = (omega, tau0, n_interface); coeffs [n_layers, L, 6]
+            host = params.detach().double().cpu().tolist()
+            layers = [dict(omega=h[0], tau=h[1], n_interface=h[2], n_nodes=sz[0],
+                           n_orders=sz[1], n_coef=sz[2]) for h, sz in zip(host, sizes)]
+            d_coef = coeffs.detach().double().contiguous()
+            plan.set_layers(layers, d_coef)
+            out = torch.empty(plan.table_shape, dtype=out_dtype, device=d_coef.device)
+            plan.solve(out)
+            _check(plan.status(), "vrte_solve_brdf status")
+            ctx.plan, ctx.layers, ctx.d_coef = plan, layers, d_coef
+            ctx.params_dtype, ctx.params_device = params.dtype, params.device
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            plan = ctx.plan
+            plan.set_layers(ctx.layers, ctx.d_coef)
+            g = plan.backward(grad_out.contiguous())
+            _check(plan.status(), "vrte_brdf_backward status")
+            n_layers = len(ctx.layers)
+            gp = g[:, :3].to(ctx.params_device, ctx.params_dtype)
+            gc = g[:, 3:].reshape(n_layers, -1, 6)
+            return gp, gc, None, None, None
+
+    return BRDFFunction
+
+
+def brdf_autograd(params, coeffs, sizes, plan, out_dtype=None):
+    """Differentiable BRDF table [n_layers, n_in, n_out, n_phi, 4, 4] of the layers described
+    by params [n_layers, 3] = (omega, tau0, n_interface) and coeffs (CUDA float64
+    [n_layers, n_coef_max, 6]); sizes: per layer (n_nodes, n_orders, n_coef); plan: a Plan
+    created with adjoint=True for these grids. Gradients flow to params and coeffs through
+    torch.autograd (vrte_brdf_backward)."""
+    import torch
+    if out_dtype is None:
+        out_dtype = torch.float64
+    return _autograd_function().apply(params, coeffs, plan, [tuple(int(v) for v in z) for z in sizes],
+                                      out_dtype)

@@ -13,50 +13,6 @@
 
 namespace vrte {
 
-struct cd {
-  double r, i;
-};
-__device__ inline cd cmul(cd a, cd b) { return cd{a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
-__device__ inline cd cdivv(cd a, cd b) {
-  double den = b.r * b.r + b.i * b.i;
-  return cd{(a.r * b.r + a.i * b.i) / den, (a.i * b.r - a.r * b.i) / den};
-}
-__device__ inline cd cexpv(cd z) {
-  double e = exp(z.r), sn, cs;
-  sincos(z.i, &sn, &cs);
-  return cd{e * cs, e * sn};
-}
-// exp(z) - 1, by its Taylor series for |z| < 1e-2
-__device__ inline cd cexpm1v(cd z) {
-  if (fabs(z.r) + fabs(z.i) < 1e-2) {
-    cd term = z, acc = z;
-    for (int k = 2; k < 10; ++k) {
-      term = cmul(term, z);
-      term.r /= k;
-      term.i /= k;
-      acc.r += term.r;
-      acc.i += term.i;
-    }
-    return acc;
-  }
-  cd e = cexpv(z);
-  return cd{e.r - 1.0, e.i};
-}
-// principal square root of a + ib without cancellation: with r = sqrt((|a| + |z|)/2),
-// sqrt(z) = (r, b/(2r)) for a >= 0 and (|b|/(2r), sign(b) r) for a < 0. (Forming
-// sqrt((|z| - a)/2) instead fails for pairs with a tiny imaginary part: |z| may round
-// below a.)
-__device__ inline cd csqrtv(double a, double b) {
-  if (b == 0.0) return a >= 0.0 ? cd{sqrt(a), 0.0} : cd{0.0, sqrt(-a)};
-  double r = sqrt(0.5 * (fabs(a) + hypot(a, b)));
-  if (a >= 0.0) return cd{r, 0.5 * b / r};
-  return cd{0.5 * fabs(b) / r, copysign(r, b)};
-}
-
-__device__ inline cd kappa_of(const double* lr, const double* li, int j) {
-  return csqrtv(lr[j], li[j]);
-}
-
 // ------------------------------------------------------------------ Y = E'X / kappa
 __global__ void k_pack_Y(int n, const double* EX, const double* lam_re, const double* lam_im,
                          double* Y, unsigned* status) {

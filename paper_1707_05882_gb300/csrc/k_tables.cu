@@ -46,14 +46,80 @@ void launch_gauss_nodes(int N, double* mu, double* w, unsigned* status, cudaStre
 }
 
 // Mueller block (a, b, c, d) of a diagonal Jones matrix diag(jp, js) on meridian frames:
-// [[a, b, 0, 0], [b, a, 0, 0], [0, 0, c, d], [0, 0, -d, c]].
-struct Blk4 { double a, b, c, d; };
+// [[a, b, 0, 0], [b, a, 0, 0], [0, 0, c, d], [0, 0, -d, c]]. T is double, or a dual number
+// carrying the derivative with respect to the interface index n.
+template <class T>
+struct Blk4 { T a, b, c, d; };
 
-__device__ inline Blk4 jones_block(double jpr, double jpi, double jsr, double jsi) {
-  double p2 = jpr * jpr + jpi * jpi, s2 = jsr * jsr + jsi * jsi;
+template <class T>
+__device__ inline Blk4<T> jones_block(T jpr, T jpi, T jsr, T jsi) {
+  T p2 = jpr * jpr + jpi * jpi, s2 = jsr * jsr + jsi * jsi;
   // z = jp * conj(js)
-  double zr = jpr * jsr + jpi * jsi, zi = jpi * jsr - jpr * jsi;
-  return Blk4{0.5 * (p2 + s2), 0.5 * (p2 - s2), zr, zi};
+  T zr = jpr * jsr + jpi * jsi, zi = jpi * jsr - jpr * jsi;
+  return Blk4<T>{0.5 * (p2 + s2), 0.5 * (p2 - s2), zr, zi};
+}
+
+template <class T>
+__device__ inline Blk4<T> scale_blk(Blk4<T> t, T f) {
+  return Blk4<T>{t.a * f, t.b * f, t.c * f, t.d * f};
+}
+
+// Interface data of table point tid for relative index nif (see k_interface); returns the
+// point's internal cosine and writes its block (reflection, transmission in or out).
+template <class T>
+__device__ inline T interface_point(int tid, int N, int n_in, T nif, bool iface,
+                                    const double* mu_nodes, const double* mu_in,
+                                    const double* mu_out, Blk4<T>& blk) {
+  const T zero = nif * 0.0;
+  if (tid < N) {
+    double c1 = mu_nodes[tid];
+    blk = Blk4<T>{zero, zero, zero, zero};
+    if (iface) {
+      // inside (index nif) towards outside (index 1)
+      T s2sq = nif * nif * (1.0 - c1 * c1);
+      if (val(s2sq) <= 1.0) {
+        T c2 = dsqrt(1.0 - s2sq);
+        T rs = (nif * c1 - c2) / (nif * c1 + c2);
+        T rp = (c1 - nif * c2) / (c1 + nif * c2);
+        blk = jones_block<T>(rp, zero, rs, zero);
+      } else {
+        // total internal reflection, c2 = i beta
+        T beta = dsqrt(s2sq - 1.0);
+        T A = nif * c1, B = beta;      // rs = (A - iB) / (A + iB)
+        T C = zero + c1, Dd = nif * beta;  // rp = (C - iD) / (C + iD)
+        T nA = A * A + B * B, nC = C * C + Dd * Dd;
+        T rsr = (A * A - B * B) / nA, rsi = -2.0 * A * B / nA;
+        T rpr = (C * C - Dd * Dd) / nC, rpi = -2.0 * C * Dd / nC;
+        blk = jones_block<T>(rpr, rpi, rsr, rsi);
+      }
+    }
+    return zero + c1;
+  }
+  if (tid < N + n_in) {
+    double me = mu_in[tid - N];
+    Blk4<T> t{zero + 1.0, zero, zero + 1.0, zero};
+    T mi = zero + me;
+    if (iface) {
+      mi = dsqrt(1.0 - (1.0 - me * me) / (nif * nif));
+      T ts = 2.0 * me / (me + nif * mi);
+      T tp = 2.0 * me / (nif * me + mi);
+      t = scale_blk<T>(jones_block<T>(tp, zero, ts, zero), nif);
+    }
+    blk = scale_blk<T>(t, zero + 1.0 / me);
+    return mi;
+  }
+  double me = mu_out[tid - N - n_in];
+  Blk4<T> t{zero + 1.0, zero, zero + 1.0, zero};
+  T mi = zero + me;
+  if (iface) {
+    mi = dsqrt(1.0 - (1.0 - me * me) / (nif * nif));
+    // inside -> outside amplitudes, radiance factor me / (nif^3 mi)
+    T ts = 2.0 * nif * mi / (nif * mi + me);
+    T tp = 2.0 * nif * mi / (mi + nif * me);
+    t = scale_blk<T>(jones_block<T>(tp, zero, ts, zero), me / (nif * nif * nif * mi));
+  }
+  blk = t;
+  return mi;
 }
 
 // Table points and interface matrices of one layer.
@@ -66,72 +132,34 @@ __global__ void k_interface(int N, int n_in, int n_out, double nif, const double
   int tid = blockIdx.x * blockDim.x + threadIdx.x;
   int total = N + n_in + n_out;
   if (tid >= total) return;
-  bool iface = nif > 1.0;
-  if (tid < N) {
-    double c1 = mu_nodes[tid];
-    pts[tid] = c1;
-    Blk4 r{0.0, 0.0, 0.0, 0.0};
-    if (iface) {
-      // inside (index nif) towards outside (index 1)
-      double s2sq = nif * nif * (1.0 - c1 * c1);
-      if (s2sq <= 1.0) {
-        double c2 = sqrt(1.0 - s2sq);
-        double rs = (nif * c1 - c2) / (nif * c1 + c2);
-        double rp = (c1 - nif * c2) / (c1 + nif * c2);
-        r = jones_block(rp, 0.0, rs, 0.0);
-      } else {
-        // total internal reflection, c2 = i beta
-        double beta = sqrt(s2sq - 1.0);
-        double A = nif * c1, B = beta;      // rs = (A - iB) / (A + iB)
-        double C = c1, Dd = nif * beta;     // rp = (C - iD) / (C + iD)
-        double nA = A * A + B * B, nC = C * C + Dd * Dd;
-        double rsr = (A * A - B * B) / nA, rsi = -2.0 * A * B / nA;
-        double rpr = (C * C - Dd * Dd) / nC, rpi = -2.0 * C * Dd / nC;
-        r = jones_block(rpr, rpi, rsr, rsi);
-      }
-    }
-    rtop4[4 * tid + 0] = r.a;
-    rtop4[4 * tid + 1] = r.b;
-    rtop4[4 * tid + 2] = r.c;
-    rtop4[4 * tid + 3] = r.d;
-  } else if (tid < N + n_in) {
-    int k = tid - N;
-    double me = mu_in[k];
-    Blk4 t{1.0, 0.0, 1.0, 0.0};
-    double mi = me;
-    if (iface) {
-      mi = sqrt(1.0 - (1.0 - me * me) / (nif * nif));
-      double ts = 2.0 * me / (me + nif * mi);
-      double tp = 2.0 * me / (nif * me + mi);
-      t = jones_block(tp, 0.0, ts, 0.0);
-      t.a *= nif; t.b *= nif; t.c *= nif; t.d *= nif;
-    }
-    pts[tid] = mi;
-    double inv = 1.0 / me;
-    min4[4 * k + 0] = t.a * inv;
-    min4[4 * k + 1] = t.b * inv;
-    min4[4 * k + 2] = t.c * inv;
-    min4[4 * k + 3] = t.d * inv;
-  } else {
-    int o = tid - N - n_in;
-    double me = mu_out[o];
-    Blk4 t{1.0, 0.0, 1.0, 0.0};
-    double mi = me;
-    if (iface) {
-      mi = sqrt(1.0 - (1.0 - me * me) / (nif * nif));
-      // inside -> outside amplitudes, radiance factor me / (nif^3 mi)
-      double ts = 2.0 * nif * mi / (nif * mi + me);
-      double tp = 2.0 * nif * mi / (mi + nif * me);
-      t = jones_block(tp, 0.0, ts, 0.0);
-      double f = me / (nif * nif * nif * mi);
-      t.a *= f; t.b *= f; t.c *= f; t.d *= f;
-    }
-    pts[tid] = mi;
-    mout4[4 * o + 0] = t.a;
-    mout4[4 * o + 1] = t.b;
-    mout4[4 * o + 2] = t.c;
-    mout4[4 * o + 3] = t.d;
-  }
+  Blk4<double> b;
+  pts[tid] = interface_point<double>(tid, N, n_in, nif, nif > 1.0, mu_nodes, mu_in, mu_out, b);
+  double* dst = tid < N ? rtop4 + 4 * tid
+                        : (tid < N + n_in ? min4 + 4 * (tid - N) : mout4 + 4 * (tid - N - n_in));
+  dst[0] = b.a;
+  dst[1] = b.b;
+  dst[2] = b.c;
+  dst[3] = b.d;
+}
+
+// Derivatives of the same data with respect to the interface index n (forward mode): dpts
+// (zero at the nodes), dmin4, dmout4, drtop4. All zero without an interface.
+__global__ void k_interface_dn(int N, int n_in, int n_out, double nif, const double* mu_nodes,
+                               const double* mu_in, const double* mu_out, double* dpts,
+                               double* dmin4, double* dmout4, double* drtop4) {
+  int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  int total = N + n_in + n_out;
+  if (tid >= total) return;
+  Blk4<dual> b;
+  dual mi = interface_point<dual>(tid, N, n_in, dual{nif, 1.0}, nif > 1.0, mu_nodes, mu_in,
+                                  mu_out, b);
+  dpts[tid] = mi.d;
+  double* dst = tid < N ? drtop4 + 4 * tid
+                        : (tid < N + n_in ? dmin4 + 4 * (tid - N) : dmout4 + 4 * (tid - N - n_in));
+  dst[0] = b.a.d;
+  dst[1] = b.b.d;
+  dst[2] = b.c.d;
+  dst[3] = b.d.d;
 }
 
 void launch_interface(int N, int n_in, int n_out, double nif, const double* mu_nodes,
@@ -142,61 +170,64 @@ void launch_interface(int N, int n_in, int n_out, double nif, const double* mu_n
                                                    pts, min4, mout4, rtop4);
 }
 
+void launch_interface_dn(int N, int n_in, int n_out, double nif, const double* mu_nodes,
+                         const double* mu_in, const double* mu_out, double* dpts, double* dmin4,
+                         double* dmout4, double* drtop4, cudaStream_t s) {
+  int total = N + n_in + n_out;
+  k_interface_dn<<<(total + 255) / 256, 256, 0, s>>>(N, n_in, n_out, nif, mu_nodes, mu_in, mu_out,
+                                                      dpts, dmin4, dmout4, drtop4);
+}
+
 // Wigner d^l_{m n}(x) seed at l0 = max(|m|, |n|):
 //   xi 2^-l0 sqrt((2 l0)! / (|m-n|! |m+n|!)) (1-x)^{|m-n|/2} (1+x)^{|m+n|/2},
 //   xi = 1 if n >= m else (-1)^(m-n), evaluated in logarithms.
-__device__ inline double wigner_seed(int m, int n, double x) {
+template <class T>
+__device__ inline T wigner_seed(int m, int n, T x) {
   int l0 = max(abs(m), abs(n));
   int a = abs(m - n), b = abs(m + n);
-  double lg = -l0 * 0.69314718055994530942 +
-              0.5 * (lgamma(2.0 * l0 + 1.0) - lgamma(a + 1.0) - lgamma(b + 1.0));
+  T lg = x * 0.0 + (-l0 * 0.69314718055994530942 +
+                    0.5 * (lgamma(2.0 * l0 + 1.0) - lgamma(a + 1.0) - lgamma(b + 1.0)));
   if (a > 0) {
-    double u = 1.0 - x;
-    if (u <= 0.0) return 0.0;
-    lg += 0.5 * a * log(u);
+    T u = 1.0 - x;
+    if (val(u) <= 0.0) return x * 0.0;
+    lg = lg + 0.5 * a * dlog(u);
   }
   if (b > 0) {
-    double u = 1.0 + x;
-    if (u <= 0.0) return 0.0;
-    lg += 0.5 * b * log(u);
+    T u = 1.0 + x;
+    if (val(u) <= 0.0) return x * 0.0;
+    lg = lg + 0.5 * b * dlog(u);
   }
-  double v = exp(lg);
+  T v = dexp(lg);
   if (n < m && ((m - n) & 1)) v = -v;
   return v;
 }
 
-// One thread per (order, point): p = d^l_{m0}, r = -(d^l_{m2} + d^l_{m,-2})/2,
-// t = -(d^l_{m2} - d^l_{m,-2})/2 for l = m..L-1 by the three-term recurrence
+// p = d^l_{m0}, r = -(d^l_{m2} + d^l_{m,-2})/2, t = -(d^l_{m2} - d^l_{m,-2})/2 at cosine x for
+// l = m..L-1 by the three-term recurrence
 //   l sqrt((l+1)^2-m^2) sqrt((l+1)^2-n^2) d^{l+1}
-//     = (2l+1)(l(l+1)x - m n) d^l - (l+1) sqrt(l^2-m^2) sqrt(l^2-n^2) d^{l-1}.
-// Layout: tab[(u * L + l) * P + k].
-__global__ void k_gsf(int L, int m0, int n_units, int P, const double* pts, double* pt, double* rt,
-                      double* tt) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  int u = blockIdx.y;
-  if (k >= P || u >= n_units) return;
-  int m = m0 + u;
-  double x = pts[k];
-  size_t base = (size_t)u * L * P + k;
+//     = (2l+1)(l(l+1)x - m n) d^l - (l+1) sqrt(l^2-m^2) sqrt(l^2-n^2) d^{l-1},
+// handed to put(l, p, r, t).
+template <class T, class PutP, class PutRT>
+__device__ inline void gsf_point(int m, int L, T x, PutP put_p, PutRT put_rt) {
   // family n = 0
   {
-    double dm1 = 0.0, d0 = 0.0;
+    T dm1 = x * 0.0, d0 = x * 0.0;
     int l0 = m;
     for (int l = l0; l < L; ++l) {
-      double d;
+      T d;
       if (l == l0) {
-        d = (m == 0) ? 1.0 : wigner_seed(m, 0, x);
+        d = (m == 0) ? x * 0.0 + 1.0 : wigner_seed<T>(m, 0, x);
       } else if (m == 0) {
         int lp = l - 1;  // Legendre
-        d = ((2 * lp + 1) * x * d0 - lp * dm1) / (lp + 1);
+        d = ((2 * lp + 1) * x * d0 - lp * dm1) / (double)(lp + 1);
       } else {
         int lp = l - 1;
         double den = lp * sqrt((double)(l * l - m * m)) * (double)l;
-        double num = (2 * lp + 1) * (lp * (double)l * x) * d0;
-        if (lp > l0) num -= l * sqrt((double)(lp * lp - m * m)) * (double)lp * dm1;
+        T num = (2 * lp + 1) * (lp * (double)l) * x * d0;
+        if (lp > l0) num = num - l * sqrt((double)(lp * lp - m * m)) * (double)lp * dm1;
         d = num / den;
       }
-      pt[base + (size_t)l * P] = d;
+      put_p(l, d, d);
       dm1 = d0;
       d0 = d;
     }
@@ -204,19 +235,19 @@ __global__ void k_gsf(int L, int m0, int n_units, int P, const double* pts, doub
   // families n = +2 and n = -2
   {
     int l0 = max(m, 2);
-    double ap = 0.0, bp = 0.0, am = 0.0, bm = 0.0;  // d^{l-1}, d^l for n = +2 and -2
+    T ap = x * 0.0, bp = x * 0.0, am = x * 0.0, bm = x * 0.0;  // d^{l-1}, d^l for n = +2 and -2
     for (int l = m; l < L; ++l) {
-      double dp2 = 0.0, dm2 = 0.0;
+      T dp2 = x * 0.0, dm2 = x * 0.0;
       if (l >= l0) {
         if (l == l0) {
-          dp2 = wigner_seed(m, 2, x);
-          dm2 = wigner_seed(m, -2, x);
+          dp2 = wigner_seed<T>(m, 2, x);
+          dm2 = wigner_seed<T>(m, -2, x);
         } else {
           int lp = l - 1;
           double s1 = sqrt((double)(l * l - m * m)) * sqrt((double)(l * l - 4));
           double den = lp * s1;
-          double c0 = (2 * lp + 1) * (lp * (double)l * x - 2.0 * m);
-          double c0m = (2 * lp + 1) * (lp * (double)l * x + 2.0 * m);
+          T c0 = (2 * lp + 1) * ((lp * (double)l) * x - 2.0 * m);
+          T c0m = (2 * lp + 1) * ((lp * (double)l) * x + 2.0 * m);
           double cpre = 0.0;
           if (lp > l0) cpre = l * sqrt((double)(lp * lp - m * m)) * sqrt((double)(lp * lp - 4));
           dp2 = (c0 * bp - cpre * ap) / den;
@@ -225,16 +256,65 @@ __global__ void k_gsf(int L, int m0, int n_units, int P, const double* pts, doub
         ap = bp; bp = dp2;
         am = bm; bm = dm2;
       }
-      rt[base + (size_t)l * P] = -0.5 * (dp2 + dm2);
-      tt[base + (size_t)l * P] = -0.5 * (dp2 - dm2);
+      put_rt(l, -0.5 * (dp2 + dm2), -0.5 * (dp2 - dm2));
     }
   }
+}
+
+// One thread per (order, point). Layout: tab[(u * L + l) * P + k].
+__global__ void k_gsf(int L, int m0, int n_units, int P, const double* pts, double* pt, double* rt,
+                      double* tt) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int u = blockIdx.y;
+  if (k >= P || u >= n_units) return;
+  size_t base = (size_t)u * L * P + k;
+  auto put_p = [&](int l, double d, double) { pt[base + (size_t)l * P] = d; };
+  auto put_rt = [&](int l, double r, double t) {
+    rt[base + (size_t)l * P] = r;
+    tt[base + (size_t)l * P] = t;
+  };
+  gsf_point<double>(m0 + u, L, pts[k], put_p, put_rt);
+}
+
+// Tangent tables for the interface-index derivative: the functions at x(n) in dual
+// arithmetic (x' = dpts = dmu_int/dn). Table 1 holds d/dn of the values at the incident
+// points and the values themselves elsewhere; table 2 the same for the outgoing points.
+// Since each assembled operator S+-(x, y) is bilinear in the tables at x and at y, an
+// assembly kernel run on table 1 (2) gives the n-derivative through the incident
+// (outgoing) cosines.
+__global__ void k_gsf_dn(int L, int m0, int n_units, int N, int n_in, int P, const double* pts,
+                         const double* dpts, double* p1, double* r1, double* t1, double* p2,
+                         double* r2, double* t2) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int u = blockIdx.y;
+  if (k >= P || u >= n_units) return;
+  const bool inc = k >= N && k < N + n_in, out = k >= N + n_in;
+  size_t base = (size_t)u * L * P + k;
+  auto put_p = [&](int l, dual d, dual) {
+    p1[base + (size_t)l * P] = inc ? d.d : d.v;
+    p2[base + (size_t)l * P] = out ? d.d : d.v;
+  };
+  auto put_rt = [&](int l, dual r, dual t) {
+    r1[base + (size_t)l * P] = inc ? r.d : r.v;
+    t1[base + (size_t)l * P] = inc ? t.d : t.v;
+    r2[base + (size_t)l * P] = out ? r.d : r.v;
+    t2[base + (size_t)l * P] = out ? t.d : t.v;
+  };
+  gsf_point<dual>(m0 + u, L, dual{pts[k], dpts[k]}, put_p, put_rt);
 }
 
 void launch_gsf_tables(const OrderBatch& b, const double* pts, double* p, double* r, double* t,
                        cudaStream_t s) {
   dim3 grid((b.P + 127) / 128, b.n_units);
   k_gsf<<<grid, 128, 0, s>>>(b.L, b.m0, b.n_units, b.P, pts, p, r, t);
+}
+
+void launch_gsf_tables_dn(const OrderBatch& b, const double* pts, const double* dpts, double* p1,
+                          double* r1, double* t1, double* p2, double* r2, double* t2,
+                          cudaStream_t s) {
+  dim3 grid((b.P + 127) / 128, b.n_units);
+  k_gsf_dn<<<grid, 128, 0, s>>>(b.L, b.m0, b.n_units, b.N, b.n_in, b.P, pts, dpts, p1, r1, t1, p2,
+                                r2, t2);
 }
 
 // wc[m][j] = (2 - delta_m0)/2 (-1)^m cos(m dphi_j), ws likewise with sin: the Fourier

@@ -24,7 +24,7 @@ using namespace vrte;
 namespace {
 enum Stage {
   ST_TABLES, ST_ASSEMBLE, ST_EIGEN, ST_MODES, ST_PARTICULAR, ST_BC_SOLVE, ST_RECON_OPS,
-  ST_RECON_HOM, ST_RECON_PART, ST_REFINE, ST_SYNTHESIS, kStages
+  ST_RECON_HOM, ST_RECON_PART, ST_REFINE, ST_SYNTHESIS, ST_ADJOINT, kStages
 };
 // mixed form: BF16 slices per FP64 operand (exact products, ~6e-16 relative per term) and
 // incident cosines per tensor-core synthesis block
@@ -40,7 +40,7 @@ constexpr double kRefineTol = 1e-7;
 const char* kStageNames[kStages] = {"tables",     "assemble",   "eigen",
                                     "modes_bc_inverse", "particular", "bc_solve",
                                     "recon_ops",  "recon_hom",  "recon_part",
-                                    "refine",     "synthesis"};
+                                    "refine",     "synthesis", "adjoint"};
 }  // namespace
 
 // Buffers of one order batch of one layer. A plan holds up to kMaxSlots of them so that
@@ -71,7 +71,11 @@ struct Work {
   double *Ln = nullptr, *RU = nullptr, *Rbp = nullptr, *Rbm = nullptr;
   int* rcount = nullptr;  // [flagged in this batch, flagged in this solve]
   int2* rlist = nullptr;
-  double* Isyn = nullptr;   // [M_max][n_in][n_out][16]
+  double* Isyn = nullptr;   // [M_max][n_in][n_out][16]; the adjoint keeps Ibar here
+  // adjoint (VRTE_FLAG_ADJOINT): per-unit workspace carved per layer, and per-layer data
+  double* bw = nullptr;
+  double *dpts = nullptr, *dmin4 = nullptr, *dmout4 = nullptr, *drtop4 = nullptr,
+         *acc = nullptr;
   double* g0tab = nullptr;  // [n_out][n_in] depth factors of the layer
   cudaStream_t stream = nullptr;  // own stream when the plan runs several slots
   cudaEvent_t done = nullptr;
@@ -184,6 +188,46 @@ void reset_stats(vrte_plan* p) {
 // buffers allocated by vrte_plan_create (kept by vrte_set_layer)
 constexpr size_t kPlanAllocs = 6;
 
+// Adjoint workspace of one order batch: consecutive [U][size] arrays for the layer's n.
+struct BwBufs {
+  double *Tb, *G0, *Qp, *Tdir, *SOI, *Cb, *nu, *SDb, *pb, *rb, *ysb, *wb, *ptmp, *rtmp, *Hb, *Ub,
+      *Utmp, *P1b, *P2b, *Kb, *E2, *F2, *Eb, *Fb, *Xc, *Yc, *Xic, *Zc, *Pmc, *Gtc, *Tc, *OmF,
+      *OmE, *Om, *kap, *D, *Ch, *zeta, *Dp2, *Ta, *Tz, *PsiT1, *PsiT2, *Ah, *SNN, *SNI, *SON,
+      *PYn, *PYi, *QNN, *QNI, *QON, *QOI, *mix[6];
+};
+
+// Doubles of the carved workspace (and the pointers when base is given).
+size_t bw_carve(double* base, size_t U, size_t n, size_t R, size_t Ro, size_t L, size_t P,
+                BwBufs* b) {
+  size_t off = 0;
+  auto take = [&](double** ptr, size_t per_unit) {
+    if (base) *ptr = base + off;
+    off += U * per_unit;
+  };
+  BwBufs d{};
+  BwBufs* t = b ? b : &d;
+  const size_t RoR = Ro * R, nR = n * R, nn = n * n, Ro2n = Ro * 2 * n, L4 = 4 * L;
+  take(&t->Tb, RoR); take(&t->G0, RoR); take(&t->Qp, RoR); take(&t->Tdir, RoR); take(&t->SOI, RoR);
+  take(&t->Cb, 2 * nR); take(&t->nu, 2 * nR); take(&t->SDb, 2 * nR);
+  take(&t->pb, nR); take(&t->rb, nR); take(&t->ysb, nR); take(&t->wb, nR); take(&t->ptmp, nR);
+  take(&t->rtmp, nR);
+  take(&t->Hb, Ro2n); take(&t->Ub, Ro2n); take(&t->Utmp, Ro2n);
+  take(&t->P1b, Ro * n); take(&t->P2b, Ro * n);
+  take(&t->Kb, 4 * nn); take(&t->E2, nn); take(&t->F2, nn); take(&t->Eb, nn); take(&t->Fb, nn);
+  take(&t->Xc, 2 * nn); take(&t->Yc, 2 * nn); take(&t->Xic, 2 * nn); take(&t->Zc, 2 * nn);
+  take(&t->Pmc, 2 * nn); take(&t->Gtc, 2 * nn); take(&t->Tc, 2 * nn);
+  take(&t->OmF, 2 * nn); take(&t->OmE, 2 * nn); take(&t->Om, 8 * nn); take(&t->kap, 2 * n);
+  take(&t->D, 4 * nR); take(&t->Ch, 4 * nR); take(&t->zeta, 4 * nR); take(&t->Dp2, 4 * nR);
+  take(&t->Ta, 2 * nR); take(&t->Tz, 2 * nR);
+  take(&t->PsiT1, 2 * Ro2n); take(&t->PsiT2, 2 * Ro2n); take(&t->Ah, 2 * Ro2n);
+  take(&t->SNN, 2 * nn); take(&t->SNI, 2 * nR); take(&t->SON, 2 * Ro * n);
+  take(&t->PYn, n * L4); take(&t->PYi, R * L4);
+  take(&t->QNN, 2 * n * L4); take(&t->QNI, 2 * n * L4); take(&t->QON, 2 * Ro * L4);
+  take(&t->QOI, Ro * L4);
+  for (int q = 0; q < 6; ++q) take(&t->mix[q], L * P);
+  return off;
+}
+
 }  // namespace
 
 extern "C" {
@@ -211,7 +255,7 @@ vrte_status vrte_plan_create(const vrte_plan_desc* d, vrte_plan** out) {
       d->n_orders_max > 1024 || d->n_coef_max < 1 || d->n_coef_max > 1024 ||
       d->n_layers_max < 1 || d->n_mu_in < 1 || d->n_mu_in > 16384 || d->n_mu_out < 1 ||
       d->n_mu_out > 16384 || d->n_phi < 1 || !d->mu_in || !d->mu_out || !d->phi ||
-      (d->flags & ~VRTE_FLAG_PROFILE) != 0)
+      (d->flags & ~(VRTE_FLAG_PROFILE | VRTE_FLAG_ADJOINT)) != 0)
     return VRTE_ERR_INVALID_ARG;
   if (d->precision != VRTE_FP64 && d->precision != VRTE_MIXED) return VRTE_ERR_INVALID_ARG;
   for (int i = 0; i < d->n_mu_in; ++i)
@@ -307,6 +351,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
                     1 + 5 * 4 * n * n + 3 * 2 * n + 1 + (tc_unit + 7) / 8 +
                     (mixed ? refine_scratch_doubles(1, p->n_in, p->n_out) + p->n_in : 0) +
                     n * kd + kd * 2 * n + 2 * kd * R;
+  const bool adjoint = (p->desc.flags & VRTE_FLAG_ADJOINT) != 0;
+  if (adjoint) per_unit += bw_carve(nullptr, 1, n, R, Ro, Lx, P, nullptr);
   size_t isyn = (size_t)Mx * p->n_in * p->n_out * 16;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
@@ -374,6 +420,11 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
     }
   }
   VRTE_ALLOC(Isyn, isyn)
+  if (adjoint) {
+    VRTE_ALLOC(bw, bw_carve(nullptr, U, n, R, Ro, Lx, P, nullptr))
+    VRTE_ALLOC(dpts, P) VRTE_ALLOC(dmin4, 4 * (size_t)p->n_in) VRTE_ALLOC(dmout4, 4 * (size_t)p->n_out)
+    VRTE_ALLOC(drtop4, 4 * (size_t)Nx) VRTE_ALLOC(acc, 3 + 6 * (size_t)p->desc.n_coef_max)
+  }
   if (nslots > 1) {
     if (!w->stream && cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess)
       return VRTE_ERR_CUDA;
@@ -386,6 +437,353 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
       cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess)
     return VRTE_ERR_CUDA;
   return VRTE_OK;
+}
+
+// One batch of U Fourier orders m0 .. m0+U-1 of layer `ly` through steps a0 (tables)
+// to a7 on stream s: the plan's precision when `mixed` follows it, else the FP64 form.
+// With `reconstruct` false the batch stops after the reconstruction operators (U+-, P1,
+// P2, Hhat and, in the FP64 form, the direct term in T1): what the adjoint needs.
+static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const double* coef,
+                          int m0, int U, bool mixed, bool reconstruct, cudaStream_t s) {
+  const int N = ly.n_nodes, n = 4 * N, L = ly.n_coef;
+  const int P = N + p->n_in + p->n_out;
+  const int R = 4 * p->n_in, Ro = 4 * p->n_out;
+  const int Meff = std::min(ly.n_orders, ly.n_coef);
+  // operator rows [U+ | U- | direct] and beams [s; d; direct] carry 4 L extra entries
+  // in the mixed form, where the direct term rides on the particular contraction
+  const int kdir = mixed ? 4 * L : 0;
+  const int ldU = 2 * n + (mixed ? p->kdir : 0);
+  OrderBatch ob{N, n, L, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef, p->d_status,
+                ldU, (long long)ldU * R};
+  p->last_n = n;
+  p->last_U = U;
+  p->last_ldU = ldU;
+  p->last_P = P;
+  p->last_Meff = Meff;
+  const long long nn = (long long)n * n, nR = (long long)n * R, Ron = (long long)Ro * n;
+  const long long sU_part = (long long)Ro * ldU;
+  const int gl = mixed ? 3 : 1;  // launches per contraction
+  // BF16 FLOPs issued per FP64 multiply-add by the sliced product
+  const double tcf = mixed ? 2.0 * kSlices * (kSlices + 1) / 2 : 0.0;
+  // boundary solve and reconstruction contractions: FP64 on the CUDA cores, or the
+  // sliced BF16 product on the tensor cores in the mixed form
+  auto gemm = [&](int M_, int N_, int K_, const double* A_, int lda_, long long sA_,
+                  const double* B_, int ldb_, long long sB_, double beta_, double* C_,
+                  int ldc_, long long sC_) {
+    if (mixed)
+      tc_gemm_store(M_, N_, K_, A_, lda_, sA_, B_, ldb_, sB_, beta_, C_, ldc_, sC_, U,
+                    kSlices, w->tcw, p->d_status, s);
+    else
+      dgemm_batched(M_, N_, K_, 1.0, A_, lda_, sA_, B_, ldb_, sB_, beta_, C_, ldc_, sC_, U,
+                    s);
+  };
+  const double dn = n, dR = R, dRo = Ro, dU = U;
+  double lsum = 0.0;  // sum over the batch of (L - m)
+  for (int u = 0; u < U; ++u) lsum += L - (m0 + u);
+  {
+    StageScope sc(p, ST_TABLES, s, 1, 30.0 * P * lsum, 24.0 * P * lsum);
+    launch_gsf_tables(ob, w->d_pts, w->gp, w->gr, w->gt, s);
+  }
+  {
+    StageScope sc(p, ST_ASSEMBLE, s, 2, 72.0 * N * N * lsum + 2.0 * dn * dn * dn * dU,
+                  8.0 * 3 * dn * dn * dU);
+    launch_assemble_EF(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, w->E, w->F, s);
+    dgemm_batched(n, n, n, 1.0, w->F, n, nn, w->E, n, nn, 0.0, w->FE, n, nn, U, s);
+  }
+  {
+    // algorithmic work counted: the nominal 25 n^3 of a real Schur decomposition with
+    // eigenvectors, the stage's dominant kernel. E'X, Y = E'X / kappa and the mode
+    // residual F'Y - X kappa (4 n^3 more; on the tensor cores in the mixed form) are
+    // not counted, so the stage's FP64 rate is that of the eigen-decomposition.
+    StageScope sc(p, ST_EIGEN, s, mixed ? 10 + 2 * (gl - 1) : 10, 25.0 * dn * dn * dn * dU,
+                  8.0 * 6 * dn * dn * dU);
+    batched_eigen(n, w->FE, w->Hs, w->Zs, w->Vs, w->X, w->lam_re, w->lam_im, w->bal, U,
+                  p->d_status, s);
+    gemm(n, n, n, w->E, n, nn, w->X, n, nn, 0.0, w->EX, n, nn);
+    launch_pack_Y(ob, w->EX, w->lam_re, w->lam_im, w->Y, s);
+    gemm(n, n, n, w->F, n, nn, w->Y, n, nn, 0.0, w->FY, n, nn);
+    // the FP64 form re-solves order 0 (diffusion mode) and any order with a poor mode
+    // residual in the 2n block form; the mixed form only catastrophic ones
+    const bool fp64 = p->desc.precision == VRTE_FP64;
+    eigen_block_fallback(n, m0, w->E, w->F, w->FY, w->X, w->Y, w->lam_re, w->lam_im,
+                         fp64 ? 1e-4 : 1e-1, fp64 ? 1 : 0, w->mode_res, w->mode_flag, w->Bm,
+                         w->Hb, w->Zb, w->Vb, w->Xb, w->kb_re, w->kb_im, w->balb, U,
+                         p->d_status, s);
+  }
+  {
+    StageScope sc(p, ST_MODES, s, 3, 16.0 * dn * dn * dn * dU, 8.0 * 12 * dn * dn * dU);
+    launch_build_K(ob, w->X, w->Y, w->lam_re, w->lam_im, w->d_rtop4, w->K, s);
+    batched_inverse(2 * n, w->K, w->Kinv, U, p->d_status, s);
+    batched_inverse(n, w->X, w->Xinv, U, p->d_status, s);
+  }
+  {
+    StageScope sc(p, ST_PARTICULAR, s, mixed ? 7 + 6 * gl : 9,
+                  72.0 * N * p->n_in * lsum + 8.0 * dn * dn * dR * dU,
+                  8.0 * 10 * dn * dR * dU);
+    sc.tensor_flops(tcf * (4.0 * dn + 2.0 * kdir) * dn * dR * dU);
+    if (mixed) {
+      // beam vectors as contractions over (l, component) on the tensor cores
+      launch_mixed_operators(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, w->d_min4,
+                             w->Ln, w->RU, w->Rbp, w->Rbm, s);
+      const long long sL = (long long)n * kdir, sB = (long long)kdir * R;
+      gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbp, R, sB, 0.0, w->Pb, R, nR);
+      gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbm, R, sB, 0.0, w->Rb, R, nR);
+    } else {
+      launch_assemble_beam(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_min4, w->Pb, w->Rb,
+                           s);
+    }
+    // near a resonance mu0 ~ 1/kappa_j the eigenbasis solve amplifies rounding by
+    // 1/(kappa_j^2 - mu0^-2) and the homogeneous part cancels it: the mixed form
+    // keeps FP64-level products here (7 slices, ~2e-15 per term)
+    gemm(n, R, n, w->F, n, nn, w->Pb, R, nR, 0.0, w->Wv, R, nR);
+    launch_particular_rhs(ob, w->Wv, w->Rb, w->d_pts, w->Wv, s);
+    gemm(n, R, n, w->Xinv, n, nn, w->Wv, R, nR, 0.0, w->Yv, R, nR);
+    launch_eigen_scale(ob, w->lam_re, w->lam_im, w->d_pts, w->Yv, s);
+    gemm(n, R, n, w->X, n, nn, w->Yv, R, nR, 0.0, w->SD, R, ob.sSD);
+    gemm(n, R, n, w->E, n, nn, w->SD, R, ob.sSD, 0.0, w->Es, R, nR);
+    launch_particular_sd(ob, w->Pb, w->Es, w->d_pts, w->SD, s);
+    launch_bc_rhs(ob, w->SD, nullptr, w->d_rtop4, w->d_pts, w->RHS, s);
+  }
+  {
+    StageScope sc(p, ST_BC_SOLVE, s, gl, 2.0 * 4 * dn * dn * dR * dU,
+                  8.0 * (4 * dn * dn + 4 * dn * dR) * dU);
+    sc.tensor_flops(tcf * 4.0 * dn * dn * dR * dU);
+    gemm(2 * n, R, 2 * n, w->Kinv, 2 * n, 4 * nn, w->RHS, R, 2 * nR, 0.0, w->C, R, 2 * nR);
+  }
+  {
+    StageScope sc(p, ST_RECON_OPS, s, mixed ? 3 + 3 * gl : 5,
+                  72.0 * N * p->n_out * lsum + 4.0 * dRo * dn * dn * dU +
+                      72.0 * p->n_in * p->n_out * lsum,
+                  8.0 * (6 * dRo * dn + dRo * dR) * dU);
+    sc.tensor_flops(tcf * 2.0 * dRo * dn * (dn + kdir) * dU);
+    if (mixed) {
+      // U+- = [M_out P(mu_o) B] x RU+-: the direct operator's columns are the left factor
+      launch_direct_operators(ob, w->gp, w->gr, w->gt, w->d_min4, w->d_mout4, w->Upm, w->SD,
+                              s);
+      gemm(Ro, 2 * n, kdir, w->Upm + 2 * n, ldU, sU_part, w->RU, 2 * n,
+           (long long)kdir * 2 * n, 0.0, w->Upm, ldU, sU_part);
+    } else {
+      launch_assemble_U(ob, w->gp, w->gr, w->gt, w->d_w_nodes, w->d_mout4, w->Upm, s);
+    }
+    gemm(Ro, n, n, w->Upm, ldU, sU_part, w->X, n, nn, 0.0, w->P1, n, Ron);
+    gemm(Ro, n, n, w->Upm + n, ldU, sU_part, w->Y, n, nn, 0.0, w->P2, n, Ron);
+    launch_build_Hhat(ob, w->P1, w->P2, w->lam_re, w->lam_im, w->d_pts, w->Hhat, s);
+    if (!mixed)
+      launch_assemble_direct(ob, w->gp, w->gr, w->gt, w->d_pts, w->d_min4, w->d_mout4, w->T1,
+                             s);
+  }
+  if (!reconstruct) return;
+  {
+    // homogeneous part: [4 n_out x 2n] x [2n x 4 n_in] per order. FP64: T1 holds the
+    // direct term and gains the homogeneous part; mixed: T1 is the homogeneous part and
+    // the direct term is the tail of the particular contraction
+    StageScope sc(p, ST_RECON_HOM, s, gl, 2.0 * dRo * dR * 2 * dn * dU,
+                  8.0 * (dRo * 2 * dn + 2 * dn * dR + 2 * dRo * dR) * dU);
+    sc.tensor_flops(tcf * dRo * dR * 2.0 * dn * dU);
+    gemm(Ro, R, 2 * n, w->Hhat, 2 * n, 2 * Ron, w->C, R, 2 * nR, mixed ? 0.0 : 1.0, w->T1, R,
+         (long long)Ro * R);
+  }
+  {
+    // particular (+ direct, mixed) part with the depth factor, into I^m
+    const double kp = 2.0 * dn + kdir;
+    StageScope sc(p, ST_RECON_PART, s, mixed ? (2 * n + kdir <= 1024 ? 1 : 2) * gl : 1,
+                  2.0 * dRo * dR * kp * dU, 8.0 * (dRo * kp + kp * dR + 2 * dRo * dR) * dU);
+    sc.tensor_flops(tcf * dRo * dR * kp * dU);
+    if (mixed) {
+      if (2 * n + kdir <= 1024) {
+        tc_gemm_part(ob, 2 * n + kdir, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1,
+                     w->g0tab, w->Isyn, kSlices, w->tcw, s);
+      } else {
+        // too deep for one exact accumulation: [U+ U-][s; d] into T1, then the direct part
+        tc_gemm_part_accum(ob, 2 * n, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1, w->g0tab,
+                           kSlices, w->tcw, s);
+        tc_gemm_part(ob, kdir, w->Upm + 2 * n, ldU, sU_part, w->SD + (size_t)2 * n * R,
+                     ob.sSD, w->T1, w->g0tab, w->Isyn, kSlices, w->tcw, s);
+      }
+    } else {
+      dgemm_part_epilogue(ob, w->Upm, w->SD, w->T1, w->g0tab, w->Isyn, s);
+    }
+  }
+  if (mixed) {
+    StageScope sc(p, ST_REFINE, s, 6, 0.0, 0.0);
+    refine_columns(ob, 2 * n + kdir, w->Kinv, w->RHS, w->C, w->Hhat, w->Upm, w->SD,
+                   w->g0tab, kSliceEps, kRefineTol, w->rscratch, w->rcount, w->rlist,
+                   U * p->n_in, w->Isyn, s);
+  }
+}
+
+// Adjoint of one order batch (forward factors of the batch already in the slot's buffers,
+// Ibar of the layer in w->Isyn): adds the batch's contributions to w->acc. Steps in the
+// order of the header of k_adjoint.cu: reconstruction and boundary reverse, particular
+// reverse, mode space, parameter chain.
+static void backward_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const double* coef,
+                           int m0, int U, cudaStream_t s) {
+  const int N = ly.n_nodes, n = 4 * N, L = ly.n_coef;
+  const int P = N + p->n_in + p->n_out;
+  const int R = 4 * p->n_in, Ro = 4 * p->n_out;
+  OrderBatch ob{N, n, L, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef, p->d_status,
+                2 * n, 2LL * n * R};
+  BwBufs b;
+  bw_carve(w->bw, U, n, R, Ro, L, P, &b);
+  const long long nn = (long long)n * n, nR = (long long)n * R, RoR = (long long)Ro * R,
+                  Ro2n = (long long)Ro * 2 * n, L4 = 4LL * L;
+  double* acc = w->acc;
+  const double* pts = w->d_pts;
+  const double* dpts = w->dpts;
+  auto gm = [&](bool tA, bool tB, int M_, int N_, int K_, double al, const double* A_, int lda,
+                long long sA, const double* B_, int ldb, long long sB, double be, double* C_,
+                int ldc, long long sC) {
+    dgemm_batched_t(tA, tB, M_, N_, K_, al, A_, lda, sA, B_, ldb, sB, be, C_, ldc, sC, U, s);
+  };
+  const double dU = U, dn = n, dR = R, dRo = Ro;
+  StageScope sc(p, ST_ADJOINT, s, 120,
+                2.0 * dU * (6 * dRo * dR * dn + 8 * dn * dn * dR + 24 * dn * dn * dR + 16 * dn * dn * dn),
+                8.0 * dU * (6 * dRo * dR + 20 * dn * dR));
+  // ---- reconstruction reverse
+  bw_tb(ob, w->Isyn, w->g0tab, b.Tb, b.G0, s);
+  gm(false, false, Ro, R, 2 * n, 1.0, w->Upm, 2 * n, Ro2n, w->SD, R, 2 * nR, 0.0, b.Qp, R, RoR);
+  bw_g0(ob, b.Tb, b.Qp, w->T1, pts, dpts, acc, s);
+  gm(true, false, 2 * n, R, Ro, 1.0, w->Hhat, 2 * n, Ro2n, b.Tb, R, RoR, 0.0, b.Cb, R, 2 * nR);
+  gm(false, true, Ro, 2 * n, R, 1.0, b.Tb, R, RoR, w->C, R, 2 * nR, 0.0, b.Hb, 2 * n, Ro2n);
+  gm(false, true, Ro, 2 * n, R, 1.0, b.G0, R, RoR, w->SD, R, 2 * nR, 0.0, b.Ub, 2 * n, Ro2n);
+  gm(true, false, 2 * n, R, Ro, 1.0, w->Upm, 2 * n, Ro2n, b.G0, R, RoR, 0.0, b.SDb, R, 2 * nR);
+  // ---- boundary system: nu = K^-T Cbar, Kbar = -nu C^T
+  gm(true, false, 2 * n, R, 2 * n, 1.0, w->Kinv, 2 * n, 4 * nn, b.Cb, R, 2 * nR, 0.0, b.nu, R,
+     2 * nR);
+  gm(false, true, 2 * n, 2 * n, R, -1.0, b.nu, R, 2 * nR, w->C, R, 2 * nR, 0.0, b.Kb, 2 * n, 4 * nn);
+  bw_kappa(ob, w->lam_re, w->lam_im, b.kap, s);
+  bw_hhat(ob, b.Hb, w->P1, w->P2, b.kap, pts, dpts, b.P1b, b.P2b, acc, s);
+  gm(false, true, Ro, n, n, 1.0, b.P1b, n, (long long)Ro * n, w->X, n, nn, 1.0, b.Ub, 2 * n, Ro2n);
+  gm(false, true, Ro, n, n, 1.0, b.P2b, n, (long long)Ro * n, w->Y, n, nn, 1.0, b.Ub + n, 2 * n,
+     Ro2n);
+  bw_K(ob, b.Kb, w->X, w->Y, b.kap, w->d_rtop4, w->drtop4, acc, s);
+  bw_rhs(ob, b.nu, w->SD, b.SDb, w->d_rtop4, w->drtop4, pts, dpts, acc, s);
+  // ---- particular solution reverse (E', F', X, lambda fixed)
+  bw_part_d(ob, w->SD, b.SDb, pts, dpts, b.pb, acc, s);
+  gm(true, false, n, R, n, -1.0, w->E, n, nn, b.pb, R, nR, 1.0, b.SDb, R, 2 * nR);
+  gm(true, false, n, R, n, 1.0, w->X, n, nn, b.SDb, R, 2 * nR, 0.0, b.ysb, R, nR);
+  bw_scale(ob, w->lam_re, w->lam_im, w->Yv, b.ysb, pts, dpts, acc, s);
+  gm(true, false, n, R, n, 1.0, w->Xinv, n, nn, b.ysb, R, nR, 0.0, b.wb, R, nR);
+  gm(true, false, n, R, n, 1.0, w->F, n, nn, b.wb, R, nR, 1.0, b.pb, R, nR);
+  bw_part_w(ob, b.wb, w->Rb, pts, dpts, b.rb, acc, s);
+  // ---- mode space: dL/dF', dL/dE' through the adjoint two-point problem
+  bw_cplx_cols(ob, w->X, w->Y, b.kap, w->d_rtop4, b.Xc, b.Yc, b.Pmc, b.Gtc, s);
+  bw_cplx_rows(n, n, n, nn, w->Xinv, b.kap, b.Xic, U, s);
+  gm(false, false, n, n, n, 1.0, b.Xic, n, 2 * nn, w->F, n, nn, 0.0, b.Zc, n, 2 * nn);
+  gm(false, false, n, n, n, 1.0, b.Xic + nn, n, 2 * nn, w->F, n, nn, 0.0, b.Zc + nn, n, 2 * nn);
+  bw_rowdiv(n, n, b.kap, b.Zc, U, s);
+  // D = [-phi-^T nu_bottom; (D phi- - R phi+)^T nu_top] (adjoint mode amplitudes)
+  for (int q = 0; q < 2; ++q) {
+    gm(true, false, n, R, n, -1.0, b.Pmc + q * nn, n, 2 * nn, b.nu + nR, R, 2 * nR, 0.0,
+       b.D + q * 2 * nR, R, 4 * nR);
+    gm(true, false, n, R, n, 1.0, b.Gtc + q * nn, n, 2 * nn, b.nu, R, 2 * nR, 0.0,
+       b.D + q * 2 * nR + nR, R, 4 * nR);
+  }
+  bw_cplx_rows(n, 2 * n, R, 2 * nR, w->C, b.kap, b.Ch, U, s);
+  for (int q = 0; q < 2; ++q) {
+    gm(false, false, n, R, n, 1.0, b.Xic + q * nn, n, 2 * nn, w->SD, R, 2 * nR, 0.0, b.Ta + q * nR,
+       R, 2 * nR);
+    gm(false, false, n, R, n, 1.0, b.Zc + q * nn, n, 2 * nn, w->SD + nR, R, 2 * nR, 0.0,
+       b.Tz + q * nR, R, 2 * nR);
+  }
+  bw_zeta(n, R, b.Ta, b.Tz, b.zeta, U, s);
+  bw_psi(ob, w->P1, w->P2, b.kap, pts, b.PsiT1, b.PsiT2, s);
+  for (int q = 0; q < 2; ++q) {
+    // D' = D - Psi2 Tb
+    gm(true, false, 2 * n, R, Ro, -1.0, b.PsiT2 + q * Ro2n, 2 * n, 2 * Ro2n, b.Tb, R, RoR, 1.0,
+       b.D + q * 2 * nR, R, 4 * nR);
+    // Ahat = (Tb Ch^T) o gf + G0 zeta^T
+    gm(false, true, Ro, 2 * n, R, 1.0, b.Tb, R, RoR, b.Ch + q * 2 * nR, R, 4 * nR, 0.0,
+       b.Ah + q * Ro2n, 2 * n, 2 * Ro2n);
+  }
+  bw_gf(ob, b.kap, pts, b.Ah, s);
+  for (int q = 0; q < 2; ++q)
+    gm(false, true, Ro, 2 * n, R, 1.0, b.G0, R, RoR, b.zeta + q * 2 * nR, R, 4 * nR, 1.0,
+       b.Ah + q * Ro2n, 2 * n, 2 * Ro2n);
+  // complex products C (+)= A op(B): re = Ar Br - Ai Bi, im = Ar Bi + Ai Br
+  auto zgm = [&](bool tA, bool tB, int M_, int N_, int K_, const double* A_, int lda, long long pA,
+                 long long sA, const double* B_, int ldb, long long pB, long long sB, double be,
+                 double* C_, int ldc, long long pC, long long sC) {
+    gm(tA, tB, M_, N_, K_, 1.0, A_, lda, sA, B_, ldb, sB, be, C_, ldc, sC);
+    gm(tA, tB, M_, N_, K_, -1.0, A_ + pA, lda, sA, B_ + pB, ldb, sB, 1.0, C_, ldc, sC);
+    gm(tA, tB, M_, N_, K_, 1.0, A_, lda, sA, B_ + pB, ldb, sB, be, C_ + pC, ldc, sC);
+    gm(tA, tB, M_, N_, K_, 1.0, A_ + pA, lda, sA, B_, ldb, sB, 1.0, C_ + pC, ldc, sC);
+  };
+  // Omega = I1 o (D' Ch^T) + (D' o I2) zeta^T + Psi1 Ahat
+  zgm(false, true, 2 * n, 2 * n, R, b.D, R, 2 * nR, 4 * nR, b.Ch, R, 2 * nR, 4 * nR, 0.0, b.Om,
+      2 * n, 4 * nn, 8 * nn);
+  bw_i1(n, ly.tau, b.kap, b.Om, U, s);
+  bw_i2(ob, b.kap, pts, b.D, b.Dp2, s);
+  zgm(false, true, 2 * n, 2 * n, R, b.Dp2, R, 2 * nR, 4 * nR, b.zeta, R, 2 * nR, 4 * nR, 1.0, b.Om,
+      2 * n, 4 * nn, 8 * nn);
+  zgm(true, false, 2 * n, 2 * n, Ro, b.PsiT1, 2 * n, Ro2n, 2 * Ro2n, b.Ah, 2 * n, Ro2n, 2 * Ro2n,
+      1.0, b.Om, 2 * n, 4 * nn, 8 * nn);
+  bw_omblk(n, b.Om, b.OmF, b.OmE, U, s);
+  // F'bar = Re(Xc^-T OmF Yc^T) / 2, E'bar = Re(Zc^T OmE Xc^T) / 2 (Zc = Yc^-1)
+  zgm(false, true, n, n, n, b.OmF, n, nn, 2 * nn, b.Yc, n, nn, 2 * nn, 0.0, b.Tc, n, nn, 2 * nn);
+  gm(true, false, n, n, n, 0.5, b.Xic, n, 2 * nn, b.Tc, n, 2 * nn, 0.0, b.Fb, n, nn);
+  gm(true, false, n, n, n, -0.5, b.Xic + nn, n, 2 * nn, b.Tc + nn, n, 2 * nn, 1.0, b.Fb, n, nn);
+  zgm(false, true, n, n, n, b.OmE, n, nn, 2 * nn, b.Xc, n, nn, 2 * nn, 0.0, b.Tc, n, nn, 2 * nn);
+  gm(true, false, n, n, n, 0.5, b.Zc, n, 2 * nn, b.Tc, n, 2 * nn, 0.0, b.Eb, n, nn);
+  gm(true, false, n, n, n, -0.5, b.Zc + nn, n, 2 * nn, b.Tc + nn, n, 2 * nn, 1.0, b.Eb, n, nn);
+  // ---- parameter chain: omega (every operator is linear in omega at fixed tables)
+  OrderBatch o2 = ob, o2pi = ob, o4 = ob;
+  o2.omega = 2.0;
+  o2pi.omega = 2.0 * kPi;
+  o4.omega = 4.0;
+  launch_assemble_EF(o2, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, b.E2, b.F2, s);
+  bw_dot_ef(n, N, b.Eb, b.E2, b.Fb, b.F2, w->d_mu_nodes, acc, U, s);
+  launch_assemble_beam(o2pi, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_min4, b.ptmp, b.rtmp, s);
+  bw_dot(nR, b.pb, nR, b.ptmp, nR, 1.0 / (2.0 * kPi), acc, U, s);
+  bw_dot(nR, b.rb, nR, b.rtmp, nR, 1.0 / (2.0 * kPi), acc, U, s);
+  launch_assemble_U(o4, w->gp, w->gr, w->gt, w->d_w_nodes, w->d_mout4, b.Utmp, s);
+  bw_dot(Ro2n, b.Ub, Ro2n, b.Utmp, Ro2n, 0.25, acc, U, s);
+  launch_assemble_direct(o2pi, w->gp, w->gr, w->gt, pts, w->d_min4, w->d_mout4, b.Tdir, s);
+  bw_dot(RoR, b.Tb, RoR, b.Tdir, RoR, 1.0 / (2.0 * kPi), acc, U, s);
+  // ---- interface index: tangent operators (tables at the incident / outgoing points and the
+  // transmission blocks replaced by their n-derivatives)
+  if (ly.n_interface > 1.0) {
+    double** mx = b.mix;
+    launch_gsf_tables_dn(ob, pts, dpts, mx[0], mx[1], mx[2], mx[3], mx[4], mx[5], s);
+    launch_assemble_beam(ob, mx[0], mx[1], mx[2], w->d_mu_nodes, w->d_min4, b.ptmp, b.rtmp, s);
+    bw_dot(nR, b.pb, nR, b.ptmp, nR, 1.0, acc + 2, U, s);
+    bw_dot(nR, b.rb, nR, b.rtmp, nR, 1.0, acc + 2, U, s);
+    launch_assemble_beam(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->dmin4, b.ptmp, b.rtmp, s);
+    bw_dot(nR, b.pb, nR, b.ptmp, nR, 1.0, acc + 2, U, s);
+    bw_dot(nR, b.rb, nR, b.rtmp, nR, 1.0, acc + 2, U, s);
+    launch_assemble_U(ob, mx[3], mx[4], mx[5], w->d_w_nodes, w->d_mout4, b.Utmp, s);
+    bw_dot(Ro2n, b.Ub, Ro2n, b.Utmp, Ro2n, 1.0, acc + 2, U, s);
+    launch_assemble_U(ob, w->gp, w->gr, w->gt, w->d_w_nodes, w->dmout4, b.Utmp, s);
+    bw_dot(Ro2n, b.Ub, Ro2n, b.Utmp, Ro2n, 1.0, acc + 2, U, s);
+    launch_assemble_direct(ob, mx[0], mx[1], mx[2], pts, w->d_min4, w->d_mout4, b.Tdir, s);
+    bw_dot(RoR, b.Tb, RoR, b.Tdir, RoR, 1.0, acc + 2, U, s);
+    launch_assemble_direct(ob, mx[3], mx[4], mx[5], pts, w->d_min4, w->d_mout4, b.Tdir, s);
+    bw_dot(RoR, b.Tb, RoR, b.Tdir, RoR, 1.0, acc + 2, U, s);
+    launch_assemble_direct(ob, w->gp, w->gr, w->gt, pts, w->dmin4, w->d_mout4, b.Tdir, s);
+    bw_dot(RoR, b.Tb, RoR, b.Tdir, RoR, 1.0, acc + 2, U, s);
+    launch_assemble_direct(ob, w->gp, w->gr, w->gt, pts, w->d_min4, w->dmout4, b.Tdir, s);
+    bw_dot(RoR, b.Tb, RoR, b.Tdir, RoR, 1.0, acc + 2, U, s);
+  }
+  // ---- expansion coefficients: Sbar of the four point families, contracted with the tables
+  bw_sbar_nn(ob, b.Eb, b.Fb, w->d_mu_nodes, w->d_w_nodes, b.SNN, s);
+  bw_sbar_ni(ob, b.pb, b.rb, w->d_mu_nodes, w->d_min4, b.SNI, s);
+  bw_sbar_on(ob, b.Ub, w->d_w_nodes, w->d_mout4, b.SON, s);
+  bw_sbar_oi(ob, b.G0, w->d_min4, w->d_mout4, b.SOI, s);
+  bw_pstack(ob, 0, N, w->gp, w->gr, w->gt, b.PYn, s);
+  bw_pstack(ob, N, p->n_in, w->gp, w->gr, w->gt, b.PYi, s);
+  gm(false, false, 2 * n, 4 * L, n, 1.0, b.SNN, n, 2 * nn, b.PYn, 4 * L, n * L4, 0.0, b.QNN,
+     4 * L, 2 * n * L4);
+  gm(false, false, 2 * n, 4 * L, R, 1.0, b.SNI, R, 2 * nR, b.PYi, 4 * L, R * L4, 0.0, b.QNI,
+     4 * L, 2 * n * L4);
+  gm(false, false, 2 * Ro, 4 * L, n, 1.0, b.SON, n, 2LL * Ro * n, b.PYn, 4 * L, n * L4, 0.0,
+     b.QON, 4 * L, 2 * Ro * L4);
+  gm(false, false, Ro, 4 * L, R, 1.0, b.SOI, R, RoR, b.PYi, 4 * L, R * L4, 0.0, b.QOI, 4 * L,
+     Ro * L4);
+  bw_bbar(ob, 0, N, b.QNN, b.QNN + n * L4, 2 * n * L4, w->gp, w->gr, w->gt, acc, s);
+  bw_bbar(ob, 0, N, b.QNI, b.QNI + n * L4, 2 * n * L4, w->gp, w->gr, w->gt, acc, s);
+  bw_bbar(ob, N + p->n_in, p->n_out, b.QON, b.QON + Ro * L4, 2 * Ro * L4, w->gp, w->gr, w->gt,
+          acc, s);
+  bw_bbar(ob, N + p->n_in, p->n_out, nullptr, b.QOI, Ro * L4, w->gp, w->gr, w->gt, acc, s);
 }
 
 static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, int out_dtype,
@@ -423,170 +821,9 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
                        p->d_mu_out, w->d_pts, w->d_min4, w->d_mout4, w->d_rtop4, s);
       launch_depth_table(N, p->n_in, p->n_out, ly.tau, w->d_pts, w->g0tab, s);
     }
-    for (int m0 = 0; m0 < Meff; m0 += p->chunk) {
-      const int U = std::min(p->chunk, Meff - m0);
-      const bool mixed = p->desc.precision == VRTE_MIXED;
-      // operator rows [U+ | U- | direct] and beams [s; d; direct] carry 4 L extra entries
-      // in the mixed form, where the direct term rides on the particular contraction
-      const int kdir = mixed ? 4 * L : 0;
-      const int ldU = 2 * n + (mixed ? p->kdir : 0);
-      OrderBatch ob{N, n, L, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef, p->d_status,
-                    ldU, (long long)ldU * R};
-      p->last_n = n;
-      p->last_U = U;
-      p->last_ldU = ldU;
-      p->last_P = P;
-      p->last_Meff = Meff;
-      const long long nn = (long long)n * n, nR = (long long)n * R, Ron = (long long)Ro * n;
-      const long long sU_part = (long long)Ro * ldU;
-      const int gl = mixed ? 3 : 1;  // launches per contraction
-      // BF16 FLOPs issued per FP64 multiply-add by the sliced product
-      const double tcf = mixed ? 2.0 * kSlices * (kSlices + 1) / 2 : 0.0;
-      // boundary solve and reconstruction contractions: FP64 on the CUDA cores, or the
-      // sliced BF16 product on the tensor cores in the mixed form
-      auto gemm = [&](int M_, int N_, int K_, const double* A_, int lda_, long long sA_,
-                      const double* B_, int ldb_, long long sB_, double beta_, double* C_,
-                      int ldc_, long long sC_) {
-        if (mixed)
-          tc_gemm_store(M_, N_, K_, A_, lda_, sA_, B_, ldb_, sB_, beta_, C_, ldc_, sC_, U,
-                        kSlices, w->tcw, p->d_status, s);
-        else
-          dgemm_batched(M_, N_, K_, 1.0, A_, lda_, sA_, B_, ldb_, sB_, beta_, C_, ldc_, sC_, U,
-                        s);
-      };
-      const double dn = n, dR = R, dRo = Ro, dU = U;
-      double lsum = 0.0;  // sum over the batch of (L - m)
-      for (int u = 0; u < U; ++u) lsum += L - (m0 + u);
-      {
-        StageScope sc(p, ST_TABLES, s, 1, 30.0 * P * lsum, 24.0 * P * lsum);
-        launch_gsf_tables(ob, w->d_pts, w->gp, w->gr, w->gt, s);
-      }
-      {
-        StageScope sc(p, ST_ASSEMBLE, s, 2, 72.0 * N * N * lsum + 2.0 * dn * dn * dn * dU,
-                      8.0 * 3 * dn * dn * dU);
-        launch_assemble_EF(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, w->E, w->F, s);
-        dgemm_batched(n, n, n, 1.0, w->F, n, nn, w->E, n, nn, 0.0, w->FE, n, nn, U, s);
-      }
-      {
-        // algorithmic work counted: the nominal 25 n^3 of a real Schur decomposition with
-        // eigenvectors, the stage's dominant kernel. E'X, Y = E'X / kappa and the mode
-        // residual F'Y - X kappa (4 n^3 more; on the tensor cores in the mixed form) are
-        // not counted, so the stage's FP64 rate is that of the eigen-decomposition.
-        StageScope sc(p, ST_EIGEN, s, mixed ? 10 + 2 * (gl - 1) : 10, 25.0 * dn * dn * dn * dU,
-                      8.0 * 6 * dn * dn * dU);
-        batched_eigen(n, w->FE, w->Hs, w->Zs, w->Vs, w->X, w->lam_re, w->lam_im, w->bal, U,
-                      p->d_status, s);
-        gemm(n, n, n, w->E, n, nn, w->X, n, nn, 0.0, w->EX, n, nn);
-        launch_pack_Y(ob, w->EX, w->lam_re, w->lam_im, w->Y, s);
-        gemm(n, n, n, w->F, n, nn, w->Y, n, nn, 0.0, w->FY, n, nn);
-        // the FP64 form re-solves order 0 (diffusion mode) and any order with a poor mode
-        // residual in the 2n block form; the mixed form only catastrophic ones
-        const bool fp64 = p->desc.precision == VRTE_FP64;
-        eigen_block_fallback(n, m0, w->E, w->F, w->FY, w->X, w->Y, w->lam_re, w->lam_im,
-                             fp64 ? 1e-4 : 1e-1, fp64 ? 1 : 0, w->mode_res, w->mode_flag, w->Bm,
-                             w->Hb, w->Zb, w->Vb, w->Xb, w->kb_re, w->kb_im, w->balb, U,
-                             p->d_status, s);
-      }
-      {
-        StageScope sc(p, ST_MODES, s, 3, 16.0 * dn * dn * dn * dU, 8.0 * 12 * dn * dn * dU);
-        launch_build_K(ob, w->X, w->Y, w->lam_re, w->lam_im, w->d_rtop4, w->K, s);
-        batched_inverse(2 * n, w->K, w->Kinv, U, p->d_status, s);
-        batched_inverse(n, w->X, w->Xinv, U, p->d_status, s);
-      }
-      {
-        StageScope sc(p, ST_PARTICULAR, s, mixed ? 7 + 6 * gl : 9,
-                      72.0 * N * p->n_in * lsum + 8.0 * dn * dn * dR * dU,
-                      8.0 * 10 * dn * dR * dU);
-        sc.tensor_flops(tcf * (4.0 * dn + 2.0 * kdir) * dn * dR * dU);
-        if (mixed) {
-          // beam vectors as contractions over (l, component) on the tensor cores
-          launch_mixed_operators(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, w->d_min4,
-                                 w->Ln, w->RU, w->Rbp, w->Rbm, s);
-          const long long sL = (long long)n * kdir, sB = (long long)kdir * R;
-          gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbp, R, sB, 0.0, w->Pb, R, nR);
-          gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbm, R, sB, 0.0, w->Rb, R, nR);
-        } else {
-          launch_assemble_beam(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_min4, w->Pb, w->Rb,
-                               s);
-        }
-        // near a resonance mu0 ~ 1/kappa_j the eigenbasis solve amplifies rounding by
-        // 1/(kappa_j^2 - mu0^-2) and the homogeneous part cancels it: the mixed form
-        // keeps FP64-level products here (7 slices, ~2e-15 per term)
-        gemm(n, R, n, w->F, n, nn, w->Pb, R, nR, 0.0, w->Wv, R, nR);
-        launch_particular_rhs(ob, w->Wv, w->Rb, w->d_pts, w->Wv, s);
-        gemm(n, R, n, w->Xinv, n, nn, w->Wv, R, nR, 0.0, w->Yv, R, nR);
-        launch_eigen_scale(ob, w->lam_re, w->lam_im, w->d_pts, w->Yv, s);
-        gemm(n, R, n, w->X, n, nn, w->Yv, R, nR, 0.0, w->SD, R, ob.sSD);
-        gemm(n, R, n, w->E, n, nn, w->SD, R, ob.sSD, 0.0, w->Es, R, nR);
-        launch_particular_sd(ob, w->Pb, w->Es, w->d_pts, w->SD, s);
-        launch_bc_rhs(ob, w->SD, nullptr, w->d_rtop4, w->d_pts, w->RHS, s);
-      }
-      {
-        StageScope sc(p, ST_BC_SOLVE, s, gl, 2.0 * 4 * dn * dn * dR * dU,
-                      8.0 * (4 * dn * dn + 4 * dn * dR) * dU);
-        sc.tensor_flops(tcf * 4.0 * dn * dn * dR * dU);
-        gemm(2 * n, R, 2 * n, w->Kinv, 2 * n, 4 * nn, w->RHS, R, 2 * nR, 0.0, w->C, R, 2 * nR);
-      }
-      {
-        StageScope sc(p, ST_RECON_OPS, s, mixed ? 3 + 3 * gl : 5,
-                      72.0 * N * p->n_out * lsum + 4.0 * dRo * dn * dn * dU +
-                          72.0 * p->n_in * p->n_out * lsum,
-                      8.0 * (6 * dRo * dn + dRo * dR) * dU);
-        sc.tensor_flops(tcf * 2.0 * dRo * dn * (dn + kdir) * dU);
-        if (mixed) {
-          // U+- = [M_out P(mu_o) B] x RU+-: the direct operator's columns are the left factor
-          launch_direct_operators(ob, w->gp, w->gr, w->gt, w->d_min4, w->d_mout4, w->Upm, w->SD,
-                                  s);
-          gemm(Ro, 2 * n, kdir, w->Upm + 2 * n, ldU, sU_part, w->RU, 2 * n,
-               (long long)kdir * 2 * n, 0.0, w->Upm, ldU, sU_part);
-        } else {
-          launch_assemble_U(ob, w->gp, w->gr, w->gt, w->d_w_nodes, w->d_mout4, w->Upm, s);
-        }
-        gemm(Ro, n, n, w->Upm, ldU, sU_part, w->X, n, nn, 0.0, w->P1, n, Ron);
-        gemm(Ro, n, n, w->Upm + n, ldU, sU_part, w->Y, n, nn, 0.0, w->P2, n, Ron);
-        launch_build_Hhat(ob, w->P1, w->P2, w->lam_re, w->lam_im, w->d_pts, w->Hhat, s);
-        if (!mixed)
-          launch_assemble_direct(ob, w->gp, w->gr, w->gt, w->d_pts, w->d_min4, w->d_mout4, w->T1,
-                                 s);
-      }
-      {
-        // homogeneous part: [4 n_out x 2n] x [2n x 4 n_in] per order. FP64: T1 holds the
-        // direct term and gains the homogeneous part; mixed: T1 is the homogeneous part and
-        // the direct term is the tail of the particular contraction
-        StageScope sc(p, ST_RECON_HOM, s, gl, 2.0 * dRo * dR * 2 * dn * dU,
-                      8.0 * (dRo * 2 * dn + 2 * dn * dR + 2 * dRo * dR) * dU);
-        sc.tensor_flops(tcf * dRo * dR * 2.0 * dn * dU);
-        gemm(Ro, R, 2 * n, w->Hhat, 2 * n, 2 * Ron, w->C, R, 2 * nR, mixed ? 0.0 : 1.0, w->T1, R,
-             (long long)Ro * R);
-      }
-      {
-        // particular (+ direct, mixed) part with the depth factor, into I^m
-        const double kp = 2.0 * dn + kdir;
-        StageScope sc(p, ST_RECON_PART, s, mixed ? (2 * n + kdir <= 1024 ? 1 : 2) * gl : 1,
-                      2.0 * dRo * dR * kp * dU, 8.0 * (dRo * kp + kp * dR + 2 * dRo * dR) * dU);
-        sc.tensor_flops(tcf * dRo * dR * kp * dU);
-        if (mixed) {
-          if (2 * n + kdir <= 1024) {
-            tc_gemm_part(ob, 2 * n + kdir, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1,
-                         w->g0tab, w->Isyn, kSlices, w->tcw, s);
-          } else {
-            // too deep for one exact accumulation: [U+ U-][s; d] into T1, then the direct part
-            tc_gemm_part_accum(ob, 2 * n, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1, w->g0tab,
-                               kSlices, w->tcw, s);
-            tc_gemm_part(ob, kdir, w->Upm + 2 * n, ldU, sU_part, w->SD + (size_t)2 * n * R,
-                         ob.sSD, w->T1, w->g0tab, w->Isyn, kSlices, w->tcw, s);
-          }
-        } else {
-          dgemm_part_epilogue(ob, w->Upm, w->SD, w->T1, w->g0tab, w->Isyn, s);
-        }
-      }
-      if (mixed) {
-        StageScope sc(p, ST_REFINE, s, 6, 0.0, 0.0);
-        refine_columns(ob, 2 * n + kdir, w->Kinv, w->RHS, w->C, w->Hhat, w->Upm, w->SD,
-                       w->g0tab, kSliceEps, kRefineTol, w->rscratch, w->rcount, w->rlist,
-                       U * p->n_in, w->Isyn, s);
-      }
-    }
+    for (int m0 = 0; m0 < Meff; m0 += p->chunk)
+      run_order_batch(p, w, ly, coef, m0, std::min(p->chunk, Meff - m0),
+                      p->desc.precision == VRTE_MIXED, true, s);
     // a launch that could not start (resources, configuration) fails the solve here
     if (cudaPeekAtLastError() != cudaSuccess) {
       cudaGetLastError();
@@ -706,9 +943,64 @@ vrte_status vrte_solve_brdf_host(vrte_plan* p, const double* h_coeffs, void* h_b
 }
 
 vrte_status vrte_brdf_backward(vrte_plan* p, const void* g, int gd, double* d_grad, void* stream) {
-  (void)g; (void)gd; (void)d_grad; (void)stream;
-  if (!p) return VRTE_ERR_INVALID_ARG;
-  return VRTE_ERR_UNSUPPORTED;
+  if (!p || !g || !d_grad) return VRTE_ERR_INVALID_ARG;
+  if (gd != VRTE_OUT_F32 && gd != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
+  if (!(p->desc.flags & VRTE_FLAG_ADJOINT) || p->n_layers < 1 || !p->ws[0].bw)
+    return VRTE_ERR_STATE;
+  cudaStream_t s0 = (cudaStream_t)stream;
+  p->last_stream = s0;
+  const int ns = p->nslots;
+  if (ns > 1) {
+    if (cudaEventRecord(p->fork, s0) != cudaSuccess) return VRTE_ERR_CUDA;
+    for (int k = 0; k < ns; ++k)
+      if (cudaStreamWaitEvent(p->ws[k].stream, p->fork, 0) != cudaSuccess) return VRTE_ERR_CUDA;
+  }
+  const size_t table = (size_t)p->n_in * p->n_out * p->n_phi * 16;
+  const size_t esz = gd == VRTE_OUT_F64 ? sizeof(double) : sizeof(float);
+  const int Lmax = p->desc.n_coef_max;
+  vrte_status result = VRTE_OK;
+  for (int lb = 0; lb < p->n_layers && result == VRTE_OK; ++lb) {
+    Work* w = &p->ws[lb % ns];
+    cudaStream_t s = ns > 1 ? w->stream : s0;
+    p->last_slot = lb % ns;
+    const vrte_layer& ly = p->layers[lb];
+    const int N = ly.n_nodes, L = ly.n_coef;
+    const int Meff = std::min(ly.n_orders, ly.n_coef);
+    const double* coef = p->d_coeffs + (size_t)lb * Lmax * 6;
+    {
+      StageScope sc(p, ST_TABLES, s, 4, 0.0, 0.0);
+      launch_gauss_nodes(N, w->d_mu_nodes, w->d_w_nodes, p->d_status, s);
+      launch_interface(N, p->n_in, p->n_out, ly.n_interface, w->d_mu_nodes, p->d_mu_in,
+                       p->d_mu_out, w->d_pts, w->d_min4, w->d_mout4, w->d_rtop4, s);
+      launch_interface_dn(N, p->n_in, p->n_out, ly.n_interface, w->d_mu_nodes, p->d_mu_in,
+                          p->d_mu_out, w->dpts, w->dmin4, w->dmout4, w->drtop4, s);
+      launch_depth_table(N, p->n_in, p->n_out, ly.tau, w->d_pts, w->g0tab, s);
+    }
+    {
+      StageScope sc(p, ST_ADJOINT, s, 2, 2.0 * table * Meff, (double)table * esz);
+      cudaMemsetAsync(w->acc, 0, (3 + 6 * (size_t)Lmax) * sizeof(double), s);
+      launch_synth_transpose(Meff, p->n_in, p->n_out, p->n_phi,
+                             (const char*)g + (size_t)lb * table * esz, gd, p->d_wc, p->d_ws,
+                             w->Isyn, s);
+    }
+    for (int m0 = 0; m0 < Meff; m0 += p->chunk) {
+      const int U = std::min(p->chunk, Meff - m0);
+      run_order_batch(p, w, ly, coef, m0, U, false, false, s);
+      backward_batch(p, w, ly, coef, m0, U, s);
+    }
+    bw_finish(L, Lmax, ly.n_interface, w->acc, d_grad + (size_t)lb * (3 + 6 * Lmax), s);
+    if (cudaPeekAtLastError() != cudaSuccess) {
+      cudaGetLastError();
+      result = VRTE_ERR_CUDA;
+    }
+  }
+  if (ns > 1)
+    for (int k = 0; k < ns; ++k)
+      if (cudaEventRecord(p->ws[k].done, p->ws[k].stream) != cudaSuccess ||
+          cudaStreamWaitEvent(s0, p->ws[k].done, 0) != cudaSuccess)
+        result = VRTE_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return VRTE_ERR_CUDA;
+  return result;
 }
 
 vrte_status vrte_plan_status(vrte_plan* p) {

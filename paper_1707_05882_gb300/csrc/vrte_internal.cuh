@@ -59,6 +59,90 @@ struct EpiPart {
   }
 };
 
+// ---------------------------------------------------------------- complex FP64 helpers
+// (modes of a complex eigenvalue pair are kept in real form in the buffers; these evaluate
+// their exponentials and depth integrals)
+struct cd {
+  double r, i;
+};
+__device__ inline cd cmul(cd a, cd b) { return cd{a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ inline cd cdivv(cd a, cd b) {
+  double den = b.r * b.r + b.i * b.i;
+  return cd{(a.r * b.r + a.i * b.i) / den, (a.i * b.r - a.r * b.i) / den};
+}
+__device__ inline cd cexpv(cd z) {
+  double e = exp(z.r), sn, cs;
+  sincos(z.i, &sn, &cs);
+  return cd{e * cs, e * sn};
+}
+// exp(z) - 1, by its Taylor series for |z| < 1e-2
+__device__ inline cd cexpm1v(cd z) {
+  if (fabs(z.r) + fabs(z.i) < 1e-2) {
+    cd term = z, acc = z;
+    for (int k = 2; k < 10; ++k) {
+      term = cmul(term, z);
+      term.r /= k;
+      term.i /= k;
+      acc.r += term.r;
+      acc.i += term.i;
+    }
+    return acc;
+  }
+  cd e = cexpv(z);
+  return cd{e.r - 1.0, e.i};
+}
+// principal square root of a + ib without cancellation: with r = sqrt((|a| + |z|)/2),
+// sqrt(z) = (r, b/(2r)) for a >= 0 and (|b|/(2r), sign(b) r) for a < 0. (Forming
+// sqrt((|z| - a)/2) instead fails for pairs with a tiny imaginary part: |z| may round
+// below a.)
+__device__ inline cd csqrtv(double a, double b) {
+  if (b == 0.0) return a >= 0.0 ? cd{sqrt(a), 0.0} : cd{0.0, sqrt(-a)};
+  double r = sqrt(0.5 * (fabs(a) + hypot(a, b)));
+  if (a >= 0.0) return cd{r, 0.5 * b / r};
+  return cd{0.5 * fabs(b) / r, copysign(r, b)};
+}
+
+__device__ inline cd kappa_of(const double* lr, const double* li, int j) {
+  return csqrtv(lr[j], li[j]);
+}
+
+
+// Forward-mode dual number: value and derivative with respect to one parameter.
+struct dual {
+  double v, d;
+};
+__host__ __device__ inline dual operator+(dual a, dual b) { return dual{a.v + b.v, a.d + b.d}; }
+__host__ __device__ inline dual operator-(dual a, dual b) { return dual{a.v - b.v, a.d - b.d}; }
+__host__ __device__ inline dual operator-(dual a) { return dual{-a.v, -a.d}; }
+__host__ __device__ inline dual operator*(dual a, dual b) { return dual{a.v * b.v, a.d * b.v + a.v * b.d}; }
+__host__ __device__ inline dual operator/(dual a, dual b) {
+  return dual{a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)};
+}
+__host__ __device__ inline dual operator+(dual a, double b) { return dual{a.v + b, a.d}; }
+__host__ __device__ inline dual operator+(double a, dual b) { return dual{a + b.v, b.d}; }
+__host__ __device__ inline dual operator-(dual a, double b) { return dual{a.v - b, a.d}; }
+__host__ __device__ inline dual operator-(double a, dual b) { return dual{a - b.v, -b.d}; }
+__host__ __device__ inline dual operator*(dual a, double b) { return dual{a.v * b, a.d * b}; }
+__host__ __device__ inline dual operator*(double a, dual b) { return dual{a * b.v, a * b.d}; }
+__host__ __device__ inline dual operator/(dual a, double b) { return dual{a.v / b, a.d / b}; }
+__host__ __device__ inline dual operator/(double a, dual b) {
+  return dual{a / b.v, -a * b.d / (b.v * b.v)};
+}
+__host__ __device__ inline dual dsqrt(dual a) {
+  double r = sqrt(a.v);
+  return dual{r, r > 0.0 ? 0.5 * a.d / r : 0.0};
+}
+__host__ __device__ inline dual dexp(dual a) {
+  double e = exp(a.v);
+  return dual{e, e * a.d};
+}
+__host__ __device__ inline dual dlog(dual a) { return dual{log(a.v), a.d / a.v}; }
+__host__ __device__ inline double val(double a) { return a; }
+__host__ __device__ inline double val(dual a) { return a.v; }
+__host__ __device__ inline double dsqrt(double a) { return sqrt(a); }
+__host__ __device__ inline double dexp(double a) { return exp(a); }
+__host__ __device__ inline double dlog(double a) { return log(a); }
+
 // ---------------------------------------------------------------- tables (k_tables.cu)
 void launch_gauss_nodes(int N, double* mu, double* w, unsigned* status, cudaStream_t s);
 void launch_interface(int N, int n_in, int n_out, double nif, const double* mu_nodes,
@@ -66,6 +150,15 @@ void launch_interface(int N, int n_in, int n_out, double nif, const double* mu_n
                       double* mout4, double* rtop4, cudaStream_t s);
 void launch_gsf_tables(const OrderBatch& b, const double* pts, double* p, double* r, double* t,
                        cudaStream_t s);
+// d/dn of the interface data (dual numbers): dpts [P], dmin4, dmout4, drtop4 (k_tables.cu)
+void launch_interface_dn(int N, int n_in, int n_out, double nif, const double* mu_nodes,
+                         const double* mu_in, const double* mu_out, double* dpts, double* dmin4,
+                         double* dmout4, double* drtop4, cudaStream_t s);
+// tangent tables: table 1 = d/dn at the incident points, table 2 = at the outgoing points,
+// the function values at every other point
+void launch_gsf_tables_dn(const OrderBatch& b, const double* pts, const double* dpts, double* p1,
+                          double* r1, double* t1, double* p2, double* r2, double* t2,
+                          cudaStream_t s);
 void launch_trig_table(int M, int n_phi, const double* phi, double* wc, double* ws, cudaStream_t s);
 
 // ---------------------------------------------------------------- assembly (k_assemble.cu)
@@ -102,6 +195,10 @@ void launch_direct_operators(const OrderBatch& b, const double* p, const double*
 void dgemm_batched(int M, int N, int K, double alpha, const double* A, int lda, long long sA,
                    const double* B, int ldb, long long sB, double beta, double* C, int ldc,
                    long long sC, int batch, cudaStream_t s);
+// the same with op(A) = A^T (A stored K x M) when tA and op(B) = B^T (B stored N x K) when tB
+void dgemm_batched_t(bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
+                     int lda, long long sA, const double* B, int ldb, long long sB, double beta,
+                     double* C, int ldc, long long sC, int batch, cudaStream_t s);
 // Reconstruction epilogue: Isyn[m][k][o][a][s] = T1[ro][rc] + g0(o, k) * (A @ B)[ro][rc]
 void dgemm_part_epilogue(const OrderBatch& b, const double* A, const double* B, const double* T1,
                          const double* g0tab, double* Isyn, cudaStream_t s);
@@ -177,5 +274,65 @@ void launch_build_Hhat(const OrderBatch& b, const double* P1, const double* P2,
 void launch_synthesis_fp64(int M, int n_in, int n_out, int n_phi, const double* Isyn,
                            const double* wc, const double* ws, void* out, int out_dtype,
                            unsigned* status, cudaStream_t s);
+
+// ---------------------------------------------------------------- adjoint (k_adjoint.cu)
+// Synthesis transpose: Ibar[m][k][o][16] from the table gradient G (FP32 or FP64).
+void launch_synth_transpose(int M, int n_in, int n_out, int n_phi, const void* G, int g_dtype,
+                            const double* wc, const double* ws, double* Ibar, cudaStream_t s);
+// acc[0] = dL/domega, acc[1] = dL/dtau0, acc[2] = dL/dn, acc[3 + 6 l + q] = dL/dcoef
+void bw_tb(const OrderBatch& b, const double* Ibar, const double* g0tab, double* Tb, double* G0,
+           cudaStream_t s);
+void bw_g0(const OrderBatch& b, const double* Tb, const double* Qp, const double* T1,
+           const double* pts, const double* dpts, double* acc, cudaStream_t s);
+void bw_kappa(const OrderBatch& b, const double* lam_re, const double* lam_im, double* kap,
+              cudaStream_t s);
+void bw_hhat(const OrderBatch& b, const double* Hb, const double* P1, const double* P2,
+             const double* kap, const double* pts, const double* dpts, double* P1b, double* P2b,
+             double* acc, cudaStream_t s);
+void bw_K(const OrderBatch& b, const double* Kb, const double* X, const double* Y,
+          const double* kap, const double* rtop4, const double* drtop4, double* acc,
+          cudaStream_t s);
+void bw_rhs(const OrderBatch& b, const double* nu, const double* SD, double* SDb,
+            const double* rtop4, const double* drtop4, const double* pts, const double* dpts,
+            double* acc, cudaStream_t s);
+void bw_part_d(const OrderBatch& b, const double* SD, const double* SDb, const double* pts,
+               const double* dpts, double* pb, double* acc, cudaStream_t s);
+void bw_scale(const OrderBatch& b, const double* lam_re, const double* lam_im, const double* ys,
+              double* ysb, const double* pts, const double* dpts, double* acc, cudaStream_t s);
+void bw_part_w(const OrderBatch& b, const double* wb, const double* r, const double* pts,
+               const double* dpts, double* rb, double* acc, cudaStream_t s);
+void bw_cplx_cols(const OrderBatch& b, const double* X, const double* Y, const double* kap,
+                  const double* rtop4, double* Xc, double* Yc, double* Pmc, double* Gtc,
+                  cudaStream_t s);
+void bw_cplx_rows(int n, int rows, int cols, long long sA, const double* A, const double* kap,
+                  double* Z, int units, cudaStream_t s);
+void bw_rowdiv(int n, int cols, const double* kap, double* Z, int units, cudaStream_t s);
+void bw_zeta(int n, int R, const double* Ta, const double* Tz, double* zeta, int units,
+             cudaStream_t s);
+void bw_psi(const OrderBatch& b, const double* P1, const double* P2, const double* kap,
+            const double* pts, double* PsiT1, double* PsiT2, cudaStream_t s);
+void bw_gf(const OrderBatch& b, const double* kap, const double* pts, double* Ah, cudaStream_t s);
+void bw_i1(int n, double tau, const double* kap, double* Om, int units, cudaStream_t s);
+void bw_i2(const OrderBatch& b, const double* kap, const double* pts, const double* Dp,
+           double* Dp2, cudaStream_t s);
+void bw_omblk(int n, const double* Om, double* OmF, double* OmE, int units, cudaStream_t s);
+void bw_dot(long long count, const double* A, long long sA, const double* B, long long sB,
+            double scale, double* dst, int units, cudaStream_t s);
+void bw_dot_ef(int n, int N, const double* Eb, const double* E2, const double* Fb,
+               const double* F2, const double* mu_nodes, double* acc, int units, cudaStream_t s);
+void bw_sbar_nn(const OrderBatch& b, const double* Eb, const double* Fb, const double* mu_nodes,
+                const double* w_nodes, double* S, cudaStream_t s);
+void bw_sbar_ni(const OrderBatch& b, const double* pb, const double* rb, const double* mu_nodes,
+                const double* min4, double* S, cudaStream_t s);
+void bw_sbar_on(const OrderBatch& b, const double* Ub, const double* w_nodes, const double* mout4,
+                double* S, cudaStream_t s);
+void bw_sbar_oi(const OrderBatch& b, const double* G0, const double* min4, const double* mout4,
+                double* S, cudaStream_t s);
+void bw_pstack(const OrderBatch& b, int y0, int ny, const double* pt, const double* rt,
+               const double* tt, double* PY, cudaStream_t s);
+void bw_bbar(const OrderBatch& b, int x0, int nx, const double* Qg, const double* Qd,
+             long long sQ, const double* pt, const double* rt, const double* tt, double* acc,
+             cudaStream_t s);
+void bw_finish(int L, int Lmax, double nif, const double* acc, double* grad, cudaStream_t s);
 
 }  // namespace vrte
