@@ -212,6 +212,70 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_backward(vr, torch, dev, n_layers=16, steps=2, warmup=1):
+    """The adjoint on the differentiation workload's shape (N = 48, M = L = 96 Mie layers with an
+    interface, 64 x 64 x 90 FP32 tables): per step one vrte_solve_brdf and one
+    vrte_brdf_backward of the loss 1/2 |F - F_target|^2 over `n_layers` of its 64 layers, on the
+    plan's concurrent streams; F_target = the table of the layers with every parameter perturbed
+    by a seeded 1-5 %."""
+    from vrte_inputs import make_config
+    cfg = make_config(5)
+    layers = [dict(l, n_coef=l["coef"].shape[0]) for l in cfg["layers"][:n_layers]]
+    rng = np.random.default_rng(5)
+    pert = [dict(l, tau=l["tau"] * (1 + rng.uniform(0.01, 0.05)),
+                 omega=min(0.999, l["omega"] * (1 + rng.uniform(0.01, 0.05))),
+                 coef=l["coef"] * (1 + rng.uniform(-0.05, 0.05, l["coef"].shape))) for l in layers]
+    Lmax = max(l["n_coef"] for l in layers)
+    plan = vr.Plan(cfg["mu_in"], cfg["mu_out"], cfg["dphi"], 48, 96, Lmax, len(layers),
+                   vr.VRTE_FP64, profile=True, adjoint=True)
+    d_pert = torch.from_numpy(vr.pack_coefficients(pert, Lmax)).to(dev)
+    plan.set_layers(pert, d_pert)
+    target = torch.empty(plan.table_shape, dtype=torch.float32, device=dev)
+    plan.solve(target)
+    d_coef = torch.from_numpy(vr.pack_coefficients(layers, Lmax)).to(dev)
+    plan.set_layers(layers, d_coef)
+    F = torch.empty(plan.table_shape, dtype=torch.float32, device=dev)
+    grad = torch.empty((len(layers), 3 + 6 * Lmax), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        plan.solve(F, stream)
+        plan.backward(F - target, grad, stream)
+    if plan.status() != 0:
+        raise SystemExit("backward failed")
+    plan.reset_stages()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for i in range(steps):
+        ev[i][0].record(stream)
+        plan.solve(F, stream)
+        G = F - target
+        ev[i][1].record(stream)
+        plan.backward(G, grad, stream)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    fwd = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+    bwd = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
+    st = plan.status()
+    stages = plan.stages()
+    plan.close()
+    orders = sum(min(l["n_orders"], l["n_coef"]) for l in layers)
+    adj = next(x for x in stages if x["name"] == "adjoint")
+    return {"workload": cfg["name"], "layers": len(layers), "order_solves": orders,
+            "N": 48, "M": 96, "L": 96, "n_in": 64, "n_out": 64, "n_phi": 90,
+            "forward_ms_per_step": fwd, "backward_ms_per_step": bwd,
+            "backward_order_solves_per_s": orders / (bwd / 1000.0),
+            "backward_over_forward": bwd / fwd, "status": int(st), "clocks": clk,
+            "adjoint_stage_ms": round(adj["ms"] / steps, 2),
+            "adjoint_stage_fp64_tflops": adj["flops"] / (adj["ms"] / 1000.0) / 1e12
+            if adj["ms"] > 0 else None,
+            "structure": "FP64 plan; backward recomputes each order batch in FP64 (eigen, "
+                         "boundary, particular), then the adjoint kernels; gradient "
+                         "[layers, 3 + 6 L] of omega, tau0, n, coefficients",
+            "steps": steps, "warmup": warmup}
+
+
 def max_over_ranks(x, dist, device):
     """Maximum of the float x over the ranks of the process group (x itself without one)."""
     if not dist:
@@ -419,6 +483,9 @@ def main():
                     help="skip timing the FP64 form beside the mixed form")
     ap.add_argument("--grid", type=int, nargs=3, metavar=("N_IN", "N_OUT", "N_PHI"),
                     help="smaller table for profiling captures (not the benchmark workload)")
+    ap.add_argument("--no-backward", action="store_true",
+                    help="skip the adjoint record (vrte_brdf_backward on 16 layers of the "
+                         "N=48, M=96 differentiation workload)")
     ap.add_argument("--workload", default="brdf", choices=["brdf", "batched"],
                     help="brdf: the N=64, M=128 layer (the benchmark line); batched: 256 "
                          "uneven layers, its own JSON line")
@@ -517,6 +584,9 @@ def main():
                        "api": "vrte_solve_brdf_host (pinned host buffers; the table leaves in "
                               "blocks of 64 incident cosines as the synthesis completes them)"}
         del h_out, d_tab
+
+    if not args.no_backward and not args.grid:
+        line["backward"] = time_backward(vr, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ly, cfg)

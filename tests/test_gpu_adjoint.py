@@ -1,11 +1,12 @@
 """The adjoint (vrte_brdf_backward and the autograd binding) against the FP64 oracle.
 
 dL/dp for L = 1/2 |F - F_target|^2 over the whole table, p = (omega, tau0, n, every
-coefficient), from the GPU's FP64 form, element by element against the oracle's gradient
-(oracle/gradient.py: Richardson-extrapolated central differences of the oracle BRDF) on small
-layers with and without a dielectric top. Tolerance: 1e-5 relative for every entry at least
-1e-3 of the largest; smaller entries (whose differences the oracle resolves less well) to
-1e-8 of the largest. The FP32-table path is checked against the FP64 gradient at the 1e-3
+coefficient), from the GPU's FP64 form, element by element against the oracle's two
+gradients on small layers with and without a dielectric top: the exact one of
+oracle/tangent.py (dual numbers through the propagator form of each order) and the
+Richardson-extrapolated central differences of oracle/gradient.py. Tolerance: 1e-5 relative
+for every entry at least 1e-3 of the largest; smaller entries (whose differences the
+difference oracle resolves less well) to 1e-8 of the largest. The FP32-table path is checked against the FP64 gradient at the 1e-3
 relative bound that FP32 rounding of the table allows.
 """
 import numpy as np
@@ -13,6 +14,7 @@ import pytest
 
 import oracle as O
 import oracle.gradient as OG
+import oracle.tangent as OT
 import paper_1707_05882_gb300 as vr
 from vrte_inputs import angle_grids
 from vrte_inputs.mie import monodisperse_coefficients
@@ -76,9 +78,13 @@ def test_adjoint_matches_oracle_gradient(nif):
     p = OG.pack(ly["omega"], ly["tau"], nif, ly["coef"])
     idx = [k for k in range(p.size) if not (k == 2 and nif <= 1.0)]
     ref = OG.loss_gradient(p, target, L, ly["n_nodes"], ly["n_orders"], *grids, indices=idx)
+    exact = OT.loss_gradient(p, target, L, ly["n_nodes"], ly["n_orders"], *grids, indices=idx)
     if nif <= 1.0:
         assert g[2] == 0.0
+    _compare(g, exact)
     _compare(g, ref)
+    big = np.abs(exact).max()
+    print(f"max |gpu - exact| / max|g| = {np.abs(g - exact).max() / big:.2e}")
 
 
 def test_adjoint_thick_layer_resolves_every_order():
