@@ -90,6 +90,71 @@ def brdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi):
     return synthesize(Im, mu_in, mu_out, dphi, n_interface)
 
 
+def btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out):
+    """Per-order downward radiance at the bottom I^m(tau0, -mu_out) [M, n_in, n_out, 4, 4].
+
+    mu_out are cosines of downward directions below the layer, which has no interface at the
+    bottom (black base or free space below): they are internal cosines as they are. The beam
+    enters through the top interface as for the BRDF.
+    """
+    coef = np.asarray(coef, dtype=float)
+    mu_in = np.atleast_1d(np.asarray(mu_in, dtype=float))
+    mu_out = np.atleast_1d(np.asarray(mu_out, dtype=float))
+    nodes = gauss_legendre_01(N)
+    mu0_int = snell_mu(mu_in, n_interface)
+    beam = fresnel_beam_in(mu_in, n_interface)
+    iface = n_interface > 1.0
+    R_top = fresnel_internal_reflection(nodes[0], n_interface) if iface else None
+    R_out = fresnel_internal_reflection(mu_out, n_interface) if iface else None
+    L = coef.shape[0]
+    Im = np.zeros((M, mu_in.size, mu_out.size, 4, 4))
+    for m in range(min(M, L)):
+        sol = solve_order(m, coef, omega, tau0, N, mu0_int, beam, R_top, nodes)
+        Im[m] = sol.reconstruct_bottom(mu_out, R_out)
+    return Im
+
+
+def btdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi):
+    """Mueller BTDF table T[n_in, n_out, n_phi, 4, 4] of one layer (FP64): the diffuse
+    radiance leaving the bottom in direction (-mu_out, phi_out) per unit irradiance mu_in I0
+    of the beam from (mu_in, phi_in) above, dphi = phi_out - phi_in, Stokes vectors on the
+    meridian frames of the propagation directions (Eq. 12 with the same Fourier factors as
+    the BRDF; no exit interface)."""
+    Im = btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out)
+    return synthesize(Im, mu_in, mu_out, dphi, 1.0)
+
+
+def single_scatter_btdf(coef, omega, tau0, n_interface, mu_in, mu_out, dphi):
+    """Exact once-scattered BTDF from the directly rotated phase matrix, independent of the
+    Fourier machinery: the beam scattered once downward,
+        (omega / 4 pi) Z(-mu, phi; -mu0, phi_in + pi) I0' int_0^tau0 e^{-t/mu0} e^{-(tau0-t)/mu} dt / mu,
+    plus, under a dielectric top, the light scattered once upward and specularly reflected
+    back down at the top (it crosses the layer once more),
+        exp(-tau0/mu) R_F(mu) (omega / 4 pi) Z(mu, phi; -mu0, phi_in + pi) I0' int_0^tau0 e^{-t/mu0} e^{-t/mu} dt / mu,
+    both divided by mu_in."""
+    mu_in = np.atleast_1d(np.asarray(mu_in, dtype=float))
+    mu_out = np.atleast_1d(np.asarray(mu_out, dtype=float))
+    dphi = np.atleast_1d(np.asarray(dphi, dtype=float))
+    mi = snell_mu(mu_in, n_interface)
+    Min = fresnel_beam_in(mu_in, n_interface)
+    Rf = fresnel_internal_reflection(mu_out, n_interface)
+    F = np.zeros((mu_in.size, mu_out.size, dphi.size, 4, 4))
+    for i in range(mu_in.size):
+        for o in range(mu_out.size):
+            x, y = 1.0 / mu_out[o], 1.0 / mi[i]
+            if abs(x - y) * tau0 < 1e-8:
+                depth = tau0 * np.exp(-x * tau0)
+            else:
+                depth = (np.exp(-y * tau0) - np.exp(-x * tau0)) / (x - y)
+            up = -np.expm1(-tau0 * (x + y)) / (x + y)
+            for j, dp in enumerate(dphi):
+                Zd = phase_matrix_direct(coef, -mu_out[o], dp, -mi[i], np.pi)
+                Zu = phase_matrix_direct(coef, mu_out[o], dp, -mi[i], np.pi)
+                I = depth * Zd + np.exp(-x * tau0) * up * Rf[o] @ Zu
+                F[i, o, j] = omega / (4 * np.pi) / mu_out[o] * I @ Min[i] / mu_in[i]
+    return F
+
+
 def single_scatter_brdf(coef, omega, tau0, n_interface, mu_in, mu_out, dphi):
     """Exact once-scattered BRDF, computed from the directly rotated phase matrix.
 

@@ -194,6 +194,65 @@ class OrderSolution:
         return out
 
 
+def _reconstruct_bottom(self, mu_out, R_out=None):
+    """I^m(tau0, -mu) for downward internal cosines mu at the bottom: [n_beams, n_out, 4, 4].
+
+    Formal solution along the downward path (tau grows downward, -mu dI/dtau = -(I - S) for
+    the direction -mu, i.e. dI/dtau = (S - I)/mu):
+        I^m(tau0, -mu) = I^m(0, -mu) exp(-tau0/mu) + int_0^tau0 S(t, -mu) exp(-(tau0 - t)/mu) dt / mu,
+        S(t, -mu) = (omega/2) sum_{s,n} alpha_n A^m(-mu, s mu_n) u_{s,n}(t)
+                    + (omega / 2 pi) A^m(-mu, -mu0) I0' exp(-t/mu0),
+    with the downward radiance entering at the top I^m(0, -mu) = R_F(mu) I^m(0, +mu) (the
+    internal specular reflection of the upward radiance at the same cosine; zero for a bare
+    top; R_out[k] the reflection matrix at mu_out[k]). With x = 1/mu the depth integrals are
+        exp(kappa t)           (Re kappa < 0):  x (exp(kappa tau0) - exp(-x tau0)) / (kappa + x)
+        exp(kappa (t - tau0))  (Re kappa >= 0): x (1 - exp(-(kappa + x) tau0)) / (kappa + x)
+        exp(-t/mu0):                            x (exp(-tau0/mu0) - exp(-x tau0)) / (x - 1/mu0),
+    each evaluated through expm1 where its denominator is small. The once-scattered beam is
+    included; the uncollided beam (a delta in direction) is not part of the diffuse field.
+    """
+    mu_out = np.atleast_1d(np.asarray(mu_out, dtype=float))
+    n_out = mu_out.size
+    t0 = self.tau0
+    G = _stack_matrix(A_matrix(self.m, self.coef, -mu_out, self.mus))     # [4 n_out, 8N]
+    GW = 0.5 * self.omega * G * self.w8[None, :]
+    H = GW @ self.V
+    mu_rows = np.repeat(mu_out, 4)
+    x = (1.0 / mu_rows)[:, None]
+    k = self.kappa[None, :]
+    a = k + x
+    small = np.abs(a * t0) < 1e-2
+    with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+        g_dec = np.where(small, x * np.exp(-x * t0) * expm1_complex(a * t0) / a,
+                         x * (np.exp(k * t0) - np.exp(-x * t0)) / a)
+        g_gro = x * -expm1_complex(-a * t0) / a
+    g_dec = np.where(np.abs(a) == 0.0, x * t0 * np.exp(-x * t0), g_dec)
+    g = np.where(self.growing[None, :], g_gro, g_dec)
+    hom = (H * g) @ self.c
+    y = (1.0 / self.rhs_mu0)[None, :]
+    d = x - y
+    with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+        g0 = np.where(np.abs(d * t0) < 1e-2, x * np.exp(-x * t0) * expm1_complex(d * t0).real / d,
+                      x * (np.exp(-y * t0) - np.exp(-x * t0)) / d)
+    g0 = np.where(d == 0.0, x * t0 * np.exp(-x * t0), g0)
+    part = GW @ self.z
+    n_b = self.mu0.size
+    direct = np.zeros((4 * n_out, 4 * n_b))
+    for i, mu0 in enumerate(self.mu0):
+        Ad = _stack_matrix(A_matrix(self.m, self.coef, -mu_out, [-mu0]))
+        direct[:, 4 * i:4 * i + 4] = self.cQ * Ad @ self.beam[i]
+    tot = (hom + (part + direct) * g0).real
+    out = tot.reshape(n_out, 4, n_b, 4).transpose(2, 0, 1, 3)
+    if R_out is not None:
+        top = self.reconstruct_top(mu_out)                               # [n_b, n_out, 4, 4]
+        att = np.exp(-t0 / mu_out)
+        out = out + np.einsum("oab,kobc->koac", np.asarray(R_out) * att[:, None, None], top)
+    return out
+
+
+OrderSolution.reconstruct_bottom = _reconstruct_bottom
+
+
 def solve_order(m, coef, omega, tau0, N, mu0_int, beam=None, R_top=None, nodes=None):
     """Solve Fourier order m for internal beam cosines mu0_int.
 
