@@ -52,7 +52,7 @@ def synthesis_weights(m: int, dphi):
     return w
 
 
-def brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out):
+def brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho=0.0):
     """Per-order internal exiting radiance I^m [M, n_in, n_out, 4, 4] plus interface data."""
     coef = np.asarray(coef, dtype=float)
     mu_in = np.atleast_1d(np.asarray(mu_in, dtype=float))
@@ -65,7 +65,7 @@ def brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out):
     L = coef.shape[0]
     Im = np.zeros((M, mu_in.size, mu_out.size, 4, 4))
     for m in range(min(M, L)):
-        sol = solve_order(m, coef, omega, tau0, N, mu0_int, beam, R_top, nodes)
+        sol = solve_order(m, coef, omega, tau0, N, mu0_int, beam, R_top, nodes, rho)
         Im[m] = sol.reconstruct_top(mu_out_int)
     return Im
 
@@ -84,13 +84,14 @@ def synthesize(Im, mu_in, mu_out, dphi, n_interface):
     return F / mu_in[:, None, None, None, None]
 
 
-def brdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi):
-    """Mueller BRDF table F[n_in, n_out, n_phi, 4, 4] of one layer (FP64)."""
-    Im = brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out)
+def brdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi, rho=0.0):
+    """Mueller BRDF table F[n_in, n_out, n_phi, 4, 4] of one layer (FP64); rho is the albedo
+    of a Lambertian base (0: black base)."""
+    Im = brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho)
     return synthesize(Im, mu_in, mu_out, dphi, n_interface)
 
 
-def btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out):
+def btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho=0.0):
     """Per-order downward radiance at the bottom I^m(tau0, -mu_out) [M, n_in, n_out, 4, 4].
 
     mu_out are cosines of downward directions below the layer, which has no interface at the
@@ -109,18 +110,18 @@ def btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out):
     L = coef.shape[0]
     Im = np.zeros((M, mu_in.size, mu_out.size, 4, 4))
     for m in range(min(M, L)):
-        sol = solve_order(m, coef, omega, tau0, N, mu0_int, beam, R_top, nodes)
+        sol = solve_order(m, coef, omega, tau0, N, mu0_int, beam, R_top, nodes, rho)
         Im[m] = sol.reconstruct_bottom(mu_out, R_out)
     return Im
 
 
-def btdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi):
+def btdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi, rho=0.0):
     """Mueller BTDF table T[n_in, n_out, n_phi, 4, 4] of one layer (FP64): the diffuse
     radiance leaving the bottom in direction (-mu_out, phi_out) per unit irradiance mu_in I0
     of the beam from (mu_in, phi_in) above, dphi = phi_out - phi_in, Stokes vectors on the
     meridian frames of the propagation directions (Eq. 12 with the same Fourier factors as
     the BRDF; no exit interface)."""
-    Im = btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out)
+    Im = btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho)
     return synthesize(Im, mu_in, mu_out, dphi, 1.0)
 
 
