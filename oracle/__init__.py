@@ -40,8 +40,8 @@ from .phase import (A_matrix, B_matrix, P_matrices, fourier_synthesis_phase,
 from .fresnel import (fresnel_beam_in, fresnel_exit, fresnel_internal_reflection,
                       fresnel_external_reflection, snell_mu)
 from .dom import OrderSolution, solve_order
-from .brdf import (brdf, brdf_orders, btdf, btdf_orders, single_scatter_brdf,
-                   single_scatter_btdf)
+from .brdf import (brdf, brdf_orders, btdf, btdf_orders, radiance, radiance_orders,
+                   single_scatter_brdf, single_scatter_btdf)
 
 __all__ = [
     "gauss_legendre_01", "gsf_tables", "wigner_d_family", "wigner_d_jacobi",
@@ -50,5 +50,5 @@ __all__ = [
     "fresnel_beam_in", "fresnel_exit", "fresnel_internal_reflection",
     "fresnel_external_reflection", "snell_mu",
     "OrderSolution", "solve_order", "brdf", "brdf_orders", "single_scatter_brdf",
-    "btdf", "btdf_orders", "single_scatter_btdf",
+    "btdf", "btdf_orders", "radiance", "radiance_orders", "single_scatter_btdf",
 ]

@@ -125,6 +125,36 @@ def btdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi, rho=0.0):
     return synthesize(Im, mu_in, mu_out, dphi, 1.0)
 
 
+def radiance_orders(coef, omega, tau0, n_interface, N, M, mu_in, tau, mu_up, mu_down, rho=0.0):
+    """Per-order internal radiance at depth tau for incident beams mu_in (external, through the
+    top): (up [M, n_in, n_up, 4, 4], down [M, n_in, n_down, 4, 4]) at the internal cosines
+    mu_up (upward) and mu_down (downward)."""
+    coef = np.asarray(coef, dtype=float)
+    mu_in = np.atleast_1d(np.asarray(mu_in, dtype=float))
+    mu_up = np.atleast_1d(np.asarray(mu_up, dtype=float))
+    mu_down = np.atleast_1d(np.asarray(mu_down, dtype=float))
+    nodes = gauss_legendre_01(N)
+    iface = n_interface > 1.0
+    R_top = fresnel_internal_reflection(nodes[0], n_interface) if iface else None
+    R_dn = fresnel_internal_reflection(mu_down, n_interface) if iface else None
+    L = coef.shape[0]
+    up = np.zeros((M, mu_in.size, mu_up.size, 4, 4))
+    dn = np.zeros((M, mu_in.size, mu_down.size, 4, 4))
+    for m in range(min(M, L)):
+        sol = solve_order(m, coef, omega, tau0, N, snell_mu(mu_in, n_interface),
+                          fresnel_beam_in(mu_in, n_interface), R_top, nodes, rho)
+        up[m], dn[m] = sol.reconstruct_depth(tau, mu_up, mu_down, R_dn)
+    return up, dn
+
+
+def radiance(coef, omega, tau0, n_interface, N, M, mu_in, tau, mu_up, mu_down, dphi, rho=0.0):
+    """Radiance field inside the layer at depth tau per unit irradiance mu_in I0 of the beam:
+    (up [n_in, n_up, n_phi, 4, 4], down [n_in, n_down, n_phi, 4, 4]), directions (+-mu, phi)
+    with dphi = phi - phi_in and Stokes vectors on their meridian frames (Eq. 12)."""
+    up, dn = radiance_orders(coef, omega, tau0, n_interface, N, M, mu_in, tau, mu_up, mu_down, rho)
+    return (synthesize(up, mu_in, mu_up, dphi, 1.0), synthesize(dn, mu_in, mu_down, dphi, 1.0))
+
+
 def single_scatter_btdf(coef, omega, tau0, n_interface, mu_in, mu_out, dphi):
     """Exact once-scattered BTDF from the directly rotated phase matrix, independent of the
     Fourier machinery: the beam scattered once downward,

@@ -274,6 +274,79 @@ def _reconstruct_bottom(self, mu_out, R_out=None):
 OrderSolution.reconstruct_bottom = _reconstruct_bottom
 
 
+def _dd_exp(a, b, T):
+    """(exp(-a T) - exp(-b T)) / (b - a), through expm1 where |(b - a) T| is small."""
+    a = np.asarray(a, dtype=complex)
+    b = np.asarray(b, dtype=complex)
+    d = b - a
+    with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+        near = np.abs(d * T) < 1e-2
+        out = np.where(near, np.exp(-a * T) * -expm1_complex(-d * T) / d,
+                       (np.exp(-a * T) - np.exp(-b * T)) / d)
+    return np.where(d == 0, T * np.exp(-a * T), out)
+
+
+def _reconstruct_depth(self, tau, mu_up, mu_down, R_down=None):
+    """Radiance inside the layer at depth tau (0 <= tau <= tau0), Sec. 2.C reconstruction:
+    upward directions +mu_up and downward directions -mu_down, each [n_beams, n, 4, 4].
+
+        I^m(tau, +mu) = I^m(tau0, +mu) e^{-(tau0 - tau)/mu} + int_tau^tau0 S(t, mu) e^{-(t - tau)/mu} dt / mu
+        I^m(tau, -mu) = I^m(0, -mu) e^{-tau/mu} + int_0^tau S(t, -mu) e^{-(tau - t)/mu} dt / mu
+
+    with S as in reconstruct_top / reconstruct_bottom, I^m(tau0, +mu) the Lambertian base's
+    isotropic radiance (zero for a black base) and I^m(0, -mu) = R_F(mu) I^m(0, +mu) under a
+    dielectric top (R_down[k] at mu_down[k]). With x = 1/mu every depth integral is a divided
+    difference D(a, b; T) = (e^{-aT} - e^{-bT})/(b - a):
+        upward,   decaying e^{kappa t}:        x e^{kappa tau} D(0, x - kappa; tau0 - tau)
+        upward,   growing e^{kappa (t-tau0)}:  x D(x, kappa; tau0 - tau)
+        upward,   beam e^{-t/mu0}:             x e^{-tau/mu0} D(0, x + 1/mu0; tau0 - tau)
+        downward, decaying:                    x D(x, -kappa; tau)
+        downward, growing:                     x e^{-kappa (tau0 - tau)} D(0, kappa + x; tau)
+        downward, beam:                        x D(1/mu0, x; tau)
+    At tau = 0 (upward) and tau = tau0 (downward) these are the top and bottom reconstructions.
+    """
+    t0 = self.tau0
+    tau = float(tau)
+    n_b = self.mu0.size
+    k = self.kappa[None, :]
+    y = (1.0 / self.rhs_mu0)[None, :]
+    out = []
+    for sign, mus in ((1.0, mu_up), (-1.0, mu_down)):
+        mus = np.atleast_1d(np.asarray(mus, dtype=float))
+        G = _stack_matrix(A_matrix(self.m, self.coef, sign * mus, self.mus))
+        GW = 0.5 * self.omega * G * self.w8[None, :]
+        H = GW @ self.V
+        x = (1.0 / np.repeat(mus, 4))[:, None]
+        if sign > 0:
+            g_dec = x * np.exp(k * tau) * _dd_exp(0.0, x - k, t0 - tau)
+            g_gro = x * _dd_exp(x, k, t0 - tau)
+            g0 = x * np.exp(-y * tau) * _dd_exp(0.0, x + y, t0 - tau)
+        else:
+            g_dec = x * _dd_exp(x, -k, tau)
+            g_gro = x * np.exp(-k * (t0 - tau)) * _dd_exp(0.0, k + x, tau)
+            g0 = x * _dd_exp(y, x, tau)
+        g = np.where(self.growing[None, :], g_gro, g_dec)
+        hom = (H * g) @ self.c
+        direct = np.zeros((4 * mus.size, 4 * n_b))
+        for i, mu0 in enumerate(self.mu0):
+            Ad = _stack_matrix(A_matrix(self.m, self.coef, sign * mus, [-mu0]))
+            direct[:, 4 * i:4 * i + 4] = self.cQ * Ad @ self.beam[i]
+        tot = (hom + (GW @ self.z + direct) * g0).real
+        if sign > 0 and self.rho > 0.0:
+            base = self.nodal(t0)[0]                       # the base's isotropic radiance
+            tot[0::4] += np.exp(-(t0 - tau) / mus)[:, None] * base[None, :]
+        res = tot.reshape(mus.size, 4, n_b, 4).transpose(2, 0, 1, 3)
+        if sign < 0 and R_down is not None:
+            top = self.reconstruct_top(mus)
+            att = np.exp(-tau / mus)
+            res = res + np.einsum("oab,kobc->koac", np.asarray(R_down) * att[:, None, None], top)
+        out.append(res)
+    return out[0], out[1]
+
+
+OrderSolution.reconstruct_depth = _reconstruct_depth
+
+
 def solve_order(m, coef, omega, tau0, N, mu0_int, beam=None, R_top=None, nodes=None, rho=0.0):
     """Solve Fourier order m for internal beam cosines mu0_int.
 
