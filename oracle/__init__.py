@@ -42,6 +42,7 @@ from .fresnel import (fresnel_beam_in, fresnel_exit, fresnel_internal_reflection
 from .dom import OrderSolution, solve_order
 from .brdf import (brdf, brdf_orders, btdf, btdf_orders, radiance, radiance_orders,
                    single_scatter_brdf, single_scatter_btdf)
+from .slab import slab_brdf, slab_reconstruct_top, solve_slab_order
 
 __all__ = [
     "gauss_legendre_01", "gsf_tables", "wigner_d_family", "wigner_d_jacobi",
@@ -51,4 +52,5 @@ __all__ = [
     "fresnel_external_reflection", "snell_mu",
     "OrderSolution", "solve_order", "brdf", "brdf_orders", "single_scatter_brdf",
     "btdf", "btdf_orders", "radiance", "radiance_orders", "single_scatter_btdf",
+    "slab_brdf", "slab_reconstruct_top", "solve_slab_order",
 ]
