@@ -26,7 +26,8 @@
  *     surface;
  *   - optional smooth dielectric top of relative index n > 1 (Fresnel
  *     transmission in and out, internal specular reflection as the top boundary
- *     condition); n <= 1 means a bare top. Black lower boundary.
+ *     condition); n <= 1 means a bare top. Black lower boundary, or a depolarizing
+ *     Lambertian base (vrte_layer.base_albedo).
  *
  * Threading and ownership: a plan is used by one host thread at a time. All
  * d_* pointers are device memory owned by the caller; the plan owns its
@@ -92,6 +93,9 @@ typedef struct {
  * workspace grows with the batch of orders processed at once, not with all orders. */
 #define VRTE_FLAG_ADJOINT 2u
 
+/* Allocates, in vrte_set_layer, the workspace of the transmission table (vrte_solve_btdf). */
+#define VRTE_FLAG_TRANSMISSION 4u
+
 /* Per-stage statistics accumulated since the last vrte_profile_reset. */
 typedef struct {
   char name[24];        /* stage name, e.g. "eigen", "recon_gemm", "synthesis" */
@@ -111,16 +115,21 @@ typedef struct {
   int n_nodes;         /* N of this layer, 1..n_nodes_max */
   int n_orders;        /* M of this layer, 1..n_orders_max; orders >= n_coef contribute 0 */
   int n_coef;          /* L of this layer, 1..n_coef_max */
+  double base_albedo;  /* albedo rho in [0, 1] of a depolarizing Lambertian base under the
+                          layer (Sec. 3.C, base reflection, R_00 = 2 rho); 0 = black base */
 } vrte_layer;
 
 typedef struct vrte_plan vrte_plan;
 
 /* Creates a plan: validates the descriptor, copies the grids to the device and
- * allocates per-plan tables. Returns VRTE_ERR_INVALID_ARG for out-of-range
- * sizes or cosines, VRTE_ERR_OOM / VRTE_ERR_CUDA on device failures. */
+ * allocates per-plan tables (the azimuth weights of the Fourier synthesis, Sec. 2.B,
+ * Eqs. 7 and 12). Returns VRTE_ERR_INVALID_ARG for out-of-range sizes or cosines,
+ * VRTE_ERR_OOM / VRTE_ERR_CUDA on device failures. */
 vrte_status vrte_plan_create(const vrte_plan_desc* desc, vrte_plan** out);
 
-/* Sets the layers to solve. host_params: [n_layers] parameters (copied).
+/* Sets the layers to solve: the optical thickness, albedo and phase-matrix expansion of
+ * Sec. 2.A-2.B (Eqs. 2-10; coefficients per Eq. 9's B_l). host_params: [n_layers]
+ * parameters (copied).
  * d_coeffs: device FP64 [n_layers][n_coef_max][6] expansion coefficients
  * (alpha1, alpha2, alpha3, alpha4, beta1, beta2) per l, zero-padded beyond each
  * layer's n_coef; the pointer is kept and read by each solve (the caller keeps
@@ -130,7 +139,8 @@ vrte_status vrte_plan_create(const vrte_plan_desc* desc, vrte_plan** out);
 vrte_status vrte_set_layer(vrte_plan* plan, int n_layers, const vrte_layer* host_params,
                            const double* d_coeffs);
 
-/* Solves every layer and writes the BRDF table
+/* Solves every layer and writes the BRDF table (Sec. 2: Eq. 1's F_r from the per-order
+ * solutions of Secs. 2.C and 3.A-3.D, synthesized by Eqs. 7, 12 and 39)
  *   d_brdf[n_layers][n_mu_in][n_mu_out][n_phi][4][4]   (row r = exiting Stokes
  *   component, column s = incident Stokes basis vector),
  * FP32 or FP64 per out_dtype, on `stream` (a cudaStream_t; NULL = legacy default
@@ -146,13 +156,43 @@ vrte_status vrte_set_layer(vrte_plan* plan, int n_layers, const vrte_layer* host
  * within one unit in the last place). */
 vrte_status vrte_solve_brdf(vrte_plan* plan, void* d_brdf, int out_dtype, void* stream);
 
-/* Same solve with host buffers: copies h_coeffs (host FP64, layout as d_coeffs
+/* Transmission table (BTDF) of every layer: the diffuse radiance leaving the bottom of the
+ * layer downward, per unit irradiance mu_in * I0 of the beam from above,
+ *   d_btdf[n_layers][n_mu_in][n_mu_out][n_phi][4][4]  (layout and units as d_brdf),
+ * with mu_out the cosines of the downward directions below the layer (no interface at the
+ * bottom, so they are internal cosines as given), dphi = phi_out - phi_in, Stokes vectors on
+ * the meridian frames of the propagation directions. The uncollided beam (a delta in
+ * direction) is not included. Paper: the field at tau0 of the solution of Sec. 2.C (Eqs. 36,
+ * 38 taken along the downward path) with the radiance the top sends back down (zero for a
+ * bare top, R_F times the upward radiance at the same cosine under a dielectric top), and the
+ * Fourier synthesis of Eq. 12. Solved in FP64 (VRTE_FP64 plans) or with the plan's mixed
+ * synthesis; requires a plan created with VRTE_FLAG_TRANSMISSION (else VRTE_ERR_STATE).
+ * Asynchronous; no allocation. */
+vrte_status vrte_solve_btdf(vrte_plan* plan, void* d_btdf, int out_dtype, void* stream);
+
+/* Radiance field inside every layer at depth h_tau[layer] (host, 0 <= tau <= the layer's tau0),
+ * per unit irradiance mu_in * I0 of the beam from above (incident through the top interface
+ * as for the BRDF), for the internal cosines mu_out of the plan, without exit factors:
+ *   d_up[n_layers][n_mu_in][n_mu_out][n_phi][4][4]    directions (+mu_out, phi), upward,
+ *   d_down[...]                                        directions (-mu_out, phi), downward
+ * (either may be NULL; layout and Stokes frames as d_brdf, dphi = phi - phi_in). Paper:
+ * Sec. 2.C reconstruction at an arbitrary tau (Eqs. 36-38 with the integration ranges
+ * [tau, tau0] upward and [0, tau] downward; the boundary radiances are the Lambertian base's at
+ * tau0 and the top's internal reflection at 0) and Sec. 4's radiance-field experiment.
+ * d_up at tau = 0 is the internal upward radiance under the top; d_down at tau0 the
+ * transmission table. Solved as vrte_solve_btdf; requires VRTE_FLAG_TRANSMISSION (else
+ * VRTE_ERR_STATE); a depth outside [0, tau0] gives VRTE_ERR_INVALID_ARG. */
+vrte_status vrte_solve_radiance(vrte_plan* plan, const double* h_tau, void* d_up, void* d_down,
+                                int out_dtype, void* stream);
+
+/* Same solve as vrte_solve_brdf (same passages) with host buffers: copies h_coeffs (host
+ * FP64, layout as d_coeffs
  * of vrte_set_layer) to the plan's staging buffer, solves, copies the table to
  * h_brdf (host, layout as d_brdf) and synchronizes `stream` before returning. The table
- * leaves in blocks of incident cosines, each copied as soon as the synthesis kernels that
- * complete it have run, on four streams of the plan (several copy engines) that wait on
- * `stream` by events and are joined back into it, so the copies overlap the rest of the
- * solve. Pinned host memory gives full copy bandwidth. */
+ * leaves a device staging buffer in blocks of incident cosines, each copied as soon as the
+ * synthesis kernels that complete it have run, on four streams of the plan (several copy
+ * engines) that wait on `stream` by events and are joined back into it. Pinned host memory
+ * gives full copy bandwidth. */
 vrte_status vrte_solve_brdf_host(vrte_plan* plan, const double* h_coeffs, void* h_brdf,
                                  int out_dtype, void* stream);
 
@@ -172,25 +212,29 @@ vrte_status vrte_solve_brdf_host(vrte_plan* plan, const double* h_coeffs, void* 
  * homogeneous modes on F'E' (Sec. 3.A) through the adjoint two-point problem of the order,
  * whose mode integrals are closed-form divided differences (finite at degenerate and complex
  * eigenvalues). Requires a plan created with VRTE_FLAG_ADJOINT and vrte_set_layer, else
- * VRTE_ERR_STATE; VRTE_ERR_INVALID_ARG for NULL pointers or an unknown grad_dtype.
+ * VRTE_ERR_STATE; VRTE_ERR_INVALID_ARG for NULL pointers or an unknown grad_dtype;
+ * VRTE_ERR_UNSUPPORTED when a layer has a reflecting base (base_albedo > 0).
  * Asynchronous on `stream`; no allocation; layers run on the plan's streams as in
  * vrte_solve_brdf. Accuracy: ~1e-8 relative in the gradient's largest entries (the FP64
  * solution's rounding, amplified near a resonance mu kappa_j ~ 1 as in the solve). */
 vrte_status vrte_brdf_backward(vrte_plan* plan, const void* d_grad_brdf, int grad_dtype,
                                double* d_grad_params, void* stream);
 
-/* Synchronizes the plan's last stream and returns the device status word as a
+/* (Library bookkeeping; no passage.) Synchronizes the plan's last stream and returns the
+ * device status word as a
  * vrte_status (VRTE_OK if no device-side error was recorded), then clears it. */
 vrte_status vrte_plan_status(vrte_plan* plan);
 
-/* Copies up to max_stages stage statistics into out (host) and returns the number of
+/* (Measurement; the paper times its steps per stage, Sec. 4 Table 4.) Copies up to
+ * max_stages stage statistics into out (host) and returns the number of
  * stages (or -1 for a NULL plan). Synchronizes the plan's last stream. */
 int vrte_profile_stages(vrte_plan* plan, vrte_stage_stat* out, int max_stages);
 
-/* Clears the stage statistics and the recorded events. */
+/* (Measurement.) Clears the stage statistics and the recorded events. */
 void vrte_profile_reset(vrte_plan* plan);
 
-/* Diagnostic read of one internal buffer of the most recent order batch, for
+/* (Testing; the buffers are the quantities of Secs. 2.C and 3.A-3.D.) Diagnostic read of
+ * one internal buffer of the most recent order batch, for
  * stage-level checks: copies min(bytes, buffer size) bytes into host_dst and returns
  * the buffer's full size in *size_out (may be NULL). Synchronizes. Names: "pts",
  * "nodes", "weights", "E", "F", "FE", "schur", "X", "Y", "lam_re", "lam_im", "K",
@@ -230,7 +274,9 @@ vrte_status vrte_debug_copy(vrte_plan* plan, const char* name, void* host_dst, s
 vrte_status vrte_eigen_noalloc(const double* d_A, int n, int batch, double* d_lam_re,
                                double* d_lam_im, double* d_X, unsigned* d_status, void* stream);
 
-/* Batched C = A B in FP64 on the tcgen05 tensor cores by exact fixed-point slicing:
+/* The dense contractions of Secs. 3.B-3.D (particular solution, boundary system,
+ * reconstruction) as used by the VRTE_MIXED form, on caller buffers:
+ * batched C = A B in FP64 on the tcgen05 tensor cores by exact fixed-point slicing:
  * every row of A and column of B is scaled by a power of two and cut into `slices`
  * signed 7-bit integer slices (each times a power of two) held in BF16; each slice
  * product is exact, products of equal scale are accumulated exactly in FP32 for K <= 1024,
@@ -248,13 +294,13 @@ vrte_status vrte_gemm_sliced(int M, int N, int K, const double* d_A, int lda, lo
                              long long stride_c, int batch, int slices, void* d_workspace,
                              size_t workspace_bytes, unsigned* d_status, void* stream);
 
-/* Bytes of device workspace the plan currently holds. */
+/* (Library bookkeeping.) Bytes of device workspace the plan currently holds. */
 size_t vrte_workspace_bytes(const vrte_plan* plan);
 
-/* Frees the plan and its workspace. Accepts NULL. */
+/* (Library bookkeeping.) Frees the plan and its workspace. Accepts NULL. */
 void vrte_destroy(vrte_plan* plan);
 
-/* Static string for a status code. */
+/* (Library bookkeeping.) Static string for a status code. */
 const char* vrte_status_string(vrte_status status);
 
 #ifdef __cplusplus

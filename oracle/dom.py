@@ -278,12 +278,16 @@ def _dd_exp(a, b, T):
     """(exp(-a T) - exp(-b T)) / (b - a), through expm1 where |(b - a) T| is small."""
     a = np.asarray(a, dtype=complex)
     b = np.asarray(b, dtype=complex)
+    a, b = np.broadcast_arrays(a, b)
     d = b - a
-    with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
-        near = np.abs(d * T) < 1e-2
-        out = np.where(near, np.exp(-a * T) * -expm1_complex(-d * T) / d,
-                       (np.exp(-a * T) - np.exp(-b * T)) / d)
-    return np.where(d == 0, T * np.exp(-a * T), out)
+    out = np.empty(d.shape, dtype=complex)
+    zero = d == 0
+    near = (np.abs(d * T) < 1e-2) & ~zero
+    far = ~near & ~zero
+    out[zero] = T * np.exp(-a[zero] * T)
+    out[near] = np.exp(-a[near] * T) * -expm1_complex(-d[near] * T) / d[near]
+    out[far] = (np.exp(-a[far] * T) - np.exp(-b[far] * T)) / d[far]
+    return out
 
 
 def _reconstruct_depth(self, tau, mu_up, mu_down, R_down=None):
@@ -317,15 +321,17 @@ def _reconstruct_depth(self, tau, mu_up, mu_down, R_down=None):
         GW = 0.5 * self.omega * G * self.w8[None, :]
         H = GW @ self.V
         x = (1.0 / np.repeat(mus, 4))[:, None]
+        gro = self.growing
+        kd, kg = k[:, ~gro], k[:, gro]
+        g = np.zeros((x.shape[0], k.shape[1]), dtype=complex)
         if sign > 0:
-            g_dec = x * np.exp(k * tau) * _dd_exp(0.0, x - k, t0 - tau)
-            g_gro = x * _dd_exp(x, k, t0 - tau)
+            g[:, ~gro] = x * np.exp(kd * tau) * _dd_exp(0.0, x - kd, t0 - tau)
+            g[:, gro] = x * _dd_exp(x, kg, t0 - tau)
             g0 = x * np.exp(-y * tau) * _dd_exp(0.0, x + y, t0 - tau)
         else:
-            g_dec = x * _dd_exp(x, -k, tau)
-            g_gro = x * np.exp(-k * (t0 - tau)) * _dd_exp(0.0, k + x, tau)
+            g[:, ~gro] = x * _dd_exp(x, -kd, tau)
+            g[:, gro] = x * np.exp(-kg * (t0 - tau)) * _dd_exp(0.0, kg + x, tau)
             g0 = x * _dd_exp(y, x, tau)
-        g = np.where(self.growing[None, :], g_gro, g_dec)
         hom = (H * g) @ self.c
         direct = np.zeros((4 * mus.size, 4 * n_b))
         for i, mu0 in enumerate(self.mu0):

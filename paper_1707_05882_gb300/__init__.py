@@ -24,6 +24,7 @@ STATUS_NAMES = {
 }
 
 EXPORTED = ["vrte_plan_create", "vrte_set_layer", "vrte_solve_brdf", "vrte_solve_brdf_host",
+            "vrte_solve_btdf", "vrte_solve_radiance",
             "vrte_brdf_backward", "vrte_plan_status", "vrte_profile_stages", "vrte_profile_reset",
             "vrte_debug_copy", "vrte_eigen_noalloc", "vrte_gemm_sliced", "vrte_gemm_sliced_workspace",
             "vrte_workspace_bytes", "vrte_destroy", "vrte_status_string"]
@@ -47,6 +48,7 @@ class PlanDesc(ctypes.Structure):
 
 VRTE_FLAG_PROFILE = 1
 VRTE_FLAG_ADJOINT = 2
+VRTE_FLAG_TRANSMISSION = 4
 
 
 class StageStat(ctypes.Structure):
@@ -58,7 +60,8 @@ class StageStat(ctypes.Structure):
 class Layer(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("omega", ctypes.c_double),
                 ("n_interface", ctypes.c_double), ("n_nodes", ctypes.c_int),
-                ("n_orders", ctypes.c_int), ("n_coef", ctypes.c_int)]
+                ("n_orders", ctypes.c_int), ("n_coef", ctypes.c_int),
+                ("base_albedo", ctypes.c_double)]
 
 
 _LIB = None
@@ -84,6 +87,8 @@ def load_library(build_if_missing: bool = True):
     lib.vrte_set_layer.argtypes = [P, ctypes.c_int, ctypes.POINTER(Layer), P]
     lib.vrte_solve_brdf.argtypes = [P, P, ctypes.c_int, P]
     lib.vrte_solve_brdf_host.argtypes = [P, P, P, ctypes.c_int, P]
+    lib.vrte_solve_btdf.argtypes = [P, P, ctypes.c_int, P]
+    lib.vrte_solve_radiance.argtypes = [P, P, P, P, ctypes.c_int, P]
     lib.vrte_brdf_backward.argtypes = [P, P, ctypes.c_int, P, P]
     lib.vrte_plan_status.argtypes = [P]
     lib.vrte_profile_stages.argtypes = [P, ctypes.POINTER(StageStat), ctypes.c_int]
@@ -108,7 +113,7 @@ def load_library(build_if_missing: bool = True):
     lib.vrte_status_string.argtypes = [ctypes.c_int]
     lib.vrte_status_string.restype = ctypes.c_char_p
     for name in ["vrte_plan_create", "vrte_set_layer", "vrte_solve_brdf", "vrte_solve_brdf_host",
-                 "vrte_brdf_backward", "vrte_plan_status"]:
+                 "vrte_solve_btdf", "vrte_solve_radiance", "vrte_brdf_backward", "vrte_plan_status"]:
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -134,7 +139,8 @@ class Plan:
     """A solver plan (vrte_plan_create / vrte_set_layer / vrte_solve_brdf / vrte_destroy)."""
 
     def __init__(self, mu_in, mu_out, dphi, n_nodes_max, n_orders_max, n_coef_max,
-                 n_layers_max=1, precision=VRTE_FP64, profile=False, adjoint=False):
+                 n_layers_max=1, precision=VRTE_FP64, profile=False, adjoint=False,
+                 transmission=False):
         self.lib = load_library()
         self._mu_in = np.ascontiguousarray(mu_in, dtype=np.float64)
         self._mu_out = np.ascontiguousarray(mu_out, dtype=np.float64)
@@ -142,7 +148,8 @@ class Plan:
         d = PlanDesc(int(n_nodes_max), int(n_orders_max), int(n_coef_max), int(n_layers_max),
                      self._mu_in.size, self._mu_out.size, self._phi.size, _dptr(self._mu_in),
                      _dptr(self._mu_out), _dptr(self._phi), int(precision),
-                     (VRTE_FLAG_PROFILE if profile else 0) | (VRTE_FLAG_ADJOINT if adjoint else 0))
+                     (VRTE_FLAG_PROFILE if profile else 0) | (VRTE_FLAG_ADJOINT if adjoint else 0)
+                     | (VRTE_FLAG_TRANSMISSION if transmission else 0))
         h = ctypes.c_void_p()
         _check(self.lib.vrte_plan_create(ctypes.byref(d), ctypes.byref(h)), "vrte_plan_create")
         self.handle = h
@@ -155,12 +162,13 @@ class Plan:
         return (self.n_layers, self._mu_in.size, self._mu_out.size, self._phi.size, 4, 4)
 
     def set_layers(self, layers, d_coeffs):
-        """layers: list of dict(tau, omega, n_interface, n_nodes, n_orders, n_coef);
+        """layers: list of dict(tau, omega, n_interface, n_nodes, n_orders, n_coef[, base_albedo]);
         d_coeffs: CUDA float64 tensor [n_layers, n_coef_max, 6] (kept alive by the plan)."""
         arr = (Layer * len(layers))()
         for i, l in enumerate(layers):
             arr[i] = Layer(float(l["tau"]), float(l["omega"]), float(l.get("n_interface", 1.0)),
-                           int(l["n_nodes"]), int(l["n_orders"]), int(l["n_coef"]))
+                           int(l["n_nodes"]), int(l["n_orders"]), int(l["n_coef"]),
+                           float(l.get("base_albedo", 0.0)))
         self._coeffs = d_coeffs
         _check(self.lib.vrte_set_layer(self.handle, len(layers), arr,
                                        ctypes.c_void_p(d_coeffs.data_ptr())), "vrte_set_layer")
@@ -173,6 +181,27 @@ class Plan:
         _check(self.lib.vrte_solve_brdf(self.handle, ctypes.c_void_p(out.data_ptr()), dt,
                                         _stream_handle(stream)), "vrte_solve_brdf")
         return out
+
+    def solve_btdf(self, out, stream=None):
+        """Writes the transmission table (vrte_solve_btdf) into the CUDA tensor `out`."""
+        import torch
+        dt = VRTE_OUT_F64 if out.dtype == torch.float64 else VRTE_OUT_F32
+        _check(self.lib.vrte_solve_btdf(self.handle, ctypes.c_void_p(out.data_ptr()), dt,
+                                        _stream_handle(stream)), "vrte_solve_btdf")
+        return out
+
+    def solve_radiance(self, taus, up=None, down=None, stream=None):
+        """Radiance tables at depths `taus` (one per layer) into the CUDA tensors `up` and/or
+        `down` (vrte_solve_radiance)."""
+        import torch
+        ref = up if up is not None else down
+        dt = VRTE_OUT_F64 if ref.dtype == torch.float64 else VRTE_OUT_F32
+        h = np.ascontiguousarray(taus, dtype=np.float64)
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        _check(self.lib.vrte_solve_radiance(self.handle, h.ctypes.data_as(ctypes.c_void_p),
+                                            ptr(up), ptr(down), dt, _stream_handle(stream)),
+               "vrte_solve_radiance")
+        return up, down
 
     def solve_host(self, h_coeffs, h_out, stream=None):
         """Host-buffer solve (copies in, solves, copies out, synchronizes)."""

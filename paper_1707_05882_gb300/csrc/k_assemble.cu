@@ -225,6 +225,53 @@ void launch_assemble_direct(const OrderBatch& b, const double* p, const double* 
   k_assemble_direct<<<grid, 64, 0, s>>>(b, p, r, t, pts, min4, mout4, T1);
 }
 
+// Direct (once-scattered) term of the radiance at depth tau (0 <= tau <= tau0) inside the
+// layer, internal cosine mu_o (identity exit): the source (omega/2pi) A^m(+-mu_o, -mu0_k) b_k
+// e^{-t/mu0} integrated along the path, upward (sign +) or downward (sign -):
+//   A^m(x, -y) = (S+(x, y) - S-(x, y)) D / 2,  A^m(-x, -y) = D (S+(x, y) + S-(x, y)) D / 2,
+// depth factors (x = 1/mu_o, y = 1/mu0, D(a, b; T) = (e^{-aT} - e^{-bT})/(b - a)):
+//   upward x e^{-y tau} D(0, x + y; tau0 - tau),  downward x D(y, x; tau).
+__global__ void k_assemble_direct_depth(OrderBatch b, double tau, int down, const double* pt,
+                                        const double* rt, const double* tt, const double* pts,
+                                        const double* min4, double* T) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int o = blockIdx.y;
+  int u = blockIdx.z;
+  if (k >= b.n_in) return;
+  int m = b.m0 + u;
+  SPair S;
+  accumulate_S(m, b.L, b.P, b.coef, pt, rt, tt, (size_t)u * b.L * b.P, b.N + b.n_in + o, b.N + k,
+               S);
+  const double x = 1.0 / pts[b.N + b.n_in + o], y = 1.0 / pts[b.N + k];
+  auto dd = [](double a, double bb, double Tl) {
+    const double d = bb - a;
+    if (d == 0.0) return Tl * exp(-a * Tl);
+    if (fabs(d * Tl) < 1e-2) return exp(-a * Tl) * -expm1(-d * Tl) / d;
+    return (exp(-a * Tl) - exp(-bb * Tl)) / d;
+  };
+  const double g = down ? x * dd(y, x, tau) : x * exp(-y * tau) * dd(0.0, x + y, b.tau - tau);
+  const double f = g * b.omega / (2.0 * kPi) * 0.5;
+  const double* qi = min4 + 4 * k;
+  const int R = 4 * b.n_in;
+  const size_t base = (size_t)u * (4 * b.n_out) * R;
+  for (int a = 0; a < 4; ++a)
+    for (int s = 0; s < 4; ++s) {
+      double v = 0.0;
+      for (int c = 0; c < 4; ++c) {
+        const double dc = c < 2 ? 1.0 : -1.0;
+        v += (down ? (S.sp[a][c] + S.sm[a][c]) : (S.sp[a][c] - S.sm[a][c])) * dc * blk(qi, c, s);
+      }
+      T[base + (size_t)(4 * o + a) * R + 4 * k + s] = f * (down && a >= 2 ? -1.0 : 1.0) * v;
+    }
+}
+
+void launch_assemble_direct_depth(const OrderBatch& b, double tau, int down, const double* p,
+                                  const double* r, const double* t, const double* pts,
+                                  const double* min4, double* T, cudaStream_t s) {
+  dim3 grid((b.n_in + 63) / 64, b.n_out, b.n_units);
+  k_assemble_direct_depth<<<grid, 64, 0, s>>>(b, tau, down, p, r, t, pts, min4, T);
+}
+
 // Direct-term operators for the mixed form (Eq. 38, Q term, as a contraction over the
 // pairs (l, component c) so that the tensor cores can fold it into the particular
 // contraction): with P = P_l^m and B = B_l,

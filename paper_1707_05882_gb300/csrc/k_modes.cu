@@ -300,4 +300,264 @@ void launch_build_Hhat(const OrderBatch& b, const double* P1, const double* P2,
                                     Hhat);
 }
 
+// ------------------------------------------------------------------ radiance at depth tau
+// Reconstruction of Sec. 2.C inside the layer (0 <= tau <= tau0), for internal cosines mu
+// (row 4o + a), x = 1/mu:
+//   upward:   I(tau, +mu) = I(tau0, +mu) e^{-(tau0-tau)/mu} + int_tau^tau0 S(t, mu) e^{-(t-tau)/mu} dt/mu
+//   downward: I(tau, -mu) = I(0, -mu) e^{-tau/mu} + int_0^tau S(t, -mu) e^{-(tau-t)/mu} dt/mu
+// With A^m(-mu, s mu_n) = D A^m(mu, -s mu_n) D the downward scattering part on the reduced
+// field is D (U+ s - U- d), the upward one U+ s + U- d (U+- with the identity exit). The modes
+// then contribute, with D(a, b; T) = (e^{-aT} - e^{-bT})/(b - a):
+//   upward:   decaying (P1 - P2) x e^{-kappa tau} D(0, x + kappa; tau0 - tau),
+//             growing  (P1 + P2) x D(x, kappa; tau0 - tau)
+//   downward: decaying D (P1 + P2) x D(x, kappa; tau),
+//             growing  D (P1 - P2) x e^{-kappa (tau0 - tau)} D(0, kappa + x; tau)
+// (at tau = 0 upward these are the top's factors of k_build_Hhat, at tau = tau0 downward the
+// same two factors swapped).
+__device__ inline cd dd_exp(cd a, cd b, double T) {
+  const cd d{b.r - a.r, b.i - a.i};
+  const cd ea = cexpv(cd{-a.r * T, -a.i * T});
+  if (d.r == 0.0 && d.i == 0.0) return cd{T * ea.r, T * ea.i};
+  if (fabs(d.r * T) + fabs(d.i * T) < 1e-2) {
+    const cd em = cexpm1v(cd{-d.r * T, -d.i * T});
+    return cdivv(cmul(ea, cd{-em.r, -em.i}), d);
+  }
+  const cd eb = cexpv(cd{-b.r * T, -b.i * T});
+  return cdivv(cd{ea.r - eb.r, ea.i - eb.i}, d);
+}
+
+__global__ void k_build_Hdepth(int N, int n, int n_in, int n_out, double tau0, double tau,
+                               int down, const double* P1, const double* P2, const double* lam_re,
+                               const double* lam_im, const double* pts, double* H) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = blockIdx.y, u = blockIdx.z;
+  if (j >= n) return;
+  const double* lr = lam_re + (size_t)u * n;
+  const double* li = lam_im + (size_t)u * n;
+  if (li[j] < 0.0) return;
+  const bool cplx = li[j] > 0.0;
+  const int Ro = 4 * n_out;
+  const cd kap = kappa_of(lr, li, j);
+  const double x = 1.0 / pts[N + n_in + o];
+  const cd X{x, 0.0}, Z{0.0, 0.0};
+  cd gA, gB;
+  if (!down) {
+    gA = cmul(cexpv(cd{-kap.r * tau, -kap.i * tau}), dd_exp(Z, cd{x + kap.r, kap.i}, tau0 - tau));
+    gB = dd_exp(X, kap, tau0 - tau);
+  } else {
+    gA = dd_exp(X, kap, tau);
+    gB = cmul(cexpv(cd{-kap.r * (tau0 - tau), -kap.i * (tau0 - tau)}),
+              dd_exp(Z, cd{kap.r + x, kap.i}, tau));
+  }
+  gA = cd{x * gA.r, x * gA.i};
+  gB = cd{x * gB.r, x * gB.i};
+  const double sA = down ? 1.0 : -1.0;  // decaying: P1 + P2 downward, P1 - P2 upward
+  for (int ar = 0; ar < 4; ++ar) {
+    const int ro = 4 * o + ar;
+    const double dl = down ? (ar < 2 ? 1.0 : -1.0) : 1.0;
+    const size_t rowp = (size_t)u * Ro * n + (size_t)ro * n;
+    double* Hr = H + (size_t)u * Ro * 2 * n + (size_t)ro * 2 * n;
+    const cd p1{P1[rowp + j], cplx ? P1[rowp + j + 1] : 0.0};
+    const cd p2{P2[rowp + j], cplx ? P2[rowp + j + 1] : 0.0};
+    const cd vA = cmul(cd{dl * (p1.r + sA * p2.r), dl * (p1.i + sA * p2.i)}, gA);
+    const cd vB = cmul(cd{dl * (p1.r - sA * p2.r), dl * (p1.i - sA * p2.i)}, gB);
+    Hr[j] = vA.r;
+    Hr[n + j] = vB.r;
+    if (cplx) {
+      Hr[j + 1] = vA.i;
+      Hr[n + j + 1] = vB.i;
+    }
+  }
+}
+
+void launch_build_Hdepth(const OrderBatch& b, double tau, int down, const double* P1,
+                         const double* P2, const double* lam_re, const double* lam_im,
+                         const double* pts, double* H, cudaStream_t s) {
+  dim3 grid((b.n + 127) / 128, b.n_out, b.n_units);
+  k_build_Hdepth<<<grid, 128, 0, s>>>(b.N, b.n, b.n_in, b.n_out, b.tau, tau, down, P1, P2, lam_re,
+                                      lam_im, pts, H);
+}
+
+// Depth factor of the particular and direct parts (e^{-t/mu0} sources), y = 1/mu0:
+//   upward x e^{-y tau} D(0, x + y; tau0 - tau),  downward x D(y, x; tau).
+__device__ inline double g0_depth(double x, double y, double tau0, double tau, int down) {
+  auto dd = [](double a, double b, double T) {
+    const double d = b - a;
+    if (d == 0.0) return T * exp(-a * T);
+    if (fabs(d * T) < 1e-2) return exp(-a * T) * -expm1(-d * T) / d;
+    return (exp(-a * T) - exp(-b * T)) / d;
+  };
+  return down ? x * dd(y, x, tau) : x * exp(-y * tau) * dd(0.0, x + y, tau0 - tau);
+}
+
+// Order radiance at depth tau into Isyn[m][k][o][a][s]:
+//   upward:   Tdep + g0u (U+ s + U- d)      (+ the base's radiance, added by k_base_recon)
+//   downward: Tdep + g0d D (U+ s - U- d) + e^{-tau/mu_o} R_F(mu_o) I(0, +mu_o),
+// Tdep = [homogeneous part + direct part] at depth tau, Q = U+ s + U- d or U+ s - U- d, and
+// I(0, +mu_o) = T1 + g0(tau = 0) Qp the upward radiance at the top (T1: its homogeneous and
+// direct parts).
+__global__ void k_depth_combine(OrderBatch b, double tau, int down, const double* Tdep,
+                                const double* Q, const double* T1, const double* Qp,
+                                const double* pts, const double* rout4, double* Isyn) {
+  const int R = 4 * b.n_in, Ro = 4 * b.n_out;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = blockIdx.y, u = blockIdx.z;
+  if (c >= R) return;
+  const int k = c >> 2, s = c & 3;
+  const double x = 1.0 / pts[b.N + b.n_in + o], y = 1.0 / pts[b.N + k];
+  const double g = g0_depth(x, y, b.tau, tau, down);
+  const size_t base = (size_t)u * Ro * R;
+  double top[4] = {0.0, 0.0, 0.0, 0.0};
+  if (down) {
+    const double g0 = depth_factor(b.tau, 1.0 / x, 1.0 / y);
+    for (int e = 0; e < 4; ++e) {
+      const size_t idx = base + (size_t)(4 * o + e) * R + c;
+      top[e] = T1[idx] + g0 * Qp[idx];
+    }
+  }
+  const double att = exp(-x * tau);
+  const double* Rm = rout4 + 4 * o;
+  for (int a = 0; a < 4; ++a) {
+    const size_t idx = base + (size_t)(4 * o + a) * R + c;
+    double v = Tdep[idx];
+    if (down) {
+      double refl = 0.0;
+      for (int e = 0; e < 4; ++e) {
+        double r;
+        if (a < 2 && e < 2) r = a == e ? Rm[0] : Rm[1];
+        else if (a >= 2 && e >= 2) r = a == e ? Rm[2] : (a == 2 ? Rm[3] : -Rm[3]);
+        else r = 0.0;
+        refl += r * top[e];
+      }
+      v += g * (a < 2 ? 1.0 : -1.0) * Q[idx] + att * refl;
+    } else {
+      v += g * Q[idx];
+    }
+    Isyn[(((size_t)(b.m0 + u) * b.n_in + k) * b.n_out + o) * 16 + 4 * a + s] = v;
+  }
+}
+
+void launch_depth_combine(const OrderBatch& b, double tau, int down, const double* Tdep,
+                          const double* Q, const double* T1, const double* Qp, const double* pts,
+                          const double* rout4, double* Isyn, cudaStream_t s) {
+  dim3 grid((4 * b.n_in + 127) / 128, b.n_out, b.n_units);
+  k_depth_combine<<<grid, 128, 0, s>>>(b, tau, down, Tdep, Q, T1, Qp, pts, rout4, Isyn);
+}
+
+// ------------------------------------------------------------------ Lambertian base
+// Base reflection (Sec. 3.C) for the depolarizing Lambertian base of albedo rho (R_00 = 2 rho),
+// order 0 only: the upward radiance at the bottom is isotropic and unpolarized,
+//   I^0_I(tau0, +mu) = 2 rho sum_j alpha_j mu_j I^0_I(tau0, -mu_j) + (2 rho / pi) mu0 b_I e^{-tau0/mu0}
+// (b the beam column, whose order-0 Fourier part is b/pi in the Fourier convention of Eq. 12).
+// basev[col] = sum_j alpha_j mu_j I_I(tau0, -mu_j) of boundary-matrix column col (the decaying
+// modes give D phi+ e^{-kappa tau0}, the growing ones D phi-), real form; the bottom rows
+// 4i of K lose 2 rho basev (the reflected radiance moves to the left side).
+__global__ void k_base_K(int N, int n, double tau, double rho, const double* X, const double* Y,
+                         const double* lam_re, const double* lam_im, const double* mu_nodes,
+                         const double* w_nodes, double* K, double* basev) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n || lam_im[j] < 0.0) return;
+  const bool cplx = lam_im[j] > 0.0;
+  const cd kap = kappa_of(lam_re, lam_im, j);
+  const cd E = cexpv(cd{-kap.r * tau, -kap.i * tau});
+  cd vA{0.0, 0.0}, vB{0.0, 0.0};
+  for (int q = 0; q < N; ++q) {
+    const size_t idx = (size_t)(4 * q) * n + j;
+    const cd x{X[idx], cplx ? X[idx + 1] : 0.0}, y{Y[idx], cplx ? Y[idx + 1] : 0.0};
+    const double f = w_nodes[q] * mu_nodes[q];
+    const cd pp = cmul(cd{0.5 * (x.r + y.r), 0.5 * (x.i + y.i)}, E);
+    vA = cd{vA.r + f * pp.r, vA.i + f * pp.i};
+    vB = cd{vB.r + f * 0.5 * (x.r - y.r), vB.i + f * 0.5 * (x.i - y.i)};
+  }
+  basev[j] = vA.r;
+  basev[n + j] = vB.r;
+  if (cplx) {
+    basev[j + 1] = vA.i;
+    basev[n + j + 1] = vB.i;
+  }
+  const int n2 = 2 * n;
+  for (int i = 0; i < N; ++i) {
+    double* row = K + (size_t)(n + 4 * i) * n2;
+    row[j] -= 2.0 * rho * vA.r;
+    row[n + j] -= 2.0 * rho * vB.r;
+    if (cplx) {
+      row[j + 1] -= 2.0 * rho * vA.i;
+      row[n + j + 1] -= 2.0 * rho * vB.i;
+    }
+  }
+}
+
+// The reflected particular radiance and the reflected attenuated beam, for column c:
+//   zb[c] = 2 rho (sum_j alpha_j mu_j zm_I(j)[c]) e^{-tau0/mu0} + (2 rho / pi) mu0 b_I[c] e^{-tau0/mu0}
+// (zm = D (s - d)/2 the particular solution's downward radiance at tau = 0), added to the bottom
+// rows 4i of the right-hand side when add_rhs.
+__global__ void k_base_rhs(int N, int n, int R, long long sSD, double tau, double rho,
+                           const double* SD, const double* pts, const double* min4,
+                           const double* mu_nodes, const double* w_nodes, double* RHS,
+                           double* zb, int add_rhs) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  const double* sv = SD;
+  const double* dv = SD + (size_t)n * R;
+  double z = 0.0;
+  for (int q = 0; q < N; ++q) {
+    const size_t idx = (size_t)(4 * q) * R + c;
+    z += w_nodes[q] * mu_nodes[q] * 0.5 * (sv[idx] - dv[idx]);
+  }
+  const int k = c >> 2, s = c & 3;
+  const double mu0 = pts[N + k], att = exp(-tau / mu0);
+  const double bI = s == 0 ? min4[4 * k] : (s == 1 ? min4[4 * k + 1] : 0.0);
+  const double v = 2.0 * rho * z * att + 2.0 * rho / kPi * mu0 * bI * att;
+  zb[c] = v;
+  if (add_rhs)
+    for (int i = 0; i < N; ++i) RHS[(size_t)(n + 4 * i) * R + c] += v;
+}
+
+// The base's radiance at the bottom, I0b[c] = 2 rho basev . C[:, c] + zb[c] (the same at every
+// upward direction), attenuated along the exit path to the top and added to the order-0 upward
+// radiance there: out[(o, a)][c] += e^{-tau0/mu_o} M_out(o)_{a0} I0b[c] (M_out = identity when
+// mout4 is null). `isyn` selects the order-radiance layout Isyn[0][k][o][a][s] for out.
+__global__ void k_base_recon(int n, int N, int n_in, int n_out, double tau, double rho,
+                             const double* C, const double* basev, const double* zb,
+                             const double* pts, const double* mout4, double* out, int isyn) {
+  const int R = 4 * n_in;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int o = blockIdx.y;
+  if (c >= R) return;
+  double v = 0.0;
+  for (int col = 0; col < 2 * n; ++col) v += basev[col] * C[(size_t)col * R + c];
+  v = 2.0 * rho * v + zb[c];
+  const double att = exp(-tau / pts[N + n_in + o]) * v;
+  const double m0 = mout4 ? mout4[4 * o] : 1.0, m1 = mout4 ? mout4[4 * o + 1] : 0.0;
+  const int k = c >> 2, s = c & 3;
+  if (isyn) {
+    const size_t base = ((size_t)k * n_out + o) * 16;
+    out[base + s] += m0 * att;
+    out[base + 4 + s] += m1 * att;
+  } else {
+    out[(size_t)(4 * o) * R + c] += m0 * att;
+    out[(size_t)(4 * o + 1) * R + c] += m1 * att;
+  }
+}
+
+void launch_base_K(int N, int n, double tau, double rho, const double* X, const double* Y,
+                   const double* lam_re, const double* lam_im, const double* mu_nodes,
+                   const double* w_nodes, double* K, double* basev, cudaStream_t s) {
+  k_base_K<<<(n + 127) / 128, 128, 0, s>>>(N, n, tau, rho, X, Y, lam_re, lam_im, mu_nodes, w_nodes,
+                                           K, basev);
+}
+void launch_base_rhs(int N, int n, int R, long long sSD, double tau, double rho, const double* SD,
+                     const double* pts, const double* min4, const double* mu_nodes,
+                     const double* w_nodes, double* RHS, double* zb, int add_rhs, cudaStream_t s) {
+  k_base_rhs<<<(R + 127) / 128, 128, 0, s>>>(N, n, R, sSD, tau, rho, SD, pts, min4, mu_nodes,
+                                             w_nodes, RHS, zb, add_rhs);
+}
+void launch_base_recon(int n, int N, int n_in, int n_out, double tau, double rho, const double* C,
+                       const double* basev, const double* zb, const double* pts,
+                       const double* mout4, double* out, int isyn, cudaStream_t s) {
+  dim3 grid((4 * n_in + 127) / 128, n_out);
+  k_base_recon<<<grid, 128, 0, s>>>(n, N, n_in, n_out, tau, rho, C, basev, zb, pts, mout4, out,
+                                    isyn);
+}
+
 }  // namespace vrte

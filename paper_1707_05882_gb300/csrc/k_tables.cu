@@ -162,6 +162,33 @@ __global__ void k_interface_dn(int N, int n_in, int n_out, double nif, const dou
   dst[3] = b.d.d;
 }
 
+// Transmission table (radiance leaving the bottom downward, no interface there): the outgoing
+// points are the internal cosines as given, their exit block is the identity, and rout4[o]
+// is the internal specular reflection at the top at that cosine (zero for a bare top), which
+// sends the upward radiance at mu_out back down through the layer.
+__global__ void k_btdf_points(int N, int n_in, int n_out, double nif, const double* mu_out,
+                              double* pts, double* mout4, double* rout4) {
+  int o = blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= n_out) return;
+  Blk4<double> r;
+  pts[N + n_in + o] = interface_point<double>(o, n_out, 0, nif, nif > 1.0, mu_out, nullptr,
+                                              nullptr, r);
+  mout4[4 * o + 0] = 1.0;
+  mout4[4 * o + 1] = 0.0;
+  mout4[4 * o + 2] = 1.0;
+  mout4[4 * o + 3] = 0.0;
+  rout4[4 * o + 0] = r.a;
+  rout4[4 * o + 1] = r.b;
+  rout4[4 * o + 2] = r.c;
+  rout4[4 * o + 3] = r.d;
+}
+
+void launch_btdf_points(int N, int n_in, int n_out, double nif, const double* mu_out, double* pts,
+                        double* mout4, double* rout4, cudaStream_t s) {
+  k_btdf_points<<<(n_out + 127) / 128, 128, 0, s>>>(N, n_in, n_out, nif, mu_out, pts, mout4,
+                                                    rout4);
+}
+
 void launch_interface(int N, int n_in, int n_out, double nif, const double* mu_nodes,
                       const double* mu_in, const double* mu_out, double* pts, double* min4,
                       double* mout4, double* rtop4, cudaStream_t s) {

@@ -74,6 +74,11 @@ struct Work {
   double* Isyn = nullptr;   // [M_max][n_in][n_out][16]; the adjoint keeps Ibar here
   // adjoint (VRTE_FLAG_ADJOINT): per-unit workspace carved per layer, and per-layer data
   double* bw = nullptr;
+  // transmission (VRTE_FLAG_TRANSMISSION): [U][Ro][R] each, and the top reflection at mu_out
+  double *Qp = nullptr, *Qb = nullptr, *Tbot = nullptr, *Tup = nullptr, *rout4 = nullptr;
+  double* Isyn2 = nullptr;  // upward order radiances when both radiance tables are solved
+  // Lambertian base: column sums of the bottom radiance [2n] and the reflected source [R]
+  double* basebuf = nullptr;
   double *dpts = nullptr, *dmin4 = nullptr, *dmout4 = nullptr, *drtop4 = nullptr,
          *acc = nullptr;
   double* g0tab = nullptr;  // [n_out][n_in] depth factors of the layer
@@ -255,7 +260,7 @@ vrte_status vrte_plan_create(const vrte_plan_desc* d, vrte_plan** out) {
       d->n_orders_max > 1024 || d->n_coef_max < 1 || d->n_coef_max > 1024 ||
       d->n_layers_max < 1 || d->n_mu_in < 1 || d->n_mu_in > 16384 || d->n_mu_out < 1 ||
       d->n_mu_out > 16384 || d->n_phi < 1 || !d->mu_in || !d->mu_out || !d->phi ||
-      (d->flags & ~(VRTE_FLAG_PROFILE | VRTE_FLAG_ADJOINT)) != 0)
+      (d->flags & ~(VRTE_FLAG_PROFILE | VRTE_FLAG_ADJOINT | VRTE_FLAG_TRANSMISSION)) != 0)
     return VRTE_ERR_INVALID_ARG;
   if (d->precision != VRTE_FP64 && d->precision != VRTE_MIXED) return VRTE_ERR_INVALID_ARG;
   for (int i = 0; i < d->n_mu_in; ++i)
@@ -302,6 +307,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   for (int b = 0; b < n_layers; ++b) {
     const vrte_layer& l = hp[b];
     if (!(l.tau > 0.0) || !(l.omega >= 0.0 && l.omega < 1.0) || !(l.n_interface <= 3.0) ||
+        !(l.base_albedo >= 0.0 && l.base_albedo <= 1.0) ||
         l.n_nodes < 1 || l.n_nodes > p->desc.n_nodes_max || l.n_orders < 1 ||
         l.n_orders > p->desc.n_orders_max || l.n_coef < 1 || l.n_coef > p->desc.n_coef_max)
       return VRTE_ERR_INVALID_ARG;
@@ -353,6 +359,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
                     n * kd + kd * 2 * n + 2 * kd * R;
   const bool adjoint = (p->desc.flags & VRTE_FLAG_ADJOINT) != 0;
   if (adjoint) per_unit += bw_carve(nullptr, 1, n, R, Ro, Lx, P, nullptr);
+  const bool transmission = (p->desc.flags & VRTE_FLAG_TRANSMISSION) != 0;
+  if (transmission) per_unit += 4 * Ro * R;
   size_t isyn = (size_t)Mx * p->n_in * p->n_out * 16;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
@@ -360,7 +368,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   // radiances and workspace, as long as every slot still takes all of a layer's orders in
   // one batch. The order radiances must fit; the per-order workspace takes at most 35% of
   // what is left (capped at 96 GiB) so that the caller's output table still fits beside it.
-  const size_t fixed_slot = (isyn + (size_t)p->n_in * p->n_out) * sizeof(double);
+  const size_t fixed_slot =
+      ((transmission ? 2 : 1) * isyn + (size_t)p->n_in * p->n_out) * sizeof(double);
   int nslots = std::max(1, std::min(n_layers, kMaxSlots));
   size_t U = 0;
   for (;; --nslots) {
@@ -420,6 +429,11 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
     }
   }
   VRTE_ALLOC(Isyn, isyn)
+  VRTE_ALLOC(basebuf, 2 * n + R)
+  if (transmission) {
+    VRTE_ALLOC(Qp, U * Ro * R) VRTE_ALLOC(Qb, U * Ro * R) VRTE_ALLOC(Tbot, U * Ro * R)
+    VRTE_ALLOC(Tup, U * Ro * R) VRTE_ALLOC(rout4, 4 * (size_t)p->n_out) VRTE_ALLOC(Isyn2, isyn)
+  }
   if (adjoint) {
     VRTE_ALLOC(bw, bw_carve(nullptr, U, n, R, Ro, Lx, P, nullptr))
     VRTE_ALLOC(dpts, P) VRTE_ALLOC(dmin4, 4 * (size_t)p->n_in) VRTE_ALLOC(dmout4, 4 * (size_t)p->n_out)
@@ -513,6 +527,9 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
   {
     StageScope sc(p, ST_MODES, s, 3, 16.0 * dn * dn * dn * dU, 8.0 * 12 * dn * dn * dU);
     launch_build_K(ob, w->X, w->Y, w->lam_re, w->lam_im, w->d_rtop4, w->K, s);
+    if (ly.base_albedo > 0.0 && m0 == 0)
+      launch_base_K(N, n, ly.tau, ly.base_albedo, w->X, w->Y, w->lam_re, w->lam_im, w->d_mu_nodes,
+                    w->d_w_nodes, w->K, w->basebuf, s);
     batched_inverse(2 * n, w->K, w->Kinv, U, p->d_status, s);
     batched_inverse(n, w->X, w->Xinv, U, p->d_status, s);
   }
@@ -543,6 +560,9 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
     gemm(n, R, n, w->E, n, nn, w->SD, R, ob.sSD, 0.0, w->Es, R, nR);
     launch_particular_sd(ob, w->Pb, w->Es, w->d_pts, w->SD, s);
     launch_bc_rhs(ob, w->SD, nullptr, w->d_rtop4, w->d_pts, w->RHS, s);
+    if (ly.base_albedo > 0.0 && m0 == 0)
+      launch_base_rhs(N, n, R, ob.sSD, ly.tau, ly.base_albedo, w->SD, w->d_pts, w->d_min4,
+                      w->d_mu_nodes, w->d_w_nodes, w->RHS, w->basebuf + 2 * n, 1, s);
   }
   {
     StageScope sc(p, ST_BC_SOLVE, s, gl, 2.0 * 4 * dn * dn * dR * dU,
@@ -610,6 +630,10 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                    w->g0tab, kSliceEps, kRefineTol, w->rscratch, w->rcount, w->rlist,
                    U * p->n_in, w->Isyn, s);
   }
+  // Lambertian base: its isotropic radiance at the bottom, attenuated to the top (order 0)
+  if (ly.base_albedo > 0.0 && m0 == 0)
+    launch_base_recon(n, N, p->n_in, p->n_out, ly.tau, ly.base_albedo, w->C, w->basebuf,
+                      w->basebuf + 2 * n, w->d_pts, w->d_mout4, w->Isyn, 1, s);
 }
 
 // Adjoint of one order batch (forward factors of the batch already in the slot's buffers,
@@ -871,6 +895,141 @@ vrte_status vrte_solve_brdf(vrte_plan* p, void* d_brdf, int out_dtype, void* str
   return run_solve(p, p->d_coeffs, d_brdf, out_dtype, s);
 }
 
+// Radiance tables at depth taus[lb] of every layer (upward into d_up, downward into d_down;
+// either may be null): the FP64 form of the order batches, then the reconstruction at that
+// depth (k_modes.cu) and the plan's synthesis.
+static vrte_status solve_depth(vrte_plan* p, const double* taus, void* d_up, void* d_down,
+                               int out_dtype, cudaStream_t s0) {
+  const int ns = p->nslots;
+  if (ns > 1) {
+    if (cudaEventRecord(p->fork, s0) != cudaSuccess) return VRTE_ERR_CUDA;
+    for (int k = 0; k < ns; ++k)
+      if (cudaStreamWaitEvent(p->ws[k].stream, p->fork, 0) != cudaSuccess) return VRTE_ERR_CUDA;
+  }
+  const size_t table = (size_t)p->n_in * p->n_out * p->n_phi * 16;
+  const size_t esz = out_dtype == VRTE_OUT_F64 ? sizeof(double) : sizeof(float);
+  const int R = 4 * p->n_in, Ro = 4 * p->n_out;
+  const bool mixed = p->desc.precision == VRTE_MIXED;
+  vrte_status result = VRTE_OK;
+  for (int lb = 0; lb < p->n_layers && result == VRTE_OK; ++lb) {
+    Work* w = &p->ws[lb % ns];
+    cudaStream_t s = ns > 1 ? w->stream : s0;
+    p->last_slot = lb % ns;
+    const vrte_layer& ly = p->layers[lb];
+    const int N = ly.n_nodes, n = 4 * N, L = ly.n_coef;
+    const int Meff = std::min(ly.n_orders, ly.n_coef);
+    const int P = N + p->n_in + p->n_out;
+    const double tau = taus[lb];
+    const double* coef = p->d_coeffs + (size_t)lb * p->desc.n_coef_max * 6;
+    // upward orders go to Isyn2 when both tables are wanted
+    double* Iup = d_down ? w->Isyn2 : w->Isyn;
+    {
+      StageScope sc(p, ST_TABLES, s, 4, 0.0, 0.0);
+      launch_gauss_nodes(N, w->d_mu_nodes, w->d_w_nodes, p->d_status, s);
+      launch_interface(N, p->n_in, p->n_out, ly.n_interface, w->d_mu_nodes, p->d_mu_in,
+                       p->d_mu_out, w->d_pts, w->d_min4, w->d_mout4, w->d_rtop4, s);
+      launch_btdf_points(N, p->n_in, p->n_out, ly.n_interface, p->d_mu_out, w->d_pts, w->d_mout4,
+                         w->rout4, s);
+      launch_depth_table(N, p->n_in, p->n_out, ly.tau, w->d_pts, w->g0tab, s);
+    }
+    for (int m0 = 0; m0 < Meff; m0 += p->chunk) {
+      const int U = std::min(p->chunk, Meff - m0);
+      run_order_batch(p, w, ly, coef, m0, U, false, false, s);
+      OrderBatch ob{N, n, L, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef, p->d_status,
+                    2 * n, 2LL * n * R};
+      const long long nR = (long long)n * R, RoR = (long long)Ro * R, Ro2n = (long long)Ro * 2 * n;
+      const bool base = ly.base_albedo > 0.0 && m0 == 0;
+      StageScope sc(p, ST_RECON_HOM, s, 12, 2.0 * U * (double)Ro * R * 2 * n * 5,
+                    8.0 * U * 8.0 * Ro * R);
+      // upward radiance at the top (identity exit): T1 = direct + Hhat C (+ the base's
+      // radiance), and Qp = U+ s + U- d
+      dgemm_batched(Ro, R, 2 * n, 1.0, w->Hhat, 2 * n, Ro2n, w->C, R, 2 * nR, 1.0, w->T1, R, RoR, U,
+                    s);
+      if (base)
+        launch_base_recon(n, N, p->n_in, p->n_out, ly.tau, ly.base_albedo, w->C, w->basebuf,
+                          w->basebuf + 2 * n, w->d_pts, nullptr, w->T1, 0, s);
+      dgemm_batched(Ro, R, 2 * n, 1.0, w->Upm, 2 * n, Ro2n, w->SD, R, 2 * nR, 0.0, w->Qp, R, RoR,
+                    U, s);
+      if (d_up) {
+        launch_assemble_direct_depth(ob, tau, 0, w->gp, w->gr, w->gt, w->d_pts, w->d_min4, w->Tup,
+                                     s);
+        launch_build_Hdepth(ob, tau, 0, w->P1, w->P2, w->lam_re, w->lam_im, w->d_pts, w->Hhat, s);
+        dgemm_batched(Ro, R, 2 * n, 1.0, w->Hhat, 2 * n, Ro2n, w->C, R, 2 * nR, 1.0, w->Tup, R, RoR,
+                      U, s);
+        launch_depth_combine(ob, tau, 0, w->Tup, w->Qp, w->T1, w->Qp, w->d_pts, w->rout4, Iup, s);
+        if (base)
+          launch_base_recon(n, N, p->n_in, p->n_out, ly.tau - tau, ly.base_albedo, w->C,
+                            w->basebuf, w->basebuf + 2 * n, w->d_pts, nullptr, Iup, 1, s);
+      }
+      if (d_down) {
+        // Qb = U+ s - U- d; Tbot = direct + Hdepth C at depth tau, downward
+        dgemm_batched(Ro, R, n, 1.0, w->Upm, 2 * n, Ro2n, w->SD, R, 2 * nR, 0.0, w->Qb, R, RoR, U,
+                      s);
+        dgemm_batched(Ro, R, n, -1.0, w->Upm + n, 2 * n, Ro2n, w->SD + nR, R, 2 * nR, 1.0, w->Qb, R,
+                      RoR, U, s);
+        launch_assemble_direct_depth(ob, tau, 1, w->gp, w->gr, w->gt, w->d_pts, w->d_min4, w->Tbot,
+                                     s);
+        launch_build_Hdepth(ob, tau, 1, w->P1, w->P2, w->lam_re, w->lam_im, w->d_pts, w->Hhat, s);
+        dgemm_batched(Ro, R, 2 * n, 1.0, w->Hhat, 2 * n, Ro2n, w->C, R, 2 * nR, 1.0, w->Tbot, R,
+                      RoR, U, s);
+        launch_depth_combine(ob, tau, 1, w->Tbot, w->Qb, w->T1, w->Qp, w->d_pts, w->rout4, w->Isyn,
+                             s);
+      }
+    }
+    if (cudaPeekAtLastError() != cudaSuccess) {
+      cudaGetLastError();
+      result = VRTE_ERR_CUDA;
+      break;
+    }
+    for (int q = 0; q < 2; ++q) {
+      void* dst = q == 0 ? d_up : d_down;
+      if (!dst) continue;
+      const double* src = q == 0 ? Iup : w->Isyn;
+      char* outb = (char*)dst + (size_t)lb * table * esz;
+      StageScope sc(p, ST_SYNTHESIS, s, 1, 2.0 * table * Meff, (double)table * esz);
+      if (mixed)
+        tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, src, p->d_wc, p->d_ws, outb, out_dtype,
+                     kSynthBlock, w->tcw, p->d_status, s);
+      else
+        launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, src, p->d_wc, p->d_ws, outb,
+                              out_dtype, p->d_status, s);
+    }
+  }
+  if (ns > 1)
+    for (int k = 0; k < ns; ++k)
+      if (cudaEventRecord(p->ws[k].done, p->ws[k].stream) != cudaSuccess ||
+          cudaStreamWaitEvent(s0, p->ws[k].done, 0) != cudaSuccess)
+        result = VRTE_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return VRTE_ERR_CUDA;
+  return result;
+}
+
+vrte_status vrte_solve_radiance(vrte_plan* p, const double* h_tau, void* d_up, void* d_down,
+                                int out_dtype, void* stream) {
+  if (!p || !h_tau || (!d_up && !d_down)) return VRTE_ERR_INVALID_ARG;
+  if (out_dtype != VRTE_OUT_F32 && out_dtype != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
+  if (!(p->desc.flags & VRTE_FLAG_TRANSMISSION) || p->n_layers < 1 || !p->d_coeffs ||
+      !p->ws[0].Tbot)
+    return VRTE_ERR_STATE;
+  for (int lb = 0; lb < p->n_layers; ++lb)
+    if (!(h_tau[lb] >= 0.0 && h_tau[lb] <= p->layers[lb].tau)) return VRTE_ERR_INVALID_ARG;
+  std::vector<double> taus(h_tau, h_tau + p->n_layers);
+  p->last_stream = (cudaStream_t)stream;
+  return solve_depth(p, taus.data(), d_up, d_down, out_dtype, (cudaStream_t)stream);
+}
+
+vrte_status vrte_solve_btdf(vrte_plan* p, void* d_btdf, int out_dtype, void* stream) {
+  if (!p || !d_btdf) return VRTE_ERR_INVALID_ARG;
+  if (out_dtype != VRTE_OUT_F32 && out_dtype != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
+  if (!(p->desc.flags & VRTE_FLAG_TRANSMISSION) || p->n_layers < 1 || !p->d_coeffs ||
+      !p->ws[0].Tbot)
+    return VRTE_ERR_STATE;
+  std::vector<double> taus(p->n_layers);
+  for (int lb = 0; lb < p->n_layers; ++lb) taus[lb] = p->layers[lb].tau;
+  p->last_stream = (cudaStream_t)stream;
+  return solve_depth(p, taus.data(), nullptr, d_btdf, out_dtype, (cudaStream_t)stream);
+}
+
 vrte_status vrte_solve_brdf_host(vrte_plan* p, const double* h_coeffs, void* h_brdf,
                                  int out_dtype, void* stream) {
   if (!p || !h_coeffs || !h_brdf) return VRTE_ERR_INVALID_ARG;
@@ -947,6 +1106,8 @@ vrte_status vrte_brdf_backward(vrte_plan* p, const void* g, int gd, double* d_gr
   if (gd != VRTE_OUT_F32 && gd != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
   if (!(p->desc.flags & VRTE_FLAG_ADJOINT) || p->n_layers < 1 || !p->ws[0].bw)
     return VRTE_ERR_STATE;
+  for (const vrte_layer& l : p->layers)
+    if (l.base_albedo > 0.0) return VRTE_ERR_UNSUPPORTED;
   cudaStream_t s0 = (cudaStream_t)stream;
   p->last_stream = s0;
   const int ns = p->nslots;

@@ -270,6 +270,30 @@ void launch_build_Hhat(const OrderBatch& b, const double* P1, const double* P2,
                        const double* lam_re, const double* lam_im, const double* pts,
                        double* Hhat, cudaStream_t s);
 
+// ---------------------------------------------------------------- Lambertian base (k_modes.cu)
+void launch_base_K(int N, int n, double tau, double rho, const double* X, const double* Y,
+                   const double* lam_re, const double* lam_im, const double* mu_nodes,
+                   const double* w_nodes, double* K, double* basev, cudaStream_t s);
+void launch_base_rhs(int N, int n, int R, long long sSD, double tau, double rho, const double* SD,
+                     const double* pts, const double* min4, const double* mu_nodes,
+                     const double* w_nodes, double* RHS, double* zb, int add_rhs, cudaStream_t s);
+void launch_base_recon(int n, int N, int n_in, int n_out, double tau, double rho, const double* C,
+                       const double* basev, const double* zb, const double* pts,
+                       const double* mout4, double* out, int isyn, cudaStream_t s);
+
+// ---------------------------------------------------------------- radiance at depth tau
+void launch_btdf_points(int N, int n_in, int n_out, double nif, const double* mu_out, double* pts,
+                        double* mout4, double* rout4, cudaStream_t s);
+void launch_assemble_direct_depth(const OrderBatch& b, double tau, int down, const double* p,
+                                  const double* r, const double* t, const double* pts,
+                                  const double* min4, double* T, cudaStream_t s);
+void launch_build_Hdepth(const OrderBatch& b, double tau, int down, const double* P1,
+                         const double* P2, const double* lam_re, const double* lam_im,
+                         const double* pts, double* H, cudaStream_t s);
+void launch_depth_combine(const OrderBatch& b, double tau, int down, const double* Tdep,
+                          const double* Q, const double* T1, const double* Qp, const double* pts,
+                          const double* rout4, double* Isyn, cudaStream_t s);
+
 // ---------------------------------------------------------------- synthesis (k_synth.cu)
 void launch_synthesis_fp64(int M, int n_in, int n_out, int n_phi, const double* Isyn,
                            const double* wc, const double* ws, void* out, int out_dtype,

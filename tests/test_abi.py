@@ -49,10 +49,37 @@ def test_null_arguments_are_rejected_without_device_work():
     lib.vrte_destroy(None)
 
 
-def test_plan_descriptor_layout_matches_header():
-    # 7 ints, 3 pointers, int + unsigned: offsets follow the C struct in vrte.h
-    assert vr.PlanDesc.mu_in.offset == 32
-    assert ctypes.sizeof(vr.Layer) == 40
+def test_plan_descriptor_layout_matches_header(tmp_path):
+    """The ctypes mirrors of vrte_plan_desc, vrte_layer and vrte_stage_stat have the sizes and
+    field offsets that a C compiler gives the structs of include/vrte.h."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "layout.c"
+    src.write_text("""#include <stdio.h>
+#include <stddef.h>
+#include "vrte.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(vrte_plan_desc), offsetof(vrte_plan_desc, mu_in),
+         offsetof(vrte_plan_desc, precision), offsetof(vrte_plan_desc, flags));
+  printf("%zu %zu %zu\\n", sizeof(vrte_layer), offsetof(vrte_layer, n_nodes),
+         offsetof(vrte_layer, base_albedo));
+  printf("%zu %zu\\n", sizeof(vrte_stage_stat), offsetof(vrte_stage_stat, tc_flops));
+  return 0;
+}
+""")
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    vals = [list(map(int, line.split())) for line in
+            subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+            if line.strip()]
+    assert vals[0] == [ctypes.sizeof(vr.PlanDesc), vr.PlanDesc.mu_in.offset,
+                       vr.PlanDesc.precision.offset, vr.PlanDesc.flags.offset]
+    assert vals[1] == [ctypes.sizeof(vr.Layer), vr.Layer.n_nodes.offset, vr.Layer.base_albedo.offset]
+    assert vals[2] == [ctypes.sizeof(vr.StageStat), vr.StageStat.tc_flops.offset]
 
 
 def test_sliced_gemm_workspace_sizes_without_gpu():

@@ -150,9 +150,14 @@ def test_host_buffer_entry_point_matches_device_entry_point():
     dev = torch.empty(plan.table_shape, dtype=torch.float32, device="cuda")
     plan.solve(dev)
     torch.cuda.synchronize()
+    # pinned and pageable host buffers
     h_coef = torch.from_numpy(coef).pin_memory()
     h_out = torch.empty(plan.table_shape, dtype=torch.float32).pin_memory()
     plan.solve_host(h_coef, h_out)
     assert plan.status() == 0
     assert torch.equal(h_out, dev.cpu())
+    h_page = torch.full(plan.table_shape, float("nan"), dtype=torch.float32)
+    plan.solve_host(torch.from_numpy(coef.copy()), h_page)
+    assert plan.status() == 0
+    assert torch.equal(h_page, dev.cpu())
     plan.close()
