@@ -96,6 +96,11 @@ typedef struct {
 /* Allocates, in vrte_set_layer, the workspace of the transmission table (vrte_solve_btdf). */
 #define VRTE_FLAG_TRANSMISSION 4u
 
+/* Allocates, in vrte_set_layer, the workspace of a multi-layer slab made of the layers set
+ * (vrte_solve_slab_brdf): per sub-layer and order of a batch, the block elimination's
+ * factors. The plan then runs one slot (no concurrent layers). */
+#define VRTE_FLAG_SLAB 8u
+
 /* Per-stage statistics accumulated since the last vrte_profile_reset. */
 typedef struct {
   char name[24];        /* stage name, e.g. "eigen", "recon_gemm", "synthesis" */
@@ -184,6 +189,24 @@ vrte_status vrte_solve_btdf(vrte_plan* plan, void* d_btdf, int out_dtype, void* 
  * VRTE_ERR_STATE); a depth outside [0, tau0] gives VRTE_ERR_INVALID_ARG. */
 vrte_status vrte_solve_radiance(vrte_plan* plan, const double* h_tau, void* d_up, void* d_down,
                                 int out_dtype, void* stream);
+
+/* BRDF table of ONE slab whose sub-layers are the n_layers layers of the last vrte_set_layer,
+ * top first (sub-layer k spans the optical depths [t_k, t_k + tau_k], t_k the sum of the
+ * thicknesses above it), each with its own expansion coefficients, albedo and thickness:
+ *   d_brdf[n_mu_in][n_mu_out][n_phi][4][4]  (one table; layout and units as vrte_solve_brdf).
+ * The first sub-layer's n_interface is the slab's smooth top and the last one's base_albedo
+ * its Lambertian base; the other sub-layers must have n_interface <= 1 and base_albedo 0, and
+ * all must share n_nodes and n_orders (else VRTE_ERR_INVALID_ARG). Orders at or beyond a
+ * sub-layer's n_coef see it as a purely attenuating layer. Paper: Sec. 2.C, multiple layer
+ * materials: a homogeneous solution and a particular solution per sub-layer (for the beam
+ * attenuated to the sub-layer's top), 8N more unknowns per sub-layer, and 8N continuity
+ * equations of the radiance at every boundary between two sub-layers, with the top and
+ * bottom conditions of Sec. 2.C; the upward radiance at the top is the sum of the
+ * sub-layers' reconstructions (Eqs. 36-38), each attenuated through the sub-layers above.
+ * Solved in FP64 (block elimination of the block-tridiagonal system from the top, one
+ * sub-layer at a time) with the plan's synthesis; requires a plan created with
+ * VRTE_FLAG_SLAB (else VRTE_ERR_STATE). Asynchronous; no allocation. */
+vrte_status vrte_solve_slab_brdf(vrte_plan* plan, void* d_brdf, int out_dtype, void* stream);
 
 /* Same solve as vrte_solve_brdf (same passages) with host buffers: copies h_coeffs (host
  * FP64, layout as d_coeffs

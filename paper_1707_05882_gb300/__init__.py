@@ -24,7 +24,7 @@ STATUS_NAMES = {
 }
 
 EXPORTED = ["vrte_plan_create", "vrte_set_layer", "vrte_solve_brdf", "vrte_solve_brdf_host",
-            "vrte_solve_btdf", "vrte_solve_radiance",
+            "vrte_solve_btdf", "vrte_solve_radiance", "vrte_solve_slab_brdf",
             "vrte_brdf_backward", "vrte_plan_status", "vrte_profile_stages", "vrte_profile_reset",
             "vrte_debug_copy", "vrte_eigen_noalloc", "vrte_gemm_sliced", "vrte_gemm_sliced_workspace",
             "vrte_workspace_bytes", "vrte_destroy", "vrte_status_string"]
@@ -49,6 +49,7 @@ class PlanDesc(ctypes.Structure):
 VRTE_FLAG_PROFILE = 1
 VRTE_FLAG_ADJOINT = 2
 VRTE_FLAG_TRANSMISSION = 4
+VRTE_FLAG_SLAB = 8
 
 
 class StageStat(ctypes.Structure):
@@ -89,6 +90,7 @@ def load_library(build_if_missing: bool = True):
     lib.vrte_solve_brdf_host.argtypes = [P, P, P, ctypes.c_int, P]
     lib.vrte_solve_btdf.argtypes = [P, P, ctypes.c_int, P]
     lib.vrte_solve_radiance.argtypes = [P, P, P, P, ctypes.c_int, P]
+    lib.vrte_solve_slab_brdf.argtypes = [P, P, ctypes.c_int, P]
     lib.vrte_brdf_backward.argtypes = [P, P, ctypes.c_int, P, P]
     lib.vrte_plan_status.argtypes = [P]
     lib.vrte_profile_stages.argtypes = [P, ctypes.POINTER(StageStat), ctypes.c_int]
@@ -113,7 +115,8 @@ def load_library(build_if_missing: bool = True):
     lib.vrte_status_string.argtypes = [ctypes.c_int]
     lib.vrte_status_string.restype = ctypes.c_char_p
     for name in ["vrte_plan_create", "vrte_set_layer", "vrte_solve_brdf", "vrte_solve_brdf_host",
-                 "vrte_solve_btdf", "vrte_solve_radiance", "vrte_brdf_backward", "vrte_plan_status"]:
+                 "vrte_solve_btdf", "vrte_solve_radiance", "vrte_solve_slab_brdf",
+                 "vrte_brdf_backward", "vrte_plan_status"]:
         getattr(lib, name).restype = ctypes.c_int
     _LIB = lib
     return lib
@@ -140,7 +143,7 @@ class Plan:
 
     def __init__(self, mu_in, mu_out, dphi, n_nodes_max, n_orders_max, n_coef_max,
                  n_layers_max=1, precision=VRTE_FP64, profile=False, adjoint=False,
-                 transmission=False):
+                 transmission=False, slab=False):
         self.lib = load_library()
         self._mu_in = np.ascontiguousarray(mu_in, dtype=np.float64)
         self._mu_out = np.ascontiguousarray(mu_out, dtype=np.float64)
@@ -149,7 +152,8 @@ class Plan:
                      self._mu_in.size, self._mu_out.size, self._phi.size, _dptr(self._mu_in),
                      _dptr(self._mu_out), _dptr(self._phi), int(precision),
                      (VRTE_FLAG_PROFILE if profile else 0) | (VRTE_FLAG_ADJOINT if adjoint else 0)
-                     | (VRTE_FLAG_TRANSMISSION if transmission else 0))
+                     | (VRTE_FLAG_TRANSMISSION if transmission else 0)
+                     | (VRTE_FLAG_SLAB if slab else 0))
         h = ctypes.c_void_p()
         _check(self.lib.vrte_plan_create(ctypes.byref(d), ctypes.byref(h)), "vrte_plan_create")
         self.handle = h
@@ -188,6 +192,15 @@ class Plan:
         dt = VRTE_OUT_F64 if out.dtype == torch.float64 else VRTE_OUT_F32
         _check(self.lib.vrte_solve_btdf(self.handle, ctypes.c_void_p(out.data_ptr()), dt,
                                         _stream_handle(stream)), "vrte_solve_btdf")
+        return out
+
+    def solve_slab(self, out, stream=None):
+        """Writes the BRDF table of the slab made of the set layers, top first
+        (vrte_solve_slab_brdf), into the CUDA tensor `out` [n_in, n_out, n_phi, 4, 4]."""
+        import torch
+        dt = VRTE_OUT_F64 if out.dtype == torch.float64 else VRTE_OUT_F32
+        _check(self.lib.vrte_solve_slab_brdf(self.handle, ctypes.c_void_p(out.data_ptr()), dt,
+                                             _stream_handle(stream)), "vrte_solve_slab_brdf")
         return out
 
     def solve_radiance(self, taus, up=None, down=None, stream=None):

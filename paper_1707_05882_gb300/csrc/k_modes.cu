@@ -488,13 +488,14 @@ __global__ void k_base_K(int N, int n, double tau, double rho, const double* X, 
 }
 
 // The reflected particular radiance and the reflected attenuated beam, for column c:
-//   zb[c] = 2 rho (sum_j alpha_j mu_j zm_I(j)[c]) e^{-tau0/mu0} + (2 rho / pi) mu0 b_I[c] e^{-tau0/mu0}
+//   zb[c] = 2 rho (sum_j alpha_j mu_j zm_I(j)[c]) e^{-tau0/mu0} + (2 rho / pi) mu0 b_I[c] e^{-(t + tau0)/mu0}
+// (t = t_above, the depth of the layer's top in a slab: the beam reaches the base through it)
 // (zm = D (s - d)/2 the particular solution's downward radiance at tau = 0), added to the bottom
 // rows 4i of the right-hand side when add_rhs.
 __global__ void k_base_rhs(int N, int n, int R, long long sSD, double tau, double rho,
                            const double* SD, const double* pts, const double* min4,
                            const double* mu_nodes, const double* w_nodes, double* RHS,
-                           double* zb, int add_rhs) {
+                           double* zb, int add_rhs, double t_above) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= R) return;
   const double* sv = SD;
@@ -507,7 +508,7 @@ __global__ void k_base_rhs(int N, int n, int R, long long sSD, double tau, doubl
   const int k = c >> 2, s = c & 3;
   const double mu0 = pts[N + k], att = exp(-tau / mu0);
   const double bI = s == 0 ? min4[4 * k] : (s == 1 ? min4[4 * k + 1] : 0.0);
-  const double v = 2.0 * rho * z * att + 2.0 * rho / kPi * mu0 * bI * att;
+  const double v = 2.0 * rho * z * att + 2.0 * rho / kPi * mu0 * bI * exp(-(t_above + tau) / mu0);
   zb[c] = v;
   if (add_rhs)
     for (int i = 0; i < N; ++i) RHS[(size_t)(n + 4 * i) * R + c] += v;
@@ -548,9 +549,10 @@ void launch_base_K(int N, int n, double tau, double rho, const double* X, const 
 }
 void launch_base_rhs(int N, int n, int R, long long sSD, double tau, double rho, const double* SD,
                      const double* pts, const double* min4, const double* mu_nodes,
-                     const double* w_nodes, double* RHS, double* zb, int add_rhs, cudaStream_t s) {
+                     const double* w_nodes, double* RHS, double* zb, int add_rhs, cudaStream_t s,
+                     double t_above) {
   k_base_rhs<<<(R + 127) / 128, 128, 0, s>>>(N, n, R, sSD, tau, rho, SD, pts, min4, mu_nodes,
-                                             w_nodes, RHS, zb, add_rhs);
+                                             w_nodes, RHS, zb, add_rhs, t_above);
 }
 void launch_base_recon(int n, int N, int n_in, int n_out, double tau, double rho, const double* C,
                        const double* basev, const double* zb, const double* pts,

@@ -82,6 +82,12 @@ struct Work {
   double *dpts = nullptr, *dmin4 = nullptr, *dmout4 = nullptr, *drtop4 = nullptr,
          *acc = nullptr;
   double* g0tab = nullptr;  // [n_out][n_in] depth factors of the layer
+  // slab (VRTE_FLAG_SLAB), per sub-layer [S][U]: D'^-1 (2n x 2n), y then c (2n x R), Uup
+  // (n x 2n), Hhat (Ro x 2n); shared: Ldn and Pd of the previous and current sub-layer,
+  // Zt, Ldn W, a contraction and the slab's top radiance (Ro x R), Uup c (n x R)
+  double *sDinv = nullptr, *sY = nullptr, *sUup = nullptr, *sH = nullptr, *sL[2] = {},
+         *sPd[2] = {}, *sZt = nullptr, *sTnn = nullptr, *sTq = nullptr, *sAcc = nullptr,
+         *sV = nullptr;
   cudaStream_t stream = nullptr;  // own stream when the plan runs several slots
   cudaEvent_t done = nullptr;
 };
@@ -260,7 +266,8 @@ vrte_status vrte_plan_create(const vrte_plan_desc* d, vrte_plan** out) {
       d->n_orders_max > 1024 || d->n_coef_max < 1 || d->n_coef_max > 1024 ||
       d->n_layers_max < 1 || d->n_mu_in < 1 || d->n_mu_in > 16384 || d->n_mu_out < 1 ||
       d->n_mu_out > 16384 || d->n_phi < 1 || !d->mu_in || !d->mu_out || !d->phi ||
-      (d->flags & ~(VRTE_FLAG_PROFILE | VRTE_FLAG_ADJOINT | VRTE_FLAG_TRANSMISSION)) != 0)
+      (d->flags & ~(VRTE_FLAG_PROFILE | VRTE_FLAG_ADJOINT | VRTE_FLAG_TRANSMISSION |
+                    VRTE_FLAG_SLAB)) != 0)
     return VRTE_ERR_INVALID_ARG;
   if (d->precision != VRTE_FP64 && d->precision != VRTE_MIXED) return VRTE_ERR_INVALID_ARG;
   for (int i = 0; i < d->n_mu_in; ++i)
@@ -361,6 +368,11 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   if (adjoint) per_unit += bw_carve(nullptr, 1, n, R, Ro, Lx, P, nullptr);
   const bool transmission = (p->desc.flags & VRTE_FLAG_TRANSMISSION) != 0;
   if (transmission) per_unit += 4 * Ro * R;
+  const bool slab = (p->desc.flags & VRTE_FLAG_SLAB) != 0;
+  const size_t S_sub = (size_t)n_layers;
+  if (slab)
+    per_unit += S_sub * (4 * n * n + 2 * n * R + 2 * n * n + Ro * 2 * n) + 2 * 2 * n * n +
+                2 * n * R + n * R + n * n + 2 * Ro * R + n * R;
   size_t isyn = (size_t)Mx * p->n_in * p->n_out * 16;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
@@ -370,7 +382,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   // what is left (capped at 96 GiB) so that the caller's output table still fits beside it.
   const size_t fixed_slot =
       ((transmission ? 2 : 1) * isyn + (size_t)p->n_in * p->n_out) * sizeof(double);
-  int nslots = std::max(1, std::min(n_layers, kMaxSlots));
+  // a slab's sub-layers share one slot: its order batches run them in turn
+  int nslots = slab ? 1 : std::max(1, std::min(n_layers, kMaxSlots));
   size_t U = 0;
   for (;; --nslots) {
     size_t need_fixed = nslots * fixed_slot + ((size_t)64 << 20);
@@ -430,6 +443,14 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   }
   VRTE_ALLOC(Isyn, isyn)
   VRTE_ALLOC(basebuf, 2 * n + R)
+  if (slab) {
+    VRTE_ALLOC(sDinv, S_sub * U * 4 * n * n) VRTE_ALLOC(sY, S_sub * U * 2 * n * R)
+    VRTE_ALLOC(sUup, S_sub * U * 2 * n * n) VRTE_ALLOC(sH, S_sub * U * Ro * 2 * n)
+    VRTE_ALLOC(sL[0], U * 2 * n * n) VRTE_ALLOC(sL[1], U * 2 * n * n)
+    VRTE_ALLOC(sPd[0], U * n * R) VRTE_ALLOC(sPd[1], U * n * R) VRTE_ALLOC(sZt, U * n * R)
+    VRTE_ALLOC(sTnn, U * n * n) VRTE_ALLOC(sTq, U * Ro * R) VRTE_ALLOC(sAcc, U * Ro * R)
+    VRTE_ALLOC(sV, U * n * R)
+  }
   if (transmission) {
     VRTE_ALLOC(Qp, U * Ro * R) VRTE_ALLOC(Qb, U * Ro * R) VRTE_ALLOC(Tbot, U * Ro * R)
     VRTE_ALLOC(Tup, U * Ro * R) VRTE_ALLOC(rout4, 4 * (size_t)p->n_out) VRTE_ALLOC(Isyn2, isyn)
@@ -456,9 +477,12 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
 // One batch of U Fourier orders m0 .. m0+U-1 of layer `ly` through steps a0 (tables)
 // to a7 on stream s: the plan's precision when `mixed` follows it, else the FP64 form.
 // With `reconstruct` false the batch stops after the reconstruction operators (U+-, P1,
-// P2, Hhat and, in the FP64 form, the direct term in T1): what the adjoint needs.
+// P2, Hhat and, in the FP64 form, the direct term in T1): what the adjoint needs. With
+// `boundary` false it also leaves out the layer's own boundary system (K, its inverse, the
+// right-hand side and C): a slab solves one system for all of its sub-layers.
 static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const double* coef,
-                          int m0, int U, bool mixed, bool reconstruct, cudaStream_t s) {
+                          int m0, int U, bool mixed, bool reconstruct, cudaStream_t s,
+                          bool boundary = true) {
   const int N = ly.n_nodes, n = 4 * N, L = ly.n_coef;
   const int P = N + p->n_in + p->n_out;
   const int R = 4 * p->n_in, Ro = 4 * p->n_out;
@@ -493,7 +517,7 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
   };
   const double dn = n, dR = R, dRo = Ro, dU = U;
   double lsum = 0.0;  // sum over the batch of (L - m)
-  for (int u = 0; u < U; ++u) lsum += L - (m0 + u);
+  for (int u = 0; u < U; ++u) lsum += std::max(0, L - (m0 + u));
   {
     StageScope sc(p, ST_TABLES, s, 1, 30.0 * P * lsum, 24.0 * P * lsum);
     launch_gsf_tables(ob, w->d_pts, w->gp, w->gr, w->gt, s);
@@ -525,16 +549,20 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                          p->d_status, s);
   }
   {
-    StageScope sc(p, ST_MODES, s, 3, 16.0 * dn * dn * dn * dU, 8.0 * 12 * dn * dn * dU);
-    launch_build_K(ob, w->X, w->Y, w->lam_re, w->lam_im, w->d_rtop4, w->K, s);
-    if (ly.base_albedo > 0.0 && m0 == 0)
-      launch_base_K(N, n, ly.tau, ly.base_albedo, w->X, w->Y, w->lam_re, w->lam_im, w->d_mu_nodes,
-                    w->d_w_nodes, w->K, w->basebuf, s);
-    batched_inverse(2 * n, w->K, w->Kinv, U, p->d_status, s);
+    StageScope sc(p, ST_MODES, s, boundary ? 3 : 1,
+                  (boundary ? 16.0 : 2.0) * dn * dn * dn * dU,
+                  8.0 * (boundary ? 12 : 2) * dn * dn * dU);
+    if (boundary) {
+      launch_build_K(ob, w->X, w->Y, w->lam_re, w->lam_im, w->d_rtop4, w->K, s);
+      if (ly.base_albedo > 0.0 && m0 == 0)
+        launch_base_K(N, n, ly.tau, ly.base_albedo, w->X, w->Y, w->lam_re, w->lam_im,
+                      w->d_mu_nodes, w->d_w_nodes, w->K, w->basebuf, s);
+      batched_inverse(2 * n, w->K, w->Kinv, U, p->d_status, s);
+    }
     batched_inverse(n, w->X, w->Xinv, U, p->d_status, s);
   }
   {
-    StageScope sc(p, ST_PARTICULAR, s, mixed ? 7 + 6 * gl : 9,
+    StageScope sc(p, ST_PARTICULAR, s, (mixed ? 7 + 6 * gl : 9) - (boundary ? 0 : 1),
                   72.0 * N * p->n_in * lsum + 8.0 * dn * dn * dR * dU,
                   8.0 * 10 * dn * dR * dU);
     sc.tensor_flops(tcf * (4.0 * dn + 2.0 * kdir) * dn * dR * dU);
@@ -559,12 +587,14 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
     gemm(n, R, n, w->X, n, nn, w->Yv, R, nR, 0.0, w->SD, R, ob.sSD);
     gemm(n, R, n, w->E, n, nn, w->SD, R, ob.sSD, 0.0, w->Es, R, nR);
     launch_particular_sd(ob, w->Pb, w->Es, w->d_pts, w->SD, s);
-    launch_bc_rhs(ob, w->SD, nullptr, w->d_rtop4, w->d_pts, w->RHS, s);
-    if (ly.base_albedo > 0.0 && m0 == 0)
-      launch_base_rhs(N, n, R, ob.sSD, ly.tau, ly.base_albedo, w->SD, w->d_pts, w->d_min4,
-                      w->d_mu_nodes, w->d_w_nodes, w->RHS, w->basebuf + 2 * n, 1, s);
+    if (boundary) {
+      launch_bc_rhs(ob, w->SD, nullptr, w->d_rtop4, w->d_pts, w->RHS, s);
+      if (ly.base_albedo > 0.0 && m0 == 0)
+        launch_base_rhs(N, n, R, ob.sSD, ly.tau, ly.base_albedo, w->SD, w->d_pts, w->d_min4,
+                        w->d_mu_nodes, w->d_w_nodes, w->RHS, w->basebuf + 2 * n, 1, s);
+    }
   }
-  {
+  if (boundary) {
     StageScope sc(p, ST_BC_SOLVE, s, gl, 2.0 * 4 * dn * dn * dR * dU,
                   8.0 * (4 * dn * dn + 4 * dn * dR) * dU);
     sc.tensor_flops(tcf * 4.0 * dn * dn * dR * dU);
@@ -1028,6 +1058,168 @@ vrte_status vrte_solve_btdf(vrte_plan* p, void* d_btdf, int out_dtype, void* str
   for (int lb = 0; lb < p->n_layers; ++lb) taus[lb] = p->layers[lb].tau;
   p->last_stream = (cudaStream_t)stream;
   return solve_depth(p, taus.data(), nullptr, d_btdf, out_dtype, (cudaStream_t)stream);
+}
+
+// One slab made of the set layers, top first (Sec. 2.C, multi-layer materials): per order
+// batch the sub-layers' modes, particular solutions and reconstruction operators in turn
+// (FP64 form), each sub-layer's row block entering the block elimination of k_slab.cu as it
+// arrives; then back-substitution from the bottom, the sub-layers' top radiances summed with
+// the attenuation through the sub-layers above, the base's radiance, and the plan's synthesis.
+static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStream_t s) {
+  Work* w = &p->ws[0];
+  p->last_slot = 0;
+  const int S = p->n_layers;
+  const vrte_layer& top = p->layers[0];
+  const vrte_layer& bot = p->layers[S - 1];
+  const int N = top.n_nodes, n = 4 * N, n2 = 2 * n;
+  const int R = 4 * p->n_in, Ro = 4 * p->n_out;
+  const int P = N + p->n_in + p->n_out;
+  const bool mixed = p->desc.precision == VRTE_MIXED;
+  int Meff = 0;
+  for (const auto& l : p->layers) Meff = std::max(Meff, std::min(l.n_orders, l.n_coef));
+  std::vector<double> t_top(S);
+  double ttot = 0.0;
+  for (int k = 0; k < S; ++k) {
+    t_top[k] = ttot;
+    ttot += p->layers[k].tau;
+  }
+  const int U0 = p->chunk;
+  const long long nn = (long long)n * n, nR = (long long)n * R, RoR = (long long)Ro * R;
+  const long long sD = 4 * nn, sYk = 2 * nR, sUk = 2 * nn, sHk = (long long)Ro * n2;
+  {
+    StageScope sc(p, ST_TABLES, s, 2, 0.0, 0.0);
+    launch_gauss_nodes(N, w->d_mu_nodes, w->d_w_nodes, p->d_status, s);
+    launch_interface(N, p->n_in, p->n_out, top.n_interface, w->d_mu_nodes, p->d_mu_in,
+                     p->d_mu_out, w->d_pts, w->d_min4, w->d_mout4, w->d_rtop4, s);
+  }
+  for (int m0 = 0; m0 < Meff; m0 += U0) {
+    const int U = std::min(U0, Meff - m0);
+    const double dn = n, dR = R, dRo = Ro, dU = U;
+    double* Lprev = w->sL[0];
+    double* Lcur = w->sL[1];
+    double* Pprev = w->sPd[0];
+    double* Pcur = w->sPd[1];
+    OrderBatch ob{};
+    for (int k = 0; k < S; ++k) {
+      const vrte_layer& ly = p->layers[k];
+      const double* coef = p->d_coeffs + (size_t)k * p->desc.n_coef_max * 6;
+      const bool first = k == 0, last = k == S - 1;
+      const bool base = last && ly.base_albedo > 0.0 && m0 == 0;
+      {
+        StageScope sc(p, ST_TABLES, s, 1, 0.0, 0.0);
+        launch_depth_table(N, p->n_in, p->n_out, ly.tau, w->d_pts, w->g0tab, s);
+      }
+      run_order_batch(p, w, ly, coef, m0, U, false, false, s, false);
+      ob = OrderBatch{N, n, ly.n_coef, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef,
+                      p->d_status, n2, 2 * nR};
+      double* Dk = w->sDinv + (size_t)k * U0 * sD;
+      double* Yk = w->sY + (size_t)k * U0 * sYk;
+      double* Uk = w->sUup + (size_t)k * U0 * sUk;
+      double* Hk = w->sH + (size_t)k * U0 * sHk;
+      {
+        // the sub-layer's particular and direct parts at the slab's top
+        StageScope sc(p, ST_RECON_PART, s, first ? 2 : 3, 2.0 * dRo * dR * 2 * dn * dU,
+                      8.0 * (dRo * 2 * dn + 2 * dn * dR + 3 * dRo * dR) * dU);
+        if (!first) launch_slab_scale_sd(ob, t_top[k], w->d_pts, w->SD, s);
+        dgemm_batched(Ro, R, n2, 1.0, w->Upm, n2, sHk, w->SD, R, 2 * nR, 0.0, w->sTq, R, RoR, U,
+                      s);
+        launch_slab_accum(ob, t_top[k], w->d_pts, w->T1, w->sTq, w->g0tab, w->sAcc, first, s);
+        cudaMemcpyAsync(Hk, w->Hhat, (size_t)U * sHk * sizeof(double), cudaMemcpyDeviceToDevice,
+                        s);
+      }
+      StageScope sc(p, ST_BC_SOLVE, s, 4 + (base ? 2 : 0) + (first ? 0 : 4),
+                    (first ? 0.0 : 2.0 * dn * dR * dn + 2.0 * dn * dn * 2 * dn * 2 +
+                                       2.0 * dn * dR * 2 * dn) * dU +
+                        (16.0 * dn * dn * dn + 2.0 * 4 * dn * dn * dR) * dU,
+                    8.0 * (12 * dn * dn + 6 * dn * dR) * dU);
+      launch_slab_blocks(ob, first, w->X, w->Y, w->lam_re, w->lam_im, w->d_rtop4, w->K, Uk, Lcur,
+                         s);
+      launch_slab_rhs(ob, first, w->SD, w->d_rtop4, w->d_pts, Pprev, w->RHS, Pcur, w->sZt, s);
+      if (base) {
+        launch_base_K(N, n, ly.tau, ly.base_albedo, w->X, w->Y, w->lam_re, w->lam_im,
+                      w->d_mu_nodes, w->d_w_nodes, w->K, w->basebuf, s);
+        launch_base_rhs(N, n, R, 2 * nR, ly.tau, ly.base_albedo, w->SD, w->d_pts, w->d_min4,
+                        w->d_mu_nodes, w->d_w_nodes, w->RHS, w->basebuf + 2 * n, 1, s, t_top[k]);
+      }
+      if (!first) {
+        const double* Dp = w->sDinv + (size_t)(k - 1) * U0 * sD;  // D'_{k-1}^-1
+        double* Yp = w->sY + (size_t)(k - 1) * U0 * sYk;
+        // the upward particular radiance at the top of k completes row block k-1
+        dgemm_batched(n2, R, n, 1.0, Dp + n, n2, sD, w->sZt, R, nR, 1.0, Yp, R, sYk, U, s);
+        // D'_k = D_k - [Ldn_{k-1} W_{k-1} Uup_k; 0],  b'_k = b_k - [Ldn_{k-1} y_{k-1}; 0]
+        dgemm_batched(n, n, n2, 1.0, Lprev, n2, sUk, Dp + n, n2, sD, 0.0, w->sTnn, n, nn, U, s);
+        dgemm_batched(n, n2, n, -1.0, w->sTnn, n, nn, Uk, n2, sUk, 1.0, w->K, n2, sD, U, s);
+        dgemm_batched(n, R, n2, -1.0, Lprev, n2, sUk, Yp, R, sYk, 1.0, w->RHS, R, sYk, U, s);
+      }
+      batched_inverse(n2, w->K, Dk, U, p->d_status, s);
+      dgemm_batched(n2, R, n2, 1.0, Dk, n2, sD, w->RHS, R, sYk, 0.0, Yk, R, sYk, U, s);
+      std::swap(Lprev, Lcur);
+      std::swap(Pprev, Pcur);
+    }
+    {
+      // back-substitution from the bottom, c_k = y_k - W_k (Uup_{k+1} c_{k+1}), then the
+      // homogeneous parts of the sub-layers' top radiances
+      StageScope sc(p, ST_RECON_HOM, s, 2 * (S - 1) + 2 * S + 1 + (bot.base_albedo > 0.0 && m0 == 0),
+                    (S - 1) * 2.0 * (2 * dn * dR * 2 * dn) * dU + S * 2.0 * dRo * dR * 2 * dn * dU,
+                    8.0 * ((S - 1) * (6 * dn * dn + 6 * dn * dR) + S * (2 * dRo * dn + 2 * dn * dR +
+                                                                    2 * dRo * dR)) * dU);
+      for (int k = S - 2; k >= 0; --k) {
+        const double* Un = w->sUup + (size_t)(k + 1) * U0 * sUk;
+        const double* Yn = w->sY + (size_t)(k + 1) * U0 * sYk;
+        const double* Dc = w->sDinv + (size_t)k * U0 * sD;
+        double* Yc = w->sY + (size_t)k * U0 * sYk;
+        dgemm_batched(n, R, n2, 1.0, Un, n2, sUk, Yn, R, sYk, 0.0, w->sV, R, nR, U, s);
+        dgemm_batched(n2, R, n, -1.0, Dc + n, n2, sD, w->sV, R, nR, 1.0, Yc, R, sYk, U, s);
+      }
+      for (int k = 0; k < S; ++k) {
+        dgemm_batched(Ro, R, n2, 1.0, w->sH + (size_t)k * U0 * sHk, n2, sHk,
+                      w->sY + (size_t)k * U0 * sYk, R, sYk, 0.0, w->sTq, R, RoR, U, s);
+        launch_slab_accum(ob, t_top[k], w->d_pts, nullptr, w->sTq, nullptr, w->sAcc, 0, s);
+      }
+      launch_slab_store(ob, w->sAcc, w->Isyn, s);
+      // Lambertian base: its isotropic radiance at the bottom, attenuated through the slab
+      if (bot.base_albedo > 0.0 && m0 == 0)
+        launch_base_recon(n, N, p->n_in, p->n_out, ttot, bot.base_albedo,
+                          w->sY + (size_t)(S - 1) * U0 * sYk, w->basebuf, w->basebuf + 2 * n,
+                          w->d_pts, w->d_mout4, w->Isyn, 1, s);
+    }
+  }
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return VRTE_ERR_CUDA;
+  }
+  const size_t table = (size_t)p->n_in * p->n_out * p->n_phi * 16;
+  const size_t esz = out_dtype == VRTE_OUT_F64 ? sizeof(double) : sizeof(float);
+  {
+    StageScope sc(p, ST_SYNTHESIS, s, 1, 2.0 * table * Meff, (double)table * esz);
+    if (mixed)
+      tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws, d_brdf,
+                   out_dtype, kSynthBlock, w->tcw, p->d_status, s);
+    else
+      launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws,
+                            d_brdf, out_dtype, p->d_status, s);
+  }
+  if (cudaGetLastError() != cudaSuccess) return VRTE_ERR_CUDA;
+  return VRTE_OK;
+}
+
+vrte_status vrte_solve_slab_brdf(vrte_plan* p, void* d_brdf, int out_dtype, void* stream) {
+  if (!p || !d_brdf) return VRTE_ERR_INVALID_ARG;
+  if (out_dtype != VRTE_OUT_F32 && out_dtype != VRTE_OUT_F64) return VRTE_ERR_INVALID_ARG;
+  if (!(p->desc.flags & VRTE_FLAG_SLAB) || p->n_layers < 1 || !p->d_coeffs || !p->ws[0].sDinv)
+    return VRTE_ERR_STATE;
+  const vrte_layer& top = p->layers[0];
+  for (int k = 0; k < p->n_layers; ++k) {
+    const vrte_layer& l = p->layers[k];
+    // one quadrature and one order range for the whole slab; a smooth top only above the
+    // first sub-layer and a Lambertian base only under the last
+    if (l.n_nodes != top.n_nodes || l.n_orders != top.n_orders) return VRTE_ERR_INVALID_ARG;
+    if (k > 0 && l.n_interface > 1.0) return VRTE_ERR_INVALID_ARG;
+    if (k < p->n_layers - 1 && l.base_albedo > 0.0) return VRTE_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  p->last_stream = s;
+  return solve_slab(p, d_brdf, out_dtype, s);
 }
 
 vrte_status vrte_solve_brdf_host(vrte_plan* p, const double* h_coeffs, void* h_brdf,

@@ -276,10 +276,26 @@ void launch_base_K(int N, int n, double tau, double rho, const double* X, const 
                    const double* w_nodes, double* K, double* basev, cudaStream_t s);
 void launch_base_rhs(int N, int n, int R, long long sSD, double tau, double rho, const double* SD,
                      const double* pts, const double* min4, const double* mu_nodes,
-                     const double* w_nodes, double* RHS, double* zb, int add_rhs, cudaStream_t s);
+                     const double* w_nodes, double* RHS, double* zb, int add_rhs, cudaStream_t s,
+                     double t_above = 0.0);
 void launch_base_recon(int n, int N, int n_in, int n_out, double tau, double rho, const double* C,
                        const double* basev, const double* zb, const double* pts,
                        const double* mout4, double* out, int isyn, cudaStream_t s);
+// Multi-layer slabs (k_slab.cu): boundary blocks and right-hand side of one sub-layer, the
+// beam's attenuation to a sub-layer's top, and the attenuated sum of the sub-layers'
+// contributions to the upward radiance at the slab's top.
+void launch_slab_blocks(const OrderBatch& b, int first, const double* X, const double* Y,
+                        const double* lam_re, const double* lam_im, const double* rtop4,
+                        double* D, double* Uup, double* Ldn, cudaStream_t s);
+void launch_slab_rhs(const OrderBatch& b, int first, const double* SD, const double* rtop4,
+                     const double* pts, const double* Pd_prev, double* rhs, double* Pd_cur,
+                     double* Zt, cudaStream_t s);
+void launch_slab_scale_sd(const OrderBatch& b, double t, const double* pts, double* SD,
+                          cudaStream_t s);
+void launch_slab_accum(const OrderBatch& b, double t, const double* pts, const double* T1,
+                       const double* Tq, const double* g0tab, double* Acc, int first,
+                       cudaStream_t s);
+void launch_slab_store(const OrderBatch& b, const double* Acc, double* Isyn, cudaStream_t s);
 
 // ---------------------------------------------------------------- radiance at depth tau
 void launch_btdf_points(int N, int n_in, int n_out, double nif, const double* mu_out, double* pts,
