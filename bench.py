@@ -276,6 +276,154 @@ def time_backward(vr, torch, dev, n_layers=16, steps=2, warmup=1):
             "steps": steps, "warmup": warmup}
 
 
+def time_slab(vr, torch, dev, n_sub=4, steps=2, warmup=1):
+    """A multi-layer slab (vrte_solve_slab_brdf) of `n_sub` sub-layers of the differentiation
+    workload's shape (N = 48, M = L = 96 Mie sub-layers, the first one's interface as the top,
+    64 x 64 x 90 FP64 table), timed beside the same layers solved as independent layers
+    (vrte_solve_brdf, FP64 plan): the slab's cost over the independent solves is its block
+    elimination and the attenuated sum of the sub-layers' top radiances."""
+    from vrte_inputs import make_config
+    cfg = make_config(5)
+    layers = [dict(l, n_coef=l["coef"].shape[0]) for l in cfg["layers"][:n_sub]]
+    sub = [dict(l, n_interface=(l["n_interface"] if k == 0 else 1.0))
+           for k, l in enumerate(layers)]
+    Lmax = max(l["n_coef"] for l in layers)
+    d_coef = torch.from_numpy(vr.pack_coefficients(sub, Lmax)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for name, slab in (("slab", True), ("independent", False)):
+        plan = vr.Plan(cfg["mu_in"], cfg["mu_out"], cfg["dphi"], 48, 96, Lmax, n_sub,
+                       vr.VRTE_FP64, profile=True, slab=slab)
+        plan.set_layers(sub, d_coef)
+        shape = plan.table_shape[1:] if slab else plan.table_shape
+        out = torch.empty(shape, dtype=torch.float32, device=dev)
+        run = plan.solve_slab if slab else plan.solve
+        for _ in range(warmup):
+            run(out, stream)
+        torch.cuda.synchronize()
+        plan.reset_stages()
+        clocks = ClockSampler(torch.cuda.current_device())
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            run(out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        st = plan.status()
+        stages = {x["name"]: round(x["ms"] / steps, 2) for x in plan.stages() if x["ms"] > 0}
+        plan.close()
+        if st != 0:
+            raise SystemExit(f"slab record: {name} solve failed ({st})")
+        res[name] = {"ms_per_solve": e0.elapsed_time(e1) / steps, "stage_ms": stages,
+                     "clocks": clk}
+    orders = n_sub * 96
+    return {"workload": f"slab of {n_sub} sub-layers of {cfg['name']}", "sub_layers": n_sub,
+            "N": 48, "M": 96, "L": 96, "n_in": 64, "n_out": 64, "n_phi": 90,
+            "ms_per_slab": res["slab"]["ms_per_solve"],
+            "sub_layer_order_solves_per_s": orders / (res["slab"]["ms_per_solve"] / 1000.0),
+            "independent_layers_ms": res["independent"]["ms_per_solve"],
+            "slab_over_independent": res["slab"]["ms_per_solve"] /
+            res["independent"]["ms_per_solve"],
+            "slab_stage_ms": res["slab"]["stage_ms"],
+            "independent_stage_ms": res["independent"]["stage_ms"],
+            "clocks": res["slab"]["clocks"],
+            "structure": "FP64 plans, FP32 tables; the slab runs its sub-layers in turn on one "
+                         "stream, the independent solve on the plan's concurrent streams",
+            "steps": steps, "warmup": warmup}
+
+
+def _timed_solves(plan, out, stream, steps, warmup, torch):
+    """Device time per vrte_solve_brdf call (CUDA events on `stream`, after `warmup` calls)."""
+    for _ in range(warmup):
+        plan.solve(out, stream)
+    torch.cuda.synchronize()
+    plan.reset_stages()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        plan.solve(out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def time_batched(vr, torch, dev, subset_stride=16):
+    """The batched workload (256 uneven layers, 64 x 64 x 90 FP32 tables) in one mixed-form
+    call: one direct step after one warm-up, then the same call captured once into a CUDA graph
+    and replayed as one graph launch per step. FP64-plain beside the mixed form on a stratified
+    subset (every `subset_stride`-th layer), since 256 FP64 layers take minutes."""
+    from vrte_inputs import make_config
+    cfg = make_config(4)
+    layers = [dict(l, n_coef=l["coef"].shape[0]) for l in cfg["layers"]]
+    coef = vr.pack_coefficients(layers)
+    d_coef = torch.from_numpy(coef).to(dev)
+    stream = torch.cuda.Stream(dev)
+    orders = lambda ls: sum(min(l["n_orders"], l["n_coef"]) for l in ls)
+    rec = {"workload": cfg["name"], "layers": len(layers), "order_solves": orders(layers),
+           "n_in": 64, "n_out": 64, "n_phi": 90, "out_dtype": "f32"}
+    plan = vr.Plan(cfg["mu_in"], cfg["mu_out"], cfg["dphi"], max(l["n_nodes"] for l in layers),
+                   max(l["n_orders"] for l in layers), coef.shape[1], len(layers), vr.VRTE_MIXED,
+                   profile=False)
+    plan.set_layers(layers, d_coef)
+    out = torch.empty(plan.table_shape, dtype=torch.float32, device=dev)
+    clocks = ClockSampler(torch.cuda.current_device())
+    ms = _timed_solves(plan, out, stream, 1, 1, torch)
+    launches = int(sum(st["launches"] for st in plan.stages()))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream, capture_error_mode="relaxed"):
+        plan.solve(out, stream)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        g.replay()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms_graph = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    st = plan.status()
+    del g
+    plan.close()
+    del out
+    torch.cuda.empty_cache()
+    if st != 0:
+        raise SystemExit(f"batched record: solve failed ({st})")
+    rec.update({"mixed_ms_per_step": ms, "order_solves_per_s": rec["order_solves"] / (ms / 1e3),
+                "graph_ms_per_step": ms_graph,
+                "graph_order_solves_per_s": rec["order_solves"] / (ms_graph / 1e3),
+                "gpu_launches_per_step": launches, "host_launches_per_graph_step": 1,
+                "clocks": clk})
+    sub = layers[::subset_stride]
+    scoef = vr.pack_coefficients(sub)
+    d_scoef = torch.from_numpy(scoef).to(dev)
+    sres = {}
+    for name, prec in (("mixed", vr.VRTE_MIXED), ("fp64", vr.VRTE_FP64)):
+        plan = vr.Plan(cfg["mu_in"], cfg["mu_out"], cfg["dphi"], max(l["n_nodes"] for l in sub),
+                       max(l["n_orders"] for l in sub), scoef.shape[1], len(sub), prec)
+        plan.set_layers(sub, d_scoef)
+        out = torch.empty(plan.table_shape, dtype=torch.float32, device=dev)
+        sres[name] = _timed_solves(plan, out, stream, 1, 1, torch)
+        if plan.status() != 0:
+            raise SystemExit(f"batched record: subset {name} solve failed")
+        plan.close()
+        del out
+        torch.cuda.empty_cache()
+    rec["subset"] = {"layers": len(sub), "every": subset_stride, "order_solves": orders(sub),
+                     "mixed_ms": sres["mixed"], "fp64_plain_ms": sres["fp64"],
+                     "mixed_over_fp64_speedup": sres["fp64"] / sres["mixed"]}
+    rec["structure"] = ("one plan, one vrte_solve_brdf call per step; layers on up to 4 "
+                        "concurrent streams (one workspace slot each), all orders of a layer "
+                        "batched; graph: the same call captured once, one graph launch per step")
+    rec["steps"], rec["warmup"] = 1, 1
+    return rec
+
+
 def max_over_ranks(x, dist, device):
     """Maximum of the float x over the ranks of the process group (x itself without one)."""
     if not dist:
@@ -486,6 +634,12 @@ def main():
     ap.add_argument("--no-backward", action="store_true",
                     help="skip the adjoint record (vrte_brdf_backward on 16 layers of the "
                          "N=48, M=96 differentiation workload)")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched record (256 uneven layers in one mixed-form call, "
+                         "direct and graph-replayed; FP64-plain on a 16-layer subset)")
+    ap.add_argument("--no-slab", action="store_true",
+                    help="skip the multi-layer slab record (vrte_solve_slab_brdf on 4 sub-layers "
+                         "of the N=48, M=96 workload)")
     ap.add_argument("--workload", default="brdf", choices=["brdf", "batched"],
                     help="brdf: the N=64, M=128 layer (the benchmark line); batched: 256 "
                          "uneven layers, its own JSON line")
@@ -584,15 +738,20 @@ def main():
                        "api": "vrte_solve_brdf_host (pinned host buffers; the table leaves in "
                               "blocks of 64 incident cosines as the synthesis completes them)"}
         del h_out, d_tab
+    plan.close()
+    torch.cuda.empty_cache()
 
     if not args.no_backward and not args.grid:
         line["backward"] = time_backward(vr, torch, dev)
+    if not args.no_slab and not args.grid:
+        line["slab"] = time_slab(vr, torch, dev)
+    if not args.no_batched and not args.grid:
+        line["batched"] = time_batched(vr, torch, dev)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ly, cfg)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    plan.close()
     if dist:
         dist.destroy_process_group()
 
