@@ -45,17 +45,17 @@ __device__ inline void house3(double x, double y, double z, double& tau, double&
   v2 = z * sc;
 }
 
-__global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __restrict__ A,
+__global__ void __launch_bounds__(EIG_THREADS, 1) k_eigen(int n, const double* __restrict__ A,
                                                        double* Hbuf, double* Zbuf, double* Vbuf,
                                                        double* lam_re, double* lam_im,
                                                        double* scale, const int* mask,
                                                        unsigned* status) {
-  extern __shared__ double vsh[];  // Householder vector, n entries; then the sweep's
-                                   // reflectors (tau, v1, v2, tau v1, tau v2), n entries each
+  extern __shared__ double vsh[];  // Householder vector of the Hessenberg step, n entries;
+                                   // the balancing's norms and scalings, 3 n more
   __shared__ double red[32];
-  __shared__ double bal[2][2];  // balancing decision (f, 1/f) of row i, at bal[i & 1]
   __shared__ double hred[4];    // Hessenberg step: (|x|^2 below the subdiagonal, beta, tau, 1/(alpha - beta))
   __shared__ int ired[32];
+  __shared__ double W[8][8];     // sweep: warp 0's window of H, element (r, c) at [r & 7][c & 7]
   __shared__ double refl[2][5];  // reflectors (tau, v1, v2, tau v1, tau v2) of the current
                                  // and the next sweep step
   int u = blockIdx.x;
@@ -65,11 +65,6 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
   double* H = Hbuf + (size_t)u * n * n;
   double* Z = Zbuf + (size_t)u * n * n;
   double* V = Vbuf + (size_t)u * n * n;
-  double* rtau = vsh + n;
-  double* rv1 = rtau + n;
-  double* rv2 = rv1 + n;
-  double* rtv1 = rv2 + n;  // tau v1 and tau v2 of each step (five-operation updates)
-  double* rtv2 = rtv1 + n;
   double* wr = lam_re + (size_t)u * n;
   double* wi = lam_im + (size_t)u * n;
   double* dsc = scale + (size_t)u * n;
@@ -83,45 +78,58 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
   for (int i = tid; i < n; i += nt) dsc[i] = 1.0;
   __syncthreads();
 
-  // ---- 1. balancing: D^-1 H D with power-of-two entries, Gauss-Seidel sweeps. The row and
-  // column norms and the scaling decision come from warp 0 alone (FP64 instructions cost the
-  // same for one active warp as for every warp repeating them).
-  for (int sweep = 0; sweep < 32; ++sweep) {
-    int changed = 0;
-    for (int i = 0; i < n; ++i) {
-      if (warp == 0) {
-        double c = 0.0, r = 0.0;
-        for (int j = lane; j < n; j += 32) {
-          if (j == i) continue;
-          c += fabs(H[(size_t)j * n + i]);
-          r += fabs(H[(size_t)i * n + j]);
+  // ---- 1. balancing: D^-1 H D with power-of-two entries (Parlett-Reinsch criterion). Each
+  // sweep takes the off-diagonal row and column norms of every index at once and rescales,
+  // together, every index whose scaling by 2^e, e = rint(log2(r / c) / 4), lowers c + r by
+  // more than 5 %, until a sweep changes nothing. Deciding all indices from one set of norms
+  // costs two passes over H per sweep instead of one barrier per index; the quarter (not
+  // half) of log2(r / c) damps the simultaneous steps, which otherwise can oscillate between
+  // two scalings, to the norm the one-index-at-a-time sweeps reach.
+  {
+    double* cn = vsh + n;   // column norms, then the inverse scalings
+    double* rn = cn + n;    // row norms
+    double* fs = rn + n;    // scaling of the sweep (1 = none)
+    for (int sweep = 0; sweep < 32; ++sweep) {
+      for (int j = tid; j < n; j += nt) {
+        double c0 = 0.0, c1 = 0.0;
+        for (int i = 0; i + 1 < n; i += 2) {
+          c0 += (i == j) ? 0.0 : fabs(H[(size_t)i * n + j]);
+          c1 += (i + 1 == j) ? 0.0 : fabs(H[(size_t)(i + 1) * n + j]);
         }
-        for (int off = 16; off > 0; off >>= 1) {
-          c += __shfl_xor_sync(0xffffffffu, c, off);
-          r += __shfl_xor_sync(0xffffffffu, r, off);
-        }
-        double f = 0.0, finv = 0.0;  // f = 0: row i stays
+        if (n & 1) c0 += (n - 1 == j) ? 0.0 : fabs(H[(size_t)(n - 1) * n + j]);
+        cn[j] = c0 + c1;
+      }
+      for (int i = warp; i < n; i += nwarps) {
+        double r = 0.0;
+        for (int j = lane; j < n; j += 32) r += (j == i) ? 0.0 : fabs(H[(size_t)i * n + j]);
+        for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xffffffffu, r, off);
+        if (lane == 0) rn[i] = r;
+      }
+      __syncthreads();
+      int changed = 0;
+      for (int i = tid; i < n; i += nt) {
+        const double c = cn[i], r = rn[i];
+        double f = 1.0, finv = 1.0;
         if (c > 0.0 && r > 0.0 && isfinite(c) && isfinite(r)) {
-          const int e2 = (int)rint(0.5 * log2(r / c));
+          const int e2 = (int)rint(0.25 * log2(r / c));
           if (e2 != 0) {
             const double ff = ldexp(1.0, e2);
             if (!(c * ff + r / ff >= 0.95 * (c + r))) { f = ff; finv = ldexp(1.0, -e2); }
           }
         }
-        if (lane == 0) { bal[i & 1][0] = f; bal[i & 1][1] = finv; }
+        fs[i] = f;
+        cn[i] = finv;  // this thread's own entry, read above
+        if (f != 1.0) changed = 1;
       }
-      __syncthreads();
-      const double f = bal[i & 1][0], finv = bal[i & 1][1];
-      if (f == 0.0) continue;  // uniform: nothing changed, the next row reads the same H
-      for (int j = tid; j < n; j += nt) {
-        H[(size_t)i * n + j] *= finv;
-        H[(size_t)j * n + i] *= f;
+      if (!__syncthreads_or(changed)) break;
+      // H[i][j] <- H[i][j] f_j / f_i (exact: powers of two)
+      for (size_t e = tid; e < (size_t)n * n; e += nt) {
+        const int i = (int)(e / n), j = (int)(e - (size_t)i * n);
+        if (fs[i] != 1.0 || fs[j] != 1.0) H[e] = H[e] * fs[j] * cn[i];
       }
-      if (tid == 0) dsc[i] *= f;
-      changed = 1;
+      for (int i = tid; i < n; i += nt) dsc[i] *= fs[i];
       __syncthreads();
     }
-    if (!changed) break;
   }
   __syncthreads();
 
@@ -345,97 +353,177 @@ __global__ void __launch_bounds__(EIG_THREADS) k_eigen(int n, const double* __re
         const double tv1 = tau * v1, tv2 = tau * v2;
         refl[l & 1][0] = tau; refl[l & 1][1] = v1; refl[l & 1][2] = v2;
         refl[l & 1][3] = tv1; refl[l & 1][4] = tv2;
-        rtau[0] = tau; rv1[0] = v1; rv2[0] = v2; rtv1[0] = tv1; rtv2[0] = tv2;
+      }
+    }
+    // the window of the first step: rows l .. l+3, columns l .. l+3 (column l+4 enters at step l)
+    if (warp == 0) {
+      for (int e = lane; e < 16; e += 32) {
+        const int r = l + (e >> 2), c = l + (e & 3);
+        if (r <= hi && c < n) W[r & 7][c & 7] = H[(size_t)r * n + c];
       }
     }
     __syncthreads();
+    // Each step k applies P_k = I - tau v v^T, v = (1, v1, v2), to H from both sides and to
+    // Z from the right; every element update is w = h0 + v1 h1 + v2 h2, then
+    // h -= (tau, tau v1, tau v2) w (five FP64 operations). Dependent FP64 operations are
+    // slow on this part, so the chain from one reflector to the next is kept short: the step
+    // splits into three disjoint sets of elements done concurrently, with one barrier:
+    //   warp 0 carries the bulge in a shared-memory window W of rows k .. k+3 and columns
+    //   k-1 .. k+4: the left update of columns c0 .. k+2, the right update of rows
+    //   k .. min(k+3, hi) (all that the next reflector reads), then that reflector;
+    //   warp 1 brings column k+4 into the window (its rows k, k+1 hold the far update of
+    //   step k-1) and applies the left update to columns k+3 and k+4, which steps k+1 and
+    //   k+2 read first;
+    //   warps 2.. apply the rest: the left update of columns k+5 .. n-1, the right update of
+    //   rows 0 .. k-1, and Z <- Z P_k, issuing the loads of two tasks before their updates.
+    // Row k leaves the window for H at the end of step k (columns c0 .. k+2 from warp 0,
+    // k+3 .. k+4 from warp 1), with the two zeros of column k-1; row k+4 is read ahead by
+    // warp 0 (nothing touches it before step k+1). Every element receives the same
+    // operations in the same order as in a step done by all threads one update after the
+    // other.
+    const int ft = tid - 64, fn = nt - 64;
     for (int k = l; k <= hi - 1; ++k) {
       const int nr = (k < hi - 1) ? 3 : 2;
       const double tau = refl[k & 1][0], v1 = refl[k & 1][1], v2 = refl[k & 1][2];
       const double tv1 = refl[k & 1][3], tv2 = refl[k & 1][4];
-      // each update: w = h0 + v1 h1 + v2 h2, then h -= (tau, tau v1, tau v2) w (five FP64
-      // operations per element)
-      // right-update rows rotate so that rows k+1 .. k+3 (the next bulge column) fall on
-      // lanes 0 .. 2 of warp 0
-      double nb = 0.0;
-      if (tau != 0.0) {
-        int c0 = (k > l) ? k - 1 : l;
-        // left: rows k..k+nr-1, columns c0..n-1
-        for (int j = c0 + tid; j < n; j += nt) {
-          double h0 = H[(size_t)k * n + j], h1 = H[(size_t)(k + 1) * n + j];
-          double h2 = (nr == 3) ? H[(size_t)(k + 2) * n + j] : 0.0;
-          const double w = fma(v2, h2, fma(v1, h1, h0));
-          H[(size_t)k * n + j] = fma(-tau, w, h0);
-          H[(size_t)(k + 1) * n + j] = fma(-tv1, w, h1);
-          if (nr == 3) H[(size_t)(k + 2) * n + j] = fma(-tv2, w, h2);
+      const int rmax = min(k + 3, hi);
+      const int c0 = (k > l) ? k - 1 : l;
+      if (warp == 0) {
+        // row k+4 (lanes 8..12: columns k..k+4), read ahead
+        double ent = 0.0;
+        const bool row4 = lane >= 8 && lane < 13 && k + 4 <= hi && k + lane - 8 < n;
+        if (row4) ent = H[(size_t)(k + 4) * n + k + lane - 8];
+        double nb = 0.0;
+        if (tau != 0.0) {
+          // left: rows k..k+nr-1, columns c0 .. k+2 (what the right update reads)
+          {
+            const int j = c0 + lane;
+            if (j <= min(k + 2, n - 1)) {
+              const double h0 = W[k & 7][j & 7], h1 = W[(k + 1) & 7][j & 7];
+              const double h2 = (nr == 3) ? W[(k + 2) & 7][j & 7] : 0.0;
+              const double w = fma(v2, h2, fma(v1, h1, h0));
+              W[k & 7][j & 7] = fma(-tau, w, h0);
+              W[(k + 1) & 7][j & 7] = fma(-tv1, w, h1);
+              if (nr == 3) W[(k + 2) & 7][j & 7] = fma(-tv2, w, h2);
+            }
+          }
+          __syncwarp();
+          if (k > l && lane == 0) {
+            W[(k + 1) & 7][(k - 1) & 7] = 0.0;
+            if (nr == 3) W[(k + 2) & 7][(k - 1) & 7] = 0.0;
+          }
+          // right: columns k..k+nr-1, rows k..rmax; row k + lane on lane `lane`, so rows
+          // k+1 .. k+3 (the next bulge column) sit on lanes 1 .. 3
+          {
+            const int i = k + lane;
+            if (i <= rmax) {
+              const double h0 = W[i & 7][k & 7], h1 = W[i & 7][(k + 1) & 7];
+              const double h2 = (nr == 3) ? W[i & 7][(k + 2) & 7] : 0.0;
+              const double w = fma(v2, h2, fma(v1, h1, h0));
+              const double g0 = fma(-tau, w, h0);
+              W[i & 7][k & 7] = g0;
+              nb = g0;
+              W[i & 7][(k + 1) & 7] = fma(-tv1, w, h1);
+              if (nr == 3) W[i & 7][(k + 2) & 7] = fma(-tv2, w, h2);
+            }
+          }
+          __syncwarp();
         }
-        __syncthreads();
-        if (k > l && tid == 0) {
+        // reflector of step k + 1 from column k of rows k+1 .. k+3
+        if (k + 1 <= hi - 1) {
+          const int nr1 = (k + 1 < hi - 1) ? 3 : 2;
+          double x, y, z;
+          if (tau != 0.0) {
+            x = __shfl_sync(0xffffffffu, nb, 1);
+            y = __shfl_sync(0xffffffffu, nb, 2);
+            z = __shfl_sync(0xffffffffu, nb, 3);
+          } else {
+            x = W[(k + 1) & 7][k & 7];
+            y = W[(k + 2) & 7][k & 7];
+            z = (nr1 == 3) ? W[(k + 3) & 7][k & 7] : 0.0;
+          }
+          double t1, w1, w2;
+          house3(x, y, nr1 == 3 ? z : 0.0, t1, w1, w2);
+          if (nr1 == 2) w2 = 0.0;
+          if (lane == 0) {
+            const double tw1 = t1 * w1, tw2 = t1 * w2;
+            refl[(k + 1) & 1][0] = t1; refl[(k + 1) & 1][1] = w1; refl[(k + 1) & 1][2] = w2;
+            refl[(k + 1) & 1][3] = tw1; refl[(k + 1) & 1][4] = tw2;
+          }
+        }
+        // row k+4 enters the window (its slot held row k-4); row k leaves (columns c0 .. k+2)
+        if (row4) W[(k + 4) & 7][(k + lane - 8) & 7] = ent;
+        {
+          const int c = c0 + lane;
+          if (c <= min(k + 2, n - 1)) H[(size_t)k * n + c] = W[k & 7][c & 7];
+        }
+        if (tau != 0.0 && k > l && lane == 0) {
           H[(size_t)(k + 1) * n + k - 1] = 0.0;
           if (nr == 3) H[(size_t)(k + 2) * n + k - 1] = 0.0;
         }
-        // right: columns k..k+nr-1, rows 0..min(k+3, hi)
-        const int rows = min(k + 3, hi) + 1;
-        for (int t = tid; t < rows; t += nt) {
-          int i = k + 1 + t;
-          if (i >= rows) i -= rows;
-          double h0 = H[(size_t)i * n + k], h1 = H[(size_t)i * n + k + 1];
-          double h2 = (nr == 3) ? H[(size_t)i * n + k + 2] : 0.0;
-          const double w = fma(v2, h2, fma(v1, h1, h0));
-          const double g0 = fma(-tau, w, h0);
-          H[(size_t)i * n + k] = g0;
-          if (t == tid) nb = g0;
-          H[(size_t)i * n + k + 1] = fma(-tv1, w, h1);
-          if (nr == 3) H[(size_t)i * n + k + 2] = fma(-tv2, w, h2);
-        }
-      }
-      // reflector of step k + 1 from column k of rows k+1 .. k+3 (warp 0)
-      if (k + 1 <= hi - 1 && warp == 0) {
-        const int nr1 = (k + 1 < hi - 1) ? 3 : 2;
-        double x, y, z;
+      } else if (warp == 1) {
+        // column k+4 enters the window (lanes 0..3: rows k..rmax; its slot held column k-4)
+        const int j4 = k + 4;
+        const bool col4 = lane < 4 && j4 < n && k + lane <= rmax;
+        if (col4) W[(k + lane) & 7][j4 & 7] = H[(size_t)(k + lane) * n + j4];
+        __syncwarp();
+        const int j = k + 3 + lane;
         if (tau != 0.0) {
-          x = __shfl_sync(0xffffffffu, nb, 0);
-          y = __shfl_sync(0xffffffffu, nb, 1);
-          z = __shfl_sync(0xffffffffu, nb, 2);
-        } else {
-          x = H[(size_t)(k + 1) * n + k];
-          y = H[(size_t)(k + 2) * n + k];
-          z = (nr1 == 3) ? H[(size_t)(k + 3) * n + k] : 0.0;
+          // left update of columns k+3, k+4 (read first at steps k+1 and k+2)
+          if (lane < 2 && j < n) {
+            const double h0 = W[k & 7][j & 7], h1 = W[(k + 1) & 7][j & 7];
+            const double h2 = (nr == 3) ? W[(k + 2) & 7][j & 7] : 0.0;
+            const double w = fma(v2, h2, fma(v1, h1, h0));
+            W[k & 7][j & 7] = fma(-tau, w, h0);
+            W[(k + 1) & 7][j & 7] = fma(-tv1, w, h1);
+            if (nr == 3) W[(k + 2) & 7][j & 7] = fma(-tv2, w, h2);
+          }
+          __syncwarp();
         }
-        double t1, w1, w2;
-        house3(x, y, nr1 == 3 ? z : 0.0, t1, w1, w2);
-        if (nr1 == 2) w2 = 0.0;
-        if (lane == 0) {
-          const double tw1 = t1 * w1, tw2 = t1 * w2;
-          refl[(k + 1) & 1][0] = t1; refl[(k + 1) & 1][1] = w1; refl[(k + 1) & 1][2] = w2;
-          refl[(k + 1) & 1][3] = tw1; refl[(k + 1) & 1][4] = tw2;
-          rtau[k + 1 - l] = t1; rv1[k + 1 - l] = w1; rv2[k + 1 - l] = w2;
-          rtv1[k + 1 - l] = tw1; rtv2[k + 1 - l] = tw2;
+        // row k leaves the window (columns k+3, k+4)
+        if (lane < 2 && j < n) H[(size_t)k * n + j] = W[k & 7][j & 7];
+      } else if (tau != 0.0) {
+        // tasks: far columns of the left update, far rows of the right update, rows of Z;
+        // task t updates p[0], p[s], p[2 s]
+        const int jf = k + 5;
+        const int nA = max(0, n - jf), nAB = nA + k, nT = nAB + n;
+        auto task = [&](int t, int& s) -> double* {
+          if (t < nA) { s = n; return H + (size_t)k * n + jf + t; }
+          if (t < nAB) { s = 1; return H + (size_t)(t - nA) * n + k; }
+          s = n;
+          return Z + (size_t)k * n + (t - nAB);
+        };
+        for (int t = ft; t < nT; t += 2 * fn) {
+          int sa, sb = 0;
+          double* pa = task(t, sa);
+          const bool hb = t + fn < nT;
+          double* pb = hb ? task(t + fn, sb) : pa;
+          const double a0 = pa[0], a1 = pa[sa], a2 = (nr == 3) ? pa[2 * sa] : 0.0;
+          double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+          if (hb) {
+            b0 = pb[0];
+            b1 = pb[sb];
+            b2 = (nr == 3) ? pb[2 * sb] : 0.0;
+          }
+          const double wa = fma(v2, a2, fma(v1, a1, a0));
+          pa[0] = fma(-tau, wa, a0);
+          pa[sa] = fma(-tv1, wa, a1);
+          if (nr == 3) pa[2 * sa] = fma(-tv2, wa, a2);
+          if (hb) {
+            const double wb = fma(v2, b2, fma(v1, b1, b0));
+            pb[0] = fma(-tau, wb, b0);
+            pb[sb] = fma(-tv1, wb, b1);
+            if (nr == 3) pb[2 * sb] = fma(-tv2, wb, b2);
+          }
         }
       }
       __syncthreads();
     }
-    // Schur vectors: Z <- Z P_l ... P_{hi-1}, deferred to the end of the sweep. Each row of
-    // Z transforms on its own, so a thread carries its row through all reflectors with a
-    // sliding window of three columns (the same arithmetic, in the same order, as
-    // applying each reflector at its step).
-    for (int i = tid; i < n; i += nt) {
-      double za = Z[(size_t)l * n + i], zb = Z[(size_t)(l + 1) * n + i];
-      for (int k = l; k <= hi - 1; ++k) {
-        const int nr = (k < hi - 1) ? 3 : 2;
-        double zc = (nr == 3) ? Z[(size_t)(k + 2) * n + i] : 0.0;
-        const double tau = rtau[k - l];
-        if (tau != 0.0) {
-          const double w = fma(rv2[k - l], zc, fma(rv1[k - l], zb, za));
-          za = fma(-tau, w, za);
-          zb = fma(-rtv1[k - l], w, zb);
-          if (nr == 3) zc = fma(-rtv2[k - l], w, zc);
-        }
-        Z[(size_t)k * n + i] = za;
-        za = zb;
-        zb = zc;
-      }
-      Z[(size_t)hi * n + i] = za;
+    // the rows still in the window after the last step (k = hi - 1) go back to H
+    if (warp == 0) {
+      const int k = hi - 1, c0 = (k > l) ? k - 1 : l;
+      const int r = k + 1 + (lane >> 3), c = c0 + (lane & 7);
+      if (r <= hi && c <= min(k + 4, n - 1)) H[(size_t)r * n + c] = W[r & 7][c & 7];
     }
     __syncthreads();
   }
@@ -584,7 +672,7 @@ void dgemm_batched_mask(bool tA, bool tB, int M, int N, int K, double alpha, con
 void batched_eigen(int n, const double* A, double* H, double* Z, double* V, double* X,
                    double* lam_re, double* lam_im, double* scale, int batch, unsigned* status,
                    cudaStream_t s, const int* mask) {
-  size_t smem = 6 * (size_t)n * sizeof(double);
+  size_t smem = 4 * (size_t)n * sizeof(double);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(k_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   k_eigen<<<batch, EIG_THREADS, smem, s>>>(n, A, H, Z, V, lam_re, lam_im, scale, mask, status);
