@@ -45,6 +45,39 @@ __device__ inline void house3(double x, double y, double z, double& tau, double&
   v2 = z * sc;
 }
 
+// sum_i v[i] p[i s]: the loads of eight terms are issued before their multiply-adds, into two
+// partial sums (a single running sum waited on each load in turn)
+__device__ inline double dotv(int len, const double* v, const double* p, size_t s) {
+  double w0 = 0.0, w1 = 0.0;
+  int i = 0;
+  for (; i + 8 <= len; i += 8, p += 8 * s) {
+    double a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = p[q * s];
+#pragma unroll
+    for (int q = 0; q < 8; q += 2) {
+      w0 = fma(v[i + q], a[q], w0);
+      w1 = fma(v[i + q + 1], a[q + 1], w1);
+    }
+  }
+  for (; i < len; ++i, p += s) w0 = fma(v[i], p[0], w0);
+  return w0 + w1;
+}
+
+// p[i s] -= v[i] w, eight loads issued before their updates (a store and the next load are
+// otherwise kept in order, the compiler not knowing that they never overlap)
+__device__ inline void axpyv(int len, const double* v, double* p, size_t s, double w) {
+  int i = 0;
+  for (; i + 8 <= len; i += 8, p += 8 * s) {
+    double a[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = p[q * s];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) p[q * s] = fma(-v[i + q], w, a[q]);
+  }
+  for (; i < len; ++i, p += s) p[0] = fma(-v[i], w, p[0]);
+}
+
 __global__ void __launch_bounds__(EIG_THREADS, 1) k_eigen(int n, const double* __restrict__ A,
                                                        double* Hbuf, double* Zbuf, double* Vbuf,
                                                        double* lam_re, double* lam_im,
@@ -165,25 +198,21 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eigen(int n, const double* _
     for (int i = tid; i < len; i += nt) H[(size_t)(k + 1 + i) * n + k] = (i == 0) ? beta : 0.0;
     // left: rows k+1.., columns k+1..
     for (int j = k + 1 + tid; j < n; j += nt) {
-      double w = 0.0;
-      for (int i = 0; i < len; ++i) w += vsh[i] * H[(size_t)(k + 1 + i) * n + j];
-      w *= tau;
-      for (int i = 0; i < len; ++i) H[(size_t)(k + 1 + i) * n + j] -= vsh[i] * w;
+      double* Hj = H + (size_t)(k + 1) * n + j;
+      const double w = dotv(len, vsh, Hj, n) * tau;
+      axpyv(len, vsh, Hj, n, w);
     }
     __syncthreads();
     // right: every row of H and of Z (thread per row; Z column-major)
     for (int i = tid; i < n; i += nt) {
       double* Hi = H + (size_t)i * n + k + 1;
-      double w = 0.0;
-      for (int j = 0; j < len; ++j) w += Hi[j] * vsh[j];
-      w *= tau;
-      for (int j = 0; j < len; ++j) Hi[j] -= w * vsh[j];
+      const double w = dotv(len, vsh, Hi, 1) * tau;
+      axpyv(len, vsh, Hi, 1, w);
     }
     for (int i = tid; i < n; i += nt) {
-      double w = 0.0;
-      for (int j = 0; j < len; ++j) w += Z[(size_t)(k + 1 + j) * n + i] * vsh[j];
-      w *= tau;
-      for (int j = 0; j < len; ++j) Z[(size_t)(k + 1 + j) * n + i] -= w * vsh[j];
+      double* Zi = Z + (size_t)(k + 1) * n + i;
+      const double w = dotv(len, vsh, Zi, n) * tau;
+      axpyv(len, vsh, Zi, n, w);
     }
     __syncthreads();
   }
