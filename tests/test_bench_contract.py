@@ -44,5 +44,10 @@ def test_roofline_picks_the_bounding_unit():
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
     r = bench.roofline([dict(tensor_stage, ms=200.0), fp64_stage], clk, "mixed")
     assert r["bound"] == "tensor" and r["kernel_stage"] == "recon_part"
-    assert abs(r["achieved"] - 1.2e14 / 0.200 / 1e12) < 1e-9
+    # achieved: the algorithmic (FP64-equivalent) rate; peak: the BF16 rate scaled by the
+    # algorithmic FLOPs per slice-product FLOP, so frac is also the slice products' BF16 fraction
+    assert abs(r["achieved"] - 4.4e12 / 0.200 / 1e12) < 1e-9
+    assert abs(r["slice_products_tflops"] - 1.2e14 / 0.200 / 1e12) < 1e-9
+    assert abs(r["peak"] - r["bf16_peak"] * 4.4e12 / 1.2e14) < 1e-9
+    assert abs(r["frac"] - r["slice_products_tflops"] / r["bf16_peak"]) < 1e-12
     assert r["unit"] == "TFLOP/s"
