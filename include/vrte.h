@@ -98,7 +98,7 @@ typedef struct {
 
 /* Allocates, in vrte_set_layer, the workspace of a multi-layer slab made of the layers set
  * (vrte_solve_slab_brdf): per sub-layer and order of a batch, the block elimination's
- * factors. The plan then runs one slot (no concurrent layers). */
+ * factors, held once by the plan beside its workspace slots. */
 #define VRTE_FLAG_SLAB 8u
 
 /* Per-stage statistics accumulated since the last vrte_profile_reset. */
@@ -204,8 +204,10 @@ vrte_status vrte_solve_radiance(vrte_plan* plan, const double* h_tau, void* d_up
  * bottom conditions of Sec. 2.C; the upward radiance at the top is the sum of the
  * sub-layers' reconstructions (Eqs. 36-38), each attenuated through the sub-layers above.
  * Solved in FP64 (block elimination of the block-tridiagonal system from the top, one
- * sub-layer at a time) with the plan's synthesis; requires a plan created with
- * VRTE_FLAG_SLAB (else VRTE_ERR_STATE). Asynchronous; no allocation. */
+ * sub-layer at a time, while the mode stages of the next sub-layers run on the plan's other
+ * workspace slots and their streams, forked from and joined back into `stream`) with the
+ * plan's synthesis; requires a plan created with VRTE_FLAG_SLAB (else VRTE_ERR_STATE).
+ * Asynchronous; no allocation. */
 vrte_status vrte_solve_slab_brdf(vrte_plan* plan, void* d_brdf, int out_dtype, void* stream);
 
 /* Same solve as vrte_solve_brdf (same passages) with host buffers: copies h_coeffs (host

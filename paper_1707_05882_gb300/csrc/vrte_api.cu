@@ -90,6 +90,8 @@ struct Work {
          *sV = nullptr;
   cudaStream_t stream = nullptr;  // own stream when the plan runs several slots
   cudaEvent_t done = nullptr;
+  // slab on several slots: the slot's modes are ready / the slot may be reused
+  cudaEvent_t ready = nullptr, freed = nullptr;
 };
 constexpr int kMaxSlots = 4;
 
@@ -326,10 +328,12 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   free_workspace(p, kPlanAllocs);
   for (Work& x : p->ws) {
     cudaStream_t st_ = x.stream;
-    cudaEvent_t ev_ = x.done;
+    cudaEvent_t ev_ = x.done, er_ = x.ready, ef_ = x.freed;
     x = Work();
     x.stream = st_;
     x.done = ev_;
+    x.ready = er_;
+    x.freed = ef_;
   }
   p->last_U = 0;
   p->layers.assign(hp, hp + n_layers);
@@ -370,9 +374,12 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   if (transmission) per_unit += 4 * Ro * R;
   const bool slab = (p->desc.flags & VRTE_FLAG_SLAB) != 0;
   const size_t S_sub = (size_t)n_layers;
-  if (slab)
-    per_unit += S_sub * (4 * n * n + 2 * n * R + 2 * n * n + Ro * 2 * n) + 2 * 2 * n * n +
-                2 * n * R + n * R + n * n + 2 * Ro * R + n * R;
+  // a slab's elimination buffers, once per plan (slot 0): per sub-layer and order D'^-1, y,
+  // Uup, Hhat; shared Ldn x 2, Pd x 2, Zt, Ldn W, a contraction, the top radiance, Uup c
+  const size_t slab_unit =
+      slab ? S_sub * (4 * n * n + 2 * n * R + 2 * n * n + Ro * 2 * n) + 2 * 2 * n * n +
+                 2 * n * R + n * R + n * n + 2 * Ro * R + n * R
+           : 0;
   size_t isyn = (size_t)Mx * p->n_in * p->n_out * 16;
   size_t free_b = 0, total_b = 0;
   cudaMemGetInfo(&free_b, &total_b);
@@ -382,8 +389,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   // what is left (capped at 96 GiB) so that the caller's output table still fits beside it.
   const size_t fixed_slot =
       ((transmission ? 2 : 1) * isyn + (size_t)p->n_in * p->n_out) * sizeof(double);
-  // a slab's sub-layers share one slot: its order batches run them in turn
-  int nslots = slab ? 1 : std::max(1, std::min(n_layers, kMaxSlots));
+  int nslots = std::max(1, std::min(n_layers, kMaxSlots));
   size_t U = 0;
   for (;; --nslots) {
     size_t need_fixed = nslots * fixed_slot + ((size_t)64 << 20);
@@ -392,7 +398,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
       continue;
     }
     size_t budget = std::min((size_t)(0.35 * (double)(free_b - need_fixed)), (size_t)96 << 30);
-    size_t units = budget / nslots / (per_unit * sizeof(double));
+    size_t units = budget / ((nslots * per_unit + slab_unit) * sizeof(double));
     units = std::max<size_t>(1, std::min<size_t>(units, (size_t)Mx));
     U = units;
     if (nslots == 1 || units == (size_t)Mx) break;
@@ -443,7 +449,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   }
   VRTE_ALLOC(Isyn, isyn)
   VRTE_ALLOC(basebuf, 2 * n + R)
-  if (slab) {
+  if (slab && slot == 0) {
     VRTE_ALLOC(sDinv, S_sub * U * 4 * n * n) VRTE_ALLOC(sY, S_sub * U * 2 * n * R)
     VRTE_ALLOC(sUup, S_sub * U * 2 * n * n) VRTE_ALLOC(sH, S_sub * U * Ro * 2 * n)
     VRTE_ALLOC(sL[0], U * 2 * n * n) VRTE_ALLOC(sL[1], U * 2 * n * n)
@@ -464,6 +470,11 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
     if (!w->stream && cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess)
       return VRTE_ERR_CUDA;
     if (!w->done && cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming) != cudaSuccess)
+      return VRTE_ERR_CUDA;
+    if (slab && ((!w->ready && cudaEventCreateWithFlags(&w->ready, cudaEventDisableTiming) !=
+                                   cudaSuccess) ||
+                 (!w->freed && cudaEventCreateWithFlags(&w->freed, cudaEventDisableTiming) !=
+                                   cudaSuccess)))
       return VRTE_ERR_CUDA;
   }
   }
@@ -1066,11 +1077,18 @@ vrte_status vrte_solve_btdf(vrte_plan* p, void* d_btdf, int out_dtype, void* str
 // arrives; then back-substitution from the bottom, the sub-layers' top radiances summed with
 // the attenuation through the sub-layers above, the base's radiance, and the plan's synthesis.
 static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStream_t s) {
+  // slot 0 holds the elimination buffers; sub-layer k computes its modes on slot k mod ns,
+  // on the slot's own stream when the plan has several, so that the mode stages (eigen-
+  // decompositions first of all) of consecutive sub-layers run concurrently while the
+  // caller's stream carries the elimination, one sub-layer after the other. Each slot's
+  // `ready` event hands its modes to the elimination, its `freed` event hands the slot back.
   Work* w = &p->ws[0];
+  const int ns = p->nslots;
   p->last_slot = 0;
   const int S = p->n_layers;
   const vrte_layer& top = p->layers[0];
   const vrte_layer& bot = p->layers[S - 1];
+  Work* wl = &p->ws[(S - 1) % ns];  // the last sub-layer's slot (the base's buffers)
   const int N = top.n_nodes, n = 4 * N, n2 = 2 * n;
   const int R = 4 * p->n_in, Ro = 4 * p->n_out;
   const int P = N + p->n_in + p->n_out;
@@ -1086,11 +1104,19 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
   const int U0 = p->chunk;
   const long long nn = (long long)n * n, nR = (long long)n * R, RoR = (long long)Ro * R;
   const long long sD = 4 * nn, sYk = 2 * nR, sUk = 2 * nn, sHk = (long long)Ro * n2;
-  {
-    StageScope sc(p, ST_TABLES, s, 2, 0.0, 0.0);
-    launch_gauss_nodes(N, w->d_mu_nodes, w->d_w_nodes, p->d_status, s);
-    launch_interface(N, p->n_in, p->n_out, top.n_interface, w->d_mu_nodes, p->d_mu_in,
-                     p->d_mu_out, w->d_pts, w->d_min4, w->d_mout4, w->d_rtop4, s);
+  auto slot_stream = [&](int j) { return ns > 1 ? p->ws[j].stream : s; };
+  if (ns > 1) {
+    if (cudaEventRecord(p->fork, s) != cudaSuccess) return VRTE_ERR_CUDA;
+    for (int j = 0; j < ns; ++j)
+      if (cudaStreamWaitEvent(p->ws[j].stream, p->fork, 0) != cudaSuccess) return VRTE_ERR_CUDA;
+  }
+  for (int j = 0; j < std::min(ns, S); ++j) {
+    Work* wj = &p->ws[j];
+    StageScope sc(p, ST_TABLES, slot_stream(j), 2, 0.0, 0.0);
+    launch_gauss_nodes(N, wj->d_mu_nodes, wj->d_w_nodes, p->d_status, slot_stream(j));
+    launch_interface(N, p->n_in, p->n_out, top.n_interface, wj->d_mu_nodes, p->d_mu_in,
+                     p->d_mu_out, wj->d_pts, wj->d_min4, wj->d_mout4, wj->d_rtop4,
+                     slot_stream(j));
   }
   for (int m0 = 0; m0 < Meff; m0 += U0) {
     const int U = std::min(U0, Meff - m0);
@@ -1105,11 +1131,17 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
       const double* coef = p->d_coeffs + (size_t)k * p->desc.n_coef_max * 6;
       const bool first = k == 0, last = k == S - 1;
       const bool base = last && ly.base_albedo > 0.0 && m0 == 0;
+      Work* wk = &p->ws[k % ns];
+      const cudaStream_t sk = slot_stream(k % ns);
+      if (ns > 1 && cudaStreamWaitEvent(sk, wk->freed, 0) != cudaSuccess) return VRTE_ERR_CUDA;
       {
-        StageScope sc(p, ST_TABLES, s, 1, 0.0, 0.0);
-        launch_depth_table(N, p->n_in, p->n_out, ly.tau, w->d_pts, w->g0tab, s);
+        StageScope sc(p, ST_TABLES, sk, 1, 0.0, 0.0);
+        launch_depth_table(N, p->n_in, p->n_out, ly.tau, wk->d_pts, wk->g0tab, sk);
       }
-      run_order_batch(p, w, ly, coef, m0, U, false, false, s, false);
+      run_order_batch(p, wk, ly, coef, m0, U, false, false, sk, false);
+      if (ns > 1 && (cudaEventRecord(wk->ready, sk) != cudaSuccess ||
+                     cudaStreamWaitEvent(s, wk->ready, 0) != cudaSuccess))
+        return VRTE_ERR_CUDA;
       ob = OrderBatch{N, n, ly.n_coef, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef,
                       p->d_status, n2, 2 * nR};
       double* Dk = w->sDinv + (size_t)k * U0 * sD;
@@ -1120,11 +1152,11 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
         // the sub-layer's particular and direct parts at the slab's top
         StageScope sc(p, ST_RECON_PART, s, first ? 2 : 3, 2.0 * dRo * dR * 2 * dn * dU,
                       8.0 * (dRo * 2 * dn + 2 * dn * dR + 3 * dRo * dR) * dU);
-        if (!first) launch_slab_scale_sd(ob, t_top[k], w->d_pts, w->SD, s);
-        dgemm_batched(Ro, R, n2, 1.0, w->Upm, n2, sHk, w->SD, R, 2 * nR, 0.0, w->sTq, R, RoR, U,
-                      s);
-        launch_slab_accum(ob, t_top[k], w->d_pts, w->T1, w->sTq, w->g0tab, w->sAcc, first, s);
-        cudaMemcpyAsync(Hk, w->Hhat, (size_t)U * sHk * sizeof(double), cudaMemcpyDeviceToDevice,
+        if (!first) launch_slab_scale_sd(ob, t_top[k], wk->d_pts, wk->SD, s);
+        dgemm_batched(Ro, R, n2, 1.0, wk->Upm, n2, sHk, wk->SD, R, 2 * nR, 0.0, w->sTq, R, RoR,
+                      U, s);
+        launch_slab_accum(ob, t_top[k], wk->d_pts, wk->T1, w->sTq, wk->g0tab, w->sAcc, first, s);
+        cudaMemcpyAsync(Hk, wk->Hhat, (size_t)U * sHk * sizeof(double), cudaMemcpyDeviceToDevice,
                         s);
       }
       StageScope sc(p, ST_BC_SOLVE, s, 4 + (base ? 2 : 0) + (first ? 0 : 4),
@@ -1132,14 +1164,15 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
                                        2.0 * dn * dR * 2 * dn) * dU +
                         (16.0 * dn * dn * dn + 2.0 * 4 * dn * dn * dR) * dU,
                     8.0 * (12 * dn * dn + 6 * dn * dR) * dU);
-      launch_slab_blocks(ob, first, w->X, w->Y, w->lam_re, w->lam_im, w->d_rtop4, w->K, Uk, Lcur,
-                         s);
-      launch_slab_rhs(ob, first, w->SD, w->d_rtop4, w->d_pts, Pprev, w->RHS, Pcur, w->sZt, s);
+      launch_slab_blocks(ob, first, wk->X, wk->Y, wk->lam_re, wk->lam_im, wk->d_rtop4, wk->K, Uk,
+                         Lcur, s);
+      launch_slab_rhs(ob, first, wk->SD, wk->d_rtop4, wk->d_pts, Pprev, wk->RHS, Pcur, w->sZt, s);
       if (base) {
-        launch_base_K(N, n, ly.tau, ly.base_albedo, w->X, w->Y, w->lam_re, w->lam_im,
-                      w->d_mu_nodes, w->d_w_nodes, w->K, w->basebuf, s);
-        launch_base_rhs(N, n, R, 2 * nR, ly.tau, ly.base_albedo, w->SD, w->d_pts, w->d_min4,
-                        w->d_mu_nodes, w->d_w_nodes, w->RHS, w->basebuf + 2 * n, 1, s, t_top[k]);
+        launch_base_K(N, n, ly.tau, ly.base_albedo, wk->X, wk->Y, wk->lam_re, wk->lam_im,
+                      wk->d_mu_nodes, wk->d_w_nodes, wk->K, wk->basebuf, s);
+        launch_base_rhs(N, n, R, 2 * nR, ly.tau, ly.base_albedo, wk->SD, wk->d_pts, wk->d_min4,
+                        wk->d_mu_nodes, wk->d_w_nodes, wk->RHS, wk->basebuf + 2 * n, 1, s,
+                        t_top[k]);
       }
       if (!first) {
         const double* Dp = w->sDinv + (size_t)(k - 1) * U0 * sD;  // D'_{k-1}^-1
@@ -1148,13 +1181,14 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
         dgemm_batched(n2, R, n, 1.0, Dp + n, n2, sD, w->sZt, R, nR, 1.0, Yp, R, sYk, U, s);
         // D'_k = D_k - [Ldn_{k-1} W_{k-1} Uup_k; 0],  b'_k = b_k - [Ldn_{k-1} y_{k-1}; 0]
         dgemm_batched(n, n, n2, 1.0, Lprev, n2, sUk, Dp + n, n2, sD, 0.0, w->sTnn, n, nn, U, s);
-        dgemm_batched(n, n2, n, -1.0, w->sTnn, n, nn, Uk, n2, sUk, 1.0, w->K, n2, sD, U, s);
-        dgemm_batched(n, R, n2, -1.0, Lprev, n2, sUk, Yp, R, sYk, 1.0, w->RHS, R, sYk, U, s);
+        dgemm_batched(n, n2, n, -1.0, w->sTnn, n, nn, Uk, n2, sUk, 1.0, wk->K, n2, sD, U, s);
+        dgemm_batched(n, R, n2, -1.0, Lprev, n2, sUk, Yp, R, sYk, 1.0, wk->RHS, R, sYk, U, s);
       }
-      batched_inverse(n2, w->K, Dk, U, p->d_status, s);
-      dgemm_batched(n2, R, n2, 1.0, Dk, n2, sD, w->RHS, R, sYk, 0.0, Yk, R, sYk, U, s);
+      batched_inverse(n2, wk->K, Dk, U, p->d_status, s);
+      dgemm_batched(n2, R, n2, 1.0, Dk, n2, sD, wk->RHS, R, sYk, 0.0, Yk, R, sYk, U, s);
       std::swap(Lprev, Lcur);
       std::swap(Pprev, Pcur);
+      if (ns > 1 && cudaEventRecord(wk->freed, s) != cudaSuccess) return VRTE_ERR_CUDA;
     }
     {
       // back-substitution from the bottom, c_k = y_k - W_k (Uup_{k+1} c_{k+1}), then the
@@ -1180,10 +1214,17 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
       // Lambertian base: its isotropic radiance at the bottom, attenuated through the slab
       if (bot.base_albedo > 0.0 && m0 == 0)
         launch_base_recon(n, N, p->n_in, p->n_out, ttot, bot.base_albedo,
-                          w->sY + (size_t)(S - 1) * U0 * sYk, w->basebuf, w->basebuf + 2 * n,
+                          w->sY + (size_t)(S - 1) * U0 * sYk, wl->basebuf, wl->basebuf + 2 * n,
                           w->d_pts, w->d_mout4, w->Isyn, 1, s);
     }
   }
+  // join: every slot stream's work is already behind a `ready` the caller's stream waited on;
+  // the join keeps the slot streams ordered before any later use of the plan
+  if (ns > 1)
+    for (int j = 0; j < ns; ++j)
+      if (cudaEventRecord(p->ws[j].done, p->ws[j].stream) != cudaSuccess ||
+          cudaStreamWaitEvent(s, p->ws[j].done, 0) != cudaSuccess)
+        return VRTE_ERR_CUDA;
   if (cudaPeekAtLastError() != cudaSuccess) {
     cudaGetLastError();
     return VRTE_ERR_CUDA;
@@ -1479,6 +1520,8 @@ void vrte_destroy(vrte_plan* p) {
   for (Work& x : p->ws) {
     if (x.stream) cudaStreamDestroy(x.stream);
     if (x.done) cudaEventDestroy(x.done);
+    if (x.ready) cudaEventDestroy(x.ready);
+    if (x.freed) cudaEventDestroy(x.freed);
   }
   if (p->fork) cudaEventDestroy(p->fork);
   for (int c = 0; c < 4; ++c) {

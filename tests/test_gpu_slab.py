@@ -131,3 +131,17 @@ def test_slab_argument_checks():
         assert e.value.code == 2  # VRTE_ERR_STATE: no slab workspace
     finally:
         plan.close()
+
+
+def test_slab_more_sublayers_than_slots():
+    # six sub-layers on the plan's four workspace slots: slots are reused within an order
+    # batch, each sub-layer's modes waiting until the elimination has used the slot's last ones
+    N, M = 8, 16
+    base = _stack(N, M)
+    lys = [dict(base[k % 3], n_interface=(1.4 if k == 0 else 1.0),
+                base_albedo=(0.25 if k == 5 else 0.0), tau=0.2 + 0.15 * k) for k in range(6)]
+    grids = angle_grids(6, 7, 5)
+    F = _solve_slab(lys, grids)
+    G = _oracle(lys, grids, N, M)
+    e_i, e_q = _err_rows(F, G)
+    assert e_i < 1e-10 and e_q < 1e-10, (e_i, e_q)
