@@ -52,7 +52,7 @@ def synthesis_weights(m: int, dphi):
     return w
 
 
-def brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho=0.0):
+def brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho=0.0, base=None):
     """Per-order internal exiting radiance I^m [M, n_in, n_out, 4, 4] plus interface data."""
     coef = np.asarray(coef, dtype=float)
     mu_in = np.atleast_1d(np.asarray(mu_in, dtype=float))
@@ -65,7 +65,7 @@ def brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho=0.0):
     L = coef.shape[0]
     Im = np.zeros((M, mu_in.size, mu_out.size, 4, 4))
     for m in range(min(M, L)):
-        sol = solve_order(m, coef, omega, tau0, N, mu0_int, beam, R_top, nodes, rho)
+        sol = solve_order(m, coef, omega, tau0, N, mu0_int, beam, R_top, nodes, rho, base)
         Im[m] = sol.reconstruct_top(mu_out_int)
     return Im
 
@@ -84,14 +84,15 @@ def synthesize(Im, mu_in, mu_out, dphi, n_interface):
     return F / mu_in[:, None, None, None, None]
 
 
-def brdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi, rho=0.0):
+def brdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi, rho=0.0, base=None):
     """Mueller BRDF table F[n_in, n_out, n_phi, 4, 4] of one layer (FP64); rho is the albedo
-    of a Lambertian base (0: black base)."""
-    Im = brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho)
+    of a Lambertian base (0: black base), base a direction-independent 4x4 Mueller BRDF of a
+    reflecting base added to it (R_00 = 2 rho)."""
+    Im = brdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho, base)
     return synthesize(Im, mu_in, mu_out, dphi, n_interface)
 
 
-def btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho=0.0):
+def btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho=0.0, base=None):
     """Per-order downward radiance at the bottom I^m(tau0, -mu_out) [M, n_in, n_out, 4, 4].
 
     mu_out are cosines of downward directions below the layer, which has no interface at the
@@ -110,22 +111,23 @@ def btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho=0.0):
     L = coef.shape[0]
     Im = np.zeros((M, mu_in.size, mu_out.size, 4, 4))
     for m in range(min(M, L)):
-        sol = solve_order(m, coef, omega, tau0, N, mu0_int, beam, R_top, nodes, rho)
+        sol = solve_order(m, coef, omega, tau0, N, mu0_int, beam, R_top, nodes, rho, base)
         Im[m] = sol.reconstruct_bottom(mu_out, R_out)
     return Im
 
 
-def btdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi, rho=0.0):
+def btdf(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, dphi, rho=0.0, base=None):
     """Mueller BTDF table T[n_in, n_out, n_phi, 4, 4] of one layer (FP64): the diffuse
     radiance leaving the bottom in direction (-mu_out, phi_out) per unit irradiance mu_in I0
     of the beam from (mu_in, phi_in) above, dphi = phi_out - phi_in, Stokes vectors on the
     meridian frames of the propagation directions (Eq. 12 with the same Fourier factors as
     the BRDF; no exit interface)."""
-    Im = btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho)
+    Im = btdf_orders(coef, omega, tau0, n_interface, N, M, mu_in, mu_out, rho, base)
     return synthesize(Im, mu_in, mu_out, dphi, 1.0)
 
 
-def radiance_orders(coef, omega, tau0, n_interface, N, M, mu_in, tau, mu_up, mu_down, rho=0.0):
+def radiance_orders(coef, omega, tau0, n_interface, N, M, mu_in, tau, mu_up, mu_down, rho=0.0,
+                    base=None):
     """Per-order internal radiance at depth tau for incident beams mu_in (external, through the
     top): (up [M, n_in, n_up, 4, 4], down [M, n_in, n_down, 4, 4]) at the internal cosines
     mu_up (upward) and mu_down (downward)."""
@@ -142,16 +144,18 @@ def radiance_orders(coef, omega, tau0, n_interface, N, M, mu_in, tau, mu_up, mu_
     dn = np.zeros((M, mu_in.size, mu_down.size, 4, 4))
     for m in range(min(M, L)):
         sol = solve_order(m, coef, omega, tau0, N, snell_mu(mu_in, n_interface),
-                          fresnel_beam_in(mu_in, n_interface), R_top, nodes, rho)
+                          fresnel_beam_in(mu_in, n_interface), R_top, nodes, rho, base)
         up[m], dn[m] = sol.reconstruct_depth(tau, mu_up, mu_down, R_dn)
     return up, dn
 
 
-def radiance(coef, omega, tau0, n_interface, N, M, mu_in, tau, mu_up, mu_down, dphi, rho=0.0):
+def radiance(coef, omega, tau0, n_interface, N, M, mu_in, tau, mu_up, mu_down, dphi, rho=0.0,
+             base=None):
     """Radiance field inside the layer at depth tau per unit irradiance mu_in I0 of the beam:
     (up [n_in, n_up, n_phi, 4, 4], down [n_in, n_down, n_phi, 4, 4]), directions (+-mu, phi)
     with dphi = phi - phi_in and Stokes vectors on their meridian frames (Eq. 12)."""
-    up, dn = radiance_orders(coef, omega, tau0, n_interface, N, M, mu_in, tau, mu_up, mu_down, rho)
+    up, dn = radiance_orders(coef, omega, tau0, n_interface, N, M, mu_in, tau, mu_up, mu_down, rho,
+                             base)
     return (synthesize(up, mu_in, mu_up, dphi, 1.0), synthesize(dn, mu_in, mu_down, dphi, 1.0))
 
 

@@ -74,7 +74,8 @@ class OrderSolution:
     Right-hand sides are indexed (beam i, incident Stokes column s) -> i*4 + s.
     """
 
-    def __init__(self, m, coef, omega, tau0, mu_nodes, alpha, mu0, beam, R_top, rho=0.0):
+    def __init__(self, m, coef, omega, tau0, mu_nodes, alpha, mu0, beam, R_top, rho=0.0,
+                 base=None):
         self.m = m
         self.coef = np.asarray(coef, dtype=float)
         self.omega = float(omega)
@@ -124,22 +125,34 @@ class OrderSolution:
         rhs = np.zeros((n8, n_rhs))
         rhs[:4 * N] = -(self.z[down] - R @ self.z[up])
         rhs[4 * N:] = -self.z[up] * att[None, :]
-        # Lambertian base of albedo rho (Sec. 3.C, base reflection; order 0 only, as the
-        # depolarizing Lambertian reflector has no azimuth dependence): the upward radiance at
-        # the bottom is isotropic and unpolarized,
-        #   I^0(tau0, +mu) = 2 rho sum_j alpha_j mu_j I^0_I(tau0, -mu_j) + (2 rho / pi) mu0 I0'_I e^{-tau0/mu0}
-        # (R_00 = 2 rho of the paper; the beam's order-0 Fourier part is I0'/pi in the Fourier
-        # convention of Eq. 12, the same factor-2 reading as the source constant).
+        # Reflecting base (Sec. 3.C, base reflection) with a direction-independent Mueller BRDF
+        # R of the base (R = base + 2 rho e0 e0^T; the Lambertian base of albedo rho is
+        # R_00 = 2 rho): only order 0 sees it, as it has no azimuth dependence. The upward
+        # radiance at the bottom is isotropic,
+        #   I^0(tau0, +mu) = R sum_j alpha_j mu_j I^0(tau0, -mu_j) + (1/pi) mu0 R I0' e^{-tau0/mu0}
+        # (the beam's order-0 Fourier part is I0'/pi in the Fourier convention of Eq. 12, the
+        # same factor-2 reading as the source constant). An azimuth-independent R keeps its
+        # (I, Q) x (U, V) blocks zero: those couple through the sine terms, which vanish at m = 0.
         self.rho = float(rho) if m == 0 else 0.0
-        if self.rho > 0.0:
+        Rg = np.zeros((4, 4))
+        if m == 0:
+            Rg[0, 0] = 2.0 * float(rho)
+            if base is not None:
+                Rg = Rg + np.asarray(base, dtype=float).reshape(4, 4)
+        self.Rbase = Rg if np.any(Rg != 0.0) else None
+        if self.Rbase is not None:
             Rb = np.zeros((4 * N, 4 * N))
             for i in range(N):
-                Rb[4 * i, 4 * np.arange(N)] = 2.0 * self.rho * self.alpha * self.mu_nodes
+                for j in range(N):
+                    Rb[4 * i:4 * i + 4, 4 * j:4 * j + 4] = Rg * (self.alpha[j] * self.mu_nodes[j])
             self.Rb = Rb
             K[4 * N:] -= (Rb @ V[down]) * f1[None, :]
             rhs[4 * N:] += (Rb @ self.z[down]) * att[None, :]
-            ls = (2.0 * self.rho / np.pi) * self.rhs_mu0 * att * self.beam.reshape(-1, 4, 4)[:, 0, :].reshape(-1)
-            rhs[4 * N:][0::4] += ls[None, :]
+            ls = np.einsum("ab,kbs->kas", Rg, self.beam.reshape(-1, 4, 4))   # [n_beams, a, s]
+            ls = ls * (self.mu0 * np.exp(-self.tau0 / self.mu0) / np.pi)[:, None, None]
+            ls = ls.transpose(1, 0, 2).reshape(4, -1)                         # [a, 4 k + s]
+            for i in range(N):
+                rhs[4 * N + 4 * i:4 * N + 4 * i + 4] += ls
         self.K = K
         self.c = np.linalg.solve(K, rhs.astype(complex))
 
@@ -205,11 +218,11 @@ class OrderSolution:
             Ad = _stack_matrix(A_matrix(self.m, self.coef, mu_out, [-mu0]))  # [4 n_out, 4]
             direct[:, 4 * i:4 * i + 4] = self.cQ * Ad @ self.beam[i]
         tot = hom + (part + direct) * g0
-        if self.rho > 0.0:
+        if self.Rbase is not None:
             # the base's isotropic radiance I^0(tau0, +mu) attenuated along the exit path
             up = self.nodal(t0, real=False)[:4 * self.N]                   # u_up(tau0) [4N, n_rhs]
-            base = up[0]                                                 # same at every node
-            tot[0::4] += np.exp(-t0 / mu_rows[0::4])[:, None] * base[None, :]
+            for a in range(4):                                           # same at every node
+                tot[a::4] += np.exp(-t0 / mu_rows[a::4])[:, None] * up[a][None, :]
         self.max_imag = float(np.max(np.abs(tot.imag))) if np.iscomplexobj(tot) else 0.0
         out = tot.real.reshape(n_out, 4, n_b, 4).transpose(2, 0, 1, 3)
         return out
@@ -338,9 +351,10 @@ def _reconstruct_depth(self, tau, mu_up, mu_down, R_down=None):
             Ad = _stack_matrix(A_matrix(self.m, self.coef, sign * mus, [-mu0]))
             direct[:, 4 * i:4 * i + 4] = self.cQ * Ad @ self.beam[i]
         tot = (hom + (GW @ self.z + direct) * g0).real
-        if sign > 0 and self.rho > 0.0:
-            base = self.nodal(t0)[0]                       # the base's isotropic radiance
-            tot[0::4] += np.exp(-(t0 - tau) / mus)[:, None] * base[None, :]
+        if sign > 0 and self.Rbase is not None:
+            base = self.nodal(t0)[:4]                      # the base's isotropic radiance
+            for a in range(4):
+                tot[a::4] += np.exp(-(t0 - tau) / mus)[:, None] * base[a][None, :]
         res = tot.reshape(mus.size, 4, n_b, 4).transpose(2, 0, 1, 3)
         if sign < 0 and R_down is not None:
             top = self.reconstruct_top(mus)
@@ -353,13 +367,15 @@ def _reconstruct_depth(self, tau, mu_up, mu_down, R_down=None):
 OrderSolution.reconstruct_depth = _reconstruct_depth
 
 
-def solve_order(m, coef, omega, tau0, N, mu0_int, beam=None, R_top=None, nodes=None, rho=0.0):
+def solve_order(m, coef, omega, tau0, N, mu0_int, beam=None, R_top=None, nodes=None, rho=0.0,
+                base=None):
     """Solve Fourier order m for internal beam cosines mu0_int.
 
     beam[i] is the 4x4 matrix whose column s is the internal beam Stokes vector
     produced by incident Stokes basis vector s (identity without an interface).
     R_top[n] is the 4x4 internal reflection at node n (None for a bare top); rho the albedo of
-    a Lambertian base (0: black base).
+    a Lambertian base (0: black base); base a direction-independent 4x4 Mueller BRDF of the base
+    added to the Lambertian one (R_00 = 2 rho).
     """
     mu0_int = np.atleast_1d(np.asarray(mu0_int, dtype=float))
     if beam is None:
@@ -367,4 +383,4 @@ def solve_order(m, coef, omega, tau0, N, mu0_int, beam=None, R_top=None, nodes=N
     if nodes is None:
         nodes = gauss_legendre_01(N)
     mu_n, alpha = nodes
-    return OrderSolution(m, coef, omega, tau0, mu_n, alpha, mu0_int, beam, R_top, rho)
+    return OrderSolution(m, coef, omega, tau0, mu_n, alpha, mu0_int, beam, R_top, rho, base)

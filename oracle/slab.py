@@ -30,7 +30,19 @@ from .fresnel import fresnel_beam_in, fresnel_internal_reflection, snell_mu
 from .quadrature import gauss_legendre_01
 
 
-def solve_slab_order(m, sublayers, N, mu0_int, beam, R_top, rho=0.0, nodes=None):
+def _base_matrix(m, rho, base):
+    """The base's direction-independent Mueller BRDF R (R_00 = 2 rho for the Lambertian part)
+    seen by order m (only order 0), or None."""
+    if m != 0:
+        return None
+    Rg = np.zeros((4, 4))
+    Rg[0, 0] = 2.0 * float(rho)
+    if base is not None:
+        Rg = Rg + np.asarray(base, dtype=float).reshape(4, 4)
+    return Rg if np.any(Rg != 0.0) else None
+
+
+def solve_slab_order(m, sublayers, N, mu0_int, beam, R_top, rho=0.0, nodes=None, base=None):
     """Order m of a stack: list of per-sub-layer OrderSolution objects whose `c` are the stack's
     coefficients (each built with the beam attenuated to its top). sublayers: dicts with coef,
     omega, tau."""
@@ -76,45 +88,50 @@ def solve_slab_order(m, sublayers, N, mu0_int, beam, R_top, rho=0.0, nodes=None)
     att = np.exp(-sl.tau0 / sl.rhs_mu0)[None, :]
     A[row:, (K - 1) * n8:] = sl.V[up] * f1[None, :]
     b[row:] = -sl.z[up] * att
-    if rho > 0.0 and m == 0:
+    Rg = _base_matrix(m, rho, base)
+    if Rg is not None:
         Rb = np.zeros((n4, n4))
         for i in range(N):
-            Rb[4 * i, 4 * np.arange(N)] = 2.0 * rho * alpha * mu_n
+            for j in range(N):
+                Rb[4 * i:4 * i + 4, 4 * j:4 * j + 4] = Rg * (alpha[j] * mu_n[j])
         A[row:, (K - 1) * n8:] -= (Rb @ sl.V[down]) * f1[None, :]
         b[row:] += (Rb @ sl.z[down]) * att
         ttot = tops[-1] + sl.tau0
-        ls = (2.0 * rho / np.pi) * sl.rhs_mu0 * np.exp(-ttot / sl.rhs_mu0) \
-            * beam.reshape(-1, 4, 4)[:, 0, :].reshape(-1)
-        b[row:][0::4] += ls[None, :]
+        ls = np.einsum("ab,kbs->kas", Rg, beam.reshape(-1, 4, 4))
+        ls = ls * (mu0_int * np.exp(-ttot / mu0_int) / np.pi)[:, None, None]
+        ls = ls.transpose(1, 0, 2).reshape(4, -1)                 # [a, 4 k + s]
+        for i in range(N):
+            b[row + 4 * i:row + 4 * i + 4] += ls
     c = np.linalg.solve(A, b)
     for k, s in enumerate(sols):
         s.c = c[k * n8:(k + 1) * n8]
-        s.rho = 0.0
     return sols, tops
 
 
-def slab_reconstruct_top(sols, tops, mu_out, rho=0.0, m=0):
+def slab_reconstruct_top(sols, tops, mu_out, rho=0.0, m=0, base=None):
     """I^m(0, mu) [n_beams, n_out, 4, 4] of the stack at internal upward cosines mu."""
     mu_out = np.atleast_1d(np.asarray(mu_out, dtype=float))
     out = 0.0
     for s, t in zip(sols, tops):
         out = out + np.exp(-t / mu_out)[None, :, None, None] * s.reconstruct_top(mu_out)
-    if rho > 0.0 and m == 0:
+    if _base_matrix(m, rho, base) is not None:
         last = sols[-1]
-        base = last.nodal(last.tau0)[0]                     # the base's isotropic radiance
+        rad = last.nodal(last.tau0)[:4]                     # the base's isotropic radiance
         ttot = tops[-1] + last.tau0
         n_b = last.mu0.size
         add = np.zeros((n_b, mu_out.size, 4, 4))
-        add[:, :, 0, :] = (np.exp(-ttot / mu_out)[None, :, None]
-                           * base.reshape(n_b, 4)[:, None, :])
+        for a in range(4):
+            add[:, :, a, :] = (np.exp(-ttot / mu_out)[None, :, None]
+                               * rad[a].reshape(n_b, 4)[:, None, :])
         out = out + add
     return out
 
 
-def slab_brdf(sublayers, n_interface, N, M, mu_in, mu_out, dphi, rho=0.0):
+def slab_brdf(sublayers, n_interface, N, M, mu_in, mu_out, dphi, rho=0.0, base=None):
     """Mueller BRDF table F[n_in, n_out, n_phi, 4, 4] of a stack of sub-layers (top first; each
     a dict with coef [L_k, 6], omega, tau) under an optional dielectric top and over an
-    optional Lambertian base. Orders beyond every sub-layer's expansion contribute nothing."""
+    optional reflecting base (Lambertian albedo rho and/or a direction-independent Mueller BRDF
+    `base`, added). Orders beyond every sub-layer's expansion contribute nothing."""
     mu_in = np.atleast_1d(np.asarray(mu_in, dtype=float))
     mu_out = np.atleast_1d(np.asarray(mu_out, dtype=float))
     nodes = gauss_legendre_01(N)
@@ -125,6 +142,6 @@ def slab_brdf(sublayers, n_interface, N, M, mu_in, mu_out, dphi, rho=0.0):
     Lmax = max(np.asarray(s["coef"]).shape[0] for s in sublayers)
     Im = np.zeros((M, mu_in.size, mu_out.size, 4, 4))
     for m in range(min(M, Lmax)):
-        sols, tops = solve_slab_order(m, sublayers, N, mu0_int, beam, R_top, rho, nodes)
-        Im[m] = slab_reconstruct_top(sols, tops, mu_out_int, rho, m)
+        sols, tops = solve_slab_order(m, sublayers, N, mu0_int, beam, R_top, rho, nodes, base)
+        Im[m] = slab_reconstruct_top(sols, tops, mu_out_int, rho, m, base)
     return synthesize(Im, mu_in, mu_out, dphi, n_interface)

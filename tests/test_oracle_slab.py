@@ -122,3 +122,12 @@ def test_nodal_field_continuity_and_boundaries(mie):
                 * beam[:, 0, :].reshape(-1)
             target[0::4] = flux + direct
         assert np.abs(u1[:4 * N] - target).max() < 1e-12 * np.abs(u1).max()
+
+
+def test_identical_sublayers_over_a_mueller_base(mie):
+    R = np.array([[0.8, 0.15, 0, 0], [0.15, 0.4, 0, 0], [0, 0, 0.35, 0.12], [0, 0, -0.12, 0.3]])
+    grids = angle_grids(3, 4, 5)
+    F1 = O.brdf(mie, 0.9, 1.5, 1.4, 5, 12, *grids, base=R)
+    F3 = slab_brdf([dict(coef=mie, omega=0.9, tau=t) for t in (0.2, 0.9, 0.4)], 1.4, 5, 12,
+                   *grids, base=R)
+    assert _rel(F3, F1) < 1e-12
