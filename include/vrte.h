@@ -26,8 +26,9 @@
  *     surface;
  *   - optional smooth dielectric top of relative index n > 1 (Fresnel
  *     transmission in and out, internal specular reflection as the top boundary
- *     condition); n <= 1 means a bare top. Black lower boundary, or a depolarizing
- *     Lambertian base (vrte_layer.base_albedo).
+ *     condition); n <= 1 means a bare top. Black lower boundary, or a reflecting
+ *     base with a direction-independent Mueller BRDF matrix (vrte_layer.base_albedo
+ *     for the depolarizing Lambertian base, vrte_layer.base_mueller in general).
  *
  * Threading and ownership: a plan is used by one host thread at a time. All
  * d_* pointers are device memory owned by the caller; the plan owns its
@@ -122,6 +123,13 @@ typedef struct {
   int n_coef;          /* L of this layer, 1..n_coef_max */
   double base_albedo;  /* albedo rho in [0, 1] of a depolarizing Lambertian base under the
                           layer (Sec. 3.C, base reflection, R_00 = 2 rho); 0 = black base */
+  double base_mueller[16]; /* direction-independent 4x4 Mueller BRDF matrix R of a reflecting
+                          base under the layer, row-major, added to the Lambertian
+                          2 rho e0 e0^T (Sec. 3.C, base reflection, Eqs. 57-66 with R not
+                          depending on mu_i, mu_j, mu0). Scale as the paper's R: a bare base
+                          reflects the table R / (2 pi). Only order 0 sees it, so its
+                          (I, Q) x (U, V) entries R[0..1][2..3], R[2..3][0..1] must be 0;
+                          the total R_00 must lie in [0, 2]; all zero = no extra base */
 } vrte_layer;
 
 typedef struct vrte_plan vrte_plan;
@@ -140,7 +148,9 @@ vrte_status vrte_plan_create(const vrte_plan_desc* desc, vrte_plan** out);
  * layer's n_coef; the pointer is kept and read by each solve (the caller keeps
  * it alive). Allocates the solve workspace for these layers. A VRTE_MIXED plan
  * contracts over the 4 n_coef (l, component) pairs on the tensor cores and returns
- * VRTE_ERR_UNSUPPORTED when 4 n_coef > 1024 (before touching the workspace). */
+ * VRTE_ERR_UNSUPPORTED when 4 n_coef > 1024 (before touching the workspace).
+ * VRTE_ERR_INVALID_ARG for a parameter out of range (see vrte_layer), including a base
+ * matrix with a non-finite entry, a nonzero (I, Q) x (U, V) entry or R_00 outside [0, 2]. */
 vrte_status vrte_set_layer(vrte_plan* plan, int n_layers, const vrte_layer* host_params,
                            const double* d_coeffs);
 
@@ -182,7 +192,7 @@ vrte_status vrte_solve_btdf(vrte_plan* plan, void* d_btdf, int out_dtype, void* 
  *   d_down[...]                                        directions (-mu_out, phi), downward
  * (either may be NULL; layout and Stokes frames as d_brdf, dphi = phi - phi_in). Paper:
  * Sec. 2.C reconstruction at an arbitrary tau (Eqs. 36-38 with the integration ranges
- * [tau, tau0] upward and [0, tau] downward; the boundary radiances are the Lambertian base's at
+ * [tau, tau0] upward and [0, tau] downward; the boundary radiances are the reflecting base's at
  * tau0 and the top's internal reflection at 0) and Sec. 4's radiance-field experiment.
  * d_up at tau = 0 is the internal upward radiance under the top; d_down at tau0 the
  * transmission table. Solved as vrte_solve_btdf; requires VRTE_FLAG_TRANSMISSION (else
@@ -195,7 +205,8 @@ vrte_status vrte_solve_radiance(vrte_plan* plan, const double* h_tau, void* d_up
  * thicknesses above it), each with its own expansion coefficients, albedo and thickness:
  *   d_brdf[n_mu_in][n_mu_out][n_phi][4][4]  (one table; layout and units as vrte_solve_brdf).
  * The first sub-layer's n_interface is the slab's smooth top and the last one's base_albedo
- * its Lambertian base; the other sub-layers must have n_interface <= 1 and base_albedo 0, and
+ * and base_mueller its reflecting base; the other sub-layers must have n_interface <= 1 and a
+ * black base (base_albedo 0, base_mueller all 0), and
  * all must share n_nodes and n_orders (else VRTE_ERR_INVALID_ARG). Orders at or beyond a
  * sub-layer's n_coef see it as a purely attenuating layer. Paper: Sec. 2.C, multiple layer
  * materials: a homogeneous solution and a particular solution per sub-layer (for the beam
@@ -238,7 +249,8 @@ vrte_status vrte_solve_brdf_host(vrte_plan* plan, const double* h_coeffs, void* 
  * whose mode integrals are closed-form divided differences (finite at degenerate and complex
  * eigenvalues). Requires a plan created with VRTE_FLAG_ADJOINT and vrte_set_layer, else
  * VRTE_ERR_STATE; VRTE_ERR_INVALID_ARG for NULL pointers or an unknown grad_dtype;
- * VRTE_ERR_UNSUPPORTED when a layer has a reflecting base (base_albedo > 0).
+ * VRTE_ERR_UNSUPPORTED when a layer has a reflecting base (base_albedo > 0 or a nonzero
+ * base_mueller).
  * Asynchronous on `stream`; no allocation; layers run on the plan's streams as in
  * vrte_solve_brdf. Accuracy: ~1e-8 relative in the gradient's largest entries (the FP64
  * solution's rounding, amplified near a resonance mu kappa_j ~ 1 as in the solve). */

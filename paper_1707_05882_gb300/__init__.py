@@ -62,7 +62,7 @@ class Layer(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("omega", ctypes.c_double),
                 ("n_interface", ctypes.c_double), ("n_nodes", ctypes.c_int),
                 ("n_orders", ctypes.c_int), ("n_coef", ctypes.c_int),
-                ("base_albedo", ctypes.c_double)]
+                ("base_albedo", ctypes.c_double), ("base_mueller", ctypes.c_double * 16)]
 
 
 _LIB = None
@@ -166,13 +166,17 @@ class Plan:
         return (self.n_layers, self._mu_in.size, self._mu_out.size, self._phi.size, 4, 4)
 
     def set_layers(self, layers, d_coeffs):
-        """layers: list of dict(tau, omega, n_interface, n_nodes, n_orders, n_coef[, base_albedo]);
+        """layers: list of dict(tau, omega, n_interface, n_nodes, n_orders, n_coef[, base_albedo]
+        [, base_mueller]) with base_mueller a 4x4 Mueller matrix of a reflecting base
+        (row-major; the Lambertian base is base_albedo, R_00 = 2 rho);
         d_coeffs: CUDA float64 tensor [n_layers, n_coef_max, 6] (kept alive by the plan)."""
         arr = (Layer * len(layers))()
         for i, l in enumerate(layers):
+            bm = l.get("base_mueller")
+            bm = [0.0] * 16 if bm is None else [float(v) for v in np.asarray(bm, float).reshape(16)]
             arr[i] = Layer(float(l["tau"]), float(l["omega"]), float(l.get("n_interface", 1.0)),
                            int(l["n_nodes"]), int(l["n_orders"]), int(l["n_coef"]),
-                           float(l.get("base_albedo", 0.0)))
+                           float(l.get("base_albedo", 0.0)), (ctypes.c_double * 16)(*bm))
         self._coeffs = d_coeffs
         _check(self.lib.vrte_set_layer(self.handle, len(layers), arr,
                                        ctypes.c_void_p(d_coeffs.data_ptr())), "vrte_set_layer")

@@ -139,21 +139,28 @@ void dgemm_part_epilogue(const OrderBatch& b, const double* A, const double* B, 
 constexpr int BI = 16;   // panel width
 constexpr int TJ = 32;   // column tile of the outside update
 
+// T = double: the FP64 inverse. T = float: the same elimination in FP32 (the starting
+// inverse of the mixed form's Newton refinement), W an FP32 workspace. Orders u with
+// skip && !skip[u] return at once.
+template <typename T>
 __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict__ A,
-                                                 double* __restrict__ Ainv, unsigned* status) {
-  extern __shared__ double sh[];
-  double* P = sh;                  // [n][BI] panel
-  double* Cb = P + (size_t)n * BI; // [n][BI] step columns, then Z
-  double* Wb = Cb + (size_t)n * BI;// [BI][TJ] block rows of a column tile
+                                                 T* __restrict__ Ainv, unsigned* status,
+                                                 const int* __restrict__ skip) {
+  extern __shared__ __align__(16) unsigned char sh_raw[];
+  T* sh = (T*)sh_raw;
+  T* P = sh;                  // [n][BI] panel
+  T* Cb = P + (size_t)n * BI; // [n][BI] step columns, then Z
+  T* Wb = Cb + (size_t)n * BI;// [BI][TJ] block rows of a column tile
   int* perm = (int*)(Wb + BI * TJ);
-  __shared__ double red_v[16];
+  __shared__ T red_v[16];
   __shared__ int red_i[16];
-  __shared__ double rk[BI];
-  __shared__ double Q[BI][BI], G[BI][BI];
+  __shared__ T rk[BI];
+  __shared__ T Q[BI][BI], G[BI][BI];
   const int u = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+  if (skip && !skip[u]) return;
   const double* Ab = A + (size_t)u * n * n;
-  double* W = Ainv + (size_t)u * n * n;
-  for (size_t e = tid; e < (size_t)n * n; e += nt) W[e] = Ab[e];
+  T* W = Ainv + (size_t)u * n * n;
+  for (size_t e = tid; e < (size_t)n * n; e += nt) W[e] = (T)Ab[e];
   __syncthreads();
   for (int k0 = 0; k0 < n; k0 += BI) {
     const int bb = min(BI, n - k0);
@@ -165,14 +172,14 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
     // ---- panel elimination
     for (int c = 0; c < bb; ++c) {
       const int k = k0 + c;
-      double best = -1.0;
+      T best = -1;
       int bi = k;
       for (int i = k + tid; i < n; i += nt) {
-        double v = fabs(P[i * BI + c]);
+        T v = fabs(P[i * BI + c]);
         if (v > best) { best = v; bi = i; }
       }
       for (int off = 16; off > 0; off >>= 1) {
-        double ov = __shfl_down_sync(0xffffffffu, best, off);
+        T ov = __shfl_down_sync(0xffffffffu, best, off);
         int oi = __shfl_down_sync(0xffffffffu, bi, off);
         if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
       }
@@ -180,10 +187,10 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
       __syncthreads();
       if (tid < 32) {
         int nw = (nt + 31) >> 5;
-        best = tid < nw ? red_v[tid] : -1.0;
+        best = tid < nw ? red_v[tid] : (T)-1;
         bi = tid < nw ? red_i[tid] : k;
         for (int off = 16; off > 0; off >>= 1) {
-          double ov = __shfl_down_sync(0xffffffffu, best, off);
+          T ov = __shfl_down_sync(0xffffffffu, best, off);
           int oi = __shfl_down_sync(0xffffffffu, bi, off);
           if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
         }
@@ -193,7 +200,7 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
       const int p = red_i[0];
       if (p != k && tid < BI) {
         // the panel row, and the recorded columns of earlier steps, follow the swap
-        double t = P[k * BI + tid];
+        T t = P[k * BI + tid];
         P[k * BI + tid] = P[p * BI + tid];
         P[p * BI + tid] = t;
         if (tid < c) {
@@ -205,9 +212,9 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
       __syncthreads();
       for (int i = tid; i < n; i += nt) Cb[i * BI + c] = P[i * BI + c];
       __syncthreads();
-      const double piv = P[k * BI + c];
-      if (tid == 0 && (piv == 0.0 || !isfinite(piv))) atomicOr(status, ST_SINGULAR);
-      const double pinv = 1.0 / piv;
+      const T piv = P[k * BI + c];
+      if (tid == 0 && (piv == (T)0 || !isfinite(piv))) atomicOr(status, ST_SINGULAR);
+      const T pinv = (T)1 / piv;
       if (tid < bb) rk[tid] = (tid == c) ? pinv : P[k * BI + tid] * pinv;
       __syncthreads();
       for (int e = tid; e < n * bb; e += nt) {
@@ -215,7 +222,7 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
         if (i == k) {
           P[i * BI + cc] = rk[cc];
         } else {
-          double w = (cc == c) ? 0.0 : P[i * BI + cc];
+          T w = (cc == c) ? (T)0 : P[i * BI + cc];
           P[i * BI + cc] = w - Cb[i * BI + c] * rk[cc];
         }
       }
@@ -231,7 +238,7 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
       if (p != k)
         for (int j = tid; j < n; j += nt) {
           if (j >= k0 && j < k0 + bb) continue;
-          double t = W[(size_t)k * n + j];
+          T t = W[(size_t)k * n + j];
           W[(size_t)k * n + j] = W[(size_t)p * n + j];
           W[(size_t)p * n + j] = t;
         }
@@ -241,7 +248,7 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
     if (tid < bb) {
       const int col = tid;
       for (int r = 0; r < bb; ++r) {
-        double acc = (r == col) ? 1.0 : 0.0;
+        T acc = (r == col) ? (T)1 : (T)0;
         for (int c2 = 0; c2 < r; ++c2) acc -= Cb[(k0 + r) * BI + c2] * Q[c2][col];
         Q[r][col] = acc / Cb[(k0 + r) * BI + r];
       }
@@ -249,25 +256,25 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
     __syncthreads();
     if (tid < bb * bb) {
       const int r = tid / bb, c = tid - r * bb;
-      double g = Q[r][c];
+      T g = Q[r][c];
       for (int c2 = r + 1; c2 < bb; ++c2) g -= Cb[(k0 + r) * BI + c2] * Q[c2][c];
       G[r][c] = g;
     }
     __syncthreads();
     // Z overwrites C row by row (each row only reads its own entries)
     for (int i = tid; i < n; i += nt) {
-      double z[BI];
+      T z[BI];
       if (i >= k0 && i < k0 + bb) {
         const int r = i - k0;
 #pragma unroll
-        for (int c = 0; c < BI; ++c) z[c] = (c < bb) ? G[r][c] - (r == c ? 1.0 : 0.0) : 0.0;
+        for (int c = 0; c < BI; ++c) z[c] = (c < bb) ? G[r][c] - (r == c ? (T)1 : (T)0) : (T)0;
       } else {
-        double ci[BI];
+        T ci[BI];
 #pragma unroll
-        for (int c = 0; c < BI; ++c) ci[c] = (c < bb) ? Cb[i * BI + c] : 0.0;
+        for (int c = 0; c < BI; ++c) ci[c] = (c < bb) ? Cb[i * BI + c] : (T)0;
 #pragma unroll
         for (int c = 0; c < BI; ++c) {
-          double acc = 0.0;
+          T acc = 0;
 #pragma unroll
           for (int c2 = c; c2 < BI; ++c2)
             if (c2 < bb) acc -= ci[c2] * Q[c2][c];
@@ -284,14 +291,14 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
       for (int e = tid; e < bb * TJ; e += nt) {
         int c = e / TJ, jj = e - c * TJ;
         int j = j0 + jj;
-        Wb[c * TJ + jj] = (j < n) ? W[(size_t)(k0 + c) * n + j] : 0.0;
+        Wb[c * TJ + jj] = (j < n) ? W[(size_t)(k0 + c) * n + j] : (T)0;
       }
       __syncthreads();
       for (int e = tid; e < n * TJ; e += nt) {
         int i = e / TJ, jj = e - i * TJ;
         int j = j0 + jj;
         if (j >= n || (j >= k0 && j < k0 + bb)) continue;
-        double acc = W[(size_t)i * n + j];
+        T acc = W[(size_t)i * n + j];
         for (int c = 0; c < bb; ++c) acc = fma(Cb[i * BI + c], Wb[c * TJ + jj], acc);
         W[(size_t)i * n + j] = acc;
       }
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
     int p = perm[k];
     if (p != k) {
       for (int i = tid; i < n; i += nt) {
-        double t = W[(size_t)i * n + k];
+        T t = W[(size_t)i * n + k];
         W[(size_t)i * n + k] = W[(size_t)i * n + p];
         W[(size_t)i * n + p] = t;
       }
@@ -311,11 +318,104 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
   }
 }
 
-void batched_inverse(int n, double* A, double* Ainv, int batch, unsigned* status, cudaStream_t s) {
+void batched_inverse(int n, double* A, double* Ainv, int batch, unsigned* status, cudaStream_t s,
+                     const int* skip) {
   // static shared memory (reductions, Q, G) comes on top: always raise the dynamic limit
   size_t smem = (2 * (size_t)n * BI + BI * TJ) * sizeof(double) + n * sizeof(int);
-  cudaFuncSetAttribute(k_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_inverse<<<batch, 512, smem, s>>>(n, A, Ainv, status);
+  cudaFuncSetAttribute(k_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_inverse<double><<<batch, 512, smem, s>>>(n, A, Ainv, status, skip);
+}
+
+void batched_inverse_f32(int n, const double* A, float* Ainv, int batch, unsigned* status,
+                         cudaStream_t s) {
+  size_t smem = (2 * (size_t)n * BI + BI * TJ) * sizeof(float) + n * sizeof(int);
+  cudaFuncSetAttribute(k_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_inverse<float><<<batch, 512, smem, s>>>(n, A, Ainv, status, nullptr);
+}
+
+}  // namespace vrte
+
+namespace vrte {
+
+// ------------------------------------------------------------------ Newton inverse
+// Inverse of a batch of FP64 matrices with the O(n^3) work on the tensor cores: a starting
+// inverse X0 from the FP32 elimination above, then Newton-Schulz steps
+//   E_k = I - A X_k,   X_{k+1} = X_k + X_k E_k,
+// whose residual squares at every step (||E_{k+1}|| <= ||E_k||^2) while ||E_0|| < 1, each
+// step two sliced FP64-accurate products (k_tcgemm.cu). A matrix whose final max|E| is not
+// below `tol` (an FP32 start too poor or non-finite) is inverted again by the FP64
+// elimination, masked to those matrices.
+
+__global__ void k_widen(size_t count, const float* __restrict__ x, double* __restrict__ y) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count;
+       i += (size_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+// E = I - R in place, err[u] = max |E| as the bit pattern of a non-negative double (those
+// order like the doubles; a NaN compares above every finite value)
+__global__ void k_eye_minus(int n, double* R, unsigned long long* err) {
+  const int u = blockIdx.y;
+  const size_t nn = (size_t)n * n;
+  double* Ru = R + (size_t)u * nn;
+  unsigned long long m = 0;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < nn;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = e / n, j = e - i * n;
+    const double v = (i == j ? 1.0 : 0.0) - Ru[e];
+    Ru[e] = v;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
+    m = b > m ? b : m;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const unsigned long long o = __shfl_down_sync(0xffffffffu, m, off);
+    m = o > m ? o : m;
+  }
+  if ((threadIdx.x & 31) == 0 && m) atomicMax(err + u, m);
+}
+
+__global__ void k_newton_flag(int batch, const unsigned long long* err, double tol, int* flag,
+                              int* count) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= batch) return;
+  const double e = __longlong_as_double((long long)err[u]);
+  const int f = !(e <= tol);
+  flag[u] = f;
+  if (f) atomicAdd(count, 1);
+}
+
+size_t newton_inverse_scratch_bytes(int n, int batch) {
+  const size_t nn = (size_t)n * n * batch;
+  return nn * sizeof(double) + (nn + 1) * sizeof(float) + (size_t)batch * sizeof(int) +
+         sizeof(unsigned);
+}
+
+void newton_inverse(int n, const double* A, double* X, int batch, int steps, double tol,
+                    void* scratch, unsigned long long* err, int* fallback_count, void* tcw,
+                    int slices, unsigned* status, cudaStream_t s) {
+  const size_t nn = (size_t)n * n;
+  double* Rm = (double*)scratch;
+  float* x32 = (float*)(Rm + nn * batch);
+  int* flag = (int*)(x32 + nn * batch + 1);
+  // the FP32 elimination's pivot findings do not enter the plan's status: a failed start is
+  // caught by the residual below
+  unsigned* st32 = (unsigned*)(flag + batch);
+  batched_inverse_f32(n, A, x32, batch, st32, s);
+  k_widen<<<1024, 256, 0, s>>>(nn * batch, x32, X);
+  const dim3 eg((unsigned)std::min<size_t>((nn + 255) / 256, 64), batch);
+  for (int k = 0; k <= steps; ++k) {
+    tc_gemm_store(n, n, n, A, n, (long long)nn, X, n, (long long)nn, 0.0, Rm, n, (long long)nn,
+                  batch, slices, tcw, status, s);
+    cudaMemsetAsync(err, 0, batch * sizeof(unsigned long long), s);
+    k_eye_minus<<<eg, 256, 0, s>>>(n, Rm, err);
+    if (k == steps) break;
+    // X <- X E + X: the product reads X only through its slices, taken before the epilogue
+    // writes X
+    tc_gemm_store(n, n, n, X, n, (long long)nn, Rm, n, (long long)nn, 1.0, X, n, (long long)nn,
+                  batch, slices, tcw, status, s);
+  }
+  k_newton_flag<<<(batch + 127) / 128, 128, 0, s>>>(batch, err, tol, flag, fallback_count);
+  batched_inverse(n, const_cast<double*>(A), X, batch, status, s, flag);
 }
 
 }  // namespace vrte

@@ -444,15 +444,19 @@ void launch_depth_combine(const OrderBatch& b, double tau, int down, const doubl
   k_depth_combine<<<grid, 128, 0, s>>>(b, tau, down, Tdep, Q, T1, Qp, pts, rout4, Isyn);
 }
 
-// ------------------------------------------------------------------ Lambertian base
-// Base reflection (Sec. 3.C) for the depolarizing Lambertian base of albedo rho (R_00 = 2 rho),
-// order 0 only: the upward radiance at the bottom is isotropic and unpolarized,
-//   I^0_I(tau0, +mu) = 2 rho sum_j alpha_j mu_j I^0_I(tau0, -mu_j) + (2 rho / pi) mu0 b_I e^{-tau0/mu0}
+// ------------------------------------------------------------------ reflecting base
+// Base reflection (Sec. 3.C, Eqs. 57-66) for a base whose Mueller BRDF matrix R does not
+// depend on the directions (the depolarizing Lambertian base of albedo rho is R_00 = 2 rho):
+// only order 0 sees it, and the upward radiance at the bottom is the same at every node,
+//   I^0(tau0, +mu) = R sum_j alpha_j mu_j I^0(tau0, -mu_j) + (1/pi) mu0 R b e^{-tau0/mu0}
 // (b the beam column, whose order-0 Fourier part is b/pi in the Fourier convention of Eq. 12).
-// basev[col] = sum_j alpha_j mu_j I_I(tau0, -mu_j) of boundary-matrix column col (the decaying
-// modes give D phi+ e^{-kappa tau0}, the growing ones D phi-), real form; the bottom rows
-// 4i of K lose 2 rho basev (the reflected radiance moves to the left side).
-__global__ void k_base_K(int N, int n, double tau, double rho, const double* X, const double* Y,
+// R's (I, Q) x (U, V) blocks are zero (the host rejects others): an azimuth-independent base
+// cannot couple them at order 0. In the reduced form the downward radiance at the bottom of
+// component e is sgn_e (decaying modes: phi+ e^{-kappa tau0}, growing ones: phi-), sgn = D.
+// basev[e][col] = sum_j alpha_j mu_j I_e(tau0, -mu_j) of boundary-matrix column col (real
+// form; layout [4][2n]); the bottom rows n + 4i + a of K lose sum_e R_ae basev[e] (the
+// reflected radiance moves to the left side, Eq. 66).
+__global__ void k_base_K(int N, int n, double tau, BaseR Rg, const double* X, const double* Y,
                          const double* lam_re, const double* lam_im, const double* mu_nodes,
                          const double* w_nodes, double* K, double* basev) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -460,39 +464,55 @@ __global__ void k_base_K(int N, int n, double tau, double rho, const double* X, 
   const bool cplx = lam_im[j] > 0.0;
   const cd kap = kappa_of(lam_re, lam_im, j);
   const cd E = cexpv(cd{-kap.r * tau, -kap.i * tau});
-  cd vA{0.0, 0.0}, vB{0.0, 0.0};
+  cd vA[4], vB[4];
+  for (int e = 0; e < 4; ++e) vA[e] = vB[e] = cd{0.0, 0.0};
   for (int q = 0; q < N; ++q) {
-    const size_t idx = (size_t)(4 * q) * n + j;
-    const cd x{X[idx], cplx ? X[idx + 1] : 0.0}, y{Y[idx], cplx ? Y[idx + 1] : 0.0};
     const double f = w_nodes[q] * mu_nodes[q];
-    const cd pp = cmul(cd{0.5 * (x.r + y.r), 0.5 * (x.i + y.i)}, E);
-    vA = cd{vA.r + f * pp.r, vA.i + f * pp.i};
-    vB = cd{vB.r + f * 0.5 * (x.r - y.r), vB.i + f * 0.5 * (x.i - y.i)};
-  }
-  basev[j] = vA.r;
-  basev[n + j] = vB.r;
-  if (cplx) {
-    basev[j + 1] = vA.i;
-    basev[n + j + 1] = vB.i;
+    for (int e = 0; e < 4; ++e) {
+      const size_t idx = (size_t)(4 * q + e) * n + j;
+      const cd x{X[idx], cplx ? X[idx + 1] : 0.0}, y{Y[idx], cplx ? Y[idx + 1] : 0.0};
+      const double fs = e < 2 ? 0.5 * f : -0.5 * f;
+      const cd pp = cmul(cd{fs * (x.r + y.r), fs * (x.i + y.i)}, E);
+      vA[e] = cd{vA[e].r + pp.r, vA[e].i + pp.i};
+      vB[e] = cd{vB[e].r + fs * (x.r - y.r), vB[e].i + fs * (x.i - y.i)};
+    }
   }
   const int n2 = 2 * n;
-  for (int i = 0; i < N; ++i) {
-    double* row = K + (size_t)(n + 4 * i) * n2;
-    row[j] -= 2.0 * rho * vA.r;
-    row[n + j] -= 2.0 * rho * vB.r;
+  for (int e = 0; e < 4; ++e) {
+    basev[e * n2 + j] = vA[e].r;
+    basev[e * n2 + n + j] = vB[e].r;
     if (cplx) {
-      row[j + 1] -= 2.0 * rho * vA.i;
-      row[n + j + 1] -= 2.0 * rho * vB.i;
+      basev[e * n2 + j + 1] = vA[e].i;
+      basev[e * n2 + n + j + 1] = vB[e].i;
+    }
+  }
+  for (int a = 0; a < 4; ++a) {
+    cd rA{0.0, 0.0}, rB{0.0, 0.0};
+    for (int e = 0; e < 4; ++e) {
+      const double r = Rg.r[4 * a + e];
+      rA = cd{rA.r + r * vA[e].r, rA.i + r * vA[e].i};
+      rB = cd{rB.r + r * vB[e].r, rB.i + r * vB[e].i};
+    }
+    for (int i = 0; i < N; ++i) {
+      double* row = K + (size_t)(n + 4 * i + a) * n2;
+      row[j] -= rA.r;
+      row[n + j] -= rB.r;
+      if (cplx) {
+        row[j + 1] -= rA.i;
+        row[n + j + 1] -= rB.i;
+      }
     }
   }
 }
 
-// The reflected particular radiance and the reflected attenuated beam, for column c:
-//   zb[c] = 2 rho (sum_j alpha_j mu_j zm_I(j)[c]) e^{-tau0/mu0} + (2 rho / pi) mu0 b_I[c] e^{-(t + tau0)/mu0}
-// (t = t_above, the depth of the layer's top in a slab: the beam reaches the base through it)
-// (zm = D (s - d)/2 the particular solution's downward radiance at tau = 0), added to the bottom
-// rows 4i of the right-hand side when add_rhs.
-__global__ void k_base_rhs(int N, int n, int R, long long sSD, double tau, double rho,
+// The reflected particular radiance and the reflected attenuated beam, for column c = 4k + s:
+//   zb[a][c] = sum_e R_ae [ (sum_j alpha_j mu_j zm_e(j)[c]) e^{-tau0/mu0}
+//                           + (mu0 / pi) b_e[c] e^{-(t + tau0)/mu0} ]
+// (zm = D (s - d)/2 the particular solution's downward radiance at tau = 0; t = t_above, the
+// depth of the layer's top in a slab: the beam reaches the base through it; b_e[c] entry
+// (e, s) of the beam block of incident k), added to the bottom rows n + 4i + a of the
+// right-hand side when add_rhs (Eqs. 62-63).
+__global__ void k_base_rhs(int N, int n, int R, long long sSD, double tau, BaseR Rg,
                            const double* SD, const double* pts, const double* min4,
                            const double* mu_nodes, const double* w_nodes, double* RHS,
                            double* zb, int add_rhs, double t_above) {
@@ -500,66 +520,108 @@ __global__ void k_base_rhs(int N, int n, int R, long long sSD, double tau, doubl
   if (c >= R) return;
   const double* sv = SD;
   const double* dv = SD + (size_t)n * R;
-  double z = 0.0;
+  double z[4] = {0.0, 0.0, 0.0, 0.0};
   for (int q = 0; q < N; ++q) {
-    const size_t idx = (size_t)(4 * q) * R + c;
-    z += w_nodes[q] * mu_nodes[q] * 0.5 * (sv[idx] - dv[idx]);
+    const double f = 0.5 * w_nodes[q] * mu_nodes[q];
+    for (int e = 0; e < 4; ++e) {
+      const size_t idx = (size_t)(4 * q + e) * R + c;
+      z[e] += (e < 2 ? f : -f) * (sv[idx] - dv[idx]);
+    }
   }
   const int k = c >> 2, s = c & 3;
   const double mu0 = pts[N + k], att = exp(-tau / mu0);
-  const double bI = s == 0 ? min4[4 * k] : (s == 1 ? min4[4 * k + 1] : 0.0);
-  const double v = 2.0 * rho * z * att + 2.0 * rho / kPi * mu0 * bI * exp(-(t_above + tau) / mu0);
-  zb[c] = v;
-  if (add_rhs)
-    for (int i = 0; i < N; ++i) RHS[(size_t)(n + 4 * i) * R + c] += v;
+  const double fb = mu0 / kPi * exp(-(t_above + tau) / mu0);
+  const double* q4 = min4 + 4 * k;
+  double ze[4];
+  for (int e = 0; e < 4; ++e) {
+    double b = 0.0;  // entry (e, s) of the beam block [[qa, qb, 0, 0], [qb, qa, 0, 0], [0, 0, qc, qd], [0, 0, -qd, qc]]
+    if (e < 2 && s < 2) b = e == s ? q4[0] : q4[1];
+    else if (e >= 2 && s >= 2) b = e == s ? q4[2] : (e == 2 ? q4[3] : -q4[3]);
+    ze[e] = z[e] * att + fb * b;
+  }
+  for (int a = 0; a < 4; ++a) {
+    double v = 0.0;
+    for (int e = 0; e < 4; ++e) v += Rg.r[4 * a + e] * ze[e];
+    zb[(size_t)a * R + c] = v;
+    if (add_rhs)
+      for (int i = 0; i < N; ++i) RHS[(size_t)(n + 4 * i + a) * R + c] += v;
+  }
 }
 
-// The base's radiance at the bottom, I0b[c] = 2 rho basev . C[:, c] + zb[c] (the same at every
-// upward direction), attenuated along the exit path to the top and added to the order-0 upward
-// radiance there: out[(o, a)][c] += e^{-tau0/mu_o} M_out(o)_{a0} I0b[c] (M_out = identity when
-// mout4 is null). `isyn` selects the order-radiance layout Isyn[0][k][o][a][s] for out.
-__global__ void k_base_recon(int n, int N, int n_in, int n_out, double tau, double rho,
-                             const double* C, const double* basev, const double* zb,
-                             const double* pts, const double* mout4, double* out, int isyn) {
+// The base's radiance at the bottom for column c (the same at every upward direction):
+//   vb[a][c] = sum_e R_ae (basev[e] . C[:, c]) + zb[a][c].
+__global__ void k_base_value(int n, int R, BaseR Rg, const double* C, const double* basev,
+                             const double* zb, double* vb) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  const int n2 = 2 * n;
+  double d[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int col = 0; col < n2; ++col) {
+    const double cv = C[(size_t)col * R + c];
+    for (int e = 0; e < 4; ++e) d[e] += basev[e * n2 + col] * cv;
+  }
+  for (int a = 0; a < 4; ++a) {
+    double v = zb[(size_t)a * R + c];
+    for (int e = 0; e < 4; ++e) v += Rg.r[4 * a + e] * d[e];
+    vb[(size_t)a * R + c] = v;
+  }
+}
+
+// The base's radiance attenuated along the exit path and added to the order-0 upward radiance:
+// out[(o, a)][c] += e^{-tau/mu_o} (M_out(o) vb[:, c])_a (M_out = identity when mout4 is null,
+// else the exit block [[m0, m1, 0, 0], [m1, m0, 0, 0], [0, 0, m2, m3], [0, 0, -m3, m2]]).
+// `isyn` selects the order-radiance layout Isyn[0][k][o][a][s] for out.
+__global__ void k_base_add(int N, int n_in, int n_out, double tau, const double* vb,
+                           const double* pts, const double* mout4, double* out, int isyn) {
   const int R = 4 * n_in;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   const int o = blockIdx.y;
   if (c >= R) return;
-  double v = 0.0;
-  for (int col = 0; col < 2 * n; ++col) v += basev[col] * C[(size_t)col * R + c];
-  v = 2.0 * rho * v + zb[c];
-  const double att = exp(-tau / pts[N + n_in + o]) * v;
-  const double m0 = mout4 ? mout4[4 * o] : 1.0, m1 = mout4 ? mout4[4 * o + 1] : 0.0;
-  const int k = c >> 2, s = c & 3;
-  if (isyn) {
-    const size_t base = ((size_t)k * n_out + o) * 16;
-    out[base + s] += m0 * att;
-    out[base + 4 + s] += m1 * att;
+  const double att = exp(-tau / pts[N + n_in + o]);
+  double v[4];
+  for (int e = 0; e < 4; ++e) v[e] = att * vb[(size_t)e * R + c];
+  double w[4];
+  if (mout4) {
+    const double* q = mout4 + 4 * o;
+    w[0] = q[0] * v[0] + q[1] * v[1];
+    w[1] = q[1] * v[0] + q[0] * v[1];
+    w[2] = q[2] * v[2] + q[3] * v[3];
+    w[3] = -q[3] * v[2] + q[2] * v[3];
   } else {
-    out[(size_t)(4 * o) * R + c] += m0 * att;
-    out[(size_t)(4 * o + 1) * R + c] += m1 * att;
+    for (int e = 0; e < 4; ++e) w[e] = v[e];
+  }
+  const int k = c >> 2, s = c & 3;
+  for (int a = 0; a < 4; ++a) {
+    if (isyn)
+      out[((size_t)k * n_out + o) * 16 + 4 * a + s] += w[a];
+    else
+      out[(size_t)(4 * o + a) * R + c] += w[a];
   }
 }
 
-void launch_base_K(int N, int n, double tau, double rho, const double* X, const double* Y,
+void launch_base_K(int N, int n, double tau, const BaseR& Rg, const double* X, const double* Y,
                    const double* lam_re, const double* lam_im, const double* mu_nodes,
                    const double* w_nodes, double* K, double* basev, cudaStream_t s) {
-  k_base_K<<<(n + 127) / 128, 128, 0, s>>>(N, n, tau, rho, X, Y, lam_re, lam_im, mu_nodes, w_nodes,
+  k_base_K<<<(n + 127) / 128, 128, 0, s>>>(N, n, tau, Rg, X, Y, lam_re, lam_im, mu_nodes, w_nodes,
                                            K, basev);
 }
-void launch_base_rhs(int N, int n, int R, long long sSD, double tau, double rho, const double* SD,
-                     const double* pts, const double* min4, const double* mu_nodes,
-                     const double* w_nodes, double* RHS, double* zb, int add_rhs, cudaStream_t s,
-                     double t_above) {
-  k_base_rhs<<<(R + 127) / 128, 128, 0, s>>>(N, n, R, sSD, tau, rho, SD, pts, min4, mu_nodes,
+void launch_base_rhs(int N, int n, int R, long long sSD, double tau, const BaseR& Rg,
+                     const double* SD, const double* pts, const double* min4,
+                     const double* mu_nodes, const double* w_nodes, double* RHS, double* zb,
+                     int add_rhs, cudaStream_t s, double t_above) {
+  k_base_rhs<<<(R + 127) / 128, 128, 0, s>>>(N, n, R, sSD, tau, Rg, SD, pts, min4, mu_nodes,
                                              w_nodes, RHS, zb, add_rhs, t_above);
 }
-void launch_base_recon(int n, int N, int n_in, int n_out, double tau, double rho, const double* C,
-                       const double* basev, const double* zb, const double* pts,
+void launch_base_recon(int n, int N, int n_in, int n_out, double tau, const BaseR& Rg,
+                       const double* C, double* basebuf, const double* pts,
                        const double* mout4, double* out, int isyn, cudaStream_t s) {
-  dim3 grid((4 * n_in + 127) / 128, n_out);
-  k_base_recon<<<grid, 128, 0, s>>>(n, N, n_in, n_out, tau, rho, C, basev, zb, pts, mout4, out,
-                                    isyn);
+  const int R = 4 * n_in;
+  const double* basev = basebuf;
+  const double* zb = basebuf + 8 * n;
+  double* vb = basebuf + 8 * n + 4 * (size_t)R;
+  k_base_value<<<(R + 127) / 128, 128, 0, s>>>(n, R, Rg, C, basev, zb, vb);
+  dim3 grid((R + 127) / 128, n_out);
+  k_base_add<<<grid, 128, 0, s>>>(N, n_in, n_out, tau, vb, pts, mout4, out, isyn);
 }
 
 }  // namespace vrte

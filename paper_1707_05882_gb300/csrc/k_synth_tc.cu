@@ -19,7 +19,10 @@
 //   warps 2-9 drain a finished buffer (TMEM -> registers -> error-free FP32 sum ->
 //             scaled store; two warps per TMEM lane quarter, 32 columns each) while
 //             warp 1 already fills the other one.
-// Tiles run azimuth-tile fastest, so the six azimuth tiles of one row tile are in flight
+// Only one azimuth of every mirror pair (phi, -phi) of the grid is computed: the cosine class
+// is even and the sine class odd in the azimuth, so the epilogue stores each value at both
+// (for the uniform 360-azimuth grid, 181 computed columns in three tiles instead of six).
+// Tiles run azimuth-tile fastest, so the azimuth tiles of one row tile are in flight
 // together and its slices come from L2 after the first read. Every wait is bounded: on
 // timeout the kernel records ST_TIMEOUT, waits (bounded) for its copies and MMAs, frees
 // TMEM and returns.
@@ -127,21 +130,25 @@ __global__ void __launch_bounds__(256) k_synth_slice_rows(int P, long long pair0
   if (bad) atomicOr(status, ST_NONFINITE);
 }
 
-// Columns (azimuths) of both weight tables: grid (NT, 2 classes), thread = azimuth.
-__global__ void __launch_bounds__(SY_N) k_synth_slice_cols(int M, int n_phi, int NT, int KB,
-                                                           const double* __restrict__ wc,
+// Columns of both weight tables: grid (NT, 2 classes), thread = column c of the computed
+// azimuths, the grid's azimuth rep[c] (c < n_rep).
+__global__ void __launch_bounds__(SY_N) k_synth_slice_cols(int M, int n_phi, int n_rep,
+                                                           const int* __restrict__ rep, int NT,
+                                                           int KB, const double* __restrict__ wc,
                                                            const double* __restrict__ ws,
                                                            unsigned short* Bs, int* fb,
                                                            unsigned* status) {
   const int nt = blockIdx.x, cls = blockIdx.y, c = threadIdx.x;
-  const int j = nt * SY_N + c;
+  const int jc = nt * SY_N + c;
+  const bool in = jc < n_rep;
+  const int j = in ? rep[jc] : 0;
   const double* W = cls ? ws : wc;
   bool bad = false;
   int Em = 0;
-  if (j < n_phi)
+  if (in)
     for (int m = 0; m < M; ++m) Em = max(Em, exp_field(W[(size_t)m * n_phi + j], &bad));
   const int ee = scale_exp(Em);
-  fb[(size_t)cls * NT * SY_N + j] = ee;
+  fb[(size_t)cls * NT * SY_N + jc] = ee;
   const size_t tile_elems = (size_t)SY_N * SY_KB;
   const size_t slice_stride = (size_t)NT * KB * tile_elems;
   unsigned short* dst_t = Bs + (size_t)cls * SY_S * slice_stride + (size_t)nt * KB * tile_elems;
@@ -149,7 +156,7 @@ __global__ void __launch_bounds__(SY_N) k_synth_slice_cols(int M, int n_phi, int
     double v[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t)
-      v[t] = (j < n_phi && k0 + t < M) ? W[(size_t)(k0 + t) * n_phi + j] : 0.0;
+      v[t] = (in && k0 + t < M) ? W[(size_t)(k0 + t) * n_phi + j] : 0.0;
     const int kb = k0 / SY_KB;
     put_chunk<SY_S>(v, ee, dst_t + (size_t)kb * tile_elems + (swz64_offset(c, k0 - kb * SY_KB) >> 1),
                     slice_stride);
@@ -186,10 +193,10 @@ __device__ inline double synth_value(const uint32_t* x, int E2, double*) {
 
 template <typename T>
 __global__ void __launch_bounds__(SY_THREADS, 1)
-    k_synth_mma(int P, long long pair0, int n_phi, int MT, int NT, int KB,
-                const unsigned short* __restrict__ As, const int* __restrict__ ea,
-                const unsigned short* __restrict__ Bs, const int* __restrict__ fb, T* out,
-                unsigned* status) {
+    k_synth_mma(int P, long long pair0, int n_phi, int n_rep, const int* __restrict__ map,
+                int MT, int NT, int KB, const unsigned short* __restrict__ As,
+                const int* __restrict__ ea, const unsigned short* __restrict__ Bs,
+                const int* __restrict__ fb, T* out, unsigned* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ uint64_t full_bar[SY_STAGES], empty_bar[SY_STAGES], tfull_bar[2], tempty_bar[2],
       fin_bar;
@@ -346,14 +353,18 @@ __global__ void __launch_bounds__(SY_THREADS, 1)
         }
 #pragma unroll
         for (int t16 = 0; t16 < 16; ++t16) {
-          const int j = nt * SY_N + c0 + t16;
-          if (valid && j < n_phi) {
+          const int jc = nt * SY_N + c0 + t16;
+          if (valid && jc < n_rep) {
             uint32_t xs[SY_NACC];
 #pragma unroll
             for (int a = 0; a < SY_NACC; ++a) xs[a] = x[a][t16];
             T v = synth_value(xs, erow + fcol[c0 + t16], (T*)nullptr);
             bad |= !isfinite((double)v);
-            __stcs(orow + (size_t)j * 16, v);  // the table streams out (evict-first)
+            // the table streams out (evict-first), at the azimuth and at its mirror (the
+            // cosine class even, the sine class odd in the azimuth)
+            __stcs(orow + (size_t)map[jc] * 16, v);
+            const int jm = map[n_phi + jc];
+            if (jm >= 0) __stcs(orow + (size_t)jm * 16, cls ? -v : v);
           }
         }
       }
@@ -390,37 +401,40 @@ size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int k_block
   return L.a_bytes + L.e_bytes + L.b_bytes + L.f_bytes;
 }
 
-void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, const double* wc,
-                  const double* ws, void* out, int out_dtype, int k_block, void* work,
-                  unsigned* status, cudaStream_t s, const SynthHook* hook) {
+void tc_synthesis(int M, int n_in, int n_out, int n_phi, int n_rep, const int* map,
+                  const double* Isyn, const double* wc, const double* ws, void* out,
+                  int out_dtype, int k_block, void* work, unsigned* status, cudaStream_t s,
+                  const SynthHook* hook) {
   const long long pairs_total = (long long)n_in * n_out;
-  const SynthLayout Lmax = synth_layout(std::min(k_block, n_in) * n_out, M, n_phi);
+  const SynthLayout Lmax = synth_layout(std::min(k_block, n_in) * n_out, M, n_rep);
   unsigned char* w = (unsigned char*)work;
   unsigned short* As = (unsigned short*)w;
   int* ea = (int*)(w + Lmax.a_bytes);
   unsigned short* Bs = (unsigned short*)(w + Lmax.a_bytes + Lmax.e_bytes);
   int* fb = (int*)(w + Lmax.a_bytes + Lmax.e_bytes + Lmax.b_bytes);
   const int sms = sm_count();
-  k_synth_slice_cols<<<dim3(Lmax.NT, 2), SY_N, 0, s>>>(M, n_phi, Lmax.NT, Lmax.KB, wc, ws, Bs,
-                                                       fb, status);
+  k_synth_slice_cols<<<dim3(Lmax.NT, 2), SY_N, 0, s>>>(M, n_phi, n_rep, map, Lmax.NT, Lmax.KB, wc,
+                                                       ws, Bs, fb, status);
   if (out_dtype == VRTE_OUT_F64)
     cudaFuncSetAttribute(k_synth_mma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SY_SMEM);
   else
     cudaFuncSetAttribute(k_synth_mma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SY_SMEM);
   for (int k0 = 0; k0 < n_in; k0 += k_block) {
     const int kb = std::min(k_block, n_in - k0);
-    const SynthLayout L = synth_layout(kb * n_out, M, n_phi);
+    const SynthLayout L = synth_layout(kb * n_out, M, n_rep);
     const long long pair0 = (long long)k0 * n_out;
     k_synth_slice_rows<<<std::min(L.MT, 2 * sms), 256, 0, s>>>(L.P, pair0, pairs_total, M, L.MT,
                                                                L.KB, Isyn, As, ea, status);
     const int tiles = 2 * L.MT * L.NT;
     const int grid = std::min(tiles, sms);
     if (out_dtype == VRTE_OUT_F64)
-      k_synth_mma<double><<<grid, SY_THREADS, SY_SMEM, s>>>(L.P, pair0, n_phi, L.MT, L.NT, L.KB,
-                                                            As, ea, Bs, fb, (double*)out, status);
+      k_synth_mma<double><<<grid, SY_THREADS, SY_SMEM, s>>>(L.P, pair0, n_phi, n_rep, map, L.MT,
+                                                            L.NT, L.KB, As, ea, Bs, fb,
+                                                            (double*)out, status);
     else
-      k_synth_mma<float><<<grid, SY_THREADS, SY_SMEM, s>>>(L.P, pair0, n_phi, L.MT, L.NT, L.KB, As,
-                                                           ea, Bs, fb, (float*)out, status);
+      k_synth_mma<float><<<grid, SY_THREADS, SY_SMEM, s>>>(L.P, pair0, n_phi, n_rep, map, L.MT,
+                                                           L.NT, L.KB, As, ea, Bs, fb, (float*)out,
+                                                           status);
     if (hook) hook->fn(hook->user, hook->layer, k0, k0 + kb, s);
   }
 }

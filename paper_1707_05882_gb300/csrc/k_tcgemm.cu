@@ -195,12 +195,23 @@ __device__ inline void tc_decode(int t, int MT, int NT, int& u, int& mt, int& nt
   nt = idx / gm;
 }
 
+// K blocks that are zero in both operands of unit u (see TcKSkip) and are skipped: the
+// blocks lying entirely in [zk0, zk0 + zbase + zstep u); at least one block stays, so that
+// every accumulator is written.
+__device__ inline void tc_skip_range(const TcKSkip& z, int u, int KB, int& zb0, int& zb1) {
+  const int len = z.zbase + z.zstep * u;
+  zb0 = (z.zk0 + TC_KB - 1) / TC_KB;
+  zb1 = len > 0 ? min((z.zk0 + len) / TC_KB, KB) : 0;
+  if (zb1 <= zb0) zb0 = zb1 = 0;
+  if (zb0 == 0 && zb1 >= KB) zb1 = KB - 1;
+}
+
 template <class Epi>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(int M, int N, int K, int S, const unsigned short* __restrict__ As,
               const int* __restrict__ ea, const unsigned short* __restrict__ Bs,
               const int* __restrict__ fb, float* scratch, Epi epi, unsigned* status,
-              int batch) {
+              int batch, TcKSkip zskip) {
   // Persistent: CTA b takes tiles b, b + gridDim.x, ... Warp 0 bulk-copies the slice
   // tiles of each 32-wide K block into a ring of shared-memory stages, warp 1 (owner of
   // the TMEM allocation) issues the slice-pair MMAs as the stages fill, and warps 2-9
@@ -266,9 +277,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             As + (size_t)u * a_unit + (size_t)mt * KB * S * (A_TILE_BYTES / 2);
         const unsigned short* b0 =
             Bs + (size_t)u * b_unit + (size_t)nt * KB * S * (B_TILE_BYTES / 2);
+        int zb0, zb1;
+        tc_skip_range(zskip, u, KB, zb0, zb1);
         bool ok = true;
-        for (int kb = 0; kb < KB; ++kb, ++g) {
+        for (int kb = 0; kb < KB; ++kb) {
+          if (kb >= zb0 && kb < zb1) continue;  // zero in both operands of this unit
           const int s = g % nst, r = g / nst;
+          ++g;
           if (!mbar_wait(&empty_bar[s], (r & 1) ^ 1)) { ok = false; break; }
           unsigned char* st = smem + (size_t)s * stage_bytes;
           mbar_expect_tx(&full_bar[s], (unsigned)stage_bytes);
@@ -293,9 +308,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (!mbar_wait(&tempty_bar[b], (use & 1) ^ 1)) { fail(); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dbase = tmem + (uint32_t)(b * buf_cols);
+        int u, mt, nt;
+        tc_decode(t, MT, NT, u, mt, nt);
+        int zb0, zb1;
+        tc_skip_range(zskip, u, KB, zb0, zb1);
+        const int kfirst = (zb0 == 0 && zb1 > 0) ? zb1 : 0;  // first K block issued
         bool ok = true;
-        for (int kb = 0; kb < KB; ++kb, ++g) {
+        for (int kb = 0; kb < KB; ++kb) {
+          if (kb >= zb0 && kb < zb1) continue;
           const int s = g % nst, r = g / nst;
+          ++g;
           if (!mbar_wait(&full_bar[s], r & 1)) { ok = false; break; }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           unsigned char* st = smem + (size_t)s * stage_bytes;
@@ -304,7 +326,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const uint64_t adesc = smem_desc_sw64(st);
           const uint32_t alo = (uint32_t)adesc, dhi = (uint32_t)(adesc >> 32);
           const uint32_t blo = (uint32_t)smem_desc_sw64(st + S * A_TILE_BYTES);
-          const uint32_t later = kb > 0 ? 1u : 0u;
+          const uint32_t later = kb != kfirst ? 1u : 0u;
 #pragma unroll
           for (int p = 0; p < TC_MAXS; ++p)
 #pragma unroll
@@ -503,7 +525,7 @@ bool tc_shape_ok(int K, int S) { return S >= 1 && S <= TC_MAXS && K >= 1 && K <=
 template <class Epi>
 void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const double* B, int ldb,
              long long sB, Epi epi, int batch, int S, void* work, unsigned* status,
-             cudaStream_t s) {
+             cudaStream_t s, TcKSkip zskip = TcKSkip{}) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   TcLayout L = tc_layout(M, N, K, batch, S);
   unsigned char* w = (unsigned char*)work;
@@ -520,7 +542,7 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
   int smem = tc_smem_bytes(S);
   cudaFuncSetAttribute(k_tc_gemm<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   k_tc_gemm<Epi><<<tc_grid((long long)L.MT * L.NT * batch), TC_THREADS, smem, s>>>(
-      M, N, K, S, As, ea, Bs, fb, scratch, epi, status, batch);
+      M, N, K, S, As, ea, Bs, fb, scratch, epi, status, batch, zskip);
 }
 
 struct TcEpiStore {
@@ -536,17 +558,18 @@ struct TcEpiStore {
 
 void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, const double* B,
                    int ldb, long long sB, double beta, double* C, int ldc, long long sC,
-                   int batch, int S, void* work, unsigned* status, cudaStream_t s) {
+                   int batch, int S, void* work, unsigned* status, cudaStream_t s,
+                   TcKSkip zskip) {
   tc_gemm(M, N, K, A, lda, sA, B, ldb, sB, TcEpiStore{C, ldc, sC, beta}, batch, S, work, status,
-          s);
+          s, zskip);
 }
 
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                   const double* B, long long sB, const double* T1, const double* g0tab,
-                  double* Isyn, int S, void* work, cudaStream_t s) {
+                  double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip) {
   EpiPart e{T1, Isyn, g0tab, b.N, b.n_in, b.n_out, b.m0};
   tc_gemm(4 * b.n_out, 4 * b.n_in, K, A, lda, sA, B, 4 * b.n_in, sB, e, b.n_units, S, work,
-          b.status, s);
+          b.status, s, zskip);
 }
 
 // First half of a reconstruction contraction too deep for one exact accumulation
@@ -564,10 +587,10 @@ struct EpiPartAccum {
 
 void tc_gemm_part_accum(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                         const double* B, long long sB, double* T1, const double* g0tab, int S,
-                        void* work, cudaStream_t s) {
+                        void* work, cudaStream_t s, TcKSkip zskip) {
   EpiPartAccum e{T1, g0tab, b.n_in, b.n_out};
   tc_gemm(4 * b.n_out, 4 * b.n_in, K, A, lda, sA, B, 4 * b.n_in, sB, e, b.n_units, S, work,
-          b.status, s);
+          b.status, s, zskip);
 }
 
 }  // namespace vrte

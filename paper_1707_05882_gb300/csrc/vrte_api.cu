@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "vrte_internal.cuh"
@@ -36,6 +37,10 @@ constexpr int kSynthBlock = 64;
 // above which a column block is recomputed in FP64
 constexpr double kSliceEps = 2e-15;
 constexpr double kRefineTol = 1e-7;
+// mixed form: Newton-Schulz steps after the FP32 starting inverse of K and X, and the final
+// max|I - A X| above which a matrix is inverted again in FP64
+constexpr int kNewtonSteps = 3;
+constexpr double kNewtonTol = 1e-11;
 
 const char* kStageNames[kStages] = {"tables",     "assemble",   "eigen",
                                     "modes_bc_inverse", "particular", "bc_solve",
@@ -69,7 +74,9 @@ struct Work {
   double* rscratch = nullptr;
   // mixed form: factors of the (l, component) contractions for U+- and the beam vectors
   double *Ln = nullptr, *RU = nullptr, *Rbp = nullptr, *Rbm = nullptr;
-  int* rcount = nullptr;  // [flagged in this batch, flagged in this solve]
+  int* rcount = nullptr;  // [flagged in this batch, flagged in this solve, FP64 re-inverses]
+  void* nscratch = nullptr;              // mixed form: Newton inverse scratch
+  unsigned long long* nerr = nullptr;    // mixed form: final residuals [K, X][U]
   int2* rlist = nullptr;
   double* Isyn = nullptr;   // [M_max][n_in][n_out][16]; the adjoint keeps Ibar here
   // adjoint (VRTE_FLAG_ADJOINT): per-unit workspace carved per layer, and per-layer data
@@ -100,6 +107,10 @@ struct vrte_plan {
   int n_in = 0, n_out = 0, n_phi = 0;
   double *d_mu_in = nullptr, *d_mu_out = nullptr, *d_phi = nullptr;
   double *d_wc = nullptr, *d_ws = nullptr;  // [M_max][n_phi]
+  // azimuth mirror pairs of the grid (see azimuth_mirrors): [0, n_rep) the computed
+  // azimuths, [n_phi, n_phi + n_rep) their mirrors (-1: none)
+  int* d_syn_map = nullptr;
+  int n_rep = 0;
   unsigned* d_status = nullptr;
   cudaStream_t last_stream = nullptr;
   // layers
@@ -199,7 +210,7 @@ void reset_stats(vrte_plan* p) {
 }
 
 // buffers allocated by vrte_plan_create (kept by vrte_set_layer)
-constexpr size_t kPlanAllocs = 6;
+constexpr size_t kPlanAllocs = 7;
 
 // Adjoint workspace of one order batch: consecutive [U][size] arrays for the layer's n.
 struct BwBufs {
@@ -260,6 +271,51 @@ const char* vrte_status_string(vrte_status st) {
   return "unknown status";
 }
 
+// Mirror pairs of the azimuth grid for the tensor-core synthesis: the cosine class of the
+// table is even in the azimuth difference and the sine class odd (Eqs. 7, 12), so the table at
+// -phi follows from the one at phi. Returns [rep (n_phi) | mirror (n_phi)] with the computed
+// azimuths rep[0 .. n_rep) in increasing order and mirror[r] the index of the azimuth at
+// -phi_rep[r] (mod 2 pi, within 1e-12 rad), or -1 when it is not on the grid, is rep[r]
+// itself (0, pi) or was already paired.
+static std::vector<int> azimuth_mirrors(int n, const double* phi, int* n_rep) {
+  const double two_pi = 6.283185307179586476925286766559;
+  auto wrap = [&](double a) {
+    a = std::fmod(a, two_pi);
+    if (a < 0.0) a += two_pi;
+    return a;
+  };
+  std::vector<std::pair<double, int>> key(n);
+  for (int j = 0; j < n; ++j) key[j] = {wrap(phi[j]), j};
+  std::sort(key.begin(), key.end());
+  // the indices whose wrapped angle lies within 1e-12 of a (also across 0 = 2 pi)
+  auto candidates = [&](double a, std::vector<int>& out) {
+    out.clear();
+    for (double c : {a, a - two_pi, a + two_pi}) {
+      auto it = std::lower_bound(key.begin(), key.end(), std::make_pair(c - 1e-12, -1));
+      for (; it != key.end() && it->first <= c + 1e-12; ++it) out.push_back(it->second);
+    }
+  };
+  std::vector<int> map(2 * (size_t)n, -1), used(n, 0), cand;
+  int r = 0;
+  for (int j = 0; j < n; ++j) {
+    if (used[j]) continue;
+    used[j] = 1;
+    int m = -1;
+    candidates(wrap(-phi[j]), cand);
+    for (int c : cand)
+      if (!used[c]) {
+        m = c;
+        break;
+      }
+    if (m >= 0) used[m] = 1;
+    map[r] = j;
+    map[n + r] = m;
+    ++r;
+  }
+  *n_rep = r;
+  return map;
+}
+
 vrte_status vrte_plan_create(const vrte_plan_desc* d, vrte_plan** out) {
   if (!d || !out) return VRTE_ERR_INVALID_ARG;
   *out = nullptr;
@@ -290,7 +346,8 @@ vrte_status vrte_plan_create(const vrte_plan_desc* d, vrte_plan** out) {
   int Mx = d->n_orders_max;
   if ((st = allocd(p, &p->d_mu_in, p->n_in)) || (st = allocd(p, &p->d_mu_out, p->n_out)) ||
       (st = allocd(p, &p->d_phi, p->n_phi)) || (st = allocd(p, &p->d_wc, (size_t)Mx * p->n_phi)) ||
-      (st = allocd(p, &p->d_ws, (size_t)Mx * p->n_phi)) || (st = allocd(p, &p->d_status, 1))) {
+      (st = allocd(p, &p->d_ws, (size_t)Mx * p->n_phi)) || (st = allocd(p, &p->d_status, 1)) ||
+      (st = allocd(p, &p->d_syn_map, 2 * (size_t)p->n_phi))) {
     vrte_destroy(p);
     return st;
   }
@@ -301,6 +358,13 @@ vrte_status vrte_plan_create(const vrte_plan_desc* d, vrte_plan** out) {
     vrte_destroy(p);
     return VRTE_ERR_CUDA;
   }
+  {
+    std::vector<int> map = azimuth_mirrors(p->n_phi, d->phi, &p->n_rep);
+    if (cudaMemcpy(p->d_syn_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice)) {
+      vrte_destroy(p);
+      return VRTE_ERR_CUDA;
+    }
+  }
   launch_trig_table(Mx, p->n_phi, p->d_phi, p->d_wc, p->d_ws, 0);
   if (cudaDeviceSynchronize() != cudaSuccess) {
     vrte_destroy(p);
@@ -310,13 +374,27 @@ vrte_status vrte_plan_create(const vrte_plan_desc* d, vrte_plan** out) {
   return VRTE_OK;
 }
 
+// A reflecting base's matrix: finite, no (I, Q) x (U, V) coupling (order 0 cannot carry one),
+// and a total R_00 (with the Lambertian 2 rho) in [0, 2] (the bare base reflects at most the
+// unpolarized flux it receives).
+static bool base_valid(const vrte_layer& l) {
+  BaseR b;
+  layer_base(l, &b);
+  for (int i = 0; i < 16; ++i) {
+    if (!std::isfinite(b.r[i])) return false;
+    const int r = i / 4, c = i % 4;
+    if ((r < 2) != (c < 2) && b.r[i] != 0.0) return false;
+  }
+  return b.r[0] >= 0.0 && b.r[0] <= 2.0;
+}
+
 vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, const double* d_coeffs) {
   if (!p || !hp || !d_coeffs || n_layers < 1 || n_layers > p->desc.n_layers_max)
     return VRTE_ERR_INVALID_ARG;
   for (int b = 0; b < n_layers; ++b) {
     const vrte_layer& l = hp[b];
     if (!(l.tau > 0.0) || !(l.omega >= 0.0 && l.omega < 1.0) || !(l.n_interface <= 3.0) ||
-        !(l.base_albedo >= 0.0 && l.base_albedo <= 1.0) ||
+        !(l.base_albedo >= 0.0 && l.base_albedo <= 1.0) || !base_valid(l) ||
         l.n_nodes < 1 || l.n_nodes > p->desc.n_nodes_max || l.n_orders < 1 ||
         l.n_orders > p->desc.n_orders_max || l.n_coef < 1 || l.n_coef > p->desc.n_coef_max)
       return VRTE_ERR_INVALID_ARG;
@@ -353,7 +431,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   const int S = kSlices;
   size_t tc_unit = 0;
   if (mixed) {
-    size_t c[8] = {tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
+    size_t c[9] = {tc_workspace_bytes((int)(2 * n), (int)(2 * n), (int)(2 * n), 1, S),
+                   tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
                    tc_workspace_bytes((int)n, (int)n, (int)n, 1, S),
                    tc_workspace_bytes((int)n, (int)R, (int)kd, 1, S),
                    tc_workspace_bytes((int)Ro, (int)(2 * n), (int)kd, 1, S),
@@ -367,6 +446,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
                     (4 * n + kd) * R + 2 * n * R + 4 * Ro * n + Ro * (2 * n + kd) + Ro * R + n * n +
                     1 + 5 * 4 * n * n + 3 * 2 * n + 1 + (tc_unit + 7) / 8 +
                     (mixed ? refine_scratch_doubles(1, p->n_in, p->n_out) + p->n_in : 0) +
+                    (mixed ? 6 * n * n + 3 : 0) +  // Newton inverse scratch and residuals
                     n * kd + kd * 2 * n + 2 * kd * R;
   const bool adjoint = (p->desc.flags & VRTE_FLAG_ADJOINT) != 0;
   if (adjoint) per_unit += bw_carve(nullptr, 1, n, R, Ro, Lx, P, nullptr);
@@ -440,7 +520,10 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
     if ((st = alloc(p, &w->tcw, p->tcw_bytes)) != VRTE_OK ||
         (st = allocd(p, &w->rscratch, refine_scratch_doubles((int)U, p->n_in, p->n_out))) !=
             VRTE_OK ||
-        (st = allocd(p, &w->rcount, 2)) != VRTE_OK ||
+        (st = allocd(p, &w->rcount, 3)) != VRTE_OK ||
+        (st = alloc(p, &w->nscratch, newton_inverse_scratch_bytes(2 * (int)n, (int)U))) !=
+            VRTE_OK ||
+        (st = allocd(p, &w->nerr, 2 * U)) != VRTE_OK ||
         (st = allocd(p, &w->rlist, U * p->n_in)) != VRTE_OK) {
       free_workspace(p, kPlanAllocs);
       for (Work& x : p->ws) x.Isyn = nullptr;
@@ -448,7 +531,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
     }
   }
   VRTE_ALLOC(Isyn, isyn)
-  VRTE_ALLOC(basebuf, 2 * n + R)
+  VRTE_ALLOC(basebuf, base_buffer_doubles(n, R))
   if (slab && slot == 0) {
     VRTE_ALLOC(sDinv, S_sub * U * 4 * n * n) VRTE_ALLOC(sY, S_sub * U * 2 * n * R)
     VRTE_ALLOC(sUup, S_sub * U * 2 * n * n) VRTE_ALLOC(sH, S_sub * U * Ro * 2 * n)
@@ -504,6 +587,8 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
   const int ldU = 2 * n + (mixed ? p->kdir : 0);
   OrderBatch ob{N, n, L, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef, p->d_status,
                 ldU, (long long)ldU * R};
+  BaseR Rg;
+  const bool has_base = layer_base(ly, &Rg);
   p->last_n = n;
   p->last_U = U;
   p->last_ldU = ldU;
@@ -518,10 +603,10 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
   // sliced BF16 product on the tensor cores in the mixed form
   auto gemm = [&](int M_, int N_, int K_, const double* A_, int lda_, long long sA_,
                   const double* B_, int ldb_, long long sB_, double beta_, double* C_,
-                  int ldc_, long long sC_) {
+                  int ldc_, long long sC_, TcKSkip z_ = TcKSkip{}) {
     if (mixed)
       tc_gemm_store(M_, N_, K_, A_, lda_, sA_, B_, ldb_, sB_, beta_, C_, ldc_, sC_, U,
-                    kSlices, w->tcw, p->d_status, s);
+                    kSlices, w->tcw, p->d_status, s, z_);
     else
       dgemm_batched(M_, N_, K_, 1.0, A_, lda_, sA_, B_, ldb_, sB_, beta_, C_, ldc_, sC_, U,
                     s);
@@ -529,6 +614,12 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
   const double dn = n, dR = R, dRo = Ro, dU = U;
   double lsum = 0.0;  // sum over the batch of (L - m)
   for (int u = 0; u < U; ++u) lsum += std::max(0, L - (m0 + u));
+  // the (l, component) contractions of order m0 + u have no terms with l < m0 + u: K
+  // [4 (m0 + u), 4 L) of the direct operators and beams, skipped block-wise by the sliced
+  // product; kdsum = their summed depth over the batch (the algorithmic work)
+  const TcKSkip zdir{0, 4 * m0, 4};
+  const TcKSkip zpart{2 * n, 4 * m0, 4};
+  const double kdsum = 4.0 * lsum;
   {
     StageScope sc(p, ST_TABLES, s, 1, 30.0 * P * lsum, 24.0 * P * lsum);
     launch_gsf_tables(ob, w->d_pts, w->gp, w->gr, w->gt, s);
@@ -565,25 +656,33 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                   8.0 * (boundary ? 12 : 2) * dn * dn * dU);
     if (boundary) {
       launch_build_K(ob, w->X, w->Y, w->lam_re, w->lam_im, w->d_rtop4, w->K, s);
-      if (ly.base_albedo > 0.0 && m0 == 0)
-        launch_base_K(N, n, ly.tau, ly.base_albedo, w->X, w->Y, w->lam_re, w->lam_im,
+      if (has_base && m0 == 0)
+        launch_base_K(N, n, ly.tau, Rg, w->X, w->Y, w->lam_re, w->lam_im,
                       w->d_mu_nodes, w->d_w_nodes, w->K, w->basebuf, s);
-      batched_inverse(2 * n, w->K, w->Kinv, U, p->d_status, s);
+      if (mixed)
+        newton_inverse(2 * n, w->K, w->Kinv, U, kNewtonSteps, kNewtonTol, w->nscratch, w->nerr,
+                       w->rcount + 2, w->tcw, kSlices, p->d_status, s);
+      else
+        batched_inverse(2 * n, w->K, w->Kinv, U, p->d_status, s);
     }
-    batched_inverse(n, w->X, w->Xinv, U, p->d_status, s);
+    if (mixed)
+      newton_inverse(n, w->X, w->Xinv, U, kNewtonSteps, kNewtonTol, w->nscratch, w->nerr + U,
+                     w->rcount + 2, w->tcw, kSlices, p->d_status, s);
+    else
+      batched_inverse(n, w->X, w->Xinv, U, p->d_status, s);
   }
   {
     StageScope sc(p, ST_PARTICULAR, s, (mixed ? 7 + 6 * gl : 9) - (boundary ? 0 : 1),
                   72.0 * N * p->n_in * lsum + 8.0 * dn * dn * dR * dU,
                   8.0 * 10 * dn * dR * dU);
-    sc.tensor_flops(tcf * (4.0 * dn + 2.0 * kdir) * dn * dR * dU);
+    sc.tensor_flops(tcf * (4.0 * dn * dU + 2.0 * kdsum) * dn * dR);
     if (mixed) {
       // beam vectors as contractions over (l, component) on the tensor cores
       launch_mixed_operators(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, w->d_min4,
                              w->Ln, w->RU, w->Rbp, w->Rbm, s);
       const long long sL = (long long)n * kdir, sB = (long long)kdir * R;
-      gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbp, R, sB, 0.0, w->Pb, R, nR);
-      gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbm, R, sB, 0.0, w->Rb, R, nR);
+      gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbp, R, sB, 0.0, w->Pb, R, nR, zdir);
+      gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbm, R, sB, 0.0, w->Rb, R, nR, zdir);
     } else {
       launch_assemble_beam(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_min4, w->Pb, w->Rb,
                            s);
@@ -600,9 +699,9 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
     launch_particular_sd(ob, w->Pb, w->Es, w->d_pts, w->SD, s);
     if (boundary) {
       launch_bc_rhs(ob, w->SD, nullptr, w->d_rtop4, w->d_pts, w->RHS, s);
-      if (ly.base_albedo > 0.0 && m0 == 0)
-        launch_base_rhs(N, n, R, ob.sSD, ly.tau, ly.base_albedo, w->SD, w->d_pts, w->d_min4,
-                        w->d_mu_nodes, w->d_w_nodes, w->RHS, w->basebuf + 2 * n, 1, s);
+      if (has_base && m0 == 0)
+        launch_base_rhs(N, n, R, ob.sSD, ly.tau, Rg, w->SD, w->d_pts, w->d_min4,
+                        w->d_mu_nodes, w->d_w_nodes, w->RHS, w->basebuf + 8 * n, 1, s);
     }
   }
   if (boundary) {
@@ -616,13 +715,13 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                   72.0 * N * p->n_out * lsum + 4.0 * dRo * dn * dn * dU +
                       72.0 * p->n_in * p->n_out * lsum,
                   8.0 * (6 * dRo * dn + dRo * dR) * dU);
-    sc.tensor_flops(tcf * 2.0 * dRo * dn * (dn + kdir) * dU);
+    sc.tensor_flops(tcf * 2.0 * dRo * dn * (dn * dU + kdsum));
     if (mixed) {
       // U+- = [M_out P(mu_o) B] x RU+-: the direct operator's columns are the left factor
       launch_direct_operators(ob, w->gp, w->gr, w->gt, w->d_min4, w->d_mout4, w->Upm, w->SD,
                               s);
       gemm(Ro, 2 * n, kdir, w->Upm + 2 * n, ldU, sU_part, w->RU, 2 * n,
-           (long long)kdir * 2 * n, 0.0, w->Upm, ldU, sU_part);
+           (long long)kdir * 2 * n, 0.0, w->Upm, ldU, sU_part, zdir);
     } else {
       launch_assemble_U(ob, w->gp, w->gr, w->gt, w->d_w_nodes, w->d_mout4, w->Upm, s);
     }
@@ -646,20 +745,23 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
   }
   {
     // particular (+ direct, mixed) part with the depth factor, into I^m
+    // summed contraction depth over the batch: 2n per order plus, mixed, the direct term's
+    // 4 (L - m)
+    const double kpsum = 2.0 * dn * dU + (mixed ? kdsum : 0.0);
     const double kp = 2.0 * dn + kdir;
     StageScope sc(p, ST_RECON_PART, s, mixed ? (2 * n + kdir <= 1024 ? 1 : 2) * gl : 1,
-                  2.0 * dRo * dR * kp * dU, 8.0 * (dRo * kp + kp * dR + 2 * dRo * dR) * dU);
-    sc.tensor_flops(tcf * dRo * dR * kp * dU);
+                  2.0 * dRo * dR * kpsum, 8.0 * (dRo * kp + kp * dR + 2 * dRo * dR) * dU);
+    sc.tensor_flops(tcf * dRo * dR * kpsum);
     if (mixed) {
       if (2 * n + kdir <= 1024) {
         tc_gemm_part(ob, 2 * n + kdir, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1,
-                     w->g0tab, w->Isyn, kSlices, w->tcw, s);
+                     w->g0tab, w->Isyn, kSlices, w->tcw, s, zpart);
       } else {
         // too deep for one exact accumulation: [U+ U-][s; d] into T1, then the direct part
         tc_gemm_part_accum(ob, 2 * n, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1, w->g0tab,
                            kSlices, w->tcw, s);
         tc_gemm_part(ob, kdir, w->Upm + 2 * n, ldU, sU_part, w->SD + (size_t)2 * n * R,
-                     ob.sSD, w->T1, w->g0tab, w->Isyn, kSlices, w->tcw, s);
+                     ob.sSD, w->T1, w->g0tab, w->Isyn, kSlices, w->tcw, s, zdir);
       }
     } else {
       dgemm_part_epilogue(ob, w->Upm, w->SD, w->T1, w->g0tab, w->Isyn, s);
@@ -671,10 +773,11 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                    w->g0tab, kSliceEps, kRefineTol, w->rscratch, w->rcount, w->rlist,
                    U * p->n_in, w->Isyn, s);
   }
-  // Lambertian base: its isotropic radiance at the bottom, attenuated to the top (order 0)
-  if (ly.base_albedo > 0.0 && m0 == 0)
-    launch_base_recon(n, N, p->n_in, p->n_out, ly.tau, ly.base_albedo, w->C, w->basebuf,
-                      w->basebuf + 2 * n, w->d_pts, w->d_mout4, w->Isyn, 1, s);
+  // reflecting base: its radiance at the bottom (the same in every upward direction),
+  // attenuated to the top (order 0)
+  if (has_base && m0 == 0)
+    launch_base_recon(n, N, p->n_in, p->n_out, ly.tau, Rg, w->C, w->basebuf, w->d_pts,
+                      w->d_mout4, w->Isyn, 1, s);
 }
 
 // Adjoint of one order batch (forward factors of the batch already in the slot's buffers,
@@ -868,7 +971,7 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
   vrte_status result = VRTE_OK;
   for (int k = 0; k < ns && result == VRTE_OK; ++k)
     if (p->desc.precision == VRTE_MIXED &&
-        cudaMemsetAsync(p->ws[k].rcount, 0, 2 * sizeof(int), ns > 1 ? p->ws[k].stream : s0))
+        cudaMemsetAsync(p->ws[k].rcount, 0, 3 * sizeof(int), ns > 1 ? p->ws[k].stream : s0))
       result = VRTE_ERR_CUDA;
   for (int lb = 0; lb < p->n_layers && result == VRTE_OK; ++lb) {
     Work* w = &p->ws[lb % ns];
@@ -904,12 +1007,13 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
                     (double)table * esz + (double)Meff * p->n_in * p->n_out * 16 * 8);
       if (mixed) {
         const int Ss = kSlicesSynth;
-        sc.tensor_flops(2.0 * Ss * (Ss + 1) / 2 * 16.0 * p->n_in * p->n_out * p->n_phi * Meff);
+        sc.tensor_flops(2.0 * Ss * (Ss + 1) / 2 * 16.0 * p->n_in * p->n_out * p->n_rep * Meff);
       }
       SynthHook hook{hook_fn, hook_user, lb};
       if (mixed) {
-        tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws, outb, out_dtype,
-                     kSynthBlock, w->tcw, p->d_status, s, hook_fn ? &hook : nullptr);
+        tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, p->n_rep, p->d_syn_map, w->Isyn, p->d_wc,
+                     p->d_ws, outb, out_dtype, kSynthBlock, w->tcw, p->d_status, s,
+                     hook_fn ? &hook : nullptr);
       } else {
         launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws, outb,
                               out_dtype, p->d_status, s);
@@ -979,7 +1083,8 @@ static vrte_status solve_depth(vrte_plan* p, const double* taus, void* d_up, voi
       OrderBatch ob{N, n, L, m0, U, p->n_in, p->n_out, P, ly.tau, ly.omega, coef, p->d_status,
                     2 * n, 2LL * n * R};
       const long long nR = (long long)n * R, RoR = (long long)Ro * R, Ro2n = (long long)Ro * 2 * n;
-      const bool base = ly.base_albedo > 0.0 && m0 == 0;
+      BaseR Rg;
+      const bool base = layer_base(ly, &Rg) && m0 == 0;
       StageScope sc(p, ST_RECON_HOM, s, 12, 2.0 * U * (double)Ro * R * 2 * n * 5,
                     8.0 * U * 8.0 * Ro * R);
       // upward radiance at the top (identity exit): T1 = direct + Hhat C (+ the base's
@@ -987,8 +1092,8 @@ static vrte_status solve_depth(vrte_plan* p, const double* taus, void* d_up, voi
       dgemm_batched(Ro, R, 2 * n, 1.0, w->Hhat, 2 * n, Ro2n, w->C, R, 2 * nR, 1.0, w->T1, R, RoR, U,
                     s);
       if (base)
-        launch_base_recon(n, N, p->n_in, p->n_out, ly.tau, ly.base_albedo, w->C, w->basebuf,
-                          w->basebuf + 2 * n, w->d_pts, nullptr, w->T1, 0, s);
+        launch_base_recon(n, N, p->n_in, p->n_out, ly.tau, Rg, w->C, w->basebuf, w->d_pts,
+                          nullptr, w->T1, 0, s);
       dgemm_batched(Ro, R, 2 * n, 1.0, w->Upm, 2 * n, Ro2n, w->SD, R, 2 * nR, 0.0, w->Qp, R, RoR,
                     U, s);
       if (d_up) {
@@ -999,8 +1104,8 @@ static vrte_status solve_depth(vrte_plan* p, const double* taus, void* d_up, voi
                       U, s);
         launch_depth_combine(ob, tau, 0, w->Tup, w->Qp, w->T1, w->Qp, w->d_pts, w->rout4, Iup, s);
         if (base)
-          launch_base_recon(n, N, p->n_in, p->n_out, ly.tau - tau, ly.base_albedo, w->C,
-                            w->basebuf, w->basebuf + 2 * n, w->d_pts, nullptr, Iup, 1, s);
+          launch_base_recon(n, N, p->n_in, p->n_out, ly.tau - tau, Rg, w->C, w->basebuf,
+                            w->d_pts, nullptr, Iup, 1, s);
       }
       if (d_down) {
         // Qb = U+ s - U- d; Tbot = direct + Hdepth C at depth tau, downward
@@ -1029,8 +1134,8 @@ static vrte_status solve_depth(vrte_plan* p, const double* taus, void* d_up, voi
       char* outb = (char*)dst + (size_t)lb * table * esz;
       StageScope sc(p, ST_SYNTHESIS, s, 1, 2.0 * table * Meff, (double)table * esz);
       if (mixed)
-        tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, src, p->d_wc, p->d_ws, outb, out_dtype,
-                     kSynthBlock, w->tcw, p->d_status, s);
+        tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, p->n_rep, p->d_syn_map, src, p->d_wc,
+                     p->d_ws, outb, out_dtype, kSynthBlock, w->tcw, p->d_status, s);
       else
         launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, src, p->d_wc, p->d_ws, outb,
                               out_dtype, p->d_status, s);
@@ -1130,7 +1235,8 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
       const vrte_layer& ly = p->layers[k];
       const double* coef = p->d_coeffs + (size_t)k * p->desc.n_coef_max * 6;
       const bool first = k == 0, last = k == S - 1;
-      const bool base = last && ly.base_albedo > 0.0 && m0 == 0;
+      BaseR Rg;
+      const bool base = last && layer_base(ly, &Rg) && m0 == 0;
       Work* wk = &p->ws[k % ns];
       const cudaStream_t sk = slot_stream(k % ns);
       if (ns > 1 && cudaStreamWaitEvent(sk, wk->freed, 0) != cudaSuccess) return VRTE_ERR_CUDA;
@@ -1168,10 +1274,10 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
                          Lcur, s);
       launch_slab_rhs(ob, first, wk->SD, wk->d_rtop4, wk->d_pts, Pprev, wk->RHS, Pcur, w->sZt, s);
       if (base) {
-        launch_base_K(N, n, ly.tau, ly.base_albedo, wk->X, wk->Y, wk->lam_re, wk->lam_im,
+        launch_base_K(N, n, ly.tau, Rg, wk->X, wk->Y, wk->lam_re, wk->lam_im,
                       wk->d_mu_nodes, wk->d_w_nodes, wk->K, wk->basebuf, s);
-        launch_base_rhs(N, n, R, 2 * nR, ly.tau, ly.base_albedo, wk->SD, wk->d_pts, wk->d_min4,
-                        wk->d_mu_nodes, wk->d_w_nodes, wk->RHS, wk->basebuf + 2 * n, 1, s,
+        launch_base_rhs(N, n, R, 2 * nR, ly.tau, Rg, wk->SD, wk->d_pts, wk->d_min4,
+                        wk->d_mu_nodes, wk->d_w_nodes, wk->RHS, wk->basebuf + 8 * n, 1, s,
                         t_top[k]);
       }
       if (!first) {
@@ -1193,7 +1299,9 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
     {
       // back-substitution from the bottom, c_k = y_k - W_k (Uup_{k+1} c_{k+1}), then the
       // homogeneous parts of the sub-layers' top radiances
-      StageScope sc(p, ST_RECON_HOM, s, 2 * (S - 1) + 2 * S + 1 + (bot.base_albedo > 0.0 && m0 == 0),
+      BaseR Rbot;
+      const bool bot_base = layer_base(bot, &Rbot) && m0 == 0;
+      StageScope sc(p, ST_RECON_HOM, s, 2 * (S - 1) + 2 * S + 1 + 2 * bot_base,
                     (S - 1) * 2.0 * (2 * dn * dR * 2 * dn) * dU + S * 2.0 * dRo * dR * 2 * dn * dU,
                     8.0 * ((S - 1) * (6 * dn * dn + 6 * dn * dR) + S * (2 * dRo * dn + 2 * dn * dR +
                                                                     2 * dRo * dR)) * dU);
@@ -1211,11 +1319,11 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
         launch_slab_accum(ob, t_top[k], w->d_pts, nullptr, w->sTq, nullptr, w->sAcc, 0, s);
       }
       launch_slab_store(ob, w->sAcc, w->Isyn, s);
-      // Lambertian base: its isotropic radiance at the bottom, attenuated through the slab
-      if (bot.base_albedo > 0.0 && m0 == 0)
-        launch_base_recon(n, N, p->n_in, p->n_out, ttot, bot.base_albedo,
-                          w->sY + (size_t)(S - 1) * U0 * sYk, wl->basebuf, wl->basebuf + 2 * n,
-                          w->d_pts, w->d_mout4, w->Isyn, 1, s);
+      // reflecting base: its radiance at the bottom, attenuated through the slab
+      if (bot_base)
+        launch_base_recon(n, N, p->n_in, p->n_out, ttot, Rbot,
+                          w->sY + (size_t)(S - 1) * U0 * sYk, wl->basebuf, w->d_pts, w->d_mout4,
+                          w->Isyn, 1, s);
     }
   }
   // join: every slot stream's work is already behind a `ready` the caller's stream waited on;
@@ -1234,8 +1342,8 @@ static vrte_status solve_slab(vrte_plan* p, void* d_brdf, int out_dtype, cudaStr
   {
     StageScope sc(p, ST_SYNTHESIS, s, 1, 2.0 * table * Meff, (double)table * esz);
     if (mixed)
-      tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws, d_brdf,
-                   out_dtype, kSynthBlock, w->tcw, p->d_status, s);
+      tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, p->n_rep, p->d_syn_map, w->Isyn, p->d_wc,
+                   p->d_ws, d_brdf, out_dtype, kSynthBlock, w->tcw, p->d_status, s);
     else
       launch_synthesis_fp64(Meff, p->n_in, p->n_out, p->n_phi, w->Isyn, p->d_wc, p->d_ws,
                             d_brdf, out_dtype, p->d_status, s);
@@ -1256,7 +1364,7 @@ vrte_status vrte_solve_slab_brdf(vrte_plan* p, void* d_brdf, int out_dtype, void
     // first sub-layer and a Lambertian base only under the last
     if (l.n_nodes != top.n_nodes || l.n_orders != top.n_orders) return VRTE_ERR_INVALID_ARG;
     if (k > 0 && l.n_interface > 1.0) return VRTE_ERR_INVALID_ARG;
-    if (k < p->n_layers - 1 && l.base_albedo > 0.0) return VRTE_ERR_INVALID_ARG;
+    if (k < p->n_layers - 1 && layer_base(l, nullptr)) return VRTE_ERR_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
   p->last_stream = s;
@@ -1340,7 +1448,7 @@ vrte_status vrte_brdf_backward(vrte_plan* p, const void* g, int gd, double* d_gr
   if (!(p->desc.flags & VRTE_FLAG_ADJOINT) || p->n_layers < 1 || !p->ws[0].bw)
     return VRTE_ERR_STATE;
   for (const vrte_layer& l : p->layers)
-    if (l.base_albedo > 0.0) return VRTE_ERR_UNSUPPORTED;
+    if (layer_base(l, nullptr)) return VRTE_ERR_UNSUPPORTED;
   cudaStream_t s0 = (cudaStream_t)stream;
   p->last_stream = s0;
   const int ns = p->nslots;
@@ -1422,6 +1530,40 @@ vrte_status vrte_debug_copy(vrte_plan* p, const char* name, void* dst, size_t by
     double v = (double)h;
     if (size_out) *size_out = sizeof(double);
     if (dst && bytes >= sizeof(double)) memcpy(dst, &v, sizeof(double));
+    return VRTE_OK;
+  }
+  if (strcmp(name, "newton_fallbacks") == 0 || strcmp(name, "newton_residual") == 0) {
+    // mixed form: matrices inverted again in FP64 in the last solve, summed over the slots;
+    // or the final Newton residuals max|I - A X| of the last order batch, [K, X][U]
+    if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return VRTE_ERR_CUDA;
+    std::vector<double> v;
+    if (name[7] == 'f') {
+      double c = 0.0;
+      for (const Work& x : p->ws) {
+        int h = 0;
+        if (x.rcount &&
+            cudaMemcpy(&h, x.rcount + 2, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+          return VRTE_ERR_CUDA;
+        c += h;
+      }
+      v.push_back(c);
+    } else {
+      const Work& x = p->ws[p->last_slot];
+      if (!x.nerr || p->last_U == 0) return VRTE_ERR_STATE;
+      std::vector<unsigned long long> h(2 * (size_t)p->last_U);
+      for (int k = 0; k < 2; ++k)
+        if (cudaMemcpy(h.data() + (size_t)k * p->last_U, x.nerr + (size_t)k * p->chunk,
+                       p->last_U * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+          return VRTE_ERR_CUDA;
+      for (unsigned long long b : h) {
+        double d;
+        memcpy(&d, &b, sizeof(d));
+        v.push_back(d);
+      }
+    }
+    if (size_out) *size_out = v.size() * sizeof(double);
+    if (dst && bytes >= v.size() * sizeof(double)) memcpy(dst, v.data(), v.size() * sizeof(double));
     return VRTE_OK;
   }
   if (strcmp(name, "refined") == 0) {  // mixed form: column blocks recomputed in FP64

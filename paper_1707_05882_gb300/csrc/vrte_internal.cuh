@@ -202,7 +202,22 @@ void dgemm_batched_t(bool tA, bool tB, int M, int N, int K, double alpha, const 
 // Reconstruction epilogue: Isyn[m][k][o][a][s] = T1[ro][rc] + g0(o, k) * (A @ B)[ro][rc]
 void dgemm_part_epilogue(const OrderBatch& b, const double* A, const double* B, const double* T1,
                          const double* g0tab, double* Isyn, cudaStream_t s);
-void batched_inverse(int n, double* A, double* Ainv, int batch, unsigned* status, cudaStream_t s);
+// Ainv[u] = A[u]^-1 (FP64 Gauss-Jordan with partial pivoting, one CTA per matrix); with
+// skip, only the matrices u with skip[u] != 0.
+void batched_inverse(int n, double* A, double* Ainv, int batch, unsigned* status, cudaStream_t s,
+                     const int* skip = nullptr);
+// The same elimination in FP32 into an FP32 result (a starting inverse).
+void batched_inverse_f32(int n, const double* A, float* Ainv, int batch, unsigned* status,
+                         cudaStream_t s);
+// Mixed form: X[u] = A[u]^-1 from the FP32 elimination and `steps` Newton-Schulz steps
+// X <- X + X (I - A X) on the tensor cores (sliced products of `slices` slices, workspace
+// tcw); err[u] receives the final max|I - A X| (bits of a non-negative double); matrices
+// whose residual is not below tol are inverted again by the FP64 elimination, counted in
+// *fallback_count. `scratch` holds newton_inverse_scratch_bytes(n, batch).
+size_t newton_inverse_scratch_bytes(int n, int batch);
+void newton_inverse(int n, const double* A, double* X, int batch, int steps, double tol,
+                    void* scratch, unsigned long long* err, int* fallback_count, void* tcw,
+                    int slices, unsigned* status, cudaStream_t s);
 void batched_eigen(int n, const double* A, double* H, double* Z, double* V, double* X,
                    double* lam_re, double* lam_im, double* scale, int batch, unsigned* status,
                    cudaStream_t s, const int* mask = nullptr);
@@ -216,17 +231,24 @@ void eigen_block_fallback(int n, int m0, const double* E, const double* F, const
 
 // ---------------------------------------------------------------- tensor cores (k_tcgemm.cu)
 // C = A B (+ beta C) with A, B FP64 sliced into S exact 7-bit BF16 slices (relative
-// accuracy ~2^-7S per term); K <= 1024, 1 <= S <= 4. `work` holds tc_workspace_bytes.
+// accuracy ~2^-7S per term); K <= 1024, 1 <= S <= 8. `work` holds tc_workspace_bytes.
 size_t tc_workspace_bytes(int M, int N, int K, int batch, int S);
 // the part of tc_workspace_bytes that does not grow with the batch (epilogue scratch)
 size_t tc_scratch_bytes();
 bool tc_shape_ok(int K, int S);
+// A K range on which both operands of unit u are zero: [zk0, zk0 + zbase + zstep u). The
+// K blocks inside it are neither copied nor multiplied (a Fourier order m has no terms of
+// degree l < m: its (l, component) contractions start at K = 4m).
+struct TcKSkip {
+  int zk0 = 0, zbase = 0, zstep = 0;
+};
 void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, const double* B,
                    int ldb, long long sB, double beta, double* C, int ldc, long long sC,
-                   int batch, int S, void* work, unsigned* status, cudaStream_t s);
+                   int batch, int S, void* work, unsigned* status, cudaStream_t s,
+                   TcKSkip zskip = TcKSkip{});
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                   const double* B, long long sB, const double* T1, const double* g0tab,
-                  double* Isyn, int S, void* work, cudaStream_t s);
+                  double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip = TcKSkip{});
 // Mixed form: flags (order, incident) column blocks whose sliced reconstruction error
 // bound eps K max|row| max|column| exceeds tol |I_00| and recomputes them in FP64.
 void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
@@ -237,7 +259,7 @@ size_t refine_scratch_doubles(int U, int n_in, int n_out);
 // T1 += g0 (A @ B): the first part of a reconstruction contraction split in K.
 void tc_gemm_part_accum(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                         const double* B, long long sB, double* T1, const double* g0tab, int S,
-                        void* work, cudaStream_t s);
+                        void* work, cudaStream_t s, TcKSkip zskip = TcKSkip{});
 // Called on the host after the kernels that complete the table rows of incident cosines
 // k0 .. k1-1 of one layer have been enqueued on `s` (the host-buffer solve starts the copy
 // of those rows there).
@@ -249,9 +271,13 @@ struct SynthHook {
 // Synthesis of the order radiances on the tensor cores (five slices), in blocks of k_block
 // incident cosines (k_synth_tc.cu).
 size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int k_block);
-void tc_synthesis(int M, int n_in, int n_out, int n_phi, const double* Isyn, const double* wc,
-                  const double* ws, void* out, int out_dtype, int k_block, void* work,
-                  unsigned* status, cudaStream_t s, const SynthHook* hook = nullptr);
+// map: [n_phi] computed azimuths (the first n_rep entries) and [n_phi] their mirrors at -phi
+// (-1: none), written by the plan; the mirror's table entry is the computed one (cosine
+// class) or its negative (sine class).
+void tc_synthesis(int M, int n_in, int n_out, int n_phi, int n_rep, const int* map,
+                  const double* Isyn, const double* wc, const double* ws, void* out,
+                  int out_dtype, int k_block, void* work, unsigned* status, cudaStream_t s,
+                  const SynthHook* hook = nullptr);
 
 // ---------------------------------------------------------------- mode algebra (k_modes.cu)
 void launch_pack_Y(const OrderBatch& b, const double* EX, const double* lam_re,
@@ -270,16 +296,39 @@ void launch_build_Hhat(const OrderBatch& b, const double* P1, const double* P2,
                        const double* lam_re, const double* lam_im, const double* pts,
                        double* Hhat, cudaStream_t s);
 
-// ---------------------------------------------------------------- Lambertian base (k_modes.cu)
-void launch_base_K(int N, int n, double tau, double rho, const double* X, const double* Y,
+// ---------------------------------------------------------------- reflecting base (k_modes.cu)
+// Direction-independent Mueller BRDF matrix R of a reflecting base (row-major), the sum of the
+// layer's base_mueller and the Lambertian 2 rho e0 e0^T; passed to the kernels by value.
+struct BaseR {
+  double r[16];
+};
+// The base of a layer; false for a black base (R = 0).
+inline bool layer_base(const vrte_layer& l, BaseR* out) {
+  BaseR b;
+  bool any = false;
+  for (int i = 0; i < 16; ++i) {
+    b.r[i] = l.base_mueller[i];
+    any = any || b.r[i] != 0.0;
+  }
+  b.r[0] += 2.0 * l.base_albedo;
+  any = any || l.base_albedo != 0.0;
+  if (out) *out = b;
+  return any;
+}
+// Buffer of the base stage per workspace slot: basev [4][2n], zb [4][R], vb [4][R] doubles.
+inline size_t base_buffer_doubles(int n, int R) { return 8 * (size_t)n + 8 * (size_t)R; }
+void launch_base_K(int N, int n, double tau, const BaseR& Rg, const double* X, const double* Y,
                    const double* lam_re, const double* lam_im, const double* mu_nodes,
                    const double* w_nodes, double* K, double* basev, cudaStream_t s);
-void launch_base_rhs(int N, int n, int R, long long sSD, double tau, double rho, const double* SD,
-                     const double* pts, const double* min4, const double* mu_nodes,
-                     const double* w_nodes, double* RHS, double* zb, int add_rhs, cudaStream_t s,
-                     double t_above = 0.0);
-void launch_base_recon(int n, int N, int n_in, int n_out, double tau, double rho, const double* C,
-                       const double* basev, const double* zb, const double* pts,
+void launch_base_rhs(int N, int n, int R, long long sSD, double tau, const BaseR& Rg,
+                     const double* SD, const double* pts, const double* min4,
+                     const double* mu_nodes, const double* w_nodes, double* RHS, double* zb,
+                     int add_rhs, cudaStream_t s, double t_above = 0.0);
+// Adds the base's radiance at the bottom, attenuated by e^{-tau/mu_o}, to the order-0 upward
+// radiance `out` (basebuf as filled by launch_base_K and launch_base_rhs; its vb part is
+// written here).
+void launch_base_recon(int n, int N, int n_in, int n_out, double tau, const BaseR& Rg,
+                       const double* C, double* basebuf, const double* pts,
                        const double* mout4, double* out, int isyn, cudaStream_t s);
 // Multi-layer slabs (k_slab.cu): boundary blocks and right-hand side of one sub-layer, the
 // beam's attenuation to a sub-layer's top, and the attenuated sum of the sub-layers'

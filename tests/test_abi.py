@@ -64,8 +64,8 @@ def test_plan_descriptor_layout_matches_header(tmp_path):
 int main(void) {
   printf("%zu %zu %zu %zu\\n", sizeof(vrte_plan_desc), offsetof(vrte_plan_desc, mu_in),
          offsetof(vrte_plan_desc, precision), offsetof(vrte_plan_desc, flags));
-  printf("%zu %zu %zu\\n", sizeof(vrte_layer), offsetof(vrte_layer, n_nodes),
-         offsetof(vrte_layer, base_albedo));
+  printf("%zu %zu %zu %zu\\n", sizeof(vrte_layer), offsetof(vrte_layer, n_nodes),
+         offsetof(vrte_layer, base_albedo), offsetof(vrte_layer, base_mueller));
   printf("%zu %zu\\n", sizeof(vrte_stage_stat), offsetof(vrte_stage_stat, tc_flops));
   return 0;
 }
@@ -78,7 +78,8 @@ int main(void) {
             if line.strip()]
     assert vals[0] == [ctypes.sizeof(vr.PlanDesc), vr.PlanDesc.mu_in.offset,
                        vr.PlanDesc.precision.offset, vr.PlanDesc.flags.offset]
-    assert vals[1] == [ctypes.sizeof(vr.Layer), vr.Layer.n_nodes.offset, vr.Layer.base_albedo.offset]
+    assert vals[1] == [ctypes.sizeof(vr.Layer), vr.Layer.n_nodes.offset, vr.Layer.base_albedo.offset,
+                       vr.Layer.base_mueller.offset]
     assert vals[2] == [ctypes.sizeof(vr.StageStat), vr.StageStat.tc_flops.offset]
 
 

@@ -151,3 +151,23 @@ def test_mixed_matches_fp64_form_on_the_same_plan_shape():
     ei, eq = row_errors(F, G)
     assert ei < TOL_I and eq < TOL_QUV
     assert ei > 0.0  # the mixed form really ran the sliced contractions
+
+
+@pytest.mark.parametrize("grid", ["uniform_odd", "irregular"])
+def test_mixed_synthesis_azimuth_mirrors(grid):
+    """The tensor-core synthesis computes one azimuth of every pair (phi, -phi mod 2 pi) on the
+    grid and stores the mirror from it (cosine class even, sine class odd): a uniform grid of
+    odd length (0 unpaired), and an irregular grid with paired, unpaired, self-paired (0, pi),
+    repeated and out-of-range azimuths (-0.3 = 2 pi - 0.3; 7.0 paired with 4 pi - 7.0)."""
+    if grid == "uniform_odd":
+        dphi = 2 * np.pi * np.arange(13) / 13
+    else:
+        dphi = np.array([0.3, 1.7, 4.0, 2 * np.pi - 0.3, np.pi, 0.0, 2 * np.pi - 1.7, 5.1,
+                         1.7, -0.3, 7.0, 4 * np.pi - 7.0, 2.2])
+    layer = dict(tau=1.3, omega=0.93, n_interface=1.5, n_nodes=12, n_orders=24,
+                 coef=polydisperse_coefficients(1.5 + 0.001j, 5.0, 0.1, 24))
+    mu_in, mu_out, _ = angle_grids(5, 6, 4)
+    F = mixed_brdf(layer, mu_in, mu_out, dphi, out_dtype=torch.float32)
+    G = oracle_brdf(layer, mu_in, mu_out, dphi)
+    ei, eq = row_errors(F, G)
+    assert ei < TOL_I and eq < TOL_QUV, (ei, eq)

@@ -48,7 +48,7 @@ def _solve_slab(lys, grids, precision=vr.VRTE_FP64, out_dtype=torch.float64):
 def _oracle(lys, grids, N, M):
     return O.slab_brdf([dict(coef=l["coef"], omega=l["omega"], tau=l["tau"]) for l in lys],
                        lys[0].get("n_interface", 1.0), N, M, *grids,
-                       rho=lys[-1].get("base_albedo", 0.0))
+                       rho=lys[-1].get("base_albedo", 0.0), base=lys[-1].get("base_mueller"))
 
 
 def _stack(N, M, n_if=1.4, rho=0.3):
@@ -145,3 +145,27 @@ def test_slab_more_sublayers_than_slots():
     G = _oracle(lys, grids, N, M)
     e_i, e_q = _err_rows(F, G)
     assert e_i < 1e-10 and e_q < 1e-10, (e_i, e_q)
+
+
+def test_slab_over_a_polarizing_base():
+    # a direction-independent Mueller BRDF matrix under the last sub-layer (with a Lambertian
+    # part added), and the same matrix under an inner sub-layer rejected
+    R = np.array([[0.9, 0.25, 0.0, 0.0], [0.18, 0.5, 0.0, 0.0],
+                  [0.0, 0.0, 0.4, 0.15], [0.0, 0.0, -0.1, 0.3]])
+    N, M = 12, 24
+    lys = _stack(N, M, 1.4, 0.1)
+    lys[-1]["base_mueller"] = R
+    grids = angle_grids(9, 11, 7)
+    F = _solve_slab(lys, grids)
+    G = _oracle(lys, grids, N, M)
+    e_i, e_q = _err_rows(F, G)
+    assert e_i < 1e-10 and e_q < 1e-10, (e_i, e_q)
+    bad = [dict(lys[0]), dict(lys[1], base_mueller=R), dict(lys[2])]
+    plan = _plan(bad, angle_grids(2, 2, 3))
+    try:
+        out = torch.empty(plan.table_shape[1:], dtype=torch.float64, device="cuda")
+        with pytest.raises(vr.VrteError) as e:
+            plan.solve_slab(out)
+        assert e.value.code == 1  # VRTE_ERR_INVALID_ARG: a reflecting base inside the slab
+    finally:
+        plan.close()

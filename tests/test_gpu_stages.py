@@ -150,3 +150,36 @@ def test_reconstruction(solved):
         assert close(U[m, :, n:], md["Um"], 1e-13), m
         # every order against the oracle's full 8N solution, on the scale of order 0
         assert close(Is[m], solved["full"][m], 1e-11, scale), m
+
+
+@pytest.mark.parametrize("n_if", [1.0, 1.5])
+def test_mixed_inverses_newton(n_if):
+    """Mixed form: K^-1 and X^-1 from the FP32 elimination refined by Newton-Schulz steps on
+    the tensor cores reach the FP64 elimination's residual, with no FP64 re-inversion."""
+    coef = polydisperse_coefficients(1.5 + 0.001j, 6.0, 0.1, 24)
+    N, M = 20, 24
+    mu_in, mu_out, dphi = angle_grids(9, 7, 5)
+    layer = dict(tau=3.0, omega=0.97, n_interface=n_if, n_nodes=N, n_orders=M, n_coef=24)
+    plan = vr.Plan(mu_in, mu_out, dphi, N, M, 24, precision=vr.VRTE_MIXED)
+    try:
+        plan.set_layers([layer], torch.from_numpy(vr.pack_coefficients([dict(coef=coef)])).cuda())
+        out = torch.empty(plan.table_shape, dtype=torch.float32, device="cuda")
+        plan.solve(out)
+        assert plan.status() == 0
+        b = {k: plan.debug_buffer(k) for k in ["K", "Kinv", "X", "Xinv"]}
+        resid = plan.debug_buffer("newton_residual").reshape(2, M)
+        fallbacks = plan.debug_buffer("newton_fallbacks")[0]
+    finally:
+        plan.close()
+    n = 4 * N
+    K = b["K"][:M * 4 * n * n].reshape(M, 2 * n, 2 * n)
+    Ki = b["Kinv"][:M * 4 * n * n].reshape(M, 2 * n, 2 * n)
+    X = b["X"][:M * n * n].reshape(M, n, n)
+    Xi = b["Xinv"][:M * n * n].reshape(M, n, n)
+    for m in range(M):
+        rk = np.abs(K[m] @ Ki[m] - np.eye(2 * n)).max()
+        rx = np.abs(X[m] @ Xi[m] - np.eye(n)).max()
+        assert rk < 1e-10 and rx < 1e-10, (m, rk, rx)
+        # the library's own final residual agrees with numpy's (same quantity, other rounding)
+        assert resid[0, m] < 1e-11 and resid[1, m] < 1e-11, (m, resid[:, m])
+    assert fallbacks == 0
