@@ -1,6 +1,8 @@
 // Dense FP64 linear algebra on CUDA cores: batched GEMM (with an epilogue hook for the
 // reconstruction) and batched in-place Gauss-Jordan inversion with partial pivoting.
 // FP64 stays on the CUDA cores: sm_103a has no FP64 tensor-core path worth using.
+#include <algorithm>
+
 #include "vrte_internal.cuh"
 
 namespace vrte {
@@ -141,11 +143,14 @@ constexpr int TJ = 32;   // column tile of the outside update
 
 // T = double: the FP64 inverse. T = float: the same elimination in FP32 (the starting
 // inverse of the mixed form's Newton refinement), W an FP32 workspace. Orders u with
-// skip && !skip[u] return at once.
+// skip && !skip[u] return at once. CTAs from nb1 on invert a second batch (n2, A2, Ainv2),
+// so that two batches of matrices share one launch.
 template <typename T>
 __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict__ A,
                                                  T* __restrict__ Ainv, unsigned* status,
-                                                 const int* __restrict__ skip) {
+                                                 const int* __restrict__ skip, int nb1, int n2,
+                                                 const double* __restrict__ A2,
+                                                 T* __restrict__ Ainv2) {
   extern __shared__ __align__(16) unsigned char sh_raw[];
   T* sh = (T*)sh_raw;
   T* P = sh;                  // [n][BI] panel
@@ -156,8 +161,16 @@ __global__ void __launch_bounds__(512) k_inverse(int n, const double* __restrict
   __shared__ int red_i[16];
   __shared__ T rk[BI];
   __shared__ T Q[BI][BI], G[BI][BI];
-  const int u = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
-  if (skip && !skip[u]) return;
+  int u = blockIdx.x;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (u >= nb1) {
+    u -= nb1;
+    n = n2;
+    A = A2;
+    Ainv = Ainv2;
+  } else if (skip && !skip[u]) {
+    return;
+  }
   const double* Ab = A + (size_t)u * n * n;
   T* W = Ainv + (size_t)u * n * n;
   for (size_t e = tid; e < (size_t)n * n; e += nt) W[e] = (T)Ab[e];
@@ -323,14 +336,23 @@ void batched_inverse(int n, double* A, double* Ainv, int batch, unsigned* status
   // static shared memory (reductions, Q, G) comes on top: always raise the dynamic limit
   size_t smem = (2 * (size_t)n * BI + BI * TJ) * sizeof(double) + n * sizeof(int);
   cudaFuncSetAttribute(k_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_inverse<double><<<batch, 512, smem, s>>>(n, A, Ainv, status, skip);
+  k_inverse<double><<<batch, 512, smem, s>>>(n, A, Ainv, status, skip, batch, 0, nullptr, nullptr);
+}
+
+// FP32 inverses of two batches in one launch (the second may be empty: nb = 0)
+static void batched_inverse_f32_pair(int na, const double* A, float* Ainv, int nb,
+                                     const double* B, float* Binv, int batch, unsigned* status,
+                                     cudaStream_t s) {
+  const int nm = std::max(na, nb);
+  size_t smem = (2 * (size_t)nm * BI + BI * TJ) * sizeof(float) + nm * sizeof(int);
+  cudaFuncSetAttribute(k_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_inverse<float><<<(nb > 0 ? 2 : 1) * batch, 512, smem, s>>>(na, A, Ainv, status, nullptr, batch,
+                                                               nb, B, Binv);
 }
 
 void batched_inverse_f32(int n, const double* A, float* Ainv, int batch, unsigned* status,
                          cudaStream_t s) {
-  size_t smem = (2 * (size_t)n * BI + BI * TJ) * sizeof(float) + n * sizeof(int);
-  cudaFuncSetAttribute(k_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_inverse<float><<<batch, 512, smem, s>>>(n, A, Ainv, status, nullptr);
+  batched_inverse_f32_pair(n, A, Ainv, 0, nullptr, nullptr, batch, status, s);
 }
 
 }  // namespace vrte
@@ -384,38 +406,46 @@ __global__ void k_newton_flag(int batch, const unsigned long long* err, double t
   if (f) atomicAdd(count, 1);
 }
 
-size_t newton_inverse_scratch_bytes(int n, int batch) {
-  const size_t nn = (size_t)n * n * batch;
-  return nn * sizeof(double) + (nn + 1) * sizeof(float) + (size_t)batch * sizeof(int) +
-         sizeof(unsigned);
+size_t newton_inverse_scratch_bytes(int na, int nb, int batch) {
+  const size_t a = (size_t)na * na * batch, b = (size_t)nb * nb * batch;
+  return std::max(a, b) * sizeof(double) + (a + b + 2) * sizeof(float) +
+         (size_t)batch * sizeof(int) + sizeof(unsigned);
 }
 
-void newton_inverse(int n, const double* A, double* X, int batch, int steps, double tol,
-                    void* scratch, unsigned long long* err, int* fallback_count, void* tcw,
-                    int slices, unsigned* status, cudaStream_t s) {
-  const size_t nn = (size_t)n * n;
+void newton_inverse(int na, const double* A, double* XA, int nb, const double* B, double* XB,
+                    int batch, int steps, double tol, void* scratch, unsigned long long* err,
+                    int* fallback_count, void* tcw, int slices, unsigned* status, cudaStream_t s) {
+  const size_t nna = (size_t)na * na * batch, nnb = (size_t)nb * nb * batch;
   double* Rm = (double*)scratch;
-  float* x32 = (float*)(Rm + nn * batch);
-  int* flag = (int*)(x32 + nn * batch + 1);
+  float* xa32 = (float*)(Rm + std::max(nna, nnb));
+  float* xb32 = xa32 + nna + (nna & 1);
+  int* flag = (int*)(xb32 + nnb + 1);
   // the FP32 elimination's pivot findings do not enter the plan's status: a failed start is
   // caught by the residual below
   unsigned* st32 = (unsigned*)(flag + batch);
-  batched_inverse_f32(n, A, x32, batch, st32, s);
-  k_widen<<<1024, 256, 0, s>>>(nn * batch, x32, X);
-  const dim3 eg((unsigned)std::min<size_t>((nn + 255) / 256, 64), batch);
-  for (int k = 0; k <= steps; ++k) {
-    tc_gemm_store(n, n, n, A, n, (long long)nn, X, n, (long long)nn, 0.0, Rm, n, (long long)nn,
-                  batch, slices, tcw, status, s);
-    cudaMemsetAsync(err, 0, batch * sizeof(unsigned long long), s);
-    k_eye_minus<<<eg, 256, 0, s>>>(n, Rm, err);
-    if (k == steps) break;
-    // X <- X E + X: the product reads X only through its slices, taken before the epilogue
-    // writes X
-    tc_gemm_store(n, n, n, X, n, (long long)nn, Rm, n, (long long)nn, 1.0, X, n, (long long)nn,
-                  batch, slices, tcw, status, s);
+  batched_inverse_f32_pair(na, A, xa32, nb, B, xb32, batch, st32, s);
+  for (int q = 0; q < (nb > 0 ? 2 : 1); ++q) {
+    const int n = q ? nb : na;
+    const double* M = q ? B : A;
+    double* X = q ? XB : XA;
+    unsigned long long* e = err + (size_t)q * batch;
+    const size_t nn = (size_t)n * n;
+    k_widen<<<1024, 256, 0, s>>>(nn * batch, q ? xb32 : xa32, X);
+    const dim3 eg((unsigned)std::min<size_t>((nn + 255) / 256, 64), batch);
+    for (int k = 0; k <= steps; ++k) {
+      tc_gemm_store(n, n, n, M, n, (long long)nn, X, n, (long long)nn, 0.0, Rm, n,
+                    (long long)nn, batch, slices, tcw, status, s);
+      cudaMemsetAsync(e, 0, batch * sizeof(unsigned long long), s);
+      k_eye_minus<<<eg, 256, 0, s>>>(n, Rm, e);
+      if (k == steps) break;
+      // X <- X E + X: the product reads X only through its slices, taken before the
+      // epilogue writes X
+      tc_gemm_store(n, n, n, X, n, (long long)nn, Rm, n, (long long)nn, 1.0, X, n,
+                    (long long)nn, batch, slices, tcw, status, s);
+    }
+    k_newton_flag<<<(batch + 127) / 128, 128, 0, s>>>(batch, e, tol, flag, fallback_count);
+    batched_inverse(n, const_cast<double*>(M), X, batch, status, s, flag);
   }
-  k_newton_flag<<<(batch + 127) / 128, 128, 0, s>>>(batch, err, tol, flag, fallback_count);
-  batched_inverse(n, const_cast<double*>(A), X, batch, status, s, flag);
 }
 
 }  // namespace vrte

@@ -39,7 +39,7 @@ constexpr double kSliceEps = 2e-15;
 constexpr double kRefineTol = 1e-7;
 // mixed form: Newton-Schulz steps after the FP32 starting inverse of K and X, and the final
 // max|I - A X| above which a matrix is inverted again in FP64
-constexpr int kNewtonSteps = 3;
+constexpr int kNewtonSteps = 2;
 constexpr double kNewtonTol = 1e-11;
 
 const char* kStageNames[kStages] = {"tables",     "assemble",   "eigen",
@@ -446,7 +446,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
                     (4 * n + kd) * R + 2 * n * R + 4 * Ro * n + Ro * (2 * n + kd) + Ro * R + n * n +
                     1 + 5 * 4 * n * n + 3 * 2 * n + 1 + (tc_unit + 7) / 8 +
                     (mixed ? refine_scratch_doubles(1, p->n_in, p->n_out) + p->n_in : 0) +
-                    (mixed ? 6 * n * n + 3 : 0) +  // Newton inverse scratch and residuals
+                    (mixed ? 7 * n * n + 3 : 0) +  // Newton inverse scratch and residuals
                     n * kd + kd * 2 * n + 2 * kd * R;
   const bool adjoint = (p->desc.flags & VRTE_FLAG_ADJOINT) != 0;
   if (adjoint) per_unit += bw_carve(nullptr, 1, n, R, Ro, Lx, P, nullptr);
@@ -521,7 +521,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
         (st = allocd(p, &w->rscratch, refine_scratch_doubles((int)U, p->n_in, p->n_out))) !=
             VRTE_OK ||
         (st = allocd(p, &w->rcount, 3)) != VRTE_OK ||
-        (st = alloc(p, &w->nscratch, newton_inverse_scratch_bytes(2 * (int)n, (int)U))) !=
+        (st = alloc(p, &w->nscratch, newton_inverse_scratch_bytes(2 * (int)n, (int)n, (int)U))) !=
             VRTE_OK ||
         (st = allocd(p, &w->nerr, 2 * U)) != VRTE_OK ||
         (st = allocd(p, &w->rlist, U * p->n_in)) != VRTE_OK) {
@@ -659,15 +659,12 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
       if (has_base && m0 == 0)
         launch_base_K(N, n, ly.tau, Rg, w->X, w->Y, w->lam_re, w->lam_im,
                       w->d_mu_nodes, w->d_w_nodes, w->K, w->basebuf, s);
-      if (mixed)
-        newton_inverse(2 * n, w->K, w->Kinv, U, kNewtonSteps, kNewtonTol, w->nscratch, w->nerr,
-                       w->rcount + 2, w->tcw, kSlices, p->d_status, s);
-      else
-        batched_inverse(2 * n, w->K, w->Kinv, U, p->d_status, s);
+      if (!mixed) batched_inverse(2 * n, w->K, w->Kinv, U, p->d_status, s);
     }
-    if (mixed)
-      newton_inverse(n, w->X, w->Xinv, U, kNewtonSteps, kNewtonTol, w->nscratch, w->nerr + U,
-                     w->rcount + 2, w->tcw, kSlices, p->d_status, s);
+    if (mixed)  // K^-1 (with the boundary system) and X^-1, the eliminations in one launch
+      newton_inverse(boundary ? 2 * n : n, boundary ? w->K : w->X, boundary ? w->Kinv : w->Xinv,
+                     boundary ? n : 0, w->X, w->Xinv, U, kNewtonSteps, kNewtonTol, w->nscratch,
+                     w->nerr, w->rcount + 2, w->tcw, kSlices, p->d_status, s);
     else
       batched_inverse(n, w->X, w->Xinv, U, p->d_status, s);
   }
@@ -1552,7 +1549,7 @@ vrte_status vrte_debug_copy(vrte_plan* p, const char* name, void* dst, size_t by
       if (!x.nerr || p->last_U == 0) return VRTE_ERR_STATE;
       std::vector<unsigned long long> h(2 * (size_t)p->last_U);
       for (int k = 0; k < 2; ++k)
-        if (cudaMemcpy(h.data() + (size_t)k * p->last_U, x.nerr + (size_t)k * p->chunk,
+        if (cudaMemcpy(h.data() + (size_t)k * p->last_U, x.nerr + (size_t)k * p->last_U,
                        p->last_U * sizeof(unsigned long long), cudaMemcpyDeviceToHost) !=
             cudaSuccess)
           return VRTE_ERR_CUDA;

@@ -209,15 +209,16 @@ void batched_inverse(int n, double* A, double* Ainv, int batch, unsigned* status
 // The same elimination in FP32 into an FP32 result (a starting inverse).
 void batched_inverse_f32(int n, const double* A, float* Ainv, int batch, unsigned* status,
                          cudaStream_t s);
-// Mixed form: X[u] = A[u]^-1 from the FP32 elimination and `steps` Newton-Schulz steps
-// X <- X + X (I - A X) on the tensor cores (sliced products of `slices` slices, workspace
-// tcw); err[u] receives the final max|I - A X| (bits of a non-negative double); matrices
-// whose residual is not below tol are inverted again by the FP64 elimination, counted in
-// *fallback_count. `scratch` holds newton_inverse_scratch_bytes(n, batch).
-size_t newton_inverse_scratch_bytes(int n, int batch);
-void newton_inverse(int n, const double* A, double* X, int batch, int steps, double tol,
-                    void* scratch, unsigned long long* err, int* fallback_count, void* tcw,
-                    int slices, unsigned* status, cudaStream_t s);
+// Mixed form: XA[u] = A[u]^-1 (na x na) and XB[u] = B[u]^-1 (nb x nb; nb = 0: none) from
+// one FP32 elimination launch and `steps` Newton-Schulz steps X <- X + X (I - A X) on the
+// tensor cores (sliced products of `slices` slices, workspace tcw); err[q][u] receives the
+// final max|I - A X| (bits of a non-negative double); matrices whose residual is not below
+// tol are inverted again by the FP64 elimination, counted in *fallback_count. `scratch`
+// holds newton_inverse_scratch_bytes(na, nb, batch).
+size_t newton_inverse_scratch_bytes(int na, int nb, int batch);
+void newton_inverse(int na, const double* A, double* XA, int nb, const double* B, double* XB,
+                    int batch, int steps, double tol, void* scratch, unsigned long long* err,
+                    int* fallback_count, void* tcw, int slices, unsigned* status, cudaStream_t s);
 void batched_eigen(int n, const double* A, double* H, double* Z, double* V, double* X,
                    double* lam_re, double* lam_im, double* scale, int batch, unsigned* status,
                    cudaStream_t s, const int* mask = nullptr);
