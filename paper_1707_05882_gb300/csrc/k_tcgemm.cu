@@ -525,7 +525,7 @@ bool tc_shape_ok(int K, int S) { return S >= 1 && S <= TC_MAXS && K >= 1 && K <=
 template <class Epi>
 void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const double* B, int ldb,
              long long sB, Epi epi, int batch, int S, void* work, unsigned* status,
-             cudaStream_t s, TcKSkip zskip = TcKSkip{}) {
+             cudaStream_t s, TcKSkip zskip = TcKSkip{}, int max_ctas = 0) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   TcLayout L = tc_layout(M, N, K, batch, S);
   unsigned char* w = (unsigned char*)work;
@@ -541,7 +541,9 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
 #undef VRTE_SLICE_AB
   int smem = tc_smem_bytes(S);
   cudaFuncSetAttribute(k_tc_gemm<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_tc_gemm<Epi><<<tc_grid((long long)L.MT * L.NT * batch), TC_THREADS, smem, s>>>(
+  int grid = tc_grid((long long)L.MT * L.NT * batch);
+  if (max_ctas > 0) grid = std::min(grid, max_ctas);
+  k_tc_gemm<Epi><<<grid, TC_THREADS, smem, s>>>(
       M, N, K, S, As, ea, Bs, fb, scratch, epi, status, batch, zskip);
 }
 
@@ -559,9 +561,9 @@ struct TcEpiStore {
 void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, const double* B,
                    int ldb, long long sB, double beta, double* C, int ldc, long long sC,
                    int batch, int S, void* work, unsigned* status, cudaStream_t s,
-                   TcKSkip zskip) {
+                   TcKSkip zskip, int max_ctas) {
   tc_gemm(M, N, K, A, lda, sA, B, ldb, sB, TcEpiStore{C, ldc, sC, beta}, batch, S, work, status,
-          s, zskip);
+          s, zskip, max_ctas);
 }
 
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,

@@ -25,7 +25,7 @@ using namespace vrte;
 namespace {
 enum Stage {
   ST_TABLES, ST_ASSEMBLE, ST_EIGEN, ST_MODES, ST_PARTICULAR, ST_BC_SOLVE, ST_RECON_OPS,
-  ST_RECON_HOM, ST_RECON_PART, ST_REFINE, ST_SYNTHESIS, ST_ADJOINT, kStages
+  ST_RECON_HOM, ST_RECON_PART, ST_REFINE, ST_SYNTHESIS, ST_ADJOINT, ST_SIDE_OPS, kStages
 };
 // mixed form: BF16 slices per FP64 operand (exact products, ~6e-16 relative per term) and
 // incident cosines per tensor-core synthesis block
@@ -40,12 +40,15 @@ constexpr double kRefineTol = 1e-7;
 // mixed form: Newton-Schulz steps after the FP32 starting inverse of K and X, and the final
 // max|I - A X| above which a matrix is inverted again in FP64
 constexpr int kNewtonSteps = 2;
+// idle SMs that the eigen-decomposition must leave for the side stream to be used
+constexpr int kSideMinSMs = 16;
 constexpr double kNewtonTol = 1e-11;
 
 const char* kStageNames[kStages] = {"tables",     "assemble",   "eigen",
                                     "modes_bc_inverse", "particular", "bc_solve",
                                     "recon_ops",  "recon_hom",  "recon_part",
-                                    "refine",     "synthesis", "adjoint"};
+                                    "refine",     "synthesis", "adjoint",
+                                    "side_ops"};
 }  // namespace
 
 // Buffers of one order batch of one layer. A plan holds up to kMaxSlots of them so that
@@ -76,6 +79,12 @@ struct Work {
   double *Ln = nullptr, *RU = nullptr, *Rbp = nullptr, *Rbm = nullptr;
   int* rcount = nullptr;  // [flagged in this batch, flagged in this solve, FP64 re-inverses]
   void* nscratch = nullptr;              // mixed form: Newton inverse scratch
+  // mixed form, one layer in flight: the eigen-independent operators and beams run on `side`
+  // (least priority) on the SMs the eigen-decomposition leaves idle, with their own GEMM
+  // workspace; fork and join events order them against the slot's stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t side_fork = nullptr, side_join = nullptr;
+  void* tcw_side = nullptr;
   unsigned long long* nerr = nullptr;    // mixed form: final residuals [K, X][U]
   int2* rlist = nullptr;
   double* Isyn = nullptr;   // [M_max][n_in][n_out][16]; the adjoint keeps Ibar here
@@ -271,6 +280,18 @@ const char* vrte_status_string(vrte_status st) {
   return "unknown status";
 }
 
+static int device_sm_count() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+      sms = 1;
+  }
+  return sms;
+}
+
 // Mirror pairs of the azimuth grid for the tensor-core synthesis: the cosine class of the
 // table is even in the azimuth difference and the sine class odd (Eqs. 7, 12), so the table at
 // -phi follows from the one at phi. Returns [rep (n_phi) | mirror (n_phi)] with the computed
@@ -405,10 +426,13 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   cudaDeviceSynchronize();
   free_workspace(p, kPlanAllocs);
   for (Work& x : p->ws) {
-    cudaStream_t st_ = x.stream;
-    cudaEvent_t ev_ = x.done, er_ = x.ready, ef_ = x.freed;
+    cudaStream_t st_ = x.stream, sd_ = x.side;
+    cudaEvent_t ev_ = x.done, er_ = x.ready, ef_ = x.freed, sf_ = x.side_fork, sj_ = x.side_join;
     x = Work();
     x.stream = st_;
+    x.side = sd_;
+    x.side_fork = sf_;
+    x.side_join = sj_;
     x.done = ev_;
     x.ready = er_;
     x.freed = ef_;
@@ -429,7 +453,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   p->kdir = mixed ? 4 * Lx : 0;
   size_t kd = p->kdir;
   const int S = kSlices;
-  size_t tc_unit = 0;
+  size_t tc_unit = 0, tc_side_unit = 0;
   if (mixed) {
     size_t c[9] = {tc_workspace_bytes((int)(2 * n), (int)(2 * n), (int)(2 * n), 1, S),
                    tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
@@ -441,12 +465,17 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
                    tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n), 1, S),
                    tc_workspace_bytes((int)Ro, (int)R, (int)(2 * n + kd), 1, S)};
     for (size_t v : c) tc_unit = std::max(tc_unit, v - tc_scratch_bytes());
+    size_t cs[3] = {tc_workspace_bytes((int)n, (int)R, (int)kd, 1, S),
+                    tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
+                    tc_workspace_bytes((int)Ro, (int)(2 * n), (int)kd, 1, S)};
+    for (size_t v : cs) tc_side_unit = std::max(tc_side_unit, v - tc_scratch_bytes());
   }
   size_t per_unit = 3 * (size_t)Lx * P + 10 * n * n + 3 * n + 8 * n * n + 5 * n * R +
                     (4 * n + kd) * R + 2 * n * R + 4 * Ro * n + Ro * (2 * n + kd) + Ro * R + n * n +
                     1 + 5 * 4 * n * n + 3 * 2 * n + 1 + (tc_unit + 7) / 8 +
                     (mixed ? refine_scratch_doubles(1, p->n_in, p->n_out) + p->n_in : 0) +
                     (mixed ? 7 * n * n + 3 : 0) +  // Newton inverse scratch and residuals
+                    (tc_side_unit + 7) / 8 +         // GEMM workspace of the side stream
                     n * kd + kd * 2 * n + 2 * kd * R;
   const bool adjoint = (p->desc.flags & VRTE_FLAG_ADJOINT) != 0;
   if (adjoint) per_unit += bw_carve(nullptr, 1, n, R, Ro, Lx, P, nullptr);
@@ -524,6 +553,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
         (st = alloc(p, &w->nscratch, newton_inverse_scratch_bytes(2 * (int)n, (int)n, (int)U))) !=
             VRTE_OK ||
         (st = allocd(p, &w->nerr, 2 * U)) != VRTE_OK ||
+        (nslots == 1 &&
+         (st = alloc(p, &w->tcw_side, tc_side_unit * U + tc_scratch_bytes())) != VRTE_OK) ||
         (st = allocd(p, &w->rlist, U * p->n_in)) != VRTE_OK) {
       free_workspace(p, kPlanAllocs);
       for (Work& x : p->ws) x.Isyn = nullptr;
@@ -548,6 +579,17 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
     VRTE_ALLOC(bw, bw_carve(nullptr, U, n, R, Ro, Lx, P, nullptr))
     VRTE_ALLOC(dpts, P) VRTE_ALLOC(dmin4, 4 * (size_t)p->n_in) VRTE_ALLOC(dmout4, 4 * (size_t)p->n_out)
     VRTE_ALLOC(drtop4, 4 * (size_t)Nx) VRTE_ALLOC(acc, 3 + 6 * (size_t)p->desc.n_coef_max)
+  }
+  if (mixed && nslots == 1) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if ((!w->side &&
+         cudaStreamCreateWithPriority(&w->side, cudaStreamNonBlocking, least) != cudaSuccess) ||
+        (!w->side_fork &&
+         cudaEventCreateWithFlags(&w->side_fork, cudaEventDisableTiming) != cudaSuccess) ||
+        (!w->side_join &&
+         cudaEventCreateWithFlags(&w->side_join, cudaEventDisableTiming) != cudaSuccess))
+      return VRTE_ERR_CUDA;
   }
   if (nslots > 1) {
     if (!w->stream && cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -620,6 +662,12 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
   const TcKSkip zdir{0, 4 * m0, 4};
   const TcKSkip zpart{2 * n, 4 * m0, 4};
   const double kdsum = 4.0 * lsum;
+  // One layer in flight (mixed form): the eigen-decomposition holds one SM per order, and
+  // the operators and beams that do not depend on it run meanwhile on the SMs it leaves
+  // idle, on the slot's side stream (least priority; GEMMs capped at the idle SM count).
+  const int idle_sms = device_sm_count() - U;
+  const bool overlap = mixed && reconstruct && boundary && w->side && p->nslots == 1 &&
+                       idle_sms >= kSideMinSMs;
   {
     StageScope sc(p, ST_TABLES, s, 1, 30.0 * P * lsum, 24.0 * P * lsum);
     launch_gsf_tables(ob, w->d_pts, w->gp, w->gr, w->gt, s);
@@ -629,6 +677,35 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                   8.0 * 3 * dn * dn * dU);
     launch_assemble_EF(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, w->E, w->F, s);
     dgemm_batched(n, n, n, 1.0, w->F, n, nn, w->E, n, nn, 0.0, w->FE, n, nn, U, s);
+  }
+  if (overlap) {
+    const cudaStream_t ss = w->side;
+    cudaEventRecord(w->side_fork, s);
+    cudaStreamWaitEvent(ss, w->side_fork, 0);
+    auto gemm_side = [&](int M_, int N_, int K_, const double* A_, int lda_, long long sA_,
+                         const double* B_, int ldb_, long long sB_, double* C_, int ldc_,
+                         long long sC_, TcKSkip z_) {
+      tc_gemm_store(M_, N_, K_, A_, lda_, sA_, B_, ldb_, sB_, 0.0, C_, ldc_, sC_, U, kSlices,
+                    w->tcw_side, p->d_status, ss, z_, idle_sms);
+    };
+    StageScope sc(p, ST_SIDE_OPS, ss, 3 + 3 * gl + 1 + 2 + gl,
+                  72.0 * N * p->n_in * lsum + 2.0 * dn * dn * dR * dU +
+                      72.0 * N * p->n_out * lsum + 72.0 * p->n_in * p->n_out * lsum,
+                  8.0 * (4 * dn * dR + 2 * dRo * dn + dRo * dR) * dU);
+    sc.tensor_flops(tcf * (dn * dU + 2.0 * kdsum) * dn * dR + tcf * 2.0 * dRo * dn * kdsum);
+    // beam vectors (Eq. 47) as contractions over (l, component), F'p - r / mu0 (Eq. 46)
+    launch_mixed_operators(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, w->d_min4,
+                           w->Ln, w->RU, w->Rbp, w->Rbm, ss);
+    const long long sL = (long long)n * kdir, sB = (long long)kdir * R;
+    gemm_side(n, R, kdir, w->Ln, kdir, sL, w->Rbp, R, sB, w->Pb, R, nR, zdir);
+    gemm_side(n, R, kdir, w->Ln, kdir, sL, w->Rbm, R, sB, w->Rb, R, nR, zdir);
+    gemm_side(n, R, n, w->F, n, nn, w->Pb, R, nR, w->Wv, R, nR, TcKSkip{});
+    launch_particular_rhs(ob, w->Wv, w->Rb, w->d_pts, w->Wv, ss);
+    // the direct operators and U+- = [M_out P(mu_o) B] x RU+- (reconstruction, Eq. 38)
+    launch_direct_operators(ob, w->gp, w->gr, w->gt, w->d_min4, w->d_mout4, w->Upm, w->SD, ss);
+    gemm_side(Ro, 2 * n, kdir, w->Upm + 2 * n, ldU, sU_part, w->RU, 2 * n,
+              (long long)kdir * 2 * n, w->Upm, ldU, sU_part, zdir);
+    cudaEventRecord(w->side_join, ss);
   }
   {
     // algorithmic work counted: the nominal 25 n^3 of a real Schur decomposition with
@@ -669,26 +746,33 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
       batched_inverse(n, w->X, w->Xinv, U, p->d_status, s);
   }
   {
-    StageScope sc(p, ST_PARTICULAR, s, (mixed ? 7 + 6 * gl : 9) - (boundary ? 0 : 1),
-                  72.0 * N * p->n_in * lsum + 8.0 * dn * dn * dR * dU,
+    StageScope sc(p, ST_PARTICULAR, s,
+                  (overlap ? 4 + 3 * gl : (mixed ? 7 + 6 * gl : 9)) - (boundary ? 0 : 1),
+                  (overlap ? 0.0 : 72.0 * N * p->n_in * lsum + 2.0 * dn * dn * dR * dU) +
+                      6.0 * dn * dn * dR * dU,
                   8.0 * 10 * dn * dR * dU);
-    sc.tensor_flops(tcf * (4.0 * dn * dU + 2.0 * kdsum) * dn * dR);
-    if (mixed) {
-      // beam vectors as contractions over (l, component) on the tensor cores
-      launch_mixed_operators(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes, w->d_min4,
-                             w->Ln, w->RU, w->Rbp, w->Rbm, s);
-      const long long sL = (long long)n * kdir, sB = (long long)kdir * R;
-      gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbp, R, sB, 0.0, w->Pb, R, nR, zdir);
-      gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbm, R, sB, 0.0, w->Rb, R, nR, zdir);
+    sc.tensor_flops(overlap ? tcf * 3.0 * dn * dU * dn * dR
+                            : tcf * (4.0 * dn * dU + 2.0 * kdsum) * dn * dR);
+    if (overlap) {
+      cudaStreamWaitEvent(s, w->side_join, 0);  // beams, F'p - r / mu0, U+- from the side
     } else {
-      launch_assemble_beam(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_min4, w->Pb, w->Rb,
-                           s);
+      if (mixed) {
+        // beam vectors as contractions over (l, component) on the tensor cores
+        launch_mixed_operators(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_w_nodes,
+                               w->d_min4, w->Ln, w->RU, w->Rbp, w->Rbm, s);
+        const long long sL = (long long)n * kdir, sB = (long long)kdir * R;
+        gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbp, R, sB, 0.0, w->Pb, R, nR, zdir);
+        gemm(n, R, kdir, w->Ln, kdir, sL, w->Rbm, R, sB, 0.0, w->Rb, R, nR, zdir);
+      } else {
+        launch_assemble_beam(ob, w->gp, w->gr, w->gt, w->d_mu_nodes, w->d_min4, w->Pb, w->Rb,
+                             s);
+      }
+      gemm(n, R, n, w->F, n, nn, w->Pb, R, nR, 0.0, w->Wv, R, nR);
+      launch_particular_rhs(ob, w->Wv, w->Rb, w->d_pts, w->Wv, s);
     }
     // near a resonance mu0 ~ 1/kappa_j the eigenbasis solve amplifies rounding by
     // 1/(kappa_j^2 - mu0^-2) and the homogeneous part cancels it: the mixed form
     // keeps FP64-level products here (7 slices, ~2e-15 per term)
-    gemm(n, R, n, w->F, n, nn, w->Pb, R, nR, 0.0, w->Wv, R, nR);
-    launch_particular_rhs(ob, w->Wv, w->Rb, w->d_pts, w->Wv, s);
     gemm(n, R, n, w->Xinv, n, nn, w->Wv, R, nR, 0.0, w->Yv, R, nR);
     launch_eigen_scale(ob, w->lam_re, w->lam_im, w->d_pts, w->Yv, s);
     gemm(n, R, n, w->X, n, nn, w->Yv, R, nR, 0.0, w->SD, R, ob.sSD);
@@ -708,12 +792,15 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
     gemm(2 * n, R, 2 * n, w->Kinv, 2 * n, 4 * nn, w->RHS, R, 2 * nR, 0.0, w->C, R, 2 * nR);
   }
   {
-    StageScope sc(p, ST_RECON_OPS, s, mixed ? 3 + 3 * gl : 5,
-                  72.0 * N * p->n_out * lsum + 4.0 * dRo * dn * dn * dU +
-                      72.0 * p->n_in * p->n_out * lsum,
+    StageScope sc(p, ST_RECON_OPS, s, overlap ? 1 + 2 * gl : (mixed ? 3 + 3 * gl : 5),
+                  (overlap ? 0.0 : 72.0 * N * p->n_out * lsum + 72.0 * p->n_in * p->n_out * lsum) +
+                      4.0 * dRo * dn * dn * dU,
                   8.0 * (6 * dRo * dn + dRo * dR) * dU);
-    sc.tensor_flops(tcf * 2.0 * dRo * dn * (dn * dU + kdsum));
-    if (mixed) {
+    sc.tensor_flops(tcf * 2.0 * dRo * dn * (dn * dU + (overlap ? 0.0 : kdsum)));
+    if (overlap) {
+      // the direct operators and U+- came from the side stream (joined before the
+      // particular stage)
+    } else if (mixed) {
       // U+- = [M_out P(mu_o) B] x RU+-: the direct operator's columns are the left factor
       launch_direct_operators(ob, w->gp, w->gr, w->gt, w->d_min4, w->d_mout4, w->Upm, w->SD,
                               s);
@@ -1661,6 +1748,9 @@ void vrte_destroy(vrte_plan* p) {
     if (x.done) cudaEventDestroy(x.done);
     if (x.ready) cudaEventDestroy(x.ready);
     if (x.freed) cudaEventDestroy(x.freed);
+    if (x.side) cudaStreamDestroy(x.side);
+    if (x.side_fork) cudaEventDestroy(x.side_fork);
+    if (x.side_join) cudaEventDestroy(x.side_join);
   }
   if (p->fork) cudaEventDestroy(p->fork);
   for (int c = 0; c < 4; ++c) {

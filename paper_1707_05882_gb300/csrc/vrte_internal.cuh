@@ -246,7 +246,7 @@ struct TcKSkip {
 void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, const double* B,
                    int ldb, long long sB, double beta, double* C, int ldc, long long sC,
                    int batch, int S, void* work, unsigned* status, cudaStream_t s,
-                   TcKSkip zskip = TcKSkip{});
+                   TcKSkip zskip = TcKSkip{}, int max_ctas = 0);
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                   const double* B, long long sB, const double* T1, const double* g0tab,
                   double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip = TcKSkip{});
