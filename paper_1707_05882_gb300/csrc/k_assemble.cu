@@ -357,9 +357,20 @@ __global__ void k_depth_table(int N, int n_in, int n_out, double tau, const doub
   g0tab[(size_t)o * n_in + k] = depth_factor(tau, pts[N + n_in + o], pts[N + k]);
 }
 
+// The layer's beam table after the depth factors: e^{-tau0/mu0} and 1/mu0 per incident cosine.
+__global__ void k_beam_table(int N, int n_in, double tau, const double* pts, double* btab) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n_in) return;
+  const double rm = 1.0 / pts[N + k];
+  btab[k] = exp(-tau * rm);
+  btab[n_in + k] = rm;
+}
+
 void launch_depth_table(int N, int n_in, int n_out, double tau, const double* pts, double* g0tab,
                         cudaStream_t s) {
   k_depth_table<<<dim3((n_in + 127) / 128, n_out), 128, 0, s>>>(N, n_in, n_out, tau, pts, g0tab);
+  k_beam_table<<<(n_in + 127) / 128, 128, 0, s>>>(N, n_in, tau, pts,
+                                                  g0tab + (size_t)n_in * n_out);
 }
 
 // ------------------------------------------------------------------ mixed-form operators

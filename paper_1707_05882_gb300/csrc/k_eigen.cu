@@ -26,7 +26,7 @@
 
 namespace vrte {
 
-constexpr int EIG_THREADS = 256;
+constexpr int EIG_THREADS = 512;
 constexpr double EPS = 2.220446049250313e-16;
 constexpr double SAFMIN = 2.2250738585072014e-308;
 

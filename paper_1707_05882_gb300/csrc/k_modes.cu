@@ -111,52 +111,59 @@ void launch_build_K(const OrderBatch& b, const double* X, const double* Y, const
 // Reduced particular problem (Sec. 3.B, Eqs. 46-48) for beam column c = 4k + s with
 // internal cosine mu0 = pts[N + k]:  (F'E' - 1/mu0^2) s = F' p - r / mu0,
 // d = mu0 (p - E' s), Z+ = (s + d)/2, Z- = D (s - d)/2.
-__global__ void k_particular_rhs(int n, int R, int N, const double* r, const double* pts,
+// (btab: the layer's beam table, 1/mu0 per incident cosine at btab[n_in + k])
+__global__ void k_particular_rhs(int n, int R, int n_in, const double* r, const double* btab,
                                  double* w) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y, u = blockIdx.z;
   if (c >= R) return;
   size_t idx = (size_t)u * n * R + (size_t)i * R + c;
-  w[idx] -= r[idx] / pts[N + (c >> 2)];
+  w[idx] = fma(-r[idx], btab[n_in + (c >> 2)], w[idx]);
 }
 
 void launch_particular_rhs(const OrderBatch& b, const double* w_in, const double* r,
-                           const double* pts, double* w_out, cudaStream_t s) {
+                           const double* btab, double* w_out, cudaStream_t s) {
   (void)w_in;
   int R = 4 * b.n_in;
   dim3 grid((R + 127) / 128, b.n, b.n_units);
-  k_particular_rhs<<<grid, 128, 0, s>>>(b.n, R, b.N, r, pts, w_out);
+  k_particular_rhs<<<grid, 128, 0, s>>>(b.n, R, b.n_in, r, btab, w_out);
 }
 
 // y <- (Lambda - 1/mu0^2)^-1 y in the eigenbasis; a pair uses the real 2x2 block
-// [[a, b], [-b, a]] of lambda = a + ib.
-__global__ void k_eigen_scale(int n, int R, int N, const double* lam_re, const double* lam_im,
-                              const double* pts, double* y) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+// [[a, b], [-b, a]] of lambda = a + ib. One thread per (u, j, incident k): the factor is
+// formed once (one FP64 division) for the four Stokes columns of k (btab: 1/mu0 at
+// btab[n_in + k]).
+__global__ void k_eigen_scale(int n, int R, int n_in, const double* lam_re, const double* lam_im,
+                              const double* btab, double* y) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y, u = blockIdx.z;
-  if (c >= R) return;
+  if (k >= n_in) return;
   const double* lr = lam_re + (size_t)u * n;
   const double* li = lam_im + (size_t)u * n;
   if (li[j] < 0.0) return;
-  double mu0 = pts[N + (c >> 2)];
-  double cc = 1.0 / (mu0 * mu0);
-  size_t idx = (size_t)u * n * R + (size_t)j * R + c;
+  const double rm = btab[n_in + k];
+  const double cc = rm * rm;
+  double* yr = y + (size_t)u * n * R + (size_t)j * R + 4 * k;
   if (li[j] == 0.0) {
-    y[idx] /= (lr[j] - cc);
+    const double f = 1.0 / (lr[j] - cc);
+    for (int s = 0; s < 4; ++s) yr[s] *= f;
   } else {
-    double a = lr[j] - cc, bb = li[j];
-    double den = a * a + bb * bb;
-    double y0 = y[idx], y1 = y[idx + R];
-    y[idx] = (a * y0 - bb * y1) / den;
-    y[idx + R] = (bb * y0 + a * y1) / den;
+    const double a = lr[j] - cc, bb = li[j];
+    const double inv = 1.0 / fma(a, a, bb * bb);
+    const double fa = a * inv, fb = bb * inv;
+    for (int s = 0; s < 4; ++s) {
+      const double y0 = yr[s], y1 = yr[R + s];
+      yr[s] = fma(fa, y0, -fb * y1);
+      yr[R + s] = fma(fb, y0, fa * y1);
+    }
   }
 }
 
 void launch_eigen_scale(const OrderBatch& b, const double* lam_re, const double* lam_im,
-                        const double* pts, double* y, cudaStream_t s) {
+                        const double* btab, double* y, cudaStream_t s) {
   int R = 4 * b.n_in;
-  dim3 grid((R + 127) / 128, b.n, b.n_units);
-  k_eigen_scale<<<grid, 128, 0, s>>>(b.n, R, b.N, lam_re, lam_im, pts, y);
+  dim3 grid((b.n_in + 127) / 128, b.n, b.n_units);
+  k_eigen_scale<<<grid, 128, 0, s>>>(b.n, R, b.n_in, lam_re, lam_im, btab, y);
 }
 
 // d = mu0 (p - E's), written into the second half of SD = [s; d].
@@ -180,8 +187,8 @@ void launch_particular_sd(const OrderBatch& b, const double* pbeam, const double
 // Right-hand side of the boundary system (Eq. 54 with the dielectric top):
 //   top:    -(Z-(mu_i) - R_F Z+(mu_i))
 //   bottom: -Z+(mu_i) exp(-tau0 / mu0)
-__global__ void k_bc_rhs(int N, int n, int R, long long sSD, double tau, const double* SD,
-                         const double* rtop4, const double* pts, double* rhs) {
+__global__ void k_bc_rhs(int N, int n, int R, long long sSD, const double* SD,
+                         const double* rtop4, const double* btab, double* rhs) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int i = blockIdx.y, u = blockIdx.z;
   if (c >= R) return;
@@ -197,7 +204,7 @@ __global__ void k_bc_rhs(int N, int n, int R, long long sSD, double tau, const d
   const double* Rm = rtop4 + 4 * i;
   double rz[4] = {Rm[0] * zp[0] + Rm[1] * zp[1], Rm[1] * zp[0] + Rm[0] * zp[1],
                   Rm[2] * zp[2] + Rm[3] * zp[3], -Rm[3] * zp[2] + Rm[2] * zp[3]};
-  double att = exp(-tau / pts[N + (c >> 2)]);
+  const double att = btab[c >> 2];  // e^{-tau0/mu0}
   double* rb = rhs + (size_t)u * 2 * n * R;
   for (int a = 0; a < 4; ++a) {
     rb[(size_t)(4 * i + a) * R + c] = -(zm[a] - rz[a]);
@@ -206,11 +213,11 @@ __global__ void k_bc_rhs(int N, int n, int R, long long sSD, double tau, const d
 }
 
 void launch_bc_rhs(const OrderBatch& b, const double* SD, const double* d, const double* rtop4,
-                   const double* pts, double* rhs, cudaStream_t s) {
+                   const double* btab, double* rhs, cudaStream_t s) {
   (void)d;
   int R = 4 * b.n_in;
   dim3 grid((R + 127) / 128, b.N, b.n_units);
-  k_bc_rhs<<<grid, 128, 0, s>>>(b.N, b.n, R, b.sSD, b.tau, SD, rtop4, pts, rhs);
+  k_bc_rhs<<<grid, 128, 0, s>>>(b.N, b.n, R, b.sSD, SD, rtop4, btab, rhs);
 }
 
 // ------------------------------------------------------------------ reconstruction operator

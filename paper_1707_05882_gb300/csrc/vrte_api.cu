@@ -534,7 +534,7 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   VRTE_ALLOC(Pb, U * n * R) VRTE_ALLOC(Rb, U * n * R) VRTE_ALLOC(Wv, U * n * R) VRTE_ALLOC(Yv, U * n * R) VRTE_ALLOC(Es, U * n * R)
   VRTE_ALLOC(SD, U * (2 * n + kd) * R) VRTE_ALLOC(RHS, U * 2 * n * R) VRTE_ALLOC(C, U * 2 * n * R)
   VRTE_ALLOC(Upm, U * Ro * (2 * n + kd)) VRTE_ALLOC(P1, U * Ro * n) VRTE_ALLOC(P2, U * Ro * n) VRTE_ALLOC(Hhat, U * Ro * 2 * n)
-  VRTE_ALLOC(T1, U * Ro * R) VRTE_ALLOC(g0tab, (size_t)p->n_in * p->n_out)
+  VRTE_ALLOC(T1, U * Ro * R) VRTE_ALLOC(g0tab, (size_t)p->n_in * p->n_out + 2 * (size_t)p->n_in)
   VRTE_ALLOC(FY, U * n * n) VRTE_ALLOC(mode_res, U) VRTE_ALLOC(mode_flag, U)
   VRTE_ALLOC(Bm, U * 4 * n * n) VRTE_ALLOC(Hb, U * 4 * n * n) VRTE_ALLOC(Zb, U * 4 * n * n)
   VRTE_ALLOC(Vb, U * 4 * n * n) VRTE_ALLOC(Xb, U * 4 * n * n)
@@ -631,6 +631,8 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                 ldU, (long long)ldU * R};
   BaseR Rg;
   const bool has_base = layer_base(ly, &Rg);
+  // the layer's beam table (e^{-tau0/mu0}, 1/mu0), written with its depth factors
+  const double* btab = w->g0tab + (size_t)p->n_in * p->n_out;
   p->last_n = n;
   p->last_U = U;
   p->last_ldU = ldU;
@@ -700,7 +702,7 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
     gemm_side(n, R, kdir, w->Ln, kdir, sL, w->Rbp, R, sB, w->Pb, R, nR, zdir);
     gemm_side(n, R, kdir, w->Ln, kdir, sL, w->Rbm, R, sB, w->Rb, R, nR, zdir);
     gemm_side(n, R, n, w->F, n, nn, w->Pb, R, nR, w->Wv, R, nR, TcKSkip{});
-    launch_particular_rhs(ob, w->Wv, w->Rb, w->d_pts, w->Wv, ss);
+    launch_particular_rhs(ob, w->Wv, w->Rb, btab, w->Wv, ss);
     // the direct operators and U+- = [M_out P(mu_o) B] x RU+- (reconstruction, Eq. 38)
     launch_direct_operators(ob, w->gp, w->gr, w->gt, w->d_min4, w->d_mout4, w->Upm, w->SD, ss);
     gemm_side(Ro, 2 * n, kdir, w->Upm + 2 * n, ldU, sU_part, w->RU, 2 * n,
@@ -768,18 +770,18 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                              s);
       }
       gemm(n, R, n, w->F, n, nn, w->Pb, R, nR, 0.0, w->Wv, R, nR);
-      launch_particular_rhs(ob, w->Wv, w->Rb, w->d_pts, w->Wv, s);
+      launch_particular_rhs(ob, w->Wv, w->Rb, btab, w->Wv, s);
     }
     // near a resonance mu0 ~ 1/kappa_j the eigenbasis solve amplifies rounding by
     // 1/(kappa_j^2 - mu0^-2) and the homogeneous part cancels it: the mixed form
     // keeps FP64-level products here (7 slices, ~2e-15 per term)
     gemm(n, R, n, w->Xinv, n, nn, w->Wv, R, nR, 0.0, w->Yv, R, nR);
-    launch_eigen_scale(ob, w->lam_re, w->lam_im, w->d_pts, w->Yv, s);
+    launch_eigen_scale(ob, w->lam_re, w->lam_im, btab, w->Yv, s);
     gemm(n, R, n, w->X, n, nn, w->Yv, R, nR, 0.0, w->SD, R, ob.sSD);
     gemm(n, R, n, w->E, n, nn, w->SD, R, ob.sSD, 0.0, w->Es, R, nR);
     launch_particular_sd(ob, w->Pb, w->Es, w->d_pts, w->SD, s);
     if (boundary) {
-      launch_bc_rhs(ob, w->SD, nullptr, w->d_rtop4, w->d_pts, w->RHS, s);
+      launch_bc_rhs(ob, w->SD, nullptr, w->d_rtop4, btab, w->RHS, s);
       if (has_base && m0 == 0)
         launch_base_rhs(N, n, R, ob.sSD, ly.tau, Rg, w->SD, w->d_pts, w->d_min4,
                         w->d_mu_nodes, w->d_w_nodes, w->RHS, w->basebuf + 8 * n, 1, s);

@@ -178,7 +178,8 @@ void launch_assemble_direct(const OrderBatch& b, const double* p, const double* 
 // Direct (once-scattered) term as a contraction over (l, component): writes
 // Adir = M_out P_l(mu_o) B_l into columns 2n.. of the [U+ | U- | Adir] rows and
 // Bdir = (omega/2pi) (-1)^(l-m) D P_l(mu0) D b_k into rows 2n.. of [s; d; Bdir].
-// Depth factors g0tab[o][k] = depth_factor(tau, mu_o, mu0_k) of one layer.
+// Depth factors g0tab[o][k] = depth_factor(tau, mu_o, mu0_k) of one layer, followed by its
+// beam table (beam_table(g0tab)): e^{-tau0/mu0_k} then 1/mu0_k, n_in each.
 void launch_depth_table(int N, int n_in, int n_out, double tau, const double* pts, double* g0tab,
                         cudaStream_t s);
 // Mixed form: factors of the parity-split sums over (l, component) for U+-, beam p, r.
@@ -285,14 +286,15 @@ void launch_pack_Y(const OrderBatch& b, const double* EX, const double* lam_re,
                    const double* lam_im, double* Y, cudaStream_t s);
 void launch_build_K(const OrderBatch& b, const double* X, const double* Y, const double* lam_re,
                     const double* lam_im, const double* rtop4, double* K, cudaStream_t s);
+// (btab: the layer's beam table, see launch_depth_table)
 void launch_particular_rhs(const OrderBatch& b, const double* w_in, const double* r,
-                           const double* pts, double* w_out, cudaStream_t s);
+                           const double* btab, double* w_out, cudaStream_t s);
 void launch_eigen_scale(const OrderBatch& b, const double* lam_re, const double* lam_im,
-                        const double* pts, double* y, cudaStream_t s);
+                        const double* btab, double* y, cudaStream_t s);
 void launch_particular_sd(const OrderBatch& b, const double* pbeam, const double* Es,
                           const double* pts, double* d, cudaStream_t s);
 void launch_bc_rhs(const OrderBatch& b, const double* sv, const double* d, const double* rtop4,
-                   const double* pts, double* rhs, cudaStream_t s);
+                   const double* btab, double* rhs, cudaStream_t s);
 void launch_build_Hhat(const OrderBatch& b, const double* P1, const double* P2,
                        const double* lam_re, const double* lam_im, const double* pts,
                        double* Hhat, cudaStream_t s);
