@@ -14,7 +14,9 @@
 
 namespace vrte {
 
-// out[u][r] = max_c |A[u][r][c]|, c < cols: one warp per row.
+// out[u][r / 4] = max over the four rows r of a group and c < cols of |A[u][r][c]| (zeroed
+// before): one warp per row, the group's maximum by an integer max of the bit patterns
+// (non-negative doubles order like them).
 __global__ void k_row_absmax(int rows, int cols, const double* __restrict__ A, int lda,
                              long long sA, double* __restrict__ out) {
   int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -24,10 +26,13 @@ __global__ void k_row_absmax(int rows, int cols, const double* __restrict__ A, i
   double m = 0.0;
   for (int c = lane; c < cols; c += 32) m = fmax(m, fabs(a[c]));
   for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-  if (lane == 0) out[(size_t)u * rows + warp] = m;
+  if (lane == 0 && m > 0.0)
+    atomicMax((unsigned long long*)out + (size_t)u * (rows / 4) + warp / 4,
+              (unsigned long long)__double_as_longlong(m));
 }
 
-// out[u][c] = max_r |B[u][r][c]|, r < rows: one thread per column (coalesced rows).
+// out[u][c / 4] = max over the four columns c of a group and r < rows of |B[u][r][c]| (zeroed
+// before): one thread per column (coalesced rows).
 __global__ void k_col_absmax(int rows, int cols, const double* __restrict__ B, int ldb,
                              long long sB, double* __restrict__ out) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -36,46 +41,46 @@ __global__ void k_col_absmax(int rows, int cols, const double* __restrict__ B, i
   const double* b = B + (size_t)u * sB + c;
   double m = 0.0;
   for (int r = 0; r < rows; ++r) m = fmax(m, fabs(b[(size_t)r * ldb]));
-  out[(size_t)u * cols + c] = m;
+  if (m > 0.0)
+    atomicMax((unsigned long long*)out + (size_t)u * (cols / 4) + c / 4,
+              (unsigned long long)__double_as_longlong(m));
 }
 
-// One thread per (incident k, order unit u): flags the column block when, for some
-// outgoing o, the error bound of the sliced contractions exceeds tol |I^0_00(o, k)|
-// (order 0 sets the scale of the synthesized radiance at that pair).
+// The error bound of the sliced contractions against tol |I^0_00(o, k)| (order 0 sets the
+// scale of the synthesized radiance at that pair), from the row maxima per outgoing o
+// (rmH, rmU: [U][n_out]) and column maxima per incident k (cmC, cmSD: [U][n_in]), each over
+// the four Stokes rows or columns: one thread per (outgoing o, incident k),
+// which reads the order-0 reference once and tests every order u of the batch, marking the
+// column blocks (u, k) that fail in `flags` (already set for a non-finite result by the
+// reconstruction's epilogue).
 __global__ void k_flag_columns(OrderBatch b, const double* __restrict__ rmH,
                                const double* __restrict__ rmU, const double* __restrict__ cmC,
                                const double* __restrict__ cmSD, const double* __restrict__ g0tab,
                                const double* __restrict__ Isyn, double epsK1, double epsK2,
-                               double tol, int* count, int* total, int2* list, int cap) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  int u = blockIdx.y;
-  if (k >= b.n_in) return;
-  const int Ro = 4 * b.n_out, R = 4 * b.n_in;
-  double cC = 0.0, cS = 0.0;
-  for (int s = 0; s < 4; ++s) {
-    cC = fmax(cC, cmC[(size_t)u * R + 4 * k + s]);
-    cS = fmax(cS, cmSD[(size_t)u * R + 4 * k + s]);
+                               double tol, int* flags) {
+  const int o = blockIdx.x * blockDim.x + threadIdx.x;
+  const int k = blockIdx.y;
+  if (o >= b.n_out) return;
+  const double ref = Isyn[((size_t)k * b.n_out + o) * 16];
+  const double lim = isfinite(ref) ? tol * fabs(ref) : -1.0;
+  const double g0 = g0tab[(size_t)o * b.n_in + k];
+  for (int u = 0; u < b.n_units; ++u) {
+    const double rH = rmH[(size_t)u * b.n_out + o], rU = rmU[(size_t)u * b.n_out + o];
+    const double cC = cmC[(size_t)u * b.n_in + k], cS = cmSD[(size_t)u * b.n_in + k];
+    const double bound = epsK1 * rH * cC + epsK2 * g0 * rU * cS;
+    if (!(bound <= lim) && !flags[(size_t)u * b.n_in + k]) flags[(size_t)u * b.n_in + k] = 1;
   }
-  bool flag = false;
-  for (int o = 0; o < b.n_out && !flag; ++o) {
-    double rH = 0.0, rU = 0.0;
-    for (int a = 0; a < 4; ++a) {
-      rH = fmax(rH, rmH[(size_t)u * Ro + 4 * o + a]);
-      rU = fmax(rU, rmU[(size_t)u * Ro + 4 * o + a]);
-    }
-    double g0 = g0tab[(size_t)o * b.n_in + k];
-    double bound = epsK1 * rH * cC + epsK2 * g0 * rU * cS;
-    // the scale of the synthesized radiance is that of order 0 at the same pair
-    double ref = Isyn[((size_t)k * b.n_out + o) * 16];
-    double own = Isyn[(((size_t)(b.m0 + u) * b.n_in + k) * b.n_out + o) * 16];
-    if (!isfinite(own) || !isfinite(ref)) flag = true;
-    else if (bound > tol * fabs(ref)) flag = true;
-  }
-  if (flag) {
-    int slot = atomicAdd(count, 1);
-    atomicAdd(total, 1);
-    if (slot < cap) list[slot] = make_int2(u, k);
-  }
+}
+
+// The flagged column blocks into the work list of k_fix_columns.
+__global__ void k_collect_columns(int n_in, int U, const int* __restrict__ flags, int* count,
+                                  int* total, int2* list, int cap) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int u = blockIdx.y;
+  if (k >= n_in || u >= U || !flags[(size_t)u * n_in + k]) return;
+  const int slot = atomicAdd(count, 1);
+  atomicAdd(total, 1);
+  if (slot < cap) list[slot] = make_int2(u, k);
 }
 
 // Persistent grid over (flagged (u, k), block of FIX_ROWS output rows), so that the FP64
@@ -148,21 +153,24 @@ __global__ void __launch_bounds__(256) k_fix_columns(
 void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
                     const double* C, const double* Hhat, const double* Uext, const double* SD,
                     const double* g0tab, double eps, double tol, double* scratch, int* counters,
-                    int2* list, int cap, double* Isyn, cudaStream_t s) {
+                    int2* list, int cap, double* Isyn, int* nonfinite, cudaStream_t s) {
   const int U = b.n_units, n2 = 2 * b.n, R = 4 * b.n_in, Ro = 4 * b.n_out;
+  // maxima per (unit, outgoing) and per (unit, incident), each over its four Stokes entries
   double* rmH = scratch;
-  double* rmU = rmH + (size_t)U * Ro;
-  double* cmC = rmU + (size_t)U * Ro;
-  double* cmSD = cmC + (size_t)U * R;
+  double* rmU = rmH + (size_t)U * b.n_out;
+  double* cmC = rmU + (size_t)U * b.n_out;
+  double* cmSD = cmC + (size_t)U * b.n_in;
+  cudaMemsetAsync(scratch, 0, (size_t)U * 2 * (b.n_out + b.n_in) * sizeof(double), s);
   k_row_absmax<<<dim3((Ro + 7) / 8, U), 256, 0, s>>>(Ro, n2, Hhat, n2, (long long)Ro * n2, rmH);
   k_row_absmax<<<dim3((Ro + 7) / 8, U), 256, 0, s>>>(Ro, Kpart, Uext, b.ldU,
                                                       (long long)Ro * b.ldU, rmU);
   k_col_absmax<<<dim3((R + 127) / 128, U), 128, 0, s>>>(n2, R, C, R, (long long)n2 * R, cmC);
   k_col_absmax<<<dim3((R + 127) / 128, U), 128, 0, s>>>(Kpart, R, SD, R, b.sSD, cmSD);
   cudaMemsetAsync(counters, 0, sizeof(int), s);
-  k_flag_columns<<<dim3((b.n_in + 127) / 128, U), 128, 0, s>>>(
-      b, rmH, rmU, cmC, cmSD, g0tab, Isyn, eps * n2, eps * Kpart, tol, counters, counters + 1,
-      list, cap);
+  k_flag_columns<<<dim3((b.n_out + 127) / 128, b.n_in), 128, 0, s>>>(
+      b, rmH, rmU, cmC, cmSD, g0tab, Isyn, eps * n2, eps * Kpart, tol, nonfinite);
+  k_collect_columns<<<dim3((b.n_in + 127) / 128, U), 128, 0, s>>>(b.n_in, U, nonfinite, counters,
+                                                                  counters + 1, list, cap);
   size_t smem = (size_t)n2 * 4 * sizeof(double);
   k_fix_columns<<<2 * 152, 256, smem, s>>>(b, Kinv, RHS, Hhat, Uext, SD, g0tab, Kpart, counters,
                                            list, cap, Isyn);

@@ -568,8 +568,9 @@ void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, 
 
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                   const double* B, long long sB, const double* T1, const double* g0tab,
-                  double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip) {
-  EpiPart e{T1, Isyn, g0tab, b.N, b.n_in, b.n_out, b.m0};
+                  double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip,
+                  int* nonfinite) {
+  EpiPart e{T1, Isyn, g0tab, b.N, b.n_in, b.n_out, b.m0, nonfinite};
   tc_gemm(4 * b.n_out, 4 * b.n_in, K, A, lda, sA, B, 4 * b.n_in, sB, e, b.n_units, S, work,
           b.status, s, zskip);
 }

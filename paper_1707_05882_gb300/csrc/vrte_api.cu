@@ -78,6 +78,7 @@ struct Work {
   // mixed form: factors of the (l, component) contractions for U+- and the beam vectors
   double *Ln = nullptr, *RU = nullptr, *Rbp = nullptr, *Rbm = nullptr;
   int* rcount = nullptr;  // [flagged in this batch, flagged in this solve, FP64 re-inverses]
+  int* nfflag = nullptr;  // mixed form: column blocks (unit, incident) to refine, [U][n_in]
   void* nscratch = nullptr;              // mixed form: Newton inverse scratch
   // mixed form, one layer in flight: the eigen-independent operators and beams run on `side`
   // (least priority) on the SMs the eigen-decomposition leaves idle, with their own GEMM
@@ -555,7 +556,8 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
         (st = allocd(p, &w->nerr, 2 * U)) != VRTE_OK ||
         (nslots == 1 &&
          (st = alloc(p, &w->tcw_side, tc_side_unit * U + tc_scratch_bytes())) != VRTE_OK) ||
-        (st = allocd(p, &w->rlist, U * p->n_in)) != VRTE_OK) {
+        (st = allocd(p, &w->rlist, U * p->n_in)) != VRTE_OK ||
+        (st = allocd(p, &w->nfflag, U * p->n_in)) != VRTE_OK) {
       free_workspace(p, kPlanAllocs);
       for (Work& x : p->ws) x.Isyn = nullptr;
       return st;
@@ -839,15 +841,16 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                   2.0 * dRo * dR * kpsum, 8.0 * (dRo * kp + kp * dR + 2 * dRo * dR) * dU);
     sc.tensor_flops(tcf * dRo * dR * kpsum);
     if (mixed) {
+      cudaMemsetAsync(w->nfflag, 0, (size_t)U * p->n_in * sizeof(int), s);
       if (2 * n + kdir <= 1024) {
         tc_gemm_part(ob, 2 * n + kdir, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1,
-                     w->g0tab, w->Isyn, kSlices, w->tcw, s, zpart);
+                     w->g0tab, w->Isyn, kSlices, w->tcw, s, zpart, w->nfflag);
       } else {
         // too deep for one exact accumulation: [U+ U-][s; d] into T1, then the direct part
         tc_gemm_part_accum(ob, 2 * n, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1, w->g0tab,
                            kSlices, w->tcw, s);
         tc_gemm_part(ob, kdir, w->Upm + 2 * n, ldU, sU_part, w->SD + (size_t)2 * n * R,
-                     ob.sSD, w->T1, w->g0tab, w->Isyn, kSlices, w->tcw, s, zdir);
+                     ob.sSD, w->T1, w->g0tab, w->Isyn, kSlices, w->tcw, s, zdir, w->nfflag);
       }
     } else {
       dgemm_part_epilogue(ob, w->Upm, w->SD, w->T1, w->g0tab, w->Isyn, s);
@@ -857,7 +860,7 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
     StageScope sc(p, ST_REFINE, s, 6, 0.0, 0.0);
     refine_columns(ob, 2 * n + kdir, w->Kinv, w->RHS, w->C, w->Hhat, w->Upm, w->SD,
                    w->g0tab, kSliceEps, kRefineTol, w->rscratch, w->rcount, w->rlist,
-                   U * p->n_in, w->Isyn, s);
+                   U * p->n_in, w->Isyn, w->nfflag, s);
   }
   // reflecting base: its radiance at the bottom (the same in every upward direction),
   // attenuated to the top (order 0)

@@ -49,6 +49,7 @@ struct EpiPart {
   double* Isyn;
   const double* g0tab;
   int N, n_in, n_out, m0;
+  int* nonfinite = nullptr;  // optional [unit][n_in]: set for a column block with a NaN or Inf
   __device__ void operator()(int u, int i, int j, double acc) const {
     int R = 4 * n_in;
     int o = i >> 2, a = i & 3, k = j >> 2, s = j & 3;
@@ -56,6 +57,7 @@ struct EpiPart {
     double v = fma(g0, acc, T1[(size_t)u * (4 * n_out) * R + (size_t)i * R + j]);
     size_t dst = (((size_t)(m0 + u) * n_in + k) * n_out + o) * 16 + 4 * a + s;
     Isyn[dst] = v;
+    if (nonfinite && !isfinite(v)) atomicOr(nonfinite + (size_t)u * n_in + k, 1);
   }
 };
 
@@ -250,13 +252,14 @@ void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, 
                    TcKSkip zskip = TcKSkip{}, int max_ctas = 0);
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                   const double* B, long long sB, const double* T1, const double* g0tab,
-                  double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip = TcKSkip{});
+                  double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip = TcKSkip{},
+                  int* nonfinite = nullptr);
 // Mixed form: flags (order, incident) column blocks whose sliced reconstruction error
 // bound eps K max|row| max|column| exceeds tol |I_00| and recomputes them in FP64.
 void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
                     const double* C, const double* Hhat, const double* Uext, const double* SD,
                     const double* g0tab, double eps, double tol, double* scratch, int* counters,
-                    int2* list, int cap, double* Isyn, cudaStream_t s);
+                    int2* list, int cap, double* Isyn, int* nonfinite, cudaStream_t s);
 size_t refine_scratch_doubles(int U, int n_in, int n_out);
 // T1 += g0 (A @ B): the first part of a reconstruction contraction split in K.
 void tc_gemm_part_accum(const OrderBatch& b, int K, const double* A, int lda, long long sA,
