@@ -257,6 +257,16 @@ vrte_status vrte_solve_brdf_host(vrte_plan* plan, const double* h_coeffs, void* 
 vrte_status vrte_brdf_backward(vrte_plan* plan, const void* d_grad_brdf, int grad_dtype,
                                double* d_grad_params, void* stream);
 
+/* The azimuth pairing the tensor-core synthesis uses (Eqs. 7, 12: the cosine class of the table
+ * is even and the sine class odd in the azimuth difference, so the table at -phi follows from
+ * the one at phi). Host only, no GPU needed. phi: n_phi azimuths (radians, any range);
+ * map_out: 2 n_phi ints, caller-owned: map_out[0 .. n_rep) the azimuths computed, in
+ * increasing index order, and map_out[n_phi + r] the index of the azimuth at -phi[map_out[r]]
+ * (mod 2 pi, within 1e-12 rad) that is stored from it, or -1 (none on the grid, the azimuth
+ * itself at 0 or pi, or already paired); the rest of map_out is -1. *n_rep_out receives
+ * n_rep. VRTE_ERR_INVALID_ARG for NULL pointers, n_phi < 1 or a non-finite azimuth. */
+vrte_status vrte_azimuth_mirrors(int n_phi, const double* phi, int* map_out, int* n_rep_out);
+
 /* (Library bookkeeping; no passage.) Synchronizes the plan's last stream and returns the
  * device status word as a
  * vrte_status (VRTE_OK if no device-side error was recorded), then clears it. */

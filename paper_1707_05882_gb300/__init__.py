@@ -114,6 +114,8 @@ def load_library(build_if_missing: bool = True):
     lib.vrte_destroy.restype = None
     lib.vrte_status_string.argtypes = [ctypes.c_int]
     lib.vrte_status_string.restype = ctypes.c_char_p
+    lib.vrte_azimuth_mirrors.argtypes = [ctypes.c_int, P, P, P]
+    lib.vrte_azimuth_mirrors.restype = ctypes.c_int
     for name in ["vrte_plan_create", "vrte_set_layer", "vrte_solve_brdf", "vrte_solve_brdf_host",
                  "vrte_solve_btdf", "vrte_solve_radiance", "vrte_solve_slab_brdf",
                  "vrte_brdf_backward", "vrte_plan_status"]:
@@ -282,6 +284,20 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def azimuth_mirrors(dphi):
+    """vrte_azimuth_mirrors: (computed, mirror) index arrays of the azimuth pairing the
+    tensor-core synthesis uses (mirror[r] = -1 where azimuth computed[r] has no partner)."""
+    lib = load_library()
+    phi = np.ascontiguousarray(dphi, dtype=np.float64)
+    out = np.empty(2 * phi.size, dtype=np.int32)
+    n_rep = ctypes.c_int()
+    _check(lib.vrte_azimuth_mirrors(phi.size, phi.ctypes.data_as(ctypes.c_void_p),
+                                    out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n_rep)),
+           "vrte_azimuth_mirrors")
+    r = n_rep.value
+    return out[:r].copy(), out[phi.size:phi.size + r].copy()
 
 
 def pack_coefficients(layers, n_coef_max=None):

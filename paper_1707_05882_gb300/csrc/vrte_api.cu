@@ -338,6 +338,15 @@ static std::vector<int> azimuth_mirrors(int n, const double* phi, int* n_rep) {
   return map;
 }
 
+vrte_status vrte_azimuth_mirrors(int n_phi, const double* phi, int* map_out, int* n_rep_out) {
+  if (n_phi < 1 || !phi || !map_out || !n_rep_out) return VRTE_ERR_INVALID_ARG;
+  for (int j = 0; j < n_phi; ++j)
+    if (!std::isfinite(phi[j])) return VRTE_ERR_INVALID_ARG;
+  std::vector<int> map = azimuth_mirrors(n_phi, phi, n_rep_out);
+  std::copy(map.begin(), map.end(), map_out);
+  return VRTE_OK;
+}
+
 vrte_status vrte_plan_create(const vrte_plan_desc* d, vrte_plan** out) {
   if (!d || !out) return VRTE_ERR_INVALID_ARG;
   *out = nullptr;
