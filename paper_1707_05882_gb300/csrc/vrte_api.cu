@@ -741,9 +741,14 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                          p->d_status, s);
   }
   {
+    // algorithmic work: the inverses' nominal 2 m^3 each (K: m = 2n, X: m = n); the mixed
+    // form does it as an FP32 elimination and Newton-Schulz products on the tensor cores
+    // (2 per step and one residual check, each m^3 multiply-adds)
     StageScope sc(p, ST_MODES, s, boundary ? 3 : 1,
-                  (boundary ? 16.0 : 2.0) * dn * dn * dn * dU,
+                  (boundary ? 18.0 : 2.0) * dn * dn * dn * dU,
                   8.0 * (boundary ? 12 : 2) * dn * dn * dU);
+    if (mixed)
+      sc.tensor_flops(tcf * (2 * kNewtonSteps + 1) * (boundary ? 9.0 : 1.0) * dn * dn * dn * dU);
     if (boundary) {
       launch_build_K(ob, w->X, w->Y, w->lam_re, w->lam_im, w->d_rtop4, w->K, s);
       if (has_base && m0 == 0)

@@ -51,3 +51,17 @@ def test_roofline_picks_the_bounding_unit():
     assert abs(r["peak"] - r["bf16_peak"] * 4.4e12 / 1.2e14) < 1e-9
     assert abs(r["frac"] - r["slice_products_tflops"] / r["bf16_peak"]) < 1e-12
     assert r["unit"] == "TFLOP/s"
+
+
+def test_roofline_headline_skips_a_concurrent_stage():
+    # the side-stream stage's time spans its fork to its join and overlaps the eigen stage:
+    # it is reported per stage, never as the headline's dominant stage
+    clk = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []}
+    side = {"name": "side_ops", "ms": 400.0, "launches": 18, "flops": 1e12, "bytes": 1e9,
+            "tc_flops": 2.8e13}
+    fp64_stage = {"name": "eigen", "ms": 110.0, "launches": 14, "flops": 6.2e10,
+                  "bytes": 4e8, "tc_flops": 0.0}
+    r = bench.roofline([side, fp64_stage], clk, "mixed")
+    assert r["kernel_stage"] == "eigen"
+    entry = next(e for e in r["per_stage"] if e["stage"] == "side_ops")
+    assert "concurrent" in entry
