@@ -242,6 +242,8 @@ def time_backward(vr, torch, dev, n_layers=16, steps=2, warmup=1):
         plan.backward(F - target, grad, stream)
     if plan.status() != 0:
         raise SystemExit("backward failed")
+    if not bool(torch.isfinite(grad).all()):
+        raise SystemExit("backward gradient not finite")
     plan.reset_stages()
     torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())

@@ -120,14 +120,24 @@ __device__ inline DepthD depth_factors(cd kap, double x, double tau) {
   r.gD = cscale(ph, x);
   r.dD_dt = cscale(cexpv(cd{-a.r * tau, -a.i * tau}), x);
   r.dD_dx = cadd(ph, cscale(dph, x));
-  const cd b{kap.r - x, kap.i};
-  phi1_cplx(b, tau, ph, dph);
-  const double ex = exp(-x * tau);
-  const cd h = cscale(ph, ex);
-  r.gG = cscale(h, x);
+  // h = (e^{-x tau0} - e^{-kappa tau0}) / (kappa - x), taken as e^{-x tau0} Phi1(kappa - x)
+  // when Re(kappa - x) >= 0 and as e^{-kappa tau0} Phi1(x - kappa) otherwise: Phi1 of an
+  // argument with a negative real part overflows for thick layers (and the product with the
+  // vanishing exponential is then NaN)
   const cd ek = cexpv(cd{-kap.r * tau, -kap.i * tau});
+  const double ex = exp(-x * tau);
+  cd h, dh_dx;
+  if (kap.r - x >= 0.0) {
+    phi1_cplx(cd{kap.r - x, kap.i}, tau, ph, dph);
+    h = cscale(ph, ex);
+    dh_dx = csub(cscale(h, -tau), cscale(dph, ex));
+  } else {
+    phi1_cplx(cd{x - kap.r, -kap.i}, tau, ph, dph);
+    h = cmul(ph, ek);
+    dh_dx = cmul(dph, ek);
+  }
+  r.gG = cscale(h, x);
   r.dG_dt = cscale(cadd(cscale(h, -x), ek), x);
-  const cd dh_dx = csub(cscale(h, -tau), cscale(dph, ex));
   r.dG_dx = cadd(h, cscale(dh_dx, x));
   return r;
 }
@@ -611,6 +621,10 @@ __global__ void k_bw_gf(OrderBatch b, const double* kap, const double* pts, doub
 // Integral over [0, tau0] of the adjoint mode function of K times the forward mode function of
 // J (I1), for the 2n x 2n complex matrix Om (in place, Om *= I1):
 //   same block:      (exp(-kK tau0) - exp(-kJ tau0)) / (kJ - kK) = exp(-kK tau0) Phi1(kJ - kK)
+//                    (= exp(-kJ tau0) Phi1(kK - kJ), the form taken when Re(kJ - kK) < 0, so
+//                    that Phi1 never sees an argument with a negative real part: it would
+//                    overflow for thick layers, and its product with the vanishing
+//                    exponential be NaN)
 //   different block: Phi1(kK + kJ).
 __global__ void k_bw_i1(int n, double tau, const double* kap, double* Om) {
   const int J = blockIdx.x * blockDim.x + threadIdx.x;
@@ -620,8 +634,13 @@ __global__ void k_bw_i1(int n, double tau, const double* kap, double* Om) {
   const cd kK = kap_at(kp, n, K < n ? K : K - n), kJ = kap_at(kp, n, J < n ? J : J - n);
   cd f, dph;
   if ((K < n) == (J < n)) {
-    phi1_cplx(csub(kJ, kK), tau, f, dph);
-    f = cmul(f, cexpv(cd{-kK.r * tau, -kK.i * tau}));
+    if (kJ.r - kK.r >= 0.0) {
+      phi1_cplx(csub(kJ, kK), tau, f, dph);
+      f = cmul(f, cexpv(cd{-kK.r * tau, -kK.i * tau}));
+    } else {
+      phi1_cplx(csub(kK, kJ), tau, f, dph);
+      f = cmul(f, cexpv(cd{-kJ.r * tau, -kJ.i * tau}));
+    }
   } else {
     phi1_cplx(cadd(kK, kJ), tau, f, dph);
   }
@@ -634,7 +653,8 @@ __global__ void k_bw_i1(int n, double tau, const double* kap, double* Om) {
 }
 
 // Dp2 = Dp * I2 with I2(K, c) = int_0^tau0 (adjoint mode function of K) exp(-t/mu0_c) dt:
-//   decaying block exp(-y tau0) Phi1(kK - y), growing block Phi1(kK + y), y = 1/mu0.
+//   decaying block exp(-y tau0) Phi1(kK - y) (= exp(-kK tau0) Phi1(y - kK), taken when
+//   Re kK < y), growing block Phi1(kK + y), y = 1/mu0.
 __global__ void k_bw_i2(OrderBatch b, const double* kap, const double* pts, const double* Dp,
                         double* Dp2) {
   const int n = b.n, R = 4 * b.n_in;
@@ -645,8 +665,13 @@ __global__ void k_bw_i2(OrderBatch b, const double* kap, const double* pts, cons
   const double y = 1.0 / pts[b.N + (c >> 2)];
   cd f, dph;
   if (K < n) {
-    phi1_cplx(cd{kK.r - y, kK.i}, b.tau, f, dph);
-    f = cscale(f, exp(-y * b.tau));
+    if (kK.r - y >= 0.0) {
+      phi1_cplx(cd{kK.r - y, kK.i}, b.tau, f, dph);
+      f = cscale(f, exp(-y * b.tau));
+    } else {
+      phi1_cplx(cd{y - kK.r, -kK.i}, b.tau, f, dph);
+      f = cmul(f, cexpv(cd{-kK.r * b.tau, -kK.i * b.tau}));
+    }
   } else {
     phi1_cplx(cd{kK.r + y, kK.i}, b.tau, f, dph);
   }

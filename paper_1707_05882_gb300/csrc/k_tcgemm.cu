@@ -67,19 +67,20 @@ __device__ __host__ inline int tc_smem_bytes(int S) {
 
 // A rows: A[u][i][k] (row-major, lda, unit stride sA), M x K. Writes
 //   out[u][mt][kb][p] tiles (128 x 32 BF16 images) and e[u][i] (int exponent).
-// One CTA per (row block of 128, unit); each thread slices 8 consecutive k of one row.
-template <int S>
+// One CTA per (row block of TR, unit); each thread slices 8 consecutive k of one row. TR = TC_M
+// for the A operand; TR = TC_N slices the rows of a matrix stored N x K as the B operand (B^T).
+template <int S, int TR = TC_M>
 __global__ void k_slice_rows(int M, int K, const double* __restrict__ A, int lda,
                              long long sA, unsigned short* out, int* e_out, unsigned* status) {
   int mt = blockIdx.x, u = blockIdx.y;
-  int Mp = pad_to(M, TC_M), Kp = pad_to(K, TC_KB), KB = Kp / TC_KB, MT = Mp / TC_M;
-  __shared__ int ex[TC_M];
+  int Mp = pad_to(M, TR), Kp = pad_to(K, TC_KB), KB = Kp / TC_KB, MT = Mp / TR;
+  __shared__ int ex[TR];
   const double* Ab = A + (size_t)u * sA;
   bool bad = false;
   // per-row exponent: warp per row, integer max of the exponent fields
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int r = warp; r < TC_M; r += nw) {
-    int i = mt * TC_M + r;
+  for (int r = warp; r < TR; r += nw) {
+    int i = mt * TR + r;
     int Em = 0;
     if (i < M)
       for (int k = lane; k < K; k += 32) Em = max(Em, exp_field(Ab[(size_t)i * lda + k], &bad));
@@ -90,12 +91,12 @@ __global__ void k_slice_rows(int M, int K, const double* __restrict__ A, int lda
     }
   }
   __syncthreads();
-  const size_t tile_elems = (size_t)TC_M * TC_KB;
+  const size_t tile_elems = (size_t)TR * TC_KB;
   const size_t slice_stride = tile_elems;  // the S slices of a tile block are adjacent
   const int chunks = Kp / 8;
-  for (int idx = threadIdx.x; idx < TC_M * chunks; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < TR * chunks; idx += blockDim.x) {
     int r = idx / chunks, k0 = 8 * (idx - r * chunks);
-    int i = mt * TC_M + r;
+    int i = mt * TR + r;
     double v[8];
     for (int t = 0; t < 8; ++t)
       v[t] = (i < M && k0 + t < K) ? Ab[(size_t)i * lda + k0 + t] : 0.0;
@@ -110,46 +111,49 @@ __global__ void k_slice_rows(int M, int K, const double* __restrict__ A, int lda
 // into K-major tiles out[u][nt][kb][q] (64 x 32 BF16 images, row = j) and f[u][j].
 // Each thread slices 8 consecutive k of one column (consecutive threads: consecutive
 // columns, so every global load is coalesced).
-template <int S>
+// TR = TC_N for the B operand; TR = TC_M slices the columns of a matrix stored K x M as the A
+// operand (A^T). blockDim = 512 = (512 / TR) row groups x TR columns.
+template <int S, int TR = TC_N>
 __global__ void k_slice_cols(int N, int K, const double* __restrict__ B, int ldb,
                              long long sB, unsigned short* out, int* f_out, unsigned* status) {
+  constexpr int G = 512 / TR;
   int nt = blockIdx.x, u = blockIdx.y;
-  int Np = pad_to(N, TC_N), Kp = pad_to(K, TC_KB), KB = Kp / TC_KB, NT = Np / TC_N;
-  __shared__ int ex[TC_N];
-  __shared__ int red[8][TC_N];
+  int Np = pad_to(N, TR), Kp = pad_to(K, TC_KB), KB = Kp / TC_KB, NT = Np / TR;
+  __shared__ int ex[TR];
+  __shared__ int red[G][TR];
   const double* Bb = B + (size_t)u * sB;
   bool bad = false;
-  // per-column max exponent: threads over columns (coalesced rows), 8 row groups
-  int c = threadIdx.x % TC_N, g = threadIdx.x / TC_N;  // blockDim = 512 -> 8 groups
-  int j = nt * TC_N + c;
+  // per-column max exponent: threads over columns (coalesced rows), G row groups
+  int c = threadIdx.x % TR, g = threadIdx.x / TR;
+  int j = nt * TR + c;
   int Em = 0;
   if (j < N) {
     // eight independent loads in flight per thread
     int k = g;
-    for (; k + 56 < K; k += 64) {
+    for (; k + 7 * G < K; k += 8 * G) {
       double v[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) v[t] = Bb[(size_t)(k + 8 * t) * ldb + j];
+      for (int t = 0; t < 8; ++t) v[t] = Bb[(size_t)(k + G * t) * ldb + j];
 #pragma unroll
       for (int t = 0; t < 8; ++t) Em = max(Em, exp_field(v[t], &bad));
     }
-    for (; k < K; k += 8) Em = max(Em, exp_field(Bb[(size_t)k * ldb + j], &bad));
+    for (; k < K; k += G) Em = max(Em, exp_field(Bb[(size_t)k * ldb + j], &bad));
   }
   red[g][c] = Em;
   __syncthreads();
   if (g == 0) {
     int m2 = 0;
-    for (int q = 0; q < 8; ++q) m2 = max(m2, red[q][c]);
+    for (int q = 0; q < G; ++q) m2 = max(m2, red[q][c]);
     ex[c] = scale_exp(m2);
     if (j < N) f_out[(size_t)u * Np + j] = ex[c];
   }
   __syncthreads();
-  const size_t tile_elems = (size_t)TC_N * TC_KB;
+  const size_t tile_elems = (size_t)TR * TC_KB;
   const size_t slice_stride = tile_elems;  // the S slices of a tile block are adjacent
   const int chunks = Kp / 8;
-  for (int idx = threadIdx.x; idx < TC_N * chunks; idx += blockDim.x) {
-    int k0 = 8 * (idx / TC_N), cc = idx % TC_N;
-    int jj = nt * TC_N + cc;
+  for (int idx = threadIdx.x; idx < TR * chunks; idx += blockDim.x) {
+    int k0 = 8 * (idx / TR), cc = idx % TR;
+    int jj = nt * TR + cc;
     double v[8];
     for (int t = 0; t < 8; ++t)
       v[t] = (jj < N && k0 + t < K) ? Bb[(size_t)(k0 + t) * ldb + jj] : 0.0;
@@ -525,7 +529,8 @@ bool tc_shape_ok(int K, int S) { return S >= 1 && S <= TC_MAXS && K >= 1 && K <=
 template <class Epi>
 void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const double* B, int ldb,
              long long sB, Epi epi, int batch, int S, void* work, unsigned* status,
-             cudaStream_t s, TcKSkip zskip = TcKSkip{}, int max_ctas = 0) {
+             cudaStream_t s, TcKSkip zskip = TcKSkip{}, int max_ctas = 0, bool tA = false,
+             bool tB = false) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   TcLayout L = tc_layout(M, N, K, batch, S);
   unsigned char* w = (unsigned char*)work;
@@ -534,9 +539,16 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
   int* ea = (int*)(w + L.a_bytes + L.b_bytes);
   int* fb = (int*)(w + L.a_bytes + L.b_bytes + L.e_bytes);
   float* scratch = (float*)(w + L.a_bytes + L.b_bytes + L.e_bytes + L.f_bytes);
-#define VRTE_SLICE_AB(SS)                                                                  \
-  k_slice_rows<SS><<<dim3(L.MT, batch), 256, 0, s>>>(M, K, A, lda, sA, As, ea, status);  \
-  k_slice_cols<SS><<<dim3(L.NT, batch), 512, 0, s>>>(N, K, B, ldb, sB, Bs, fb, status)
+  // A rows (A^T: the columns of A stored K x M) and B columns (B^T: the rows of B stored N x K)
+#define VRTE_SLICE_AB(SS)                                                                       \
+  if (tA)                                                                                       \
+    k_slice_cols<SS, TC_M><<<dim3(L.MT, batch), 512, 0, s>>>(M, K, A, lda, sA, As, ea, status);  \
+  else                                                                                          \
+    k_slice_rows<SS, TC_M><<<dim3(L.MT, batch), 256, 0, s>>>(M, K, A, lda, sA, As, ea, status);  \
+  if (tB)                                                                                       \
+    k_slice_rows<SS, TC_N><<<dim3(L.NT, batch), 256, 0, s>>>(N, K, B, ldb, sB, Bs, fb, status);  \
+  else                                                                                          \
+    k_slice_cols<SS, TC_N><<<dim3(L.NT, batch), 512, 0, s>>>(N, K, B, ldb, sB, Bs, fb, status)
   VRTE_SLICE_DISPATCH(S, VRTE_SLICE_AB)
 #undef VRTE_SLICE_AB
   int smem = tc_smem_bytes(S);
@@ -552,9 +564,10 @@ struct TcEpiStore {
   int ldc;
   long long sC;
   double beta;
+  double alpha = 1.0;
   __device__ void operator()(int u, int i, int j, double v) const {
     double* c = C + (size_t)u * sC + (size_t)i * ldc + j;
-    *c = beta == 0.0 ? v : v + beta * *c;
+    *c = beta == 0.0 ? alpha * v : fma(alpha, v, beta * *c);
   }
 };
 
@@ -564,6 +577,14 @@ void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, 
                    TcKSkip zskip, int max_ctas) {
   tc_gemm(M, N, K, A, lda, sA, B, ldb, sB, TcEpiStore{C, ldc, sC, beta}, batch, S, work, status,
           s, zskip, max_ctas);
+}
+
+void tc_gemm_store_t(bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
+                     int lda, long long sA, const double* B, int ldb, long long sB, double beta,
+                     double* C, int ldc, long long sC, int batch, int S, void* work,
+                     unsigned* status, cudaStream_t s) {
+  tc_gemm(M, N, K, A, lda, sA, B, ldb, sB, TcEpiStore{C, ldc, sC, beta, alpha}, batch, S, work,
+          status, s, TcKSkip{}, 0, tA, tB);
 }
 
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,

@@ -464,6 +464,17 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   size_t kd = p->kdir;
   const int S = kSlices;
   size_t tc_unit = 0, tc_side_unit = 0;
+  const bool adjoint_tc = (p->desc.flags & VRTE_FLAG_ADJOINT) != 0;
+  if (adjoint_tc) {
+    // the adjoint's contractions (op(A) op(B): the workspace depends on M, N, K only)
+    const int nn2 = (int)(2 * n), ni = (int)n, Ri = (int)R, Roi = (int)Ro;
+    const int sh[9][3] = {{Roi, Ri, nn2}, {nn2, Ri, Roi}, {Roi, nn2, Ri}, {nn2, Ri, nn2},
+                          {nn2, nn2, Ri}, {Roi, ni, ni}, {ni, Ri, ni}, {ni, ni, ni},
+                          {nn2, nn2, Roi}};
+    for (const auto& q : sh)
+      if (tc_shape_ok(q[2], S))
+        tc_unit = std::max(tc_unit, tc_workspace_bytes(q[0], q[1], q[2], 1, S) - tc_scratch_bytes());
+  }
   if (mixed) {
     size_t c[9] = {tc_workspace_bytes((int)(2 * n), (int)(2 * n), (int)(2 * n), 1, S),
                    tc_workspace_bytes((int)n, (int)R, (int)n, 1, S),
@@ -552,6 +563,14 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
   if (mixed) {
     VRTE_ALLOC(Ln, U * n * kd) VRTE_ALLOC(RU, U * kd * 2 * n)
     VRTE_ALLOC(Rbp, U * kd * R) VRTE_ALLOC(Rbm, U * kd * R)
+  }
+  if (!mixed && adjoint_tc) {
+    p->tcw_bytes = tc_unit * U + tc_scratch_bytes();
+    if ((st = alloc(p, &w->tcw, p->tcw_bytes)) != VRTE_OK) {
+      free_workspace(p, kPlanAllocs);
+      for (Work& x : p->ws) x.Isyn = nullptr;
+      return st;
+    }
   }
   if (mixed) {
     size_t synth = tc_synthesis_workspace(Mx, p->n_in, p->n_out, p->n_phi, kSynthBlock);
@@ -901,10 +920,16 @@ static void backward_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const do
   double* acc = w->acc;
   const double* pts = w->d_pts;
   const double* dpts = w->dpts;
+  // the adjoint's contractions: sliced FP64-accurate products on the tensor cores (7 slices,
+  // ~1e-15 relative per term, as the mixed form's) where the depth allows, else FP64
   auto gm = [&](bool tA, bool tB, int M_, int N_, int K_, double al, const double* A_, int lda,
                 long long sA, const double* B_, int ldb, long long sB, double be, double* C_,
                 int ldc, long long sC) {
-    dgemm_batched_t(tA, tB, M_, N_, K_, al, A_, lda, sA, B_, ldb, sB, be, C_, ldc, sC, U, s);
+    if (w->tcw && tc_shape_ok(K_, kSlices))
+      tc_gemm_store_t(tA, tB, M_, N_, K_, al, A_, lda, sA, B_, ldb, sB, be, C_, ldc, sC, U,
+                      kSlices, w->tcw, p->d_status, s);
+    else
+      dgemm_batched_t(tA, tB, M_, N_, K_, al, A_, lda, sA, B_, ldb, sB, be, C_, ldc, sC, U, s);
   };
   const double dU = U, dn = n, dR = R, dRo = Ro;
   StageScope sc(p, ST_ADJOINT, s, 120,

@@ -250,6 +250,12 @@ void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, 
                    int ldb, long long sB, double beta, double* C, int ldc, long long sC,
                    int batch, int S, void* work, unsigned* status, cudaStream_t s,
                    TcKSkip zskip = TcKSkip{}, int max_ctas = 0);
+// C = alpha op(A) op(B) + beta C with op = transpose where tA / tB (A stored K x M, B stored
+// N x K), as the sliced product above.
+void tc_gemm_store_t(bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
+                     int lda, long long sA, const double* B, int ldb, long long sB, double beta,
+                     double* C, int ldc, long long sC, int batch, int S, void* work,
+                     unsigned* status, cudaStream_t s);
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                   const double* B, long long sB, const double* T1, const double* g0tab,
                   double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip = TcKSkip{},

@@ -99,6 +99,22 @@ def test_adjoint_thick_layer_resolves_every_order():
     _compare(g, ref)
 
 
+def test_adjoint_optically_thick_layer_stays_finite():
+    """tau0 = 40 with N = 8 (kappa up to ~50): the mode integrals of the adjoint two-point problem
+    pair modes whose exponentials e^{-kappa tau0} differ by far more than the FP64 range; each is
+    taken in the form whose Phi1 argument has a non-negative real part, so the gradient is finite
+    and matches the oracle's difference gradient (the eigen-form oracle keeps its exponentials
+    scaled; the propagator form of the exact one overflows at this thickness)."""
+    ly = _layer(1.33, L=8, x=2.0, omega=0.95, tau=40.0, N=8)
+    grids = angle_grids(2, 3, 4)
+    target = _target(ly, grids, seed=7)
+    g, _ = _gpu_grad(ly, grids, target)
+    assert np.all(np.isfinite(g))
+    p = OG.pack(ly["omega"], ly["tau"], ly["n_interface"], ly["coef"])
+    ref = OG.loss_gradient(p, target, ly["n_coef"], ly["n_nodes"], ly["n_orders"], *grids)
+    _compare(g, ref)
+
+
 def test_adjoint_fp32_table():
     """The gradient of the loss of an FP32 table (FP32 table gradient in, grad_dtype F32)
     equals the FP64 path's on the same values, and the FP64 gradient to 1e-3 relative."""
