@@ -49,7 +49,7 @@ __global__ void k_col_absmax(int rows, int cols, const double* __restrict__ B, i
 // The error bound of the sliced contractions against tol |I^0_00(o, k)| (order 0 sets the
 // scale of the synthesized radiance at that pair), from the row maxima per outgoing o
 // (rmH, rmU: [U][n_out]) and column maxima per incident k (cmC, cmSD: [U][n_in]), each over
-// the four Stokes rows or columns: one thread per (outgoing o, incident k),
+// the four Stokes rows or columns: one thread per (outgoing o, incident k = k0 + blockIdx.y),
 // which reads the order-0 reference once and tests every order u of the batch, marking the
 // column blocks (u, k) that fail in `flags` (already set for a non-finite result by the
 // reconstruction's epilogue).
@@ -57,9 +57,9 @@ __global__ void k_flag_columns(OrderBatch b, const double* __restrict__ rmH,
                                const double* __restrict__ rmU, const double* __restrict__ cmC,
                                const double* __restrict__ cmSD, const double* __restrict__ g0tab,
                                const double* __restrict__ Isyn, double epsK1, double epsK2,
-                               double tol, int* flags) {
+                               double tol, int k0, int* flags) {
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  const int k = blockIdx.y;
+  const int k = k0 + blockIdx.y;
   if (o >= b.n_out) return;
   const double ref = Isyn[((size_t)k * b.n_out + o) * 16];
   const double lim = isfinite(ref) ? tol * fabs(ref) : -1.0;
@@ -72,12 +72,12 @@ __global__ void k_flag_columns(OrderBatch b, const double* __restrict__ rmH,
   }
 }
 
-// The flagged column blocks into the work list of k_fix_columns.
-__global__ void k_collect_columns(int n_in, int U, const int* __restrict__ flags, int* count,
-                                  int* total, int2* list, int cap) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+// The flagged column blocks with incident k0 <= k < k1 into the work list of k_fix_columns.
+__global__ void k_collect_columns(int n_in, int k0, int k1, int U, const int* __restrict__ flags,
+                                  int* count, int* total, int2* list, int cap) {
+  const int k = k0 + blockIdx.x * blockDim.x + threadIdx.x;
   const int u = blockIdx.y;
-  if (k >= n_in || u >= U || !flags[(size_t)u * n_in + k]) return;
+  if (k >= k1 || u >= U || !flags[(size_t)u * n_in + k]) return;
   const int slot = atomicAdd(count, 1);
   atomicAdd(total, 1);
   if (slot < cap) list[slot] = make_int2(u, k);
@@ -150,12 +150,11 @@ __global__ void __launch_bounds__(256) k_fix_columns(
   }
 }
 
-void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
-                    const double* C, const double* Hhat, const double* Uext, const double* SD,
-                    const double* g0tab, double eps, double tol, double* scratch, int* counters,
-                    int2* list, int cap, double* Isyn, int* nonfinite, cudaStream_t s) {
+// maxima per (unit, outgoing) and per (unit, incident), each over its four Stokes entries,
+// in `scratch`: rmH, rmU [U][n_out], cmC, cmSD [U][n_in]
+void refine_maxima(const OrderBatch& b, int Kpart, const double* C, const double* Hhat,
+                   const double* Uext, const double* SD, double* scratch, cudaStream_t s) {
   const int U = b.n_units, n2 = 2 * b.n, R = 4 * b.n_in, Ro = 4 * b.n_out;
-  // maxima per (unit, outgoing) and per (unit, incident), each over its four Stokes entries
   double* rmH = scratch;
   double* rmU = rmH + (size_t)U * b.n_out;
   double* cmC = rmU + (size_t)U * b.n_out;
@@ -166,14 +165,35 @@ void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const do
                                                       (long long)Ro * b.ldU, rmU);
   k_col_absmax<<<dim3((R + 127) / 128, U), 128, 0, s>>>(n2, R, C, R, (long long)n2 * R, cmC);
   k_col_absmax<<<dim3((R + 127) / 128, U), 128, 0, s>>>(Kpart, R, SD, R, b.sSD, cmSD);
+}
+
+void refine_range(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
+                  const double* Hhat, const double* Uext, const double* SD, const double* g0tab,
+                  double eps, double tol, const double* scratch, int* counters, int2* list,
+                  int cap, double* Isyn, int* nonfinite, int k0, int k1, cudaStream_t s) {
+  const int U = b.n_units, n2 = 2 * b.n;
+  if (k1 <= k0) return;
+  const double* rmH = scratch;
+  const double* rmU = rmH + (size_t)U * b.n_out;
+  const double* cmC = rmU + (size_t)U * b.n_out;
+  const double* cmSD = cmC + (size_t)U * b.n_in;
   cudaMemsetAsync(counters, 0, sizeof(int), s);
-  k_flag_columns<<<dim3((b.n_out + 127) / 128, b.n_in), 128, 0, s>>>(
-      b, rmH, rmU, cmC, cmSD, g0tab, Isyn, eps * n2, eps * Kpart, tol, nonfinite);
-  k_collect_columns<<<dim3((b.n_in + 127) / 128, U), 128, 0, s>>>(b.n_in, U, nonfinite, counters,
-                                                                  counters + 1, list, cap);
+  k_flag_columns<<<dim3((b.n_out + 127) / 128, k1 - k0), 128, 0, s>>>(
+      b, rmH, rmU, cmC, cmSD, g0tab, Isyn, eps * n2, eps * Kpart, tol, k0, nonfinite);
+  k_collect_columns<<<dim3((k1 - k0 + 127) / 128, U), 128, 0, s>>>(
+      b.n_in, k0, k1, U, nonfinite, counters, counters + 1, list, cap);
   size_t smem = (size_t)n2 * 4 * sizeof(double);
   k_fix_columns<<<2 * 152, 256, smem, s>>>(b, Kinv, RHS, Hhat, Uext, SD, g0tab, Kpart, counters,
                                            list, cap, Isyn);
+}
+
+void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
+                    const double* C, const double* Hhat, const double* Uext, const double* SD,
+                    const double* g0tab, double eps, double tol, double* scratch, int* counters,
+                    int2* list, int cap, double* Isyn, int* nonfinite, cudaStream_t s) {
+  refine_maxima(b, Kpart, C, Hhat, Uext, SD, scratch, s);
+  refine_range(b, Kpart, Kinv, RHS, Hhat, Uext, SD, g0tab, eps, tol, scratch, counters, list,
+               cap, Isyn, nonfinite, 0, b.n_in, s);
 }
 
 size_t refine_scratch_doubles(int U, int n_in, int n_out) {

@@ -404,7 +404,8 @@ size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int k_block
 void tc_synthesis(int M, int n_in, int n_out, int n_phi, int n_rep, const int* map,
                   const double* Isyn, const double* wc, const double* ws, void* out,
                   int out_dtype, int k_block, void* work, unsigned* status, cudaStream_t s,
-                  const SynthHook* hook) {
+                  const SynthHook* hook, int k_lo, int k_hi, bool slice_weights) {
+  if (k_hi < 0 || k_hi > n_in) k_hi = n_in;
   const long long pairs_total = (long long)n_in * n_out;
   const SynthLayout Lmax = synth_layout(std::min(k_block, n_in) * n_out, M, n_rep);
   unsigned char* w = (unsigned char*)work;
@@ -413,14 +414,15 @@ void tc_synthesis(int M, int n_in, int n_out, int n_phi, int n_rep, const int* m
   unsigned short* Bs = (unsigned short*)(w + Lmax.a_bytes + Lmax.e_bytes);
   int* fb = (int*)(w + Lmax.a_bytes + Lmax.e_bytes + Lmax.b_bytes);
   const int sms = sm_count();
-  k_synth_slice_cols<<<dim3(Lmax.NT, 2), SY_N, 0, s>>>(M, n_phi, n_rep, map, Lmax.NT, Lmax.KB, wc,
-                                                       ws, Bs, fb, status);
+  if (slice_weights)
+    k_synth_slice_cols<<<dim3(Lmax.NT, 2), SY_N, 0, s>>>(M, n_phi, n_rep, map, Lmax.NT, Lmax.KB,
+                                                         wc, ws, Bs, fb, status);
   if (out_dtype == VRTE_OUT_F64)
     cudaFuncSetAttribute(k_synth_mma<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, SY_SMEM);
   else
     cudaFuncSetAttribute(k_synth_mma<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, SY_SMEM);
-  for (int k0 = 0; k0 < n_in; k0 += k_block) {
-    const int kb = std::min(k_block, n_in - k0);
+  for (int k0 = k_lo; k0 < k_hi; k0 += k_block) {
+    const int kb = std::min(k_block, k_hi - k0);
     const SynthLayout L = synth_layout(kb * n_out, M, n_rep);
     const long long pair0 = (long long)k0 * n_out;
     k_synth_slice_rows<<<std::min(L.MT, 2 * sms), 256, 0, s>>>(L.P, pair0, pairs_total, M, L.MT,

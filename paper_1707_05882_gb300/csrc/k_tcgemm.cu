@@ -35,6 +35,7 @@ namespace vrte {
 
 constexpr int TC_M = 128;       // output rows per CTA (MMA M)
 constexpr int TC_N = 64;        // output columns per CTA (MMA N)
+static_assert(TC_N == kTcTileCols, "column tiles of TcRange");
 constexpr int TC_KB = 32;       // K per stage (one 64-byte swizzle row of BF16)
 constexpr int TC_MAXS = 8;      // maximum number of slices
 constexpr int TC_NACC = 7;      // TMEM accumulators (see acc_index)
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(int M, int N, int K, int S, const unsigned short* __restrict__ As,
               const int* __restrict__ ea, const unsigned short* __restrict__ Bs,
               const int* __restrict__ fb, float* scratch, Epi epi, unsigned* status,
-              int batch, TcKSkip zskip) {
+              int batch, TcKSkip zskip, int nt_lo, int nt_cnt) {
   // Persistent: CTA b takes tiles b, b + gridDim.x, ... Warp 0 bulk-copies the slice
   // tiles of each 32-wide K block into a ring of shared-memory stages, warp 1 (owner of
   // the TMEM allocation) issues the slice-pair MMAs as the stages fill, and warps 2-9
@@ -229,7 +230,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int Mp = pad_to(M, TC_M), Np = pad_to(N, TC_N), Kp = pad_to(K, TC_KB);
   const int KB = Kp / TC_KB, MT = Mp / TC_M, NT = Np / TC_N;
-  const int tiles = MT * NT * batch;
+  // the column tiles nt_lo .. nt_lo + nt_cnt - 1 of every unit (all: 0, NT)
+  const int NTr = nt_cnt > 0 ? nt_cnt : NT;
+  const int tiles = MT * NTr * batch;
   const int stage_bytes = S * (A_TILE_BYTES + B_TILE_BYTES);
   const int nst = tc_stages(S);
   const int nacc = acc_count(S);
@@ -275,7 +278,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int g = 0;
       for (int t = blockIdx.x; t < tiles && !abort_flag; t += gridDim.x) {
         int u, mt, nt;
-        tc_decode(t, MT, NT, u, mt, nt);
+        tc_decode(t, MT, NTr, u, mt, nt);
+        nt += nt_lo;
         // the S slice tiles of a (tile, K block) are adjacent: one bulk copy per operand
         const unsigned short* a0 =
             As + (size_t)u * a_unit + (size_t)mt * KB * S * (A_TILE_BYTES / 2);
@@ -313,7 +317,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t dbase = tmem + (uint32_t)(b * buf_cols);
         int u, mt, nt;
-        tc_decode(t, MT, NT, u, mt, nt);
+        tc_decode(t, MT, NTr, u, mt, nt);
+        nt += nt_lo;
         int zb0, zb1;
         tc_skip_range(zskip, u, KB, zb0, zb1);
         const int kfirst = (zb0 == 0 && zb1 > 0) ? zb1 : 0;  // first K block issued
@@ -366,7 +371,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!mbar_wait(&tfull_bar[b], use & 1)) { fail(); break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       int u, mt, nt;
-      tc_decode(t, MT, NT, u, mt, nt);
+      tc_decode(t, MT, NTr, u, mt, nt);
+      nt += nt_lo;
       const int i = mt * TC_M + quad * 32 + lane;
       const int erow = (i < M) ? ea[(size_t)u * Mp + i] : 0;
       const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * buf_cols);
@@ -530,7 +536,7 @@ template <class Epi>
 void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const double* B, int ldb,
              long long sB, Epi epi, int batch, int S, void* work, unsigned* status,
              cudaStream_t s, TcKSkip zskip = TcKSkip{}, int max_ctas = 0, bool tA = false,
-             bool tB = false) {
+             bool tB = false, TcRange rg = TcRange{}) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   TcLayout L = tc_layout(M, N, K, batch, S);
   unsigned char* w = (unsigned char*)work;
@@ -549,14 +555,18 @@ void tc_gemm(int M, int N, int K, const double* A, int lda, long long sA, const 
     k_slice_rows<SS, TC_N><<<dim3(L.NT, batch), 256, 0, s>>>(N, K, B, ldb, sB, Bs, fb, status);  \
   else                                                                                          \
     k_slice_cols<SS, TC_N><<<dim3(L.NT, batch), 512, 0, s>>>(N, K, B, ldb, sB, Bs, fb, status)
-  VRTE_SLICE_DISPATCH(S, VRTE_SLICE_AB)
+  if (rg.slice) VRTE_SLICE_DISPATCH(S, VRTE_SLICE_AB)
 #undef VRTE_SLICE_AB
+  if (!rg.run) return;
+  const int nt_lo = rg.nt_cnt > 0 ? rg.nt_lo : 0;
+  const int nt_cnt = rg.nt_cnt > 0 ? std::min(rg.nt_cnt, L.NT - nt_lo) : L.NT;
+  if (nt_lo < 0 || nt_cnt <= 0) return;
   int smem = tc_smem_bytes(S);
   cudaFuncSetAttribute(k_tc_gemm<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  int grid = tc_grid((long long)L.MT * L.NT * batch);
+  int grid = tc_grid((long long)L.MT * nt_cnt * batch);
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
   k_tc_gemm<Epi><<<grid, TC_THREADS, smem, s>>>(
-      M, N, K, S, As, ea, Bs, fb, scratch, epi, status, batch, zskip);
+      M, N, K, S, As, ea, Bs, fb, scratch, epi, status, batch, zskip, nt_lo, nt_cnt);
 }
 
 struct TcEpiStore {
@@ -574,9 +584,9 @@ struct TcEpiStore {
 void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, const double* B,
                    int ldb, long long sB, double beta, double* C, int ldc, long long sC,
                    int batch, int S, void* work, unsigned* status, cudaStream_t s,
-                   TcKSkip zskip, int max_ctas) {
+                   TcKSkip zskip, int max_ctas, TcRange rg) {
   tc_gemm(M, N, K, A, lda, sA, B, ldb, sB, TcEpiStore{C, ldc, sC, beta}, batch, S, work, status,
-          s, zskip, max_ctas);
+          s, zskip, max_ctas, false, false, rg);
 }
 
 void tc_gemm_store_t(bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
@@ -590,10 +600,10 @@ void tc_gemm_store_t(bool tA, bool tB, int M, int N, int K, double alpha, const 
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                   const double* B, long long sB, const double* T1, const double* g0tab,
                   double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip,
-                  int* nonfinite) {
+                  int* nonfinite, TcRange rg) {
   EpiPart e{T1, Isyn, g0tab, b.N, b.n_in, b.n_out, b.m0, nonfinite};
   tc_gemm(4 * b.n_out, 4 * b.n_in, K, A, lda, sA, B, 4 * b.n_in, sB, e, b.n_units, S, work,
-          b.status, s, zskip);
+          b.status, s, zskip, 0, false, false, rg);
 }
 
 // First half of a reconstruction contraction too deep for one exact accumulation

@@ -143,6 +143,10 @@ struct vrte_plan {
   size_t coef_stage_bytes = 0;
   void* d_out_stage = nullptr;
   size_t out_stage_bytes = 0;
+  // host-API block-wise reconstruction: the homogeneous contraction's slices and the synthesis
+  // workspace (allocated by the first host-buffer solve that can use it; none if that fails)
+  void* d_chunk_ws = nullptr;
+  size_t chunk_ws_bytes = 0;
   std::vector<void*> allocs;
   std::vector<size_t> alloc_bytes;
   // stage statistics: launches always, event pairs when VRTE_FLAG_PROFILE is set
@@ -646,9 +650,32 @@ vrte_status vrte_set_layer(vrte_plan* p, int n_layers, const vrte_layer* hp, con
 // P2, Hhat and, in the FP64 form, the direct term in T1): what the adjoint needs. With
 // `boundary` false it also leaves out the layer's own boundary system (K, its inverse, the
 // right-hand side and C): a slab solves one system for all of its sub-layers.
+// The host-buffer solve's second workspace for a layer of n = 4N and U orders: the homogeneous
+// contraction's slices (kept while the particular contraction's stay in the slot's workspace),
+// then the synthesis workspace.
+static size_t chunk_hom_bytes(const vrte_plan* p, int n, int U) {
+  return (tc_workspace_bytes(4 * p->n_out, 4 * p->n_in, 2 * n, U, kSlices) + 1023) / 1024 * 1024;
+}
+static size_t chunk_ws_need(const vrte_plan* p, int n, int U) {
+  return chunk_hom_bytes(p, n, U) +
+         tc_synthesis_workspace(U, p->n_in, p->n_out, p->n_phi, kSynthBlock);
+}
+
+// Reconstruction and synthesis in blocks of incident cosines (host-buffer solve): the layer's
+// table, its element type, the hook that starts the copy of each finished block, the second
+// workspace; `done` is set when the batch has synthesized the table.
+struct ChunkSynth {
+  void* out;
+  int out_dtype;
+  const SynthHook* hook;
+  void* ws;
+  size_t ws_bytes;
+  bool done;
+};
+
 static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const double* coef,
                           int m0, int U, bool mixed, bool reconstruct, cudaStream_t s,
-                          bool boundary = true) {
+                          bool boundary = true, ChunkSynth* cs = nullptr) {
   const int N = ly.n_nodes, n = 4 * N, L = ly.n_coef;
   const int P = N + p->n_in + p->n_out;
   const int R = 4 * p->n_in, Ro = 4 * p->n_out;
@@ -854,6 +881,76 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                              s);
   }
   if (!reconstruct) return;
+  const bool chunked = cs && cs->ws && mixed && boundary && m0 == 0 && U == Meff && !has_base &&
+                       2 * n + kdir <= 1024 && cs->ws_bytes >= chunk_ws_need(p, n, U);
+  if (chunked) {
+    // The reconstruction, its FP64 column fixes and the synthesis per block of kSynthBlock
+    // incident cosines, so that each block's table rows leave for the host while the next
+    // block is computed. Both contractions are sliced once (the homogeneous one into the second
+    // workspace) and then run on the column tiles of each block; the operand maxima of the
+    // error bound are taken once.
+    static_assert(kSynthBlock % (kTcTileCols / 4) == 0, "blocks start on a column tile");
+    const int Kp = 2 * n + kdir;
+    void* hom_ws = cs->ws;
+    void* syn_ws = (char*)cs->ws + chunk_hom_bytes(p, n, U);
+    const long long RoR = (long long)Ro * R;
+    const double kpsum = 2.0 * dn * dU + kdsum;
+    {
+      StageScope sc(p, ST_RECON_HOM, s, 2, 0.0, 8.0 * (dRo * 2 * dn + 2 * dn * dR) * dU);
+      tc_gemm_store(Ro, R, 2 * n, w->Hhat, 2 * n, 2 * Ron, w->C, R, 2 * nR, 0.0, w->T1, R, RoR,
+                    U, kSlices, hom_ws, p->d_status, s, TcKSkip{}, 0, TcRange{true, false});
+    }
+    {
+      StageScope sc(p, ST_RECON_PART, s, 2, 0.0, 8.0 * ((double)Kp * (dRo + dR)) * dU);
+      cudaMemsetAsync(w->nfflag, 0, (size_t)U * p->n_in * sizeof(int), s);
+      tc_gemm_part(ob, Kp, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1, w->g0tab, w->Isyn,
+                   kSlices, w->tcw, s, zpart, w->nfflag, TcRange{true, false});
+    }
+    {
+      StageScope sc(p, ST_REFINE, s, 4, 0.0, 0.0);
+      refine_maxima(ob, Kp, w->C, w->Hhat, w->Upm, w->SD, w->rscratch, s);
+    }
+    const double table = (double)p->n_in * p->n_out * p->n_phi * 16;
+    const double esz = cs->out_dtype == VRTE_OUT_F64 ? 8.0 : 4.0;
+    for (int k0 = 0; k0 < p->n_in; k0 += kSynthBlock) {
+      const int k1 = std::min(p->n_in, k0 + kSynthBlock);
+      const double f = double(k1 - k0) / p->n_in;  // the block's share of the work
+      const TcRange run{false, true, 4 * k0 / kTcTileCols,
+                        (4 * (k1 - k0) + kTcTileCols - 1) / kTcTileCols};
+      {
+        StageScope sc(p, ST_RECON_HOM, s, 1, f * 2.0 * dRo * dR * 2 * dn * dU,
+                      f * 8.0 * 2 * dRo * dR * dU);
+        sc.tensor_flops(f * tcf * dRo * dR * 2.0 * dn * dU);
+        tc_gemm_store(Ro, R, 2 * n, w->Hhat, 2 * n, 2 * Ron, w->C, R, 2 * nR, 0.0, w->T1, R,
+                      RoR, U, kSlices, hom_ws, p->d_status, s, TcKSkip{}, 0, run);
+      }
+      {
+        StageScope sc(p, ST_RECON_PART, s, 1, f * 2.0 * dRo * dR * kpsum,
+                      f * 8.0 * 2 * dRo * dR * dU);
+        sc.tensor_flops(f * tcf * dRo * dR * kpsum);
+        tc_gemm_part(ob, Kp, w->Upm, ldU, sU_part, w->SD, ob.sSD, w->T1, w->g0tab, w->Isyn,
+                     kSlices, w->tcw, s, zpart, w->nfflag, run);
+      }
+      {
+        StageScope sc(p, ST_REFINE, s, 3, 0.0, 0.0);
+        refine_range(ob, Kp, w->Kinv, w->RHS, w->Hhat, w->Upm, w->SD, w->g0tab, kSliceEps,
+                     kRefineTol, w->rscratch, w->rcount, w->rlist, U * p->n_in, w->Isyn,
+                     w->nfflag, k0, k1, s);
+      }
+      {
+        StageScope sc(p, ST_SYNTHESIS, s, (k0 == 0 ? 1 : 0) + 2, f * 2.0 * table * Meff,
+                      f * (table * esz + (double)Meff * p->n_in * p->n_out * 16 * 8));
+        const int Ss = kSlicesSynth;
+        sc.tensor_flops(f * 2.0 * Ss * (Ss + 1) / 2 * 16.0 * p->n_in * p->n_out * p->n_rep *
+                        Meff);
+        tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, p->n_rep, p->d_syn_map, w->Isyn,
+                     p->d_wc, p->d_ws, cs->out, cs->out_dtype, kSynthBlock, syn_ws,
+                     p->d_status, s, cs->hook, k0, k1, k0 == 0);
+      }
+    }
+    cs->done = true;
+    return;
+  }
   {
     // homogeneous part: [4 n_out x 2n] x [2n x 4 n_in] per order. FP64: T1 holds the
     // direct term and gains the homogeneous part; mixed: T1 is the homogeneous part and
@@ -1117,17 +1214,22 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
                        p->d_mu_out, w->d_pts, w->d_min4, w->d_mout4, w->d_rtop4, s);
       launch_depth_table(N, p->n_in, p->n_out, ly.tau, w->d_pts, w->g0tab, s);
     }
+    char* outb = (char*)d_brdf + (size_t)lb * table * esz;
+    SynthHook hook{hook_fn, hook_user, lb};
+    // with a hook (host-buffer solve), a layer of one order batch reconstructs and synthesizes
+    // block by block when the second workspace is there
+    ChunkSynth cs{outb, out_dtype, &hook, p->d_chunk_ws, p->chunk_ws_bytes, false};
     for (int m0 = 0; m0 < Meff; m0 += p->chunk)
       run_order_batch(p, w, ly, coef, m0, std::min(p->chunk, Meff - m0),
-                      p->desc.precision == VRTE_MIXED, true, s);
+                      p->desc.precision == VRTE_MIXED, true, s, true,
+                      hook_fn && ns == 1 ? &cs : nullptr);
     // a launch that could not start (resources, configuration) fails the solve here
     if (cudaPeekAtLastError() != cudaSuccess) {
       cudaGetLastError();
       result = VRTE_ERR_CUDA;
       break;
     }
-    char* outb = (char*)d_brdf + (size_t)lb * table * esz;
-    {
+    if (!cs.done) {
       const bool mixed = p->desc.precision == VRTE_MIXED;
       StageScope sc(p, ST_SYNTHESIS, s,
                     mixed ? 1 + 2 * ((p->n_in + kSynthBlock - 1) / kSynthBlock) : 1,
@@ -1137,7 +1239,6 @@ static vrte_status run_solve(vrte_plan* p, const double* coeffs, void* d_brdf, i
         const int Ss = kSlicesSynth;
         sc.tensor_flops(2.0 * Ss * (Ss + 1) / 2 * 16.0 * p->n_in * p->n_out * p->n_rep * Meff);
       }
-      SynthHook hook{hook_fn, hook_user, lb};
       if (mixed) {
         tc_synthesis(Meff, p->n_in, p->n_out, p->n_phi, p->n_rep, p->d_syn_map, w->Isyn, p->d_wc,
                      p->d_ws, outb, out_dtype, kSynthBlock, w->tcw, p->d_status, s,
@@ -1521,6 +1622,29 @@ vrte_status vrte_solve_brdf_host(vrte_plan* p, const double* h_coeffs, void* h_b
     if (cudaMalloc(&p->d_out_stage, obytes) != cudaSuccess) { cudaGetLastError(); return VRTE_ERR_OOM; }
     p->out_stage_bytes = obytes;
   }
+  // the block-wise reconstruction's workspace, for the largest layer that can use it (one
+  // order batch, no base, one particular contraction); optional: without it the layer is
+  // reconstructed whole and the copies start with its synthesis
+  if (p->desc.precision == VRTE_MIXED && p->nslots == 1) {
+    size_t need = 0;
+    for (int lb = 0; lb < p->n_layers; ++lb) {
+      const vrte_layer& l = p->layers[lb];
+      const int Meff = std::min(l.n_orders, l.n_coef), n = 4 * l.n_nodes;
+      if (Meff <= p->chunk && !layer_base(l, nullptr) && 2 * n + 4 * l.n_coef <= 1024)
+        need = std::max(need, chunk_ws_need(p, n, Meff));
+    }
+    if (need > p->chunk_ws_bytes) {
+      if (p->d_chunk_ws) cudaFree(p->d_chunk_ws);
+      p->d_chunk_ws = nullptr;
+      p->chunk_ws_bytes = 0;
+      if (cudaMalloc(&p->d_chunk_ws, need) == cudaSuccess) {
+        p->chunk_ws_bytes = need;
+      } else {
+        cudaGetLastError();
+        p->d_chunk_ws = nullptr;
+      }
+    }
+  }
   if (cudaMemcpyAsync(p->d_coef_stage, h_coeffs, cbytes, cudaMemcpyHostToDevice, s) != cudaSuccess)
     return VRTE_ERR_CUDA;
   p->last_stream = s;
@@ -1777,7 +1901,7 @@ void vrte_profile_reset(vrte_plan* p) {
 
 size_t vrte_workspace_bytes(const vrte_plan* p) {
   if (!p) return 0;
-  size_t t = p->coef_stage_bytes + p->out_stage_bytes;
+  size_t t = p->coef_stage_bytes + p->out_stage_bytes + p->chunk_ws_bytes;
   for (size_t b : p->alloc_bytes) t += b;
   return t;
 }
@@ -1805,6 +1929,7 @@ void vrte_destroy(vrte_plan* p) {
   if (p->solved) cudaEventDestroy(p->solved);
   if (p->d_coef_stage) cudaFree(p->d_coef_stage);
   if (p->d_out_stage) cudaFree(p->d_out_stage);
+  if (p->d_chunk_ws) cudaFree(p->d_chunk_ws);
   delete p;
 }
 

@@ -246,10 +246,18 @@ bool tc_shape_ok(int K, int S);
 struct TcKSkip {
   int zk0 = 0, zbase = 0, zstep = 0;
 };
+// Parts of a sliced product: `slice` writes both operands' slices into the workspace, `run`
+// multiplies the column tiles [nt_lo, nt_lo + nt_cnt) of 64 columns (nt_cnt = 0: all) from the
+// slices already there (the same M, N, K, batch and workspace as the slicing call).
+struct TcRange {
+  bool slice = true, run = true;
+  int nt_lo = 0, nt_cnt = 0;
+};
+constexpr int kTcTileCols = 64;  // columns of one output tile of the sliced product
 void tc_gemm_store(int M, int N, int K, const double* A, int lda, long long sA, const double* B,
                    int ldb, long long sB, double beta, double* C, int ldc, long long sC,
                    int batch, int S, void* work, unsigned* status, cudaStream_t s,
-                   TcKSkip zskip = TcKSkip{}, int max_ctas = 0);
+                   TcKSkip zskip = TcKSkip{}, int max_ctas = 0, TcRange rg = TcRange{});
 // C = alpha op(A) op(B) + beta C with op = transpose where tA / tB (A stored K x M, B stored
 // N x K), as the sliced product above.
 void tc_gemm_store_t(bool tA, bool tB, int M, int N, int K, double alpha, const double* A,
@@ -259,13 +267,22 @@ void tc_gemm_store_t(bool tA, bool tB, int M, int N, int K, double alpha, const 
 void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long long sA,
                   const double* B, long long sB, const double* T1, const double* g0tab,
                   double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip = TcKSkip{},
-                  int* nonfinite = nullptr);
+                  int* nonfinite = nullptr, TcRange rg = TcRange{});
 // Mixed form: flags (order, incident) column blocks whose sliced reconstruction error
 // bound eps K max|row| max|column| exceeds tol |I_00| and recomputes them in FP64.
 void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
                     const double* C, const double* Hhat, const double* Uext, const double* SD,
                     const double* g0tab, double eps, double tol, double* scratch, int* counters,
                     int2* list, int cap, double* Isyn, int* nonfinite, cudaStream_t s);
+// refine_columns in two parts: the operand maxima (once, when the operands are final), then the
+// flag / collect / FP64 fix of the incident cosines k0 <= k < k1 (after their columns of I^m
+// are reconstructed).
+void refine_maxima(const OrderBatch& b, int Kpart, const double* C, const double* Hhat,
+                   const double* Uext, const double* SD, double* scratch, cudaStream_t s);
+void refine_range(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
+                  const double* Hhat, const double* Uext, const double* SD, const double* g0tab,
+                  double eps, double tol, const double* scratch, int* counters, int2* list,
+                  int cap, double* Isyn, int* nonfinite, int k0, int k1, cudaStream_t s);
 size_t refine_scratch_doubles(int U, int n_in, int n_out);
 // T1 += g0 (A @ B): the first part of a reconstruction contraction split in K.
 void tc_gemm_part_accum(const OrderBatch& b, int K, const double* A, int lda, long long sA,
@@ -285,10 +302,13 @@ size_t tc_synthesis_workspace(int M, int n_in, int n_out, int n_phi, int k_block
 // map: [n_phi] computed azimuths (the first n_rep entries) and [n_phi] their mirrors at -phi
 // (-1: none), written by the plan; the mirror's table entry is the computed one (cosine
 // class) or its negative (sine class).
+// Only the incident cosines k_lo <= k < k_hi (k_hi < 0: all); slice_weights false reuses the
+// weight slices a previous call left in `work`.
 void tc_synthesis(int M, int n_in, int n_out, int n_phi, int n_rep, const int* map,
                   const double* Isyn, const double* wc, const double* ws, void* out,
                   int out_dtype, int k_block, void* work, unsigned* status, cudaStream_t s,
-                  const SynthHook* hook = nullptr);
+                  const SynthHook* hook = nullptr, int k_lo = 0, int k_hi = -1,
+                  bool slice_weights = true);
 
 // ---------------------------------------------------------------- mode algebra (k_modes.cu)
 void launch_pack_Y(const OrderBatch& b, const double* EX, const double* lam_re,

@@ -171,3 +171,40 @@ def test_mixed_synthesis_azimuth_mirrors(grid):
     G = oracle_brdf(layer, mu_in, mu_out, dphi)
     ei, eq = row_errors(F, G)
     assert ei < TOL_I and eq < TOL_QUV, (ei, eq)
+
+
+@pytest.mark.parametrize("case", ["ragged_blocks", "mie_N64_L128"])
+def test_mixed_host_buffer_blockwise_matches_device(case):
+    """The host-buffer solve reconstructs a one-batch mixed layer and synthesizes its table in
+    blocks of 64 incident cosines (the copy of each finished block overlaps the next block's
+    work): the same column tiles, FP64 column fixes and synthesis as the device-buffer solve,
+    so the tables are equal bit for bit, and so are the counts of fixed column blocks."""
+    if case == "ragged_blocks":
+        coef = polydisperse_coefficients(1.5 + 0.001j, 6.0, 0.1, 40)
+        ly = dict(tau=2.0, omega=0.95, n_interface=1.33, n_nodes=20, n_orders=40, coef=coef)
+        grids = angle_grids(150, 37, 24)      # blocks of 64, 64 and 22 incident cosines
+    else:
+        ly = dict(make_config(3)["layers"][0])
+        grids = angle_grids(256, 96, 36)
+    ly["n_coef"] = np.asarray(ly["coef"]).shape[0]
+    coef = vr.pack_coefficients([ly])
+    plan = vr.Plan(*grids, ly["n_nodes"], ly["n_orders"], coef.shape[1], 1, vr.VRTE_MIXED)
+    try:
+        plan.set_layers([ly], torch.from_numpy(coef).cuda())
+        blocks = -(-grids[0].size // 64)
+        for dt in (torch.float32, torch.float64):
+            dev = torch.empty(plan.table_shape, dtype=dt, device="cuda")
+            plan.solve(dev)
+            torch.cuda.synchronize()
+            assert plan.status() == 0
+            fixed_dev = plan.debug_buffer("refined")[0]
+            h_out = torch.full(plan.table_shape, float("nan"), dtype=dt).pin_memory()
+            plan.reset_stages()
+            plan.solve_host(torch.from_numpy(coef).pin_memory(), h_out)
+            assert plan.status() == 0
+            refine = next(st for st in plan.stages() if st["name"] == "refine")
+            assert refine["launches"] == 4 + 3 * blocks      # the block-wise path ran
+            assert plan.debug_buffer("refined")[0] == fixed_dev
+            assert torch.equal(h_out, dev.cpu())
+    finally:
+        plan.close()
