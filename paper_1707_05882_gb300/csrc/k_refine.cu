@@ -9,7 +9,8 @@
 // (order, incident) column block from the row and column maxima of the operands,
 // compares it with the order-0 radiance I_00 of the same pair, and recomputes the flagged column
 // blocks in FP64 from the FP64 operators (boundary coefficients from K^-1 and the
-// right-hand side, then both reconstruction contractions), overwriting I^m.
+// right-hand side, written over those columns of C, then both reconstruction contractions),
+// overwriting I^m.
 #include "vrte_internal.cuh"
 
 namespace vrte {
@@ -83,56 +84,87 @@ __global__ void k_collect_columns(int n_in, int k0, int k1, int U, const int* __
   if (slot < cap) list[slot] = make_int2(u, k);
 }
 
-// Persistent grid over (flagged (u, k), block of FIX_ROWS output rows), so that the FP64
-// work spreads evenly over the SMs however few columns are flagged: FP64
-// C' = K^-1 RHS[:, 4k..4k+3] in shared memory (recomputed per row block), then one warp per
-// output row r = 4o + a:
+// The flagged column blocks are recomputed in two persistent passes over work items, so that
+// the FP64 work spreads over the SMs however few columns are flagged:
+// k_fix_coeffs: the FP64 boundary coefficients C'[:, 4k..4k+3] = K^-1 RHS[:, 4k..4k+3] of a
+//   flagged (u, k), FIX_CROWS rows per work item (one warp per row), written over the sliced
+//   product's columns of C;
+// k_fix_columns: FIX_ROWS output rows r = 4o + a per work item (one warp per row), with the
+//   block's C' and beam columns SD[:, 4k..4k+3] staged in shared memory:
 //   I^m[k][o][a][s] = sum_i Hhat[r][i] C'[i][s] + g0(o, k) sum_i U[r][i] SD[i][4k + s].
-constexpr int FIX_ROWS = 512;  // output rows per work item of k_fix_columns
+constexpr int FIX_CROWS = 64;   // coefficient rows per work item of k_fix_coeffs
+constexpr int FIX_ROWS = 64;    // output rows per work item of k_fix_columns
+constexpr int FIX_THREADS = 256;
 
-__global__ void __launch_bounds__(256) k_fix_columns(
+__global__ void __launch_bounds__(FIX_THREADS) k_fix_coeffs(
     OrderBatch b, const double* __restrict__ Kinv, const double* __restrict__ RHS,
-    const double* __restrict__ Hhat, const double* __restrict__ Uext,
-    const double* __restrict__ SD, const double* __restrict__ g0tab, int Kpart,
-    const int* __restrict__ count, const int2* __restrict__ list, int cap,
-    double* __restrict__ Isyn) {
-  extern __shared__ double Cs[];  // [2n][4]
+    const int* __restrict__ count, const int2* __restrict__ list, int cap, double* __restrict__ C) {
+  extern __shared__ double Rs[];  // [2n][4]: the right-hand side's column block
+  const int n2 = 2 * b.n, R = 4 * b.n_in;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int items = min(*count, cap);
+  const int nblk = (n2 + FIX_CROWS - 1) / FIX_CROWS;
+  for (int wi = blockIdx.x; wi < items * nblk; wi += gridDim.x) {
+    const int it = wi / nblk, i0 = (wi - it * nblk) * FIX_CROWS;
+    const int2 e = list[it];
+    const int u = e.x, k = e.y;
+    const double* rh = RHS + (size_t)u * n2 * R + 4 * k;
+    __syncthreads();  // Rs of the previous item is no longer read
+    for (int t = threadIdx.x; t < 4 * n2; t += blockDim.x) Rs[t] = rh[(size_t)(t >> 2) * R + (t & 3)];
+    __syncthreads();
+    const double* Ki = Kinv + (size_t)u * n2 * n2;
+    for (int i = i0 + warp; i < min(n2, i0 + FIX_CROWS); i += nw) {
+      double acc[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int j = lane; j < n2; j += 32) {
+        const double kv = Ki[(size_t)i * n2 + j];
+        for (int s = 0; s < 4; ++s) acc[s] = fma(kv, Rs[4 * j + s], acc[s]);
+      }
+      for (int s = 0; s < 4; ++s)
+        for (int off = 16; off > 0; off >>= 1) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], off);
+      if (lane == 0) {
+        double* dst = C + (size_t)u * n2 * R + (size_t)i * R + 4 * k;
+        for (int s = 0; s < 4; ++s) dst[s] = acc[s];
+      }
+    }
+  }
+}
+
+// staged: the beam columns (Kpart x 4) fit in shared memory beside C' (else read from SD)
+__global__ void __launch_bounds__(FIX_THREADS) k_fix_columns(
+    OrderBatch b, const double* __restrict__ C, const double* __restrict__ Hhat,
+    const double* __restrict__ Uext, const double* __restrict__ SD,
+    const double* __restrict__ g0tab, int Kpart, const int* __restrict__ count,
+    const int2* __restrict__ list, int cap, int staged, double* __restrict__ Isyn) {
+  extern __shared__ double sm[];
   const int n2 = 2 * b.n, R = 4 * b.n_in, Ro = 4 * b.n_out;
+  double* Cs = sm;           // [2n][4]: C' of the block
+  double* Ss = sm + 4 * n2;  // [Kpart][4]: the beam columns of the block (staged)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int items = min(*count, cap);
   const int nblk = (Ro + FIX_ROWS - 1) / FIX_ROWS;
   for (int wi = blockIdx.x; wi < items * nblk; wi += gridDim.x) {
     const int it = wi / nblk, r0 = (wi - it * nblk) * FIX_ROWS;
-    int2 e = list[it];
-    int u = e.x, k = e.y;
-    const double* Ki = Kinv + (size_t)u * n2 * n2;
-    const double* rh = RHS + (size_t)u * n2 * R + 4 * k;
-    __syncthreads();  // Cs of the previous item is no longer read
-    for (int i = warp; i < n2; i += nw) {
-      double acc[4] = {0.0, 0.0, 0.0, 0.0};
-      for (int j = lane; j < n2; j += 32) {
-        double kv = Ki[(size_t)i * n2 + j];
-        const double* r = rh + (size_t)j * R;
-        for (int s = 0; s < 4; ++s) acc[s] = fma(kv, r[s], acc[s]);
-      }
-      for (int s = 0; s < 4; ++s)
-        for (int off = 16; off > 0; off >>= 1) acc[s] += __shfl_xor_sync(0xffffffffu, acc[s], off);
-      if (lane == 0)
-        for (int s = 0; s < 4; ++s) Cs[4 * i + s] = acc[s];
-    }
+    const int2 e = list[it];
+    const int u = e.x, k = e.y;
+    const double* cb = C + (size_t)u * n2 * R + 4 * k;
+    const double* sd = SD + (size_t)u * b.sSD + 4 * k;
+    __syncthreads();  // the previous item's blocks are no longer read
+    for (int t = threadIdx.x; t < 4 * n2; t += blockDim.x) Cs[t] = cb[(size_t)(t >> 2) * R + (t & 3)];
+    if (staged)
+      for (int t = threadIdx.x; t < 4 * Kpart; t += blockDim.x)
+        Ss[t] = sd[(size_t)(t >> 2) * R + (t & 3)];
     __syncthreads();
     const double* H = Hhat + (size_t)u * Ro * n2;
     const double* Ub = Uext + (size_t)u * Ro * b.ldU;
-    const double* sd = SD + (size_t)u * b.sSD + 4 * k;
     for (int r = r0 + warp; r < min(Ro, r0 + FIX_ROWS); r += nw) {
       double h[4] = {0.0, 0.0, 0.0, 0.0}, q[4] = {0.0, 0.0, 0.0, 0.0};
       for (int i = lane; i < n2; i += 32) {
-        double hv = H[(size_t)r * n2 + i];
+        const double hv = H[(size_t)r * n2 + i];
         for (int s = 0; s < 4; ++s) h[s] = fma(hv, Cs[4 * i + s], h[s]);
       }
       for (int i = lane; i < Kpart; i += 32) {
-        double uv = Ub[(size_t)r * b.ldU + i];
-        const double* col = sd + (size_t)i * R;
+        const double uv = Ub[(size_t)r * b.ldU + i];
+        const double* col = staged ? Ss + 4 * i : sd + (size_t)i * R;
         for (int s = 0; s < 4; ++s) q[s] = fma(uv, col[s], q[s]);
       }
       for (int s = 0; s < 4; ++s)
@@ -141,13 +173,24 @@ __global__ void __launch_bounds__(256) k_fix_columns(
           q[s] += __shfl_xor_sync(0xffffffffu, q[s], off);
         }
       if (lane == 0) {
-        int o = r >> 2, a = r & 3;
-        double g0 = g0tab[(size_t)o * b.n_in + k];
+        const int o = r >> 2, a = r & 3;
+        const double g0 = g0tab[(size_t)o * b.n_in + k];
         double* dst = Isyn + (((size_t)(b.m0 + u) * b.n_in + k) * b.n_out + o) * 16 + 4 * a;
         for (int s = 0; s < 4; ++s) dst[s] = fma(g0, q[s], h[s]);
       }
     }
   }
+}
+
+static int fix_grid() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  return 4 * sms;
 }
 
 // maxima per (unit, outgoing) and per (unit, incident), each over its four Stokes entries,
@@ -168,7 +211,7 @@ void refine_maxima(const OrderBatch& b, int Kpart, const double* C, const double
 }
 
 void refine_range(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
-                  const double* Hhat, const double* Uext, const double* SD, const double* g0tab,
+                  double* C, const double* Hhat, const double* Uext, const double* SD, const double* g0tab,
                   double eps, double tol, const double* scratch, int* counters, int2* list,
                   int cap, double* Isyn, int* nonfinite, int k0, int k1, cudaStream_t s) {
   const int U = b.n_units, n2 = 2 * b.n;
@@ -182,18 +225,27 @@ void refine_range(const OrderBatch& b, int Kpart, const double* Kinv, const doub
       b, rmH, rmU, cmC, cmSD, g0tab, Isyn, eps * n2, eps * Kpart, tol, k0, nonfinite);
   k_collect_columns<<<dim3((k1 - k0 + 127) / 128, U), 128, 0, s>>>(
       b.n_in, k0, k1, U, nonfinite, counters, counters + 1, list, cap);
-  size_t smem = (size_t)n2 * 4 * sizeof(double);
-  k_fix_columns<<<2 * 152, 256, smem, s>>>(b, Kinv, RHS, Hhat, Uext, SD, g0tab, Kpart, counters,
-                                           list, cap, Isyn);
+  // the coefficients first (C'), then the rows from them; the work lists are read on the GPU
+  const size_t smem_c = (size_t)n2 * 4 * sizeof(double);
+  if (smem_c > 48 * 1024)
+    cudaFuncSetAttribute(k_fix_coeffs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
+  k_fix_coeffs<<<fix_grid(), FIX_THREADS, smem_c, s>>>(b, Kinv, RHS, counters, list, cap, C);
+  const size_t smem_full = smem_c + (size_t)Kpart * 4 * sizeof(double);
+  const int staged = smem_full <= (size_t)160 * 1024;
+  const size_t smem = staged ? smem_full : smem_c;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(k_fix_columns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_fix_columns<<<fix_grid(), FIX_THREADS, smem, s>>>(b, C, Hhat, Uext, SD, g0tab, Kpart,
+                                                      counters, list, cap, staged, Isyn);
 }
 
 void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
-                    const double* C, const double* Hhat, const double* Uext, const double* SD,
+                    double* C, const double* Hhat, const double* Uext, const double* SD,
                     const double* g0tab, double eps, double tol, double* scratch, int* counters,
                     int2* list, int cap, double* Isyn, int* nonfinite, cudaStream_t s) {
   refine_maxima(b, Kpart, C, Hhat, Uext, SD, scratch, s);
-  refine_range(b, Kpart, Kinv, RHS, Hhat, Uext, SD, g0tab, eps, tol, scratch, counters, list,
-               cap, Isyn, nonfinite, 0, b.n_in, s);
+  refine_range(b, Kpart, Kinv, RHS, C, Hhat, Uext, SD, g0tab, eps, tol, scratch, counters,
+               list, cap, Isyn, nonfinite, 0, b.n_in, s);
 }
 
 size_t refine_scratch_doubles(int U, int n_in, int n_out) {

@@ -932,10 +932,10 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
                      kSlices, w->tcw, s, zpart, w->nfflag, run);
       }
       {
-        StageScope sc(p, ST_REFINE, s, 3, 0.0, 0.0);
-        refine_range(ob, Kp, w->Kinv, w->RHS, w->Hhat, w->Upm, w->SD, w->g0tab, kSliceEps,
-                     kRefineTol, w->rscratch, w->rcount, w->rlist, U * p->n_in, w->Isyn,
-                     w->nfflag, k0, k1, s);
+        StageScope sc(p, ST_REFINE, s, 4, 0.0, 0.0);
+        refine_range(ob, Kp, w->Kinv, w->RHS, w->C, w->Hhat, w->Upm, w->SD, w->g0tab,
+                     kSliceEps, kRefineTol, w->rscratch, w->rcount, w->rlist, U * p->n_in,
+                     w->Isyn, w->nfflag, k0, k1, s);
       }
       {
         StageScope sc(p, ST_SYNTHESIS, s, (k0 == 0 ? 1 : 0) + 2, f * 2.0 * table * Meff,
@@ -987,7 +987,7 @@ static void run_order_batch(vrte_plan* p, Work* w, const vrte_layer& ly, const d
     }
   }
   if (mixed) {
-    StageScope sc(p, ST_REFINE, s, 6, 0.0, 0.0);
+    StageScope sc(p, ST_REFINE, s, 8, 0.0, 0.0);
     refine_columns(ob, 2 * n + kdir, w->Kinv, w->RHS, w->C, w->Hhat, w->Upm, w->SD,
                    w->g0tab, kSliceEps, kRefineTol, w->rscratch, w->rcount, w->rlist,
                    U * p->n_in, w->Isyn, w->nfflag, s);

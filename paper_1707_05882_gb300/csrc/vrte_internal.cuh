@@ -269,9 +269,10 @@ void tc_gemm_part(const OrderBatch& b, int K, const double* A, int lda, long lon
                   double* Isyn, int S, void* work, cudaStream_t s, TcKSkip zskip = TcKSkip{},
                   int* nonfinite = nullptr, TcRange rg = TcRange{});
 // Mixed form: flags (order, incident) column blocks whose sliced reconstruction error
-// bound eps K max|row| max|column| exceeds tol |I_00| and recomputes them in FP64.
+// bound eps K max|row| max|column| exceeds tol |I_00| and recomputes them in FP64 (their
+// boundary coefficients, written over those columns of C, then their columns of I^m).
 void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
-                    const double* C, const double* Hhat, const double* Uext, const double* SD,
+                    double* C, const double* Hhat, const double* Uext, const double* SD,
                     const double* g0tab, double eps, double tol, double* scratch, int* counters,
                     int2* list, int cap, double* Isyn, int* nonfinite, cudaStream_t s);
 // refine_columns in two parts: the operand maxima (once, when the operands are final), then the
@@ -280,7 +281,7 @@ void refine_columns(const OrderBatch& b, int Kpart, const double* Kinv, const do
 void refine_maxima(const OrderBatch& b, int Kpart, const double* C, const double* Hhat,
                    const double* Uext, const double* SD, double* scratch, cudaStream_t s);
 void refine_range(const OrderBatch& b, int Kpart, const double* Kinv, const double* RHS,
-                  const double* Hhat, const double* Uext, const double* SD, const double* g0tab,
+                  double* C, const double* Hhat, const double* Uext, const double* SD, const double* g0tab,
                   double eps, double tol, const double* scratch, int* counters, int2* list,
                   int cap, double* Isyn, int* nonfinite, int k0, int k1, cudaStream_t s);
 size_t refine_scratch_doubles(int U, int n_in, int n_out);

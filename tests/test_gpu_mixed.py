@@ -203,7 +203,7 @@ def test_mixed_host_buffer_blockwise_matches_device(case):
             plan.solve_host(torch.from_numpy(coef).pin_memory(), h_out)
             assert plan.status() == 0
             refine = next(st for st in plan.stages() if st["name"] == "refine")
-            assert refine["launches"] == 4 + 3 * blocks      # the block-wise path ran
+            assert refine["launches"] == 4 + 4 * blocks      # the block-wise path ran
             assert plan.debug_buffer("refined")[0] == fixed_dev
             assert torch.equal(h_out, dev.cpu())
     finally:
