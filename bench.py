@@ -755,8 +755,9 @@ def main():
                        "seconds_per_step": e2e_s / args.steps,
                        "d2h_gbs_in_step": d2h / (e2e_s / args.steps) / 1e9,
                        "d2h_link_gbs_alone": d2h / link_s / 1e9,
-                       "api": "vrte_solve_brdf_host (pinned host buffers; the table leaves in "
-                              "blocks of 64 incident cosines as the synthesis completes them)"}
+                       "api": "vrte_solve_brdf_host (pinned host buffers; the layer is "
+                              "reconstructed and synthesized in blocks of 64 incident cosines, "
+                              "each block's copy overlapping the next block's work)"}
         del h_out, d_tab
     plan.close()
     torch.cuda.empty_cache()
