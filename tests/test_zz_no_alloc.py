@@ -6,8 +6,8 @@ vrte_eigen_noalloc, which keeps its scratch in a static device array. The tests 
 it three ways: against the solver's own eigen stage on the reduced homogeneous matrices
 F'E' of a plan solve, on two calls in a row; independently of the solver, by the
 eigen-residual |A X - X Lambda| / (|A| |X|) of every matrix and by its eigenvalues as a
-sorted set against numpy's; and at the size limit n = 768 that the scratch admits for
-one matrix. The file is collected last so that a run stopping at the first failure has
+sorted set against numpy's; at the size limit n = 768 that the scratch admits for
+one matrix; and replayed from a captured CUDA graph. The file is collected last so that a run stopping at the first failure has
 run every other test.
 """
 import ctypes
@@ -136,6 +136,36 @@ def test_noalloc_eigen_at_its_size_limit():
     assert st == 0
     assert np.sum(li[0] > 0) == 2
     _check_independent(A, lr, li, X)
+
+
+def test_noalloc_eigen_replayed_from_a_captured_graph(fe_matrices):
+    """Allocating nothing, the call can be captured into a CUDA graph once a first call has
+    resolved the scratch address on the device: two replays give the direct call's
+    eigenpairs bit for bit, with the status word clear."""
+    lib = vr.load_library()
+    FE, _ = fe_matrices
+    lr0, li0, X0, st0 = _call(lib, FE)
+    assert st0 == 0
+    batch, n, _ = FE.shape
+    d_A = torch.from_numpy(np.ascontiguousarray(FE)).cuda()
+    lr = torch.full((batch, n), float("nan"), dtype=torch.float64, device="cuda")
+    li = torch.full((batch, n), float("nan"), dtype=torch.float64, device="cuda")
+    X = torch.full((batch, n, n), float("nan"), dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        code = lib.vrte_eigen_noalloc(_ptr(d_A), n, batch, _ptr(lr), _ptr(li), _ptr(X), _ptr(st),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert code == 0
+    for _ in range(2):
+        g.replay()
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        assert np.array_equal(lr.cpu().numpy(), lr0) and np.array_equal(li.cpu().numpy(), li0)
+        assert np.array_equal(X.cpu().numpy(), X0)
+        lr.fill_(float("nan"))
+        X.fill_(float("nan"))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
