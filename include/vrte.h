@@ -227,8 +227,15 @@ vrte_status vrte_solve_slab_brdf(vrte_plan* plan, void* d_brdf, int out_dtype, v
  * h_brdf (host, layout as d_brdf) and synchronizes `stream` before returning. The table
  * leaves a device staging buffer in blocks of incident cosines, each copied as soon as the
  * synthesis kernels that complete it have run, on four streams of the plan (several copy
- * engines) that wait on `stream` by events and are joined back into it. Pinned host memory
- * gives full copy bandwidth. */
+ * engines) that wait on `stream` by events and are joined back into it. In the VRTE_MIXED
+ * form a layer whose orders fit one batch, with no reflecting base and 2n + 4L <= 1024, is
+ * also reconstructed block by block (the same values as vrte_solve_brdf, bit for bit), so
+ * that the copies overlap the reconstruction; for that the first call allocates a second
+ * device workspace (the homogeneous contraction's slices and the synthesis workspace, kept
+ * by the plan and counted by vrte_workspace_bytes); if that allocation fails the layer is
+ * reconstructed whole. The staging buffers are allocated by the first call (or a call with a
+ * larger table); VRTE_ERR_OOM if they do not fit. Pinned host memory gives full copy
+ * bandwidth. */
 vrte_status vrte_solve_brdf_host(vrte_plan* plan, const double* h_coeffs, void* h_brdf,
                                  int out_dtype, void* stream);
 
