@@ -64,3 +64,48 @@ def test_order_radiance_is_smooth_across_a_resonance():
     # and the fit itself is not swamped: away from the pole the residual is at rounding level
     far = gap > 1e-6
     assert far.any() and res[far].max() < 1e-10
+
+
+def test_error_at_a_resonance_is_the_conditioning_1_over_gap():
+    """Against a reference with no resonance at all: the top radiance from the matrix
+    exponential of the augmented system d/dtau [u; s] = [[T, -M^-1 q], [0, -1/mu0]] [u; s]
+    (the beam carried as an extra state, so nothing divides by 1 + mu0 kappa_j), with the
+    top boundary condition and the black base imposed on the propagator (as in the brute-force
+    pin of the per-order solution; N = 3 and tau0 = 0.8 keep the propagator well conditioned).
+    The oracle's error grows as u / gap and no faster (measured ~3 u / gap of the largest
+    component, from gap = 1e-3 to 1e-10): the rounding that the FP64 parity tolerance widens
+    for, with the radiance itself finite and correct to that level."""
+    from scipy.linalg import expm
+    coef = polydisperse_coefficients(1.5 + 0.001j, 5.0, 0.1, 12)
+    N, tau0, omega, m = 3, 0.8, 0.9, 2
+    nodes = O.gauss_legendre_01(N)
+    R = O.fresnel_internal_reflection(nodes[0], 1.33)
+    N4 = 4 * N
+
+    def solve(mu0):
+        return O.solve_order(m, coef, omega, tau0, N, np.array([mu0]), np.eye(4)[None], R, nodes)
+
+    kap = solve(0.5).kappa
+    mu_r = -1.0 / kap[(kap.real < 0.0) & (kap.imag == 0.0)].real
+    mu_r = mu_r[(mu_r > 0.3) & (mu_r < 0.95)][0]
+    errs = {}
+    for delta in (1e-3, 1e-6, 1e-8, 1e-10):
+        mu0 = mu_r * (1.0 + delta)
+        sol = solve(mu0)
+        gap = np.abs(1.0 + mu0 * sol.kappa[sol.kappa.real < 0.0]).min()
+        err = 0.0
+        for col in range(4):
+            aug = np.zeros((8 * N + 1, 8 * N + 1))
+            aug[:-1, :-1] = sol.T
+            aug[:-1, -1] = -sol.q[:, col] / sol.m8
+            aug[-1, -1] = -1.0 / mu0
+            P = expm(aug * tau0)
+            # u(0) = [x; R x] with x = u_up(0); black base: the upward part of u(tau0) is zero
+            x = np.linalg.solve(P[:N4, :-1] @ np.vstack([np.eye(N4), sol.R]), -P[:N4, -1])
+            y = sol.nodal(0.0)[:N4, col]
+            assert np.all(np.isfinite(y))
+            err = max(err, np.abs(x - y).max() / np.abs(x).max())
+        assert err <= 10.0 * U / gap + 1e-12, (delta, err, U / gap)
+        errs[delta] = err
+    assert errs[1e-3] < 1e-11
+    assert errs[1e-10] > 100.0 * errs[1e-3]        # the 1 / gap growth is real
